@@ -1,0 +1,54 @@
+"""Tight-binding Hamiltonian of the synthetic workloads (oracle side).
+
+The paper builds H with SCC-DFTB in LATTE (Sec. II.B); that code and its parameters are
+not available, so the workloads use a one-orbital-per-site model:
+  H_ii = onsite_i,
+  H_ij = -1.0 * exp(-(r_ij - a) / (0.3 a))  for 0 < r_ij < 2.5 a  (minimum image),
+  H_ij = 0 otherwise.
+Brute force over all pairs, chunked; obviously correct, O(N^2).
+"""
+import numpy as np
+import scipy.sparse as sp
+
+RCUT = 2.5      # in units of a
+DECAY = 0.3     # in units of a
+
+
+def pair_geometry(pos_i, pos_all, box):
+    """Minimum-image separation vectors and distances from rows pos_i to all sites."""
+    d = pos_i[:, None, :] - pos_all[None, :, :]
+    d = d - box * np.round(d / box)
+    return np.sqrt(np.einsum("ijk,ijk->ij", d, d))
+
+
+def hopping(r, a=1.0):
+    """Hopping element for separation r (no cutoff applied)."""
+    return -1.0 * np.exp(-(r - a) / (DECAY * a))
+
+
+def build_h(pos, box, onsite, a=1.0, rcut=RCUT, rows=None, chunk=1024):
+    """Sparse CSR H (float64, sorted column indices, diagonal stored).
+
+    rows: optional subset of row indices; then an [len(rows), N] CSR of those rows.
+    """
+    pos = np.asarray(pos, dtype=np.float64)
+    N = pos.shape[0]
+    rows = np.arange(N) if rows is None else np.asarray(rows)
+    indptr = [0]
+    indices = []
+    data = []
+    for c0 in range(0, len(rows), chunk):
+        rr = rows[c0:c0 + chunk]
+        r = pair_geometry(pos[rr], pos, box)
+        for k, i in enumerate(rr):
+            rk = r[k]
+            nb = np.nonzero(rk < rcut * a)[0]
+            vals = hopping(rk[nb], a)
+            vals[nb == i] = onsite[i]
+            indices.append(nb)
+            data.append(vals)
+            indptr.append(indptr[-1] + len(nb))
+    H = sp.csr_matrix((np.concatenate(data), np.concatenate(indices), np.array(indptr)),
+                      shape=(len(rows), N))
+    H.sort_indices()
+    return H

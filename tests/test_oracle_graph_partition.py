@@ -1,0 +1,73 @@
+"""Pins for the oracle's graphs (brute-force dense patterns) and partitions."""
+import numpy as np
+import scipy.sparse as sp
+
+import synth
+from oracle import graph, hamiltonian, partition
+
+
+def small_h(L=4, seed=1):
+    w = synth.lattice(L, seed=seed)
+    return w, hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
+
+
+def dense_pattern(G):
+    return np.asarray(G.toarray(), dtype=bool)
+
+
+def test_h2_threshold_brute_force():
+    _, H = small_h()
+    Hd = H.toarray()
+    H2 = Hd @ Hd
+    for thr in (1e-5, 1e-2, 0.3):
+        ref = (np.abs(H2) >= thr) | np.eye(len(Hd), dtype=bool)
+        ref = ref | ref.T
+        np.testing.assert_array_equal(dense_pattern(graph.h2_threshold(H, thr)), ref)
+
+
+def test_d_threshold_symmetrises():
+    D = sp.csr_matrix(np.array([[0.5, 0.0, 0.2], [1e-6, 0.5, 0.0], [0.0, 0.0, 0.5]]))
+    G = dense_pattern(graph.d_threshold(D, 1e-5))
+    ref = np.array([[1, 0, 1], [0, 1, 0], [1, 0, 1]], dtype=bool)
+    np.testing.assert_array_equal(G, ref)
+
+
+def test_eq8_and_hk_brute_force():
+    _, H = small_h(L=5)
+    Hd = H.toarray()
+    rng = np.random.default_rng(0)
+    Dd = rng.normal(size=Hd.shape) * (rng.uniform(size=Hd.shape) < 0.05)
+    A = ((np.abs(Dd) >= 0.5) | (np.abs(Dd.T) >= 0.5) | (Hd != 0) | np.eye(len(Hd), dtype=bool)).astype(int)
+    ref = (A @ A) > 0
+    np.testing.assert_array_equal(dense_pattern(graph.eq8_symbolic(sp.csr_matrix(Dd), H, 0.5)), ref)
+    P = ((Hd != 0) | np.eye(len(Hd), dtype=bool)).astype(int)
+    ref3 = (P @ P @ P) > 0
+    np.testing.assert_array_equal(dense_pattern(graph.hk_pattern(H, 3)), ref3)
+
+
+def test_cell_ids_closed_form():
+    box = np.array([4.0, 4.0, 4.0])
+    pos = np.array([[0.1, 0.1, 0.1], [3.9, 0.1, 0.1], [0.1, 3.9, 0.1], [0.1, 0.1, 3.9], [2.0, 2.0, 2.0]])
+    np.testing.assert_array_equal(partition.cell_ids(pos, box, (2, 2, 2)), [0, 4, 2, 1, 7])
+
+
+def test_lattice_cores_are_2x2x2_blocks():
+    w = synth.lattice(8, seed=0)
+    cores = partition.spatial_cores(w["pos"], w["box"], (4, 4, 4))
+    assert len(cores) == 64 and all(len(c) == 8 for c in cores)
+    # ideal site (i,j,k) has index (i*8+j)*8+k; sites sit 0.5a from cell walls, jitter is 0.05a
+    ijk = np.stack(np.unravel_index(cores[0], (8, 8, 8)), 1)
+    assert ijk.max() <= 1 and ijk.min() == 0
+
+
+def test_halo_brute_force():
+    _, H = small_h(L=4, seed=2)
+    S = graph.h2_threshold(H, 1e-2)
+    Sd = dense_pattern(S)
+    cores = partition.block_cores(H.shape[0], 7)
+    subs, nc = partition.subgraphs(S, cores)
+    for C, idx, c in zip(cores, subs, nc):
+        assert c == len(C)
+        np.testing.assert_array_equal(idx[:c], C)
+        halo = sorted(set(np.nonzero(Sd[C].any(0))[0]) - set(C))
+        np.testing.assert_array_equal(idx[c:], halo)
