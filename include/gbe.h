@@ -1,0 +1,273 @@
+/*
+ * gbe.h -- C ABI of libgbe: graph-partitioned SP2 density matrices on one GB300.
+ *
+ * The library computes the zero-temperature density matrix D = theta(mu I - H) of a
+ * sparse Hamiltonian H with the graph-based method of Niklasson et al., "Graph-based
+ * linear scaling electronic structure theory" (Sec. II.A): a data-dependency graph
+ * S_tau (Eq. 2, Eq. 8) is cut into cores (communities, observation vi); every
+ * core+halo subgraph s gives a small dense principal submatrix x[s] of
+ * X_0 = (e_max I - H)/(e_max - e_min); one global SP2 recursive expansion
+ * (X <- X^2 or 2X - X^2, the second-order recursion the paper uses) runs on all
+ * submatrices at once; core columns are collected into D column by column (Eq. 6,
+ * observation i).
+ *
+ * Conventions for every entry point
+ *   - Return value: GBE_OK (0) or a negative GBE_E* code; gbe_strerror() names it.
+ *     gbe_last_error_message() returns a thread-local detail string for the last error.
+ *   - Work is ordered on the context's CUDA stream.  Entry points that return sizes or
+ *     reports to the host synchronise that stream; the others only enqueue.
+ *   - Pointers marked "device" must be device memory of the context's GPU; "host" means
+ *     host memory; structs carrying an on_device flag accept either.
+ *   - Inputs are borrowed for the duration of the call (and, for enqueue-only calls,
+ *     until the stream reaches the enqueued work).  Opaque objects are owned by the
+ *     library and released with the matching gbe_free_* call.  Output buffers in
+ *     gbe_ell are owned by the caller.
+ *   - There is no CPU fallback: without a usable sm_103 GPU, gbe_create returns
+ *     GBE_ENODEV and every other call GBE_EINVAL on a NULL context.
+ *   - Device-side waits are bounded; a wait that runs out reports GBE_ETIMEOUT and the
+ *     context remains usable.
+ */
+#ifndef GBE_H
+#define GBE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GBE_OK          0
+#define GBE_EINVAL     -1   /* bad argument, size or state                        */
+#define GBE_ENOMEM     -2   /* device or host allocation failed                   */
+#define GBE_ECUDA      -3   /* a CUDA runtime / driver call failed                */
+#define GBE_ETIMEOUT   -4   /* a bounded device-side wait gave up                 */
+#define GBE_ENOCONV    -5   /* SP2 reached n_max without meeting its stop rule    */
+#define GBE_ENUMERIC   -6   /* NaN or Inf met in H or in an SP2 iterate           */
+#define GBE_ECAPACITY  -7   /* a subgraph, ELL row or table exceeded its capacity */
+#define GBE_ENODEV     -8   /* no usable sm_103 device                            */
+
+typedef struct gbe_ctx gbe_ctx;
+typedef struct gbe_graph gbe_graph;
+typedef struct gbe_parts gbe_parts;
+typedef struct gbe_subs gbe_subs;
+typedef struct gbe_hamiltonian gbe_hamiltonian;
+
+/* Sparse symmetric H in CSR: rows [0, n); column indices ascending within a row;
+ * the diagonal entry of every row present.  rowptr[n+1] int64, col[nnz] int32,
+ * val[nnz] float64.  on_device = 1: device pointers; 0: host pointers (copied in). */
+typedef struct {
+    int64_t n, nnz;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const double* val;
+    int on_device;
+} gbe_csr;
+
+/* Density matrix in ELLPACK, caller-owned: row i holds column i of D (the column
+ * collection order of Eq. 6 / observation i).  col[n*width] int32, val[n*width]
+ * float64, row-major; entries of a row are packed from the front, padding has
+ * col = -1 and val = 0.  on_device selects device (1) or host (0) buffers. */
+typedef struct {
+    int64_t n, width;
+    int32_t* col;
+    double* val;
+    int on_device;
+} gbe_ell;
+
+/* Sites of the tight-binding workload: pos[n][3] float64 inside [0, box), onsite[n]. */
+typedef struct {
+    int64_t n;
+    const double* pos;
+    const double* onsite;
+    double box[3];
+    int on_device;
+} gbe_sites;
+
+/* H_ij = hop * exp(-(r - a)/(decay)) for 0 < r < rcut (minimum image), H_ii = onsite. */
+typedef struct {
+    double a, rcut, decay, hop;
+} gbe_tb_model;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, ordering work on `cuda_stream`
+ * (a cudaStream_t; NULL selects the legacy default stream).  Fails with GBE_ENODEV
+ * when the device is absent or is not compute capability 10.3. */
+int gbe_create(gbe_ctx** ctx, int device, void* cuda_stream);
+int gbe_destroy(gbe_ctx* ctx);
+/* Change the stream later calls are ordered on. */
+int gbe_set_stream(gbe_ctx* ctx, void* cuda_stream);
+/* Number of SMs of the context's device (grids are sized from it). */
+int gbe_device_sm_count(const gbe_ctx* ctx);
+const char* gbe_strerror(int code);
+const char* gbe_last_error_message(void);
+
+/* --------------------------------------------------------- Hamiltonian (a1) */
+
+/* Build CSR H from sites with a cell list on the GPU (workload model; the paper's
+ * SCC-DFTB H of Sec. II.B is not reproduced).  Output is library-owned device CSR;
+ * gbe_hamiltonian_csr() gives a device view of it.  Synchronises (reads nnz). */
+int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* sites, const gbe_tb_model* model,
+                          gbe_hamiltonian** H);
+int gbe_hamiltonian_csr(const gbe_hamiltonian* H, gbe_csr* view);
+int gbe_free_hamiltonian(gbe_hamiltonian* H);
+
+/* ------------------------------------------------------------- graph (a2) */
+
+enum {
+    GBE_GRAPH_H2_THRESH    = 0, /* edge if |(H^2)_ij| >= thresh                        Eq. 2 */
+    GBE_GRAPH_D_THRESH     = 1, /* edge if |D_ij| >= thresh or |D_ji| >= thresh        Eq. 2 on a prior D */
+    GBE_GRAPH_EQ8_SYMBOLIC = 2, /* paths of length <= 2 in pattern(floor(D)_thresh) u pattern(H)  Eq. 8, eps = 0 */
+    GBE_GRAPH_HK_PATTERN   = 3, /* paths of length <= k in pattern(H)                  */
+    GBE_GRAPH_MLP          = 4  /* edges scored by a trained gbe_mlp, union pattern(H) */
+};
+
+typedef struct gbe_mlp gbe_mlp;
+
+typedef struct {
+    int mode;                 /* GBE_GRAPH_* */
+    double thresh;            /* tau (or the H^2 threshold)                            */
+    int k;                    /* path length for GBE_GRAPH_HK_PATTERN                   */
+    const gbe_ell* D_prev;    /* prior density matrix (D_THRESH, EQ8_SYMBOLIC)          */
+    const gbe_sites* sites;   /* MLP mode: candidate pairs r < rcand                    */
+    const gbe_mlp* mlp;       /* MLP mode: trained classifier                           */
+    double rcand;             /* MLP mode: candidate radius (units of length)           */
+    double logit_cut;         /* MLP mode: keep edges with logit >= logit_cut           */
+} gbe_graph_params;
+
+/* Build S_tau on the GPU.  The graph is undirected, contains every diagonal entry, and
+ * is held either explicitly (CSR) or as "base pattern A with path length k", meaning
+ * S = pattern(A^k); partitioning expands core sets by k hops directly.  `H` is a
+ * device or host CSR.  Synchronises. */
+int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* H, const gbe_graph_params* params, gbe_graph** S);
+/* Materialise the explicit CSR of S (no-op for k = 1) and report its size. */
+int gbe_graph_size(gbe_ctx* ctx, gbe_graph* S, int64_t* n, int64_t* nnz);
+/* Copy the explicit CSR of S to host arrays rowptr[n+1] (int64) and col[nnz] (int32). */
+int gbe_graph_export(gbe_ctx* ctx, gbe_graph* S, int64_t* rowptr, int32_t* col);
+int gbe_free_graph(gbe_graph* S);
+
+/* --------------------------------------------------------- partition (a3) */
+
+enum {
+    GBE_PART_SPATIAL_CELLS = 0, /* cores = non-empty cells floor(x / box * ncell), ascending cell id */
+    GBE_PART_INDEX_BLOCKS  = 1  /* cores = consecutive blocks of core_size vertices              */
+};
+
+typedef struct {
+    int mode;
+    int ncell[3];                /* SPATIAL_CELLS */
+    const gbe_sites* sites;      /* SPATIAL_CELLS */
+    int core_size;               /* INDEX_BLOCKS  */
+    int max_sub;                 /* capacity of one core+halo subgraph (0: library default 4096) */
+} gbe_partition_params;
+
+/* Cut S into cores (communities, observation vi) and build each core+halo subgraph
+ * (Sec. II.A, Fig. 1): local index list = core vertices ascending, then halo vertices
+ * (neighbours of any core vertex, not in the core) ascending.  Synchronises (subgraph
+ * sizes size every later buffer).  GBE_ECAPACITY when a subgraph exceeds max_sub. */
+int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* params,
+                  gbe_parts** parts);
+/* Sizes: number of subgraphs P, total local indices, max subgraph size. */
+int gbe_parts_info(const gbe_parts* parts, int64_t* P, int64_t* total, int64_t* max_m);
+/* Copy to host: core_count[P] int32, sub_ptr[P+1] int64, sub_idx[total] int32. */
+int gbe_parts_export(gbe_ctx* ctx, const gbe_parts* parts, int32_t* core_count, int64_t* sub_ptr,
+                     int32_t* sub_idx);
+/* Build a partition from host arrays with the same meaning (core vertices first in
+ * each list).  Validates ranges; does not check that the lists match any graph. */
+int gbe_parts_import(gbe_ctx* ctx, int64_t n, int64_t P, const int32_t* core_count,
+                     const int64_t* sub_ptr, const int32_t* sub_idx, gbe_parts** parts);
+int gbe_free_parts(gbe_parts* parts);
+
+/* ------------------------------------------------------ SP2 (a4 - a7) */
+
+enum {
+    GBE_PREC_FP64    = 0, /* every squaring in FP64 on the FP64 pipe                          */
+    GBE_PREC_FP16X6  = 1, /* tensor cores: 3-level fp16 split, 6 products, FP32 accumulation,
+                             exact accumulation of the fixed-point leading part               */
+    GBE_PREC_BF16X3  = 2  /* tensor cores: per-element bf16 hi/lo split, 3 products            */
+};
+
+enum {
+    GBE_BRANCH_GLOBAL_TRACE = 0, /* branch from the global FP64 traces every iteration     */
+    GBE_BRANCH_REPLAY       = 1  /* apply seq_in[0..seq_len) and stop after it             */
+};
+
+enum {
+    GBE_STOP_NONE = 0, GBE_STOP_TOL = 1, GBE_STOP_STALL = 2, GBE_STOP_NMAX = 3,
+    GBE_STOP_REPLAY = 4, GBE_STOP_ERROR = 5
+};
+
+#define GBE_SEQ_MAX 256
+
+typedef struct {
+    double n_occ;          /* total occupation summed over all core positions (half filling: N/2) */
+    double idem_tol;       /* stop when e_n = |Tr X_n - Tr X_n^2| <= idem_tol (core positions)      */
+    int n_min;             /* stall rule active from this iteration on (e_n >= e_{n-2} stops)       */
+    int n_max;             /* at most this many squarings (<= GBE_SEQ_MAX)                          */
+    int prec;              /* GBE_PREC_*                                                            */
+    int fp64_tail;         /* mixed precision: replay mode runs the last fp64_tail steps in FP64;
+                              global mode switches to FP64 when e_n <= tail_switch or the mixed
+                              iteration stalls, for at least fp64_tail further steps            */
+    double tail_switch;    /* see fp64_tail (global mode)                                         */
+    int branch_mode;       /* GBE_BRANCH_*                                                          */
+    const uint8_t* seq_in; /* host; 1 = X^2, 0 = 2X - X^2 (replay mode)                             */
+    int seq_len;
+    int eps_given;         /* 1: use eps_min / eps_max below instead of Gershgorin bounds           */
+    double eps_min, eps_max;
+    double timeout_ms;     /* bound for device-side waits (0: library default, 2000 ms)             */
+} gbe_sp2_params;
+
+typedef struct {
+    int iters;             /* squarings performed                                      */
+    int fp64_iters;        /* of which in FP64                                         */
+    int stop_reason;       /* GBE_STOP_*                                               */
+    int converged;         /* 1 when stopped by tolerance, stall or replay length      */
+    int status;            /* GBE_OK or the error code the device recorded             */
+    double eps_min, eps_max;
+    double trace;          /* Tr over core positions of the final X                    */
+    double idem_err;       /* e_n of the final X                                       */
+    uint8_t seq[GBE_SEQ_MAX];
+    double t1[GBE_SEQ_MAX + 1], t2[GBE_SEQ_MAX + 1];
+    float ms_gather, ms_sp2;            /* CUDA-event times of the phases                */
+    double mma_flops;      /* tensor-core flops issued (split products included)          */
+    double alg_flops;      /* sum over iterations and subgraphs of 2 m_s^3                 */
+} gbe_sp2_report;
+
+/* Allocate the SP2 state for a partition and precision (dense padded tiles in HBM,
+ * ping-pong buffers, trace partials, device control block).  Reusable across calls. */
+int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, gbe_subs** X);
+int gbe_free_subs(gbe_subs* X);
+
+/* Enqueue one density-matrix build on the stream without synchronising:
+ * Gershgorin bounds of H (FP64, a4), gather + scale of every x[s] (a4), and the SP2
+ * loop (a5 squarings, a6 global FP64 trace + branch, a7 branch apply in the squaring
+ * epilogue), with convergence decided on the device.  `H` must be device CSR. */
+int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* params,
+                gbe_subs* X);
+/* Synchronise and read the report of the last run on X. */
+int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_report* rep);
+
+/* gbe_sp2_run + gbe_sp2_report_get.  *X NULL: allocate a new state; otherwise reuse it
+ * (it must come from the same partition and precision).  H may be host CSR (copied in).
+ * Returns GBE_ENOCONV when the run stopped at n_max, GBE_ENUMERIC / GBE_ETIMEOUT when
+ * the device recorded one, GBE_OK otherwise. */
+int gbe_sp2_submatrices(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts,
+                        const gbe_sp2_params* params, gbe_subs** X, gbe_sp2_report* rep);
+
+/* --------------------------------------------------------- assembly (a8) */
+
+/* Collect the core columns of every final x[s] into ELL D (Eq. 6): row C_s[j] of the
+ * ELL receives (sub_idx_s[k], x_s[k, j]) for k < m_s, in local order (core vertices,
+ * then halo), skipping |value| < drop_tol when drop_tol > 0.  Query: with D->col NULL
+ * the call only sets D->n and D->width (= max m_s) and returns.  GBE_ECAPACITY when
+ * D->width < max m_s.  Device D: enqueue only; host D: synchronises and copies out. */
+int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, double drop_tol, gbe_ell* D);
+
+/* Copy the final dense x_s (m_s x m_s, row-major, FP64) of subgraph s to host. */
+int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBE_H */

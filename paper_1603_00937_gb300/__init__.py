@@ -1,0 +1,408 @@
+"""Python binding of libgbe: graph-partitioned SP2 density matrices on GB300.
+
+Argument marshalling only -- every step of the computation runs in the CUDA kernels of
+libgbe.so (built in-tree by ``build.py``).  Names follow the C ABI in include/gbe.h.
+Device arrays are torch CUDA tensors (PyTorch supplies device memory and streams);
+NumPy arrays are passed as host buffers where the ABI accepts them.
+
+There is no CPU fallback: importing works without a GPU, but creating a context fails
+loudly when the library or a usable sm_103 device is missing.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbe.so")
+
+GBE_OK, GBE_EINVAL, GBE_ENOMEM, GBE_ECUDA, GBE_ETIMEOUT = 0, -1, -2, -3, -4
+GBE_ENOCONV, GBE_ENUMERIC, GBE_ECAPACITY, GBE_ENODEV = -5, -6, -7, -8
+
+GRAPH_H2_THRESH, GRAPH_D_THRESH, GRAPH_EQ8_SYMBOLIC, GRAPH_HK_PATTERN, GRAPH_MLP = 0, 1, 2, 3, 4
+PART_SPATIAL_CELLS, PART_INDEX_BLOCKS = 0, 1
+PREC_FP64, PREC_FP16X6, PREC_BF16X3 = 0, 1, 2
+BRANCH_GLOBAL_TRACE, BRANCH_REPLAY = 0, 1
+STOP_NAMES = {0: "none", 1: "tol", 2: "stall", 3: "nmax", 4: "replay", 5: "error"}
+SEQ_MAX = 256
+
+# Every entry point declared in include/gbe.h (checked by the CPU test suite).
+EXPORTS = [
+    "gbe_create", "gbe_destroy", "gbe_set_stream", "gbe_device_sm_count", "gbe_strerror",
+    "gbe_last_error_message", "gbe_build_hamiltonian", "gbe_hamiltonian_csr", "gbe_free_hamiltonian",
+    "gbe_build_graph", "gbe_graph_size", "gbe_graph_export", "gbe_free_graph", "gbe_partition",
+    "gbe_parts_info", "gbe_parts_export", "gbe_parts_import", "gbe_free_parts", "gbe_subs_create",
+    "gbe_free_subs", "gbe_sp2_run", "gbe_sp2_report_get", "gbe_sp2_submatrices", "gbe_assemble_D",
+    "gbe_subs_export",
+]
+
+
+class GbeError(RuntimeError):
+    def __init__(self, code, where, detail):
+        super().__init__("%s failed: %s (%d): %s" % (where, _strerror(code), code, detail))
+        self.code = code
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class Ell(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("width", ctypes.c_int64), ("col", ctypes.c_void_p),
+                ("val", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class Sites(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("pos", ctypes.c_void_p), ("onsite", ctypes.c_void_p),
+                ("box", ctypes.c_double * 3), ("on_device", ctypes.c_int)]
+
+
+class TbModel(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("rcut", ctypes.c_double), ("decay", ctypes.c_double),
+                ("hop", ctypes.c_double)]
+
+
+class GraphParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("thresh", ctypes.c_double), ("k", ctypes.c_int),
+                ("D_prev", ctypes.c_void_p), ("sites", ctypes.c_void_p), ("mlp", ctypes.c_void_p),
+                ("rcand", ctypes.c_double), ("logit_cut", ctypes.c_double)]
+
+
+class PartitionParams(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int), ("ncell", ctypes.c_int * 3), ("sites", ctypes.c_void_p),
+                ("core_size", ctypes.c_int), ("max_sub", ctypes.c_int)]
+
+
+class Sp2Params(ctypes.Structure):
+    _fields_ = [("n_occ", ctypes.c_double), ("idem_tol", ctypes.c_double), ("n_min", ctypes.c_int),
+                ("n_max", ctypes.c_int), ("prec", ctypes.c_int), ("fp64_tail", ctypes.c_int),
+                ("tail_switch", ctypes.c_double), ("branch_mode", ctypes.c_int),
+                ("seq_in", ctypes.c_void_p), ("seq_len", ctypes.c_int), ("eps_given", ctypes.c_int),
+                ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double), ("timeout_ms", ctypes.c_double)]
+
+
+class Sp2Report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("fp64_iters", ctypes.c_int), ("stop_reason", ctypes.c_int),
+                ("converged", ctypes.c_int), ("status", ctypes.c_int), ("eps_min", ctypes.c_double),
+                ("eps_max", ctypes.c_double), ("trace", ctypes.c_double), ("idem_err", ctypes.c_double),
+                ("seq", ctypes.c_uint8 * SEQ_MAX), ("t1", ctypes.c_double * (SEQ_MAX + 1)),
+                ("t2", ctypes.c_double * (SEQ_MAX + 1)), ("ms_gather", ctypes.c_float),
+                ("ms_sp2", ctypes.c_float), ("mma_flops", ctypes.c_double), ("alg_flops", ctypes.c_double)]
+
+    def as_dict(self):
+        n = self.iters
+        return dict(iters=n, fp64_iters=self.fp64_iters, stop=STOP_NAMES.get(self.stop_reason, "?"),
+                    converged=bool(self.converged), status=self.status, eps=(self.eps_min, self.eps_max),
+                    trace=self.trace, idem_err=self.idem_err, seq=list(self.seq[:n]),
+                    t1=list(self.t1[:n + 1]), t2=list(self.t2[:n + 1]), ms_gather=self.ms_gather,
+                    ms_sp2=self.ms_sp2, mma_flops=self.mma_flops, alg_flops=self.alg_flops)
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libgbe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libgbe.so not found at %s: run paper_1603_00937_gb300/build.py "
+                           "(or __graft_entry__.build()) first; there is no CPU fallback" % path)
+    lib = ctypes.CDLL(path)
+    P, I64, I32, D, C = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_char_p
+    sig = {
+        "gbe_create": (I32, [P, I32, P]), "gbe_destroy": (I32, [P]), "gbe_set_stream": (I32, [P, P]),
+        "gbe_device_sm_count": (I32, [P]), "gbe_strerror": (C, [I32]), "gbe_last_error_message": (C, []),
+        "gbe_build_hamiltonian": (I32, [P, P, P, P]), "gbe_hamiltonian_csr": (I32, [P, P]),
+        "gbe_free_hamiltonian": (I32, [P]), "gbe_build_graph": (I32, [P, P, P, P]),
+        "gbe_graph_size": (I32, [P, P, P, P]), "gbe_graph_export": (I32, [P, P, P, P]),
+        "gbe_free_graph": (I32, [P]), "gbe_partition": (I32, [P, P, P, P]),
+        "gbe_parts_info": (I32, [P, P, P, P]), "gbe_parts_export": (I32, [P, P, P, P, P]),
+        "gbe_parts_import": (I32, [P, I64, I64, P, P, P, P]), "gbe_free_parts": (I32, [P]),
+        "gbe_subs_create": (I32, [P, P, I32, P]), "gbe_free_subs": (I32, [P]),
+        "gbe_sp2_run": (I32, [P, P, P, P, P]), "gbe_sp2_report_get": (I32, [P, P, P]),
+        "gbe_sp2_submatrices": (I32, [P, P, P, P, P, P]), "gbe_assemble_D": (I32, [P, P, P, D, P]),
+        "gbe_subs_export": (I32, [P, P, I64, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _strerror(code):
+    try:
+        return load_library().gbe_strerror(code).decode()
+    except Exception:
+        return "error"
+
+
+def check(code, where):
+    if code != GBE_OK:
+        detail = load_library().gbe_last_error_message().decode(errors="replace")
+        raise GbeError(code, where, detail)
+    return code
+
+
+def _ptr(a):
+    """Raw pointer of a torch tensor (device or host) or a contiguous NumPy array."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_device(a):
+    return (not isinstance(a, np.ndarray)) and getattr(a, "is_cuda", False)
+
+
+def csr(n, rowptr, col, val):
+    """gbe_csr over (int64 rowptr, int32 col, float64 val), all torch-CUDA or all NumPy."""
+    dev = _is_device(rowptr)
+    keep = (rowptr, col, val)
+    c = Csr(n, int(col.shape[0]), _ptr(rowptr), _ptr(col), _ptr(val), 1 if dev else 0)
+    c._keep = keep
+    return c
+
+
+class Context:
+    def __init__(self, device=0, stream=None):
+        lib = load_library()
+        self._h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream) if stream is not None else None
+        check(lib.gbe_create(ctypes.byref(self._h), device, s), "gbe_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_stream(self, stream):
+        check(load_library().gbe_set_stream(self._h, ctypes.c_void_p(stream)), "gbe_set_stream")
+
+    @property
+    def sm_count(self):
+        return load_library().gbe_device_sm_count(self._h)
+
+    def close(self):
+        if self._h:
+            load_library().gbe_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Owned:
+    _free = None
+
+    def __init__(self, ctx, h):
+        self.ctx, self._h = ctx, h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            getattr(load_library(), self._free)(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian(_Owned):
+    _free = "gbe_free_hamiltonian"
+
+    def csr(self):
+        v = Csr()
+        check(load_library().gbe_hamiltonian_csr(self._h, ctypes.byref(v)), "gbe_hamiltonian_csr")
+        v._keep = self
+        return v
+
+
+class Graph(_Owned):
+    _free = "gbe_free_graph"
+
+    def size(self):
+        n, nnz = ctypes.c_int64(), ctypes.c_int64()
+        check(load_library().gbe_graph_size(self.ctx.handle, self._h, ctypes.byref(n), ctypes.byref(nnz)),
+              "gbe_graph_size")
+        return n.value, nnz.value
+
+    def export(self):
+        n, nnz = self.size()
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        col = np.zeros(max(nnz, 1), dtype=np.int32)
+        check(load_library().gbe_graph_export(self.ctx.handle, self._h, _ptr(rowptr), _ptr(col)),
+              "gbe_graph_export")
+        return rowptr, col[:nnz]
+
+
+class Parts(_Owned):
+    _free = "gbe_free_parts"
+
+    def info(self):
+        P, total, max_m = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        check(load_library().gbe_parts_info(self._h, ctypes.byref(P), ctypes.byref(total), ctypes.byref(max_m)),
+              "gbe_parts_info")
+        return P.value, total.value, max_m.value
+
+    def export(self):
+        """(core_count[P], sub_ptr[P+1], sub_idx[total]) as NumPy arrays."""
+        P, total, _ = self.info()
+        cc = np.zeros(P, dtype=np.int32)
+        sp = np.zeros(P + 1, dtype=np.int64)
+        si = np.zeros(total, dtype=np.int32)
+        check(load_library().gbe_parts_export(self.ctx.handle, self._h, _ptr(cc), _ptr(sp), _ptr(si)),
+              "gbe_parts_export")
+        return cc, sp, si
+
+
+class Subs(_Owned):
+    _free = "gbe_free_subs"
+
+    def export(self, s, m):
+        out = np.zeros((m, m), dtype=np.float64)
+        check(load_library().gbe_subs_export(self.ctx.handle, self._h, int(s), _ptr(out)), "gbe_subs_export")
+        return out
+
+
+def sites(pos, onsite, box):
+    dev = _is_device(pos)
+    s = Sites(int(pos.shape[0]), _ptr(pos), _ptr(onsite), (ctypes.c_double * 3)(*[float(b) for b in box]),
+              1 if dev else 0)
+    s._keep = (pos, onsite)
+    return s
+
+
+def tb_model(a=1.0, rcut=2.5, decay=0.3, hop=-1.0):
+    return TbModel(a, rcut, decay, hop)
+
+
+def build_hamiltonian(ctx, site_struct, model=None):
+    h = ctypes.c_void_p()
+    model = model or tb_model()
+    check(load_library().gbe_build_hamiltonian(ctx.handle, ctypes.byref(site_struct), ctypes.byref(model),
+                                               ctypes.byref(h)), "gbe_build_hamiltonian")
+    return Hamiltonian(ctx, h)
+
+
+def build_graph(ctx, H, mode, thresh=0.0, k=1, D_prev=None, site_struct=None, mlp=None, rcand=0.0,
+                logit_cut=0.0):
+    p = GraphParams(mode, thresh, k, ctypes.cast(ctypes.pointer(D_prev), ctypes.c_void_p) if D_prev is not None else None,
+                    ctypes.cast(ctypes.pointer(site_struct), ctypes.c_void_p) if site_struct is not None else None,
+                    mlp.handle if mlp is not None else None, rcand, logit_cut)
+    g = ctypes.c_void_p()
+    check(load_library().gbe_build_graph(ctx.handle, ctypes.byref(H), ctypes.byref(p), ctypes.byref(g)),
+          "gbe_build_graph")
+    return Graph(ctx, g)
+
+
+def partition(ctx, S, mode=PART_SPATIAL_CELLS, ncell=(1, 1, 1), site_struct=None, core_size=0, max_sub=0):
+    p = PartitionParams(mode, (ctypes.c_int * 3)(*ncell),
+                        ctypes.cast(ctypes.pointer(site_struct), ctypes.c_void_p) if site_struct is not None else None,
+                        core_size, max_sub)
+    h = ctypes.c_void_p()
+    check(load_library().gbe_partition(ctx.handle, S.handle, ctypes.byref(p), ctypes.byref(h)), "gbe_partition")
+    return Parts(ctx, h)
+
+
+def parts_import(ctx, n, core_count, sub_ptr, sub_idx):
+    cc = np.ascontiguousarray(core_count, dtype=np.int32)
+    sp = np.ascontiguousarray(sub_ptr, dtype=np.int64)
+    si = np.ascontiguousarray(sub_idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    check(load_library().gbe_parts_import(ctx.handle, int(n), len(cc), _ptr(cc), _ptr(sp), _ptr(si),
+                                          ctypes.byref(h)), "gbe_parts_import")
+    return Parts(ctx, h)
+
+
+def sp2_params(n_occ, prec=PREC_FP64, idem_tol=1e-10, n_min=10, n_max=100, fp64_tail=0, tail_switch=0.0,
+               seq=None, eps=None, timeout_ms=0.0):
+    buf = None
+    if seq is not None:
+        buf = np.ascontiguousarray(np.asarray(seq, dtype=np.uint8))
+    p = Sp2Params(float(n_occ), idem_tol, n_min, n_max, prec, fp64_tail, tail_switch,
+                  BRANCH_REPLAY if seq is not None else BRANCH_GLOBAL_TRACE,
+                  _ptr(buf) if buf is not None and len(buf) else None, 0 if buf is None else len(buf),
+                  1 if eps is not None else 0, eps[0] if eps is not None else 0.0,
+                  eps[1] if eps is not None else 0.0, timeout_ms)
+    if buf is not None and len(buf) == 0:
+        p.seq_in = ctypes.cast(ctypes.create_string_buffer(1), ctypes.c_void_p)
+    p._keep = buf
+    return p
+
+
+def subs_create(ctx, parts, prec):
+    h = ctypes.c_void_p()
+    check(load_library().gbe_subs_create(ctx.handle, parts.handle, prec, ctypes.byref(h)), "gbe_subs_create")
+    return Subs(ctx, h)
+
+
+def sp2_run(ctx, H, parts, params, X):
+    check(load_library().gbe_sp2_run(ctx.handle, ctypes.byref(H), parts.handle, ctypes.byref(params), X.handle),
+          "gbe_sp2_run")
+
+
+def sp2_report_get(ctx, X):
+    r = Sp2Report()
+    check(load_library().gbe_sp2_report_get(ctx.handle, X.handle, ctypes.byref(r)), "gbe_sp2_report_get")
+    return r
+
+
+def sp2_submatrices(ctx, H, parts, params, X=None):
+    """Returns (Subs, report dict).  Raises GbeError on failure (incl. ENOCONV)."""
+    h = ctypes.c_void_p(X.handle.value if X is not None else None)
+    r = Sp2Report()
+    code = load_library().gbe_sp2_submatrices(ctx.handle, ctypes.byref(H), parts.handle, ctypes.byref(params),
+                                              ctypes.byref(h), ctypes.byref(r))
+    if X is None and h.value:
+        X = Subs(ctx, h)
+    check(code, "gbe_sp2_submatrices")
+    return X, r.as_dict()
+
+
+def assemble_width(ctx, X, parts):
+    e = Ell()
+    check(load_library().gbe_assemble_D(ctx.handle, X.handle, parts.handle, 0.0, ctypes.byref(e)), "gbe_assemble_D")
+    return e.n, e.width
+
+
+def assemble_D(ctx, X, parts, col, val, drop_tol=0.0):
+    """Fill caller-owned ELL buffers col[n, width] (int32) and val[n, width] (float64)."""
+    n, width = col.shape
+    e = Ell(n, width, _ptr(col), _ptr(val), 1 if _is_device(col) else 0)
+    check(load_library().gbe_assemble_D(ctx.handle, X.handle, parts.handle, float(drop_tol), ctypes.byref(e)),
+          "gbe_assemble_D")
+    return col, val
+
+
+def ell_struct(col, val):
+    n, width = col.shape
+    e = Ell(n, width, _ptr(col), _ptr(val), 1 if _is_device(col) else 0)
+    e._keep = (col, val)
+    return e
+
+
+def ell_to_dense(col, val, n):
+    """Dense D from an ELL pair (row i of the ELL = column i of D).  Test/inspection helper."""
+    col = np.asarray(col)
+    val = np.asarray(val)
+    D = np.zeros((n, n))
+    rows = np.repeat(np.arange(n), col.shape[1]).reshape(col.shape)
+    m = col >= 0
+    D[col[m], rows[m]] = val[m]
+    return D

@@ -1,0 +1,160 @@
+// Internal declarations shared by the libgbe translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/gbe.h"
+
+// ----------------------------------------------------------------------------- errors
+void gbe_set_error(const char* fmt, ...);
+
+#define GBE_CUDA_TRY(expr)                                                               \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            gbe_set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(e_)); \
+            return GBE_ECUDA;                                                            \
+        }                                                                                \
+    } while (0)
+
+#define GBE_TRY(expr)                  \
+    do {                               \
+        int r_ = (expr);               \
+        if (r_ != GBE_OK) return r_;   \
+    } while (0)
+
+#define GBE_CHECK_ARG(cond, msg)                          \
+    do {                                                  \
+        if (!(cond)) {                                    \
+            gbe_set_error("invalid argument: %s", msg);   \
+            return GBE_EINVAL;                            \
+        }                                                 \
+    } while (0)
+
+// ----------------------------------------------------------------------------- objects
+struct gbe_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    int smem_optin = 0;
+    // small device scratch for counters and flags (4 KB), and its pinned host mirror
+    void* d_scratch = nullptr;
+    void* h_scratch = nullptr;
+};
+
+struct gbe_hamiltonian {
+    int64_t n = 0, nnz = 0;
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+};
+
+// Graph: explicit CSR of the base pattern A (undirected, diagonal present); the
+// graph it stands for is pattern(A^hops).  `full_*` caches the explicit A^hops.
+struct gbe_graph {
+    int64_t n = 0, nnz = 0;
+    int hops = 1;
+    int64_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    int64_t full_nnz = -1;
+    int64_t* full_rowptr = nullptr;
+    int32_t* full_col = nullptr;
+};
+
+struct gbe_parts {
+    int64_t n = 0;        // vertices
+    int64_t P = 0;        // subgraphs
+    int64_t total = 0;    // sum of m_s
+    int64_t max_m = 0;
+    int32_t* d_core_count = nullptr;  // [P]
+    int64_t* d_sub_ptr = nullptr;     // [P+1]
+    int32_t* d_sub_idx = nullptr;     // [total]
+    std::vector<int32_t> h_core_count;
+    std::vector<int64_t> h_sub_ptr;
+};
+
+// Device control block of one SP2 run (one per gbe_subs).
+struct Sp2Ctrl {
+    int iter;        // n of the current iterate X_n
+    int stop;        // GBE_STOP_*
+    int mode;        // 0 tensor-core squaring, 1 FP64 squaring
+    int fmt;         // storage of X_n: 0 split planes, 1 FP64
+    int cur;         // ping-pong side holding X_n
+    int branch;      // 1: X_{n+1} = X_n^2, 0: 2 X_n - X_n^2 (valid while stop == 0)
+    int status;      // GBE_OK or an error code recorded on the device
+    int fp64_iters;
+    int switch_iter; // first FP64 iteration in mixed runs (-1 before the switch)
+    int pending;     // a squaring kernel ran since the last decision
+    int n_min, n_max, branch_mode, seq_len, fp64_tail, prec, eps_given;
+    unsigned long long eps_min_key, eps_max_key;  // order-preserving keys for atomics
+    double eps_min, eps_max;
+    double n_occ, idem_tol, tail_switch;
+    long long timeout_cycles;
+    uint8_t seq_in[GBE_SEQ_MAX];
+    uint8_t seq[GBE_SEQ_MAX];
+    double t1[GBE_SEQ_MAX + 1];
+    double t2[GBE_SEQ_MAX + 1];
+};
+
+// Work item of a squaring kernel: output tile (I, J), I <= J, of subgraph s.
+struct TileItem {
+    int s, I, J, pad;
+};
+
+struct SubsGeom {
+    // per subgraph (device)
+    const int64_t* off;    // element offset of x_s in a plane
+    const int32_t* mpad;   // padded size (multiple of 128)
+    const int32_t* m;      // m_s
+    const int32_t* c;      // core count
+};
+
+struct gbe_subs {
+    const gbe_parts* parts = nullptr;
+    int prec = 0;
+    int64_t P = 0;
+    int64_t total_elems = 0;    // sum of mpad^2
+    int max_mpad = 0;
+    std::vector<int64_t> h_off;
+    std::vector<int32_t> h_mpad, h_m, h_c;
+    int64_t* d_off = nullptr;
+    int32_t* d_mpad = nullptr;
+    int32_t* d_m = nullptr;
+    int32_t* d_c = nullptr;
+    // storage
+    uint16_t* planes[2] = {nullptr, nullptr};  // tensor-core path: 4 planes x total_elems, fp16/bf16 bits
+    double* f64[2] = {nullptr, nullptr};       // FP64 iterates
+    // work lists
+    TileItem* d_items_tc = nullptr;  int n_items_tc = 0;   // 128x128 tiles
+    TileItem* d_items_64 = nullptr;  int n_items_64 = 0;   // 64x64 tiles
+    double* d_partials = nullptr;    int max_units = 0;    // [2][max_units] (t1, t2)
+    Sp2Ctrl* d_ctrl = nullptr;
+    Sp2Ctrl* h_ctrl = nullptr;       // pinned
+    // tensor maps for the split planes (opaque 128-byte CUtensorMap blobs)
+    alignas(64) unsigned char tmap[2][128];
+    bool tmap_ok = false;
+    // phase timing
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    double alg_flops_per_iter = 0.0, mma_flops_per_iter = 0.0, fp64_flops_per_iter = 0.0;
+};
+
+// ----------------------------------------------------------------------------- blocked layout
+// A padded m x m submatrix (mpad multiple of 128) is stored as 128 x 64 blocks, block
+// (r / 128, c / 64) at index (r / 128) * (mpad / 64) + c / 64, row-major inside a block.
+__host__ __device__ inline int64_t blk_index(int64_t off, int mpad, int r, int c) {
+    return off + ((int64_t)((r >> 7) * (mpad >> 6) + (c >> 6)) << 13) + ((r & 127) << 6) + (c & 63);
+}
+
+// ----------------------------------------------------------------------------- launchers
+int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X);
+int gbe_tc_make_tmaps(gbe_subs* X);
+int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X);
+int gbe_tc_prepare(gbe_ctx* ctx);
+
+// helpers
+int gbe_alloc(void** p, size_t bytes);
+int gbe_sync(gbe_ctx* ctx);

@@ -1,0 +1,776 @@
+// SP2 on core+halo submatrices: state, Gershgorin bounds, gather, device-side branch
+// decisions, the FP64 squaring, column assembly and export.
+//
+// One density-matrix build (Sec. II.A: Eq. 6 with the recursive zero-temperature
+// expansion D = lim f_n(...f_0(H)), f_n(X) = X^2 or 2X - X^2):
+//   gershgorin  -> e_min, e_max of the whole H                      (FP64)
+//   gather      -> X_0[s] = (e_max I - x[s]) / (e_max - e_min)        per subgraph
+//   decide      -> global FP64 traces over core positions, branch / stop
+//   repeat: square (tensor-core or FP64 kernel; branch applied in its epilogue) -> decide
+// The decision lives in a device control block, so the host enqueues a fixed number
+// of slots and finished runs turn later slots into immediate exits.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gbe_internal.h"
+#include "split.cuh"
+
+// ----------------------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned long long dkey(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum in a fixed order (deterministic for a fixed blockDim).
+template <int NT>
+__device__ double block_sum_d(double v, double* sh) {
+    v = warp_sum_d(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < NT / 32) ? sh[l] : 0.0;
+        r = warp_sum_d(r);
+    }
+    return r;  // valid in thread 0
+}
+
+// ----------------------------------------------------------------------------- Gershgorin
+__global__ void __launch_bounds__(256) gershgorin_kernel(const int64_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ col,
+                                                         const double* __restrict__ val, int64_t n,
+                                                         Sp2Ctrl* ctrl) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double lo = INFINITY, hi = -INFINITY;
+    bool bad = false;
+    for (int64_t i = warp; i < n; i += nwarps) {
+        double off = 0.0, d = 0.0;
+        for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+            double v = val[p];
+            if (!isfinite(v)) bad = true;
+            if (col[p] == i) d = v; else off += fabs(v);
+        }
+        off = warp_sum_d(off);
+        d = warp_sum_d(d);
+        lo = fmin(lo, d - off);
+        hi = fmax(hi, d + off);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&ctrl->status, GBE_ENUMERIC);
+    if (lane == 0 && lo <= hi) {
+        atomicMin(&ctrl->eps_min_key, dkey(lo));
+        atomicMax(&ctrl->eps_max_key, dkey(hi));
+    }
+}
+
+// ----------------------------------------------------------------------------- gather
+// One CTA per subgraph: row a of x_s is row idx_s[a] of H restricted to idx_s; local
+// column of a global column found by binary search in the sorted core and halo lists.
+__device__ __forceinline__ int find_local(const int32_t* idx, int c, int m, int g) {
+    int lo = 0, hi = c - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = idx[mid];
+        if (v == g) return mid;
+        if (v < g) lo = mid + 1; else hi = mid - 1;
+    }
+    lo = c; hi = m - 1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        int v = idx[mid];
+        if (v == g) return mid;
+        if (v < g) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+__global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ col,
+                                                     const double* __restrict__ val,
+                                                     const int64_t* __restrict__ sub_ptr,
+                                                     const int32_t* __restrict__ sub_idx, SubsGeom g,
+                                                     int prec, uint16_t* planes, int64_t plane_stride,
+                                                     double* f, double* partials, int max_units) {
+    extern __shared__ int32_t sidx[];
+    __shared__ double red[8];
+    const int s = blockIdx.x;
+    const int m = g.m[s], c = g.c[s], mpad = g.mpad[s];
+    const int64_t off = g.off[s];
+    const int64_t base = sub_ptr[s];
+    for (int a = threadIdx.x; a < m; a += blockDim.x) sidx[a] = sub_idx[base + a];
+    __syncthreads();
+    double emin, emax;
+    if (ctrl->eps_given) { emin = ctrl->eps_min; emax = ctrl->eps_max; }
+    else { emin = dkey_inv(ctrl->eps_min_key); emax = dkey_inv(ctrl->eps_max_key); }
+    const double range = emax - emin;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double t1 = 0.0, t2 = 0.0;
+    for (int a = warp; a < m; a += 8) {
+        const int64_t gi = sidx[a];
+        for (int64_t p = rowptr[gi] + lane; p < rowptr[gi + 1]; p += 32) {
+            const int b = find_local(sidx, c, m, col[p]);
+            if (b < 0) continue;
+            const double h = val[p];
+            const double x = ((a == b ? emax : 0.0) - h) / range;
+            const int64_t e = blk_index(off, mpad, a, b);
+            if (prec == GBE_PREC_FP64) {
+                f[e] = x;
+            } else if (prec == GBE_PREC_FP16X6) {
+                OzSplit o = oz_split_d(x);
+                planes[e] = o.s0;
+                planes[e + plane_stride] = o.s1;
+                planes[e + 2 * plane_stride] = o.s2;
+                planes[e + 3 * plane_stride] = o.s1s;
+            } else {
+                __nv_bfloat16 hi = __double2bfloat16(x);
+                planes[e] = b_bits(hi);
+                planes[e + plane_stride] = b_bits(__double2bfloat16(x - (double)__bfloat162float(hi)));
+            }
+            if (a < c) {
+                t2 += x * x;
+                if (a == b) t1 += x;
+            }
+        }
+    }
+    double s1 = block_sum_d<256>(t1, red);
+    double s2 = block_sum_d<256>(t2, red);
+    if (threadIdx.x == 0) {
+        partials[s] = s1;
+        partials[max_units + s] = s2;
+        if (s == 0) { ctrl->eps_min = emin; ctrl->eps_max = emax; }
+    }
+}
+
+// ----------------------------------------------------------------------------- decide
+// Global FP64 traces over core positions -> stop rule and branch of the next step.
+// kind: 0 after the gather (X_0), 1 after a tensor-core step, 2 after an FP64 step.
+__global__ void __launch_bounds__(512) decide_kernel(Sp2Ctrl* ctrl, const double* __restrict__ partials,
+                                                     int max_units, int n_units, int kind) {
+    __shared__ double red[16];
+    __shared__ int run;
+    if (threadIdx.x == 0) run = (kind == 0) ? 1 : ctrl->pending;
+    __syncthreads();
+    if (!run) return;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n_units; i += 512) {
+        a += partials[i];
+        b += partials[max_units + i];
+    }
+    double t1 = block_sum_d<512>(a, red);
+    double t2 = block_sum_d<512>(b, red);
+    if (threadIdx.x != 0) return;
+    Sp2Ctrl* C = ctrl;
+    C->pending = 0;
+    if (kind != 0) {
+        const int n_prev = C->iter;
+        C->seq[n_prev] = (uint8_t)C->branch;
+        C->iter = n_prev + 1;
+        C->cur ^= 1;
+        C->fmt = (kind == 2) ? 1 : 0;
+        if (kind == 2) C->fp64_iters++;
+    }
+    const int n = C->iter;
+    C->t1[n] = t1;
+    C->t2[n] = t2;
+    if (C->status != GBE_OK || !isfinite(t1) || !isfinite(t2)) {
+        if (C->status == GBE_OK) C->status = GBE_ENUMERIC;
+        C->stop = GBE_STOP_ERROR;
+        return;
+    }
+    const double e = fabs(t1 - t2);
+    const bool mixed = (C->prec != GBE_PREC_FP64);
+    if (C->branch_mode == GBE_BRANCH_REPLAY) {
+        if (n >= C->seq_len || n >= C->n_max) { C->stop = GBE_STOP_REPLAY; return; }
+        C->branch = C->seq_in[n] ? 1 : 0;
+        if (mixed && C->mode == 0 && n >= C->seq_len - C->fp64_tail) { C->mode = 1; C->switch_iter = n; }
+        return;
+    }
+    const bool stalled = (n >= C->n_min && n >= 2 && e >= fabs(C->t1[n - 2] - C->t2[n - 2]));
+    if (mixed && C->mode == 0 && C->fp64_tail > 0) {
+        if (e <= C->tail_switch || e <= C->idem_tol || stalled) { C->mode = 1; C->switch_iter = n; }
+    } else {
+        const int since = (C->switch_iter >= 0) ? n - C->switch_iter : n;
+        const bool tail_done = !mixed || C->fp64_tail == 0 || since >= C->fp64_tail;
+        const bool stall_ok = (C->switch_iter < 0) || (since >= 2);
+        if (e <= C->idem_tol && tail_done) { C->stop = GBE_STOP_TOL; return; }
+        if (stalled && stall_ok && tail_done) { C->stop = GBE_STOP_STALL; return; }
+    }
+    if (n >= C->n_max) { C->stop = GBE_STOP_NMAX; return; }
+    C->branch = (fabs(t2 - C->n_occ) < fabs(2.0 * t1 - t2 - C->n_occ)) ? 1 : 0;
+}
+
+// ----------------------------------------------------------------------------- FP64 squaring
+// 64 x 64 output tiles (I <= J) of X_{n+1} = f(X_n) per subgraph, DFMA with register
+// blocking; the branch is applied in the epilogue and the tile is mirrored to (J, I).
+__device__ __forceinline__ double load_x(int fmt, int prec, const uint16_t* pl, int64_t ps, const double* f,
+                                         int64_t e) {
+    if (fmt == 1) return f[e];
+    if (prec == GBE_PREC_FP16X6) return oz_value(pl[e], pl[e + ps], pl[e + 2 * ps]);
+    return bf_value(pl[e], pl[e + ps]);
+}
+
+__global__ void __launch_bounds__(256) square_fp64_kernel(Sp2Ctrl* ctrl, SubsGeom g,
+                                                          const TileItem* __restrict__ items, int n_items,
+                                                          uint16_t* planes0, uint16_t* planes1,
+                                                          int64_t plane_stride, double* f0, double* f1,
+                                                          double* partials, int max_units) {
+    __shared__ double As[2][16][64];
+    __shared__ double Bs[2][16][64];
+    __shared__ double red[8];
+    __shared__ int hdr[5];
+    if (threadIdx.x == 0) {
+        hdr[0] = (ctrl->stop == 0 && ctrl->mode == 1);
+        hdr[1] = ctrl->cur;
+        hdr[2] = ctrl->fmt;
+        hdr[3] = ctrl->branch;
+        hdr[4] = ctrl->prec;
+    }
+    __syncthreads();
+    if (!hdr[0]) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->pending = 1;
+    const int cur = hdr[1], fmt = hdr[2], branch = hdr[3], prec = hdr[4];
+    const uint16_t* pin = cur ? planes1 : planes0;
+    const double* fin = cur ? f1 : f0;
+    double* fout = cur ? f0 : f1;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int lr = threadIdx.x >> 2, lk = (threadIdx.x & 3) * 4;
+
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const TileItem w = items[it];
+        const int mpad = g.mpad[w.s], m = g.m[w.s], c = g.c[w.s];
+        const int64_t off = g.off[w.s];
+        const int kend = (m + 15) & ~15;
+        double acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        const int ra = w.I * 64 + lr, rb = w.J * 64 + lr;
+        double va[4], vb[4];
+        auto fetch = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                va[q] = load_x(fmt, prec, pin, plane_stride, fin, blk_index(off, mpad, ra, k0 + lk + q));
+                vb[q] = load_x(fmt, prec, pin, plane_stride, fin, blk_index(off, mpad, rb, k0 + lk + q));
+            }
+        };
+        fetch(0);
+        int buf = 0;
+        for (int k0 = 0; k0 < kend; k0 += 16) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                As[buf][lk + q][lr] = va[q];
+                Bs[buf][lk + q][lr] = vb[q];
+            }
+            __syncthreads();
+            if (k0 + 16 < kend) fetch(k0 + 16);
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            buf ^= 1;
+        }
+        double t1 = 0.0, t2 = 0.0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = w.I * 64 + ty + 16 * i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cc = w.J * 64 + tx + 16 * j;
+                const int64_t e = blk_index(off, mpad, r, cc);
+                double x = acc[i][j];
+                if (!branch) x = 2.0 * load_x(fmt, prec, pin, plane_stride, fin, e) - x;
+                fout[e] = x;
+                if (w.I != w.J) fout[blk_index(off, mpad, cc, r)] = x;
+                const int wgt = (r < c) + ((w.I != w.J) && (cc < c));
+                t2 += wgt * (x * x);
+                if (r == cc && r < c) t1 += x;
+            }
+        }
+        double s1 = block_sum_d<256>(t1, red);
+        double s2 = block_sum_d<256>(t2, red);
+        if (threadIdx.x == 0) {
+            partials[it] = s1;
+            partials[max_units + it] = s2;
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------- assembly
+// One CTA per subgraph, one warp per core column j: ELL row idx_s[j] <- (idx_s[k], x_s[j,k]).
+__global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, const int64_t* __restrict__ sub_ptr,
+                                                       const int32_t* __restrict__ sub_idx, SubsGeom g,
+                                                       const uint16_t* planes0, const uint16_t* planes1,
+                                                       int64_t plane_stride, const double* f0, const double* f1,
+                                                       int64_t width, int32_t* ell_col, double* ell_val,
+                                                       double drop_tol) {
+    const int s = blockIdx.x;
+    const int m = g.m[s], c = g.c[s], mpad = g.mpad[s];
+    const int64_t off = g.off[s], base = sub_ptr[s];
+    const int cur = ctrl->cur, fmt = ctrl->fmt, prec = ctrl->prec;
+    const uint16_t* pl = cur ? planes1 : planes0;
+    const double* f = cur ? f1 : f0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < c; j += 8) {
+        const int64_t row = sub_idx[base + j];
+        int32_t* oc = ell_col + row * width;
+        double* ov = ell_val + row * width;
+        int pos = 0;
+        for (int k0 = 0; k0 < m; k0 += 32) {
+            const int k = k0 + lane;
+            double v = 0.0;
+            int gk = -1;
+            if (k < m) {
+                v = load_x(fmt, prec, pl, plane_stride, f, blk_index(off, mpad, j, k));
+                gk = sub_idx[base + k];
+            }
+            const bool keep = (k < m) && !(drop_tol > 0.0 && fabs(v) < drop_tol);
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int p = pos + __popc(bal & ((1u << lane) - 1u));
+                oc[p] = gk;
+                ov[p] = v;
+            }
+            pos += __popc(bal);
+        }
+        for (int p = pos + lane; p < width; p += 32) {
+            oc[p] = -1;
+            ov[p] = 0.0;
+        }
+    }
+}
+
+__global__ void fill_ell_kernel(int64_t total, int32_t* col, double* val) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        col[i] = -1;
+        val[i] = 0.0;
+    }
+}
+
+__global__ void export_kernel(const Sp2Ctrl* ctrl, SubsGeom g, int s, const uint16_t* planes0,
+                              const uint16_t* planes1, int64_t plane_stride, const double* f0, const double* f1,
+                              double* out) {
+    const int m = g.m[s], mpad = g.mpad[s];
+    const int64_t off = g.off[s];
+    const int cur = ctrl->cur, fmt = ctrl->fmt, prec = ctrl->prec;
+    const uint16_t* pl = cur ? planes1 : planes0;
+    const double* f = cur ? f1 : f0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)m * m; i += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / m), cc = (int)(i % m);
+        out[i] = load_x(fmt, prec, pl, plane_stride, f, blk_index(off, mpad, r, cc));
+    }
+}
+
+// ============================================================================= host side
+static SubsGeom geom_of(const gbe_subs* X) { return SubsGeom{X->d_off, X->d_mpad, X->d_m, X->d_c}; }
+
+extern "C" int gbe_parts_import(gbe_ctx* ctx, int64_t n, int64_t P, const int32_t* core_count,
+                                const int64_t* sub_ptr, const int32_t* sub_idx, gbe_parts** out) {
+    GBE_CHECK_ARG(ctx && out && core_count && sub_ptr && sub_idx, "NULL argument");
+    GBE_CHECK_ARG(n > 0 && n < INT32_MAX && P > 0, "bad sizes");
+    GBE_CHECK_ARG(sub_ptr[0] == 0, "sub_ptr[0] must be 0");
+    int64_t max_m = 0;
+    for (int64_t s = 0; s < P; ++s) {
+        const int64_t m = sub_ptr[s + 1] - sub_ptr[s];
+        GBE_CHECK_ARG(m > 0, "empty subgraph");
+        GBE_CHECK_ARG(core_count[s] > 0 && core_count[s] <= m, "core count out of range");
+        max_m = std::max(max_m, m);
+    }
+    const int64_t total = sub_ptr[P];
+    for (int64_t i = 0; i < total; ++i) GBE_CHECK_ARG(sub_idx[i] >= 0 && sub_idx[i] < n, "sub_idx out of range");
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    gbe_parts* p = new gbe_parts();
+    p->n = n; p->P = P; p->total = total; p->max_m = max_m;
+    p->h_core_count.assign(core_count, core_count + P);
+    p->h_sub_ptr.assign(sub_ptr, sub_ptr + P + 1);
+    int r = GBE_OK;
+    if ((r = gbe_alloc((void**)&p->d_core_count, P * 4)) != GBE_OK ||
+        (r = gbe_alloc((void**)&p->d_sub_ptr, (P + 1) * 8)) != GBE_OK ||
+        (r = gbe_alloc((void**)&p->d_sub_idx, total * 4)) != GBE_OK) {
+        gbe_free_parts(p);
+        return r;
+    }
+    cudaMemcpyAsync(p->d_core_count, core_count, P * 4, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(p->d_sub_ptr, sub_ptr, (P + 1) * 8, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(p->d_sub_idx, sub_idx, total * 4, cudaMemcpyHostToDevice, ctx->stream);
+    GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    *out = p;
+    return GBE_OK;
+}
+
+extern "C" int gbe_parts_info(const gbe_parts* p, int64_t* P, int64_t* total, int64_t* max_m) {
+    GBE_CHECK_ARG(p != nullptr, "parts is NULL");
+    if (P) *P = p->P;
+    if (total) *total = p->total;
+    if (max_m) *max_m = p->max_m;
+    return GBE_OK;
+}
+
+extern "C" int gbe_parts_export(gbe_ctx* ctx, const gbe_parts* p, int32_t* core_count, int64_t* sub_ptr,
+                                int32_t* sub_idx) {
+    GBE_CHECK_ARG(ctx && p, "NULL argument");
+    if (core_count) memcpy(core_count, p->h_core_count.data(), p->P * 4);
+    if (sub_ptr) memcpy(sub_ptr, p->h_sub_ptr.data(), (p->P + 1) * 8);
+    if (sub_idx) {
+        GBE_CUDA_TRY(cudaMemcpyAsync(sub_idx, p->d_sub_idx, p->total * 4, cudaMemcpyDeviceToHost, ctx->stream));
+        GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    return GBE_OK;
+}
+
+extern "C" int gbe_free_parts(gbe_parts* p) {
+    if (!p) return GBE_OK;
+    cudaFree(p->d_core_count);
+    cudaFree(p->d_sub_ptr);
+    cudaFree(p->d_sub_idx);
+    delete p;
+    return GBE_OK;
+}
+
+extern "C" int gbe_free_subs(gbe_subs* X) {
+    if (!X) return GBE_OK;
+    cudaFree(X->d_off); cudaFree(X->d_mpad); cudaFree(X->d_m); cudaFree(X->d_c);
+    for (int i = 0; i < 2; ++i) { cudaFree(X->planes[i]); cudaFree(X->f64[i]); }
+    cudaFree(X->d_items_tc); cudaFree(X->d_items_64); cudaFree(X->d_partials); cudaFree(X->d_ctrl);
+    if (X->h_ctrl) cudaFreeHost(X->h_ctrl);
+    for (int i = 0; i < 3; ++i) if (X->ev[i]) cudaEventDestroy(X->ev[i]);
+    delete X;
+    return GBE_OK;
+}
+
+static void make_items(const std::vector<int32_t>& dim, const std::vector<int32_t>& cost, int tile,
+                       std::vector<TileItem>& items) {
+    items.clear();
+    const int64_t P = (int64_t)dim.size();
+    std::vector<int64_t> order(P);
+    for (int64_t s = 0; s < P; ++s) order[s] = s;
+    // longest K first, so a static round-robin over persistent CTAs stays balanced
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    for (int64_t s : order) {
+        const int T = (dim[s] + tile - 1) / tile;
+        for (int I = 0; I < T; ++I)
+            for (int J = I; J < T; ++J) items.push_back(TileItem{(int)s, I, J, 0});
+    }
+}
+
+extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, gbe_subs** out) {
+    GBE_CHECK_ARG(ctx && parts && out, "NULL argument");
+    GBE_CHECK_ARG(prec == GBE_PREC_FP64 || prec == GBE_PREC_FP16X6 || prec == GBE_PREC_BF16X3, "unknown prec");
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    gbe_subs* X = new gbe_subs();
+    X->parts = parts;
+    X->prec = prec;
+    X->P = parts->P;
+    X->h_off.resize(X->P); X->h_mpad.resize(X->P); X->h_m.resize(X->P); X->h_c.resize(X->P);
+    int64_t total = 0;
+    double alg = 0.0, mma = 0.0, f64 = 0.0;
+    const int nprod = (prec == GBE_PREC_FP16X6) ? 6 : 3;
+    for (int64_t s = 0; s < X->P; ++s) {
+        const int m = (int)(parts->h_sub_ptr[s + 1] - parts->h_sub_ptr[s]);
+        const int mpad = (m + 127) & ~127;
+        X->h_m[s] = m; X->h_mpad[s] = mpad; X->h_c[s] = parts->h_core_count[s];
+        X->h_off[s] = total;
+        total += (int64_t)mpad * mpad;
+        X->max_mpad = std::max(X->max_mpad, mpad);
+        alg += 2.0 * (double)m * m * m;
+        const int T = mpad / 128, kk = (m + 31) & ~31;
+        mma += (double)nprod * 2.0 * 128.0 * 128.0 * kk * (T * (T + 1) / 2);
+        const int T64 = (m + 63) / 64, k16 = (m + 15) & ~15;
+        f64 += 2.0 * 64.0 * 64.0 * k16 * (T64 * (T64 + 1) / 2);
+    }
+    X->total_elems = total;
+    X->alg_flops_per_iter = alg;
+    X->mma_flops_per_iter = mma;
+    X->fp64_flops_per_iter = f64;
+    std::vector<TileItem> it_tc, it_64;
+    std::vector<int32_t> m64(X->P);
+    for (int64_t s = 0; s < X->P; ++s) m64[s] = X->h_m[s];
+    make_items(X->h_mpad, X->h_mpad, 128, it_tc);
+    make_items(m64, X->h_mpad, 64, it_64);
+    X->n_items_tc = (int)it_tc.size();
+    X->n_items_64 = (int)it_64.size();
+    X->max_units = (int)std::max<int64_t>(X->P, std::max(X->n_items_tc, X->n_items_64));
+    int r = GBE_OK;
+#define ALLOC(ptr, bytes) if (r == GBE_OK) r = gbe_alloc((void**)&(ptr), (bytes))
+    ALLOC(X->d_off, X->P * 8);
+    ALLOC(X->d_mpad, X->P * 4);
+    ALLOC(X->d_m, X->P * 4);
+    ALLOC(X->d_c, X->P * 4);
+    ALLOC(X->d_items_tc, std::max<int64_t>(1, X->n_items_tc) * sizeof(TileItem));
+    ALLOC(X->d_items_64, std::max<int64_t>(1, X->n_items_64) * sizeof(TileItem));
+    ALLOC(X->d_partials, 2 * (int64_t)X->max_units * 8);
+    ALLOC(X->d_ctrl, sizeof(Sp2Ctrl));
+    for (int i = 0; i < 2; ++i) {
+        ALLOC(X->f64[i], total * 8);
+        if (prec != GBE_PREC_FP64) ALLOC(X->planes[i], 4 * total * 2);
+    }
+#undef ALLOC
+    if (r != GBE_OK) { gbe_free_subs(X); return r; }
+    if (cudaMallocHost((void**)&X->h_ctrl, sizeof(Sp2Ctrl)) != cudaSuccess) {
+        gbe_free_subs(X);
+        gbe_set_error("cudaMallocHost(ctrl) failed");
+        return GBE_ENOMEM;
+    }
+    for (int i = 0; i < 3; ++i) cudaEventCreate(&X->ev[i]);
+    cudaStream_t st = ctx->stream;
+    cudaMemcpyAsync(X->d_off, X->h_off.data(), X->P * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(X->d_mpad, X->h_mpad.data(), X->P * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(X->d_m, X->h_m.data(), X->P * 4, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(X->d_c, X->h_c.data(), X->P * 4, cudaMemcpyHostToDevice, st);
+    if (X->n_items_tc) cudaMemcpyAsync(X->d_items_tc, it_tc.data(), it_tc.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
+    if (X->n_items_64) cudaMemcpyAsync(X->d_items_64, it_64.data(), it_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
+    for (int i = 0; i < 2; ++i) {
+        cudaMemsetAsync(X->f64[i], 0, total * 8, st);
+        if (X->planes[i]) cudaMemsetAsync(X->planes[i], 0, 4 * total * 2, st);
+    }
+    GBE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (prec != GBE_PREC_FP64) {
+        r = gbe_tc_make_tmaps(X);
+        if (r != GBE_OK) { gbe_free_subs(X); return r; }
+    }
+    *out = X;
+    return GBE_OK;
+}
+
+int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X) {
+    const int blocks = std::max(1, std::min<int>((int)((H->n + 7) / 8), ctx->sm_count * 8));
+    gershgorin_kernel<<<blocks, 256, 0, ctx->stream>>>(H->rowptr, H->col, H->val, H->n, X->d_ctrl);
+    GBE_CUDA_TRY(cudaGetLastError());
+    return GBE_OK;
+}
+
+extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* prm,
+                           gbe_subs* X) {
+    GBE_CHECK_ARG(ctx && H && parts && prm && X, "NULL argument");
+    GBE_CHECK_ARG(H->on_device, "gbe_sp2_run needs a device CSR (use gbe_sp2_submatrices for host H)");
+    GBE_CHECK_ARG(X->parts == parts, "state was created for another partition");
+    GBE_CHECK_ARG(H->n == parts->n, "H and partition sizes differ");
+    GBE_CHECK_ARG(prm->prec == X->prec, "params.prec differs from the state's precision");
+    GBE_CHECK_ARG(prm->n_max > 0 && prm->n_max <= GBE_SEQ_MAX, "n_max out of range");
+    GBE_CHECK_ARG(prm->branch_mode == GBE_BRANCH_GLOBAL_TRACE || prm->branch_mode == GBE_BRANCH_REPLAY, "branch_mode");
+    GBE_CHECK_ARG(prm->branch_mode != GBE_BRANCH_REPLAY || (prm->seq_in && prm->seq_len >= 0 && prm->seq_len <= GBE_SEQ_MAX),
+                  "replay needs seq_in / seq_len <= GBE_SEQ_MAX");
+    GBE_CHECK_ARG(parts->max_m <= 8192, "subgraph larger than 8192");
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    Sp2Ctrl* C = X->h_ctrl;
+    // the pinned block may still be read by an earlier enqueued copy
+    GBE_CUDA_TRY(cudaStreamSynchronize(st));
+    memset(C, 0, sizeof(Sp2Ctrl));
+    C->mode = (prm->prec == GBE_PREC_FP64) ? 1 : 0;
+    C->fmt = (prm->prec == GBE_PREC_FP64) ? 1 : 0;
+    C->switch_iter = -1;
+    C->n_min = prm->n_min;
+    C->n_max = prm->n_max;
+    C->branch_mode = prm->branch_mode;
+    C->seq_len = prm->branch_mode == GBE_BRANCH_REPLAY ? prm->seq_len : 0;
+    C->fp64_tail = prm->fp64_tail;
+    C->prec = prm->prec;
+    C->eps_given = prm->eps_given;
+    C->eps_min = prm->eps_min;
+    C->eps_max = prm->eps_max;
+    C->eps_min_key = ~0ull;
+    C->eps_max_key = 0ull;
+    C->n_occ = prm->n_occ;
+    C->idem_tol = prm->idem_tol;
+    C->tail_switch = prm->tail_switch;
+    const double tmo = prm->timeout_ms > 0 ? prm->timeout_ms : 2000.0;
+    C->timeout_cycles = (long long)(tmo * 2.2e6);
+    if (C->branch_mode == GBE_BRANCH_REPLAY && C->seq_len) memcpy(C->seq_in, prm->seq_in, C->seq_len);
+    if (C->prec != GBE_PREC_FP64 && C->branch_mode == GBE_BRANCH_REPLAY && C->seq_len <= C->fp64_tail) C->mode = 1;
+    GBE_CUDA_TRY(cudaMemcpyAsync(X->d_ctrl, C, sizeof(Sp2Ctrl), cudaMemcpyHostToDevice, st));
+    cudaEventRecord(X->ev[0], st);
+    if (!prm->eps_given) GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
+    const int64_t ps = X->total_elems;
+    if (X->prec == GBE_PREC_FP64) GBE_CUDA_TRY(cudaMemsetAsync(X->f64[0], 0, ps * 8, st));
+    else GBE_CUDA_TRY(cudaMemsetAsync(X->planes[0], 0, 4 * ps * 2, st));
+    const size_t smem = (size_t)parts->max_m * 4;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    gather_kernel<<<(unsigned)X->P, 256, smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr,
+                                                      parts->d_sub_idx, geom_of(X), X->prec, X->planes[0], ps,
+                                                      X->f64[0], X->d_partials, X->max_units);
+    GBE_CUDA_TRY(cudaGetLastError());
+    decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, (int)X->P, 0);
+    cudaEventRecord(X->ev[1], st);
+    const int grid64 = std::max(1, std::min(X->n_items_64, ctx->sm_count * 4));
+    for (int slot = 0; slot < prm->n_max; ++slot) {
+        if (X->prec != GBE_PREC_FP64) {
+            GBE_TRY(gbe_tc_launch_square(ctx, X));
+            decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_tc, 1);
+        }
+        if (X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0) {
+            square_fp64_kernel<<<grid64, 256, 0, st>>>(X->d_ctrl, geom_of(X), X->d_items_64, X->n_items_64,
+                                                       X->planes[0], X->planes[1], ps, X->f64[0], X->f64[1],
+                                                       X->d_partials, X->max_units);
+            decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_64, 2);
+        }
+    }
+    GBE_CUDA_TRY(cudaGetLastError());
+    cudaEventRecord(X->ev[2], st);
+    return GBE_OK;
+}
+
+extern "C" int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_report* rep) {
+    GBE_CHECK_ARG(ctx && X && rep, "NULL argument");
+    GBE_CUDA_TRY(cudaMemcpyAsync(X->h_ctrl, X->d_ctrl, sizeof(Sp2Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+    GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    const Sp2Ctrl* C = X->h_ctrl;
+    memset(rep, 0, sizeof(*rep));
+    rep->iters = C->iter;
+    rep->fp64_iters = C->fp64_iters;
+    rep->stop_reason = C->stop;
+    rep->converged = (C->stop == GBE_STOP_TOL || C->stop == GBE_STOP_STALL || C->stop == GBE_STOP_REPLAY);
+    rep->status = C->status;
+    rep->eps_min = C->eps_min;
+    rep->eps_max = C->eps_max;
+    rep->trace = C->t1[C->iter];
+    rep->idem_err = fabs(C->t1[C->iter] - C->t2[C->iter]);
+    memcpy(rep->seq, C->seq, GBE_SEQ_MAX);
+    memcpy(rep->t1, C->t1, sizeof(rep->t1));
+    memcpy(rep->t2, C->t2, sizeof(rep->t2));
+    cudaEventElapsedTime(&rep->ms_gather, X->ev[0], X->ev[1]);
+    cudaEventElapsedTime(&rep->ms_sp2, X->ev[1], X->ev[2]);
+    const int mixed_iters = C->iter - C->fp64_iters;
+    rep->mma_flops = X->mma_flops_per_iter * mixed_iters;
+    rep->alg_flops = X->alg_flops_per_iter * C->iter;
+    return GBE_OK;
+}
+
+// Host CSR -> temporary device copy.
+struct DevCsr {
+    gbe_csr view{};
+    void* buf = nullptr;
+    ~DevCsr() { if (buf) cudaFree(buf); }
+};
+
+static int csr_to_device(gbe_ctx* ctx, const gbe_csr* H, DevCsr& d) {
+    if (H->on_device) { d.view = *H; return GBE_OK; }
+    const size_t b0 = (H->n + 1) * 8, b1 = ((H->nnz * 4 + 15) / 16) * 16, b2 = H->nnz * 8;
+    GBE_TRY(gbe_alloc(&d.buf, b0 + b1 + b2));
+    char* p = (char*)d.buf;
+    GBE_CUDA_TRY(cudaMemcpyAsync(p, H->rowptr, b0, cudaMemcpyHostToDevice, ctx->stream));
+    GBE_CUDA_TRY(cudaMemcpyAsync(p + b0, H->col, H->nnz * 4, cudaMemcpyHostToDevice, ctx->stream));
+    GBE_CUDA_TRY(cudaMemcpyAsync(p + b0 + b1, H->val, b2, cudaMemcpyHostToDevice, ctx->stream));
+    d.view = *H;
+    d.view.rowptr = (const int64_t*)p;
+    d.view.col = (const int32_t*)(p + b0);
+    d.view.val = (const double*)(p + b0 + b1);
+    d.view.on_device = 1;
+    return GBE_OK;
+}
+
+extern "C" int gbe_sp2_submatrices(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts,
+                                   const gbe_sp2_params* prm, gbe_subs** X, gbe_sp2_report* rep) {
+    GBE_CHECK_ARG(ctx && H && parts && prm && X, "NULL argument");
+    bool created = false;
+    if (*X == nullptr) {
+        GBE_TRY(gbe_subs_create(ctx, parts, prm->prec, X));
+        created = true;
+    }
+    DevCsr d;
+    int r = csr_to_device(ctx, H, d);
+    if (r == GBE_OK) r = gbe_sp2_run(ctx, &d.view, parts, prm, *X);
+    gbe_sp2_report tmp;
+    gbe_sp2_report* R = rep ? rep : &tmp;
+    if (r == GBE_OK) r = gbe_sp2_report_get(ctx, *X, R);
+    if (r != GBE_OK) {
+        if (created) { gbe_free_subs(*X); *X = nullptr; }
+        return r;
+    }
+    if (R->status != GBE_OK) {
+        gbe_set_error("device recorded status %d (%s)", R->status, gbe_strerror(R->status));
+        return R->status;
+    }
+    if (R->stop_reason == GBE_STOP_NMAX) {
+        gbe_set_error("SP2 stopped at n_max=%d with idempotency error %.3e", prm->n_max, R->idem_err);
+        return GBE_ENOCONV;
+    }
+    return GBE_OK;
+}
+
+extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, double drop_tol, gbe_ell* D) {
+    GBE_CHECK_ARG(ctx && X && parts && D, "NULL argument");
+    GBE_CHECK_ARG(X->parts == parts, "state was created for another partition");
+    if (D->col == nullptr) {
+        D->n = parts->n;
+        D->width = parts->max_m;
+        return GBE_OK;
+    }
+    GBE_CHECK_ARG(D->val != nullptr && D->n == parts->n, "D buffers / n");
+    if (D->width < parts->max_m) {
+        gbe_set_error("ELL width %lld < max subgraph size %lld", (long long)D->width, (long long)parts->max_m);
+        return GBE_ECAPACITY;
+    }
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int64_t total = D->n * D->width;
+    int32_t* col = D->col;
+    double* val = D->val;
+    void* tmp = nullptr;
+    if (!D->on_device) {
+        const int64_t col_bytes = ((total * 4 + 15) / 16) * 16;
+        GBE_TRY(gbe_alloc(&tmp, col_bytes + total * 8));
+        col = (int32_t*)tmp;
+        val = (double*)((char*)tmp + col_bytes);
+    }
+    fill_ell_kernel<<<ctx->sm_count * 4, 256, 0, st>>>(total, col, val);
+    assemble_kernel<<<(unsigned)X->P, 256, 0, st>>>(X->d_ctrl, parts->d_sub_ptr, parts->d_sub_idx, geom_of(X),
+                                                      X->planes[0], X->planes[1], X->total_elems, X->f64[0],
+                                                      X->f64[1], D->width, col, val, drop_tol);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && !D->on_device) {
+        e = cudaMemcpyAsync(D->col, col, total * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(D->val, val, total * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) {
+        gbe_set_error("assemble: %s", cudaGetErrorString(e));
+        return GBE_ECUDA;
+    }
+    return GBE_OK;
+}
+
+extern "C" int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out) {
+    GBE_CHECK_ARG(ctx && X && out && s >= 0 && s < X->P, "bad argument");
+    const int64_t m = X->h_m[s];
+    void* tmp = nullptr;
+    GBE_TRY(gbe_alloc(&tmp, m * m * 8));
+    export_kernel<<<ctx->sm_count, 256, 0, ctx->stream>>>(X->d_ctrl, geom_of(X), (int)s, X->planes[0], X->planes[1],
+                                                          X->total_elems, X->f64[0], X->f64[1], (double*)tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, m * m * 8, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) {
+        gbe_set_error("export: %s", cudaGetErrorString(e));
+        return GBE_ECUDA;
+    }
+    return GBE_OK;
+}

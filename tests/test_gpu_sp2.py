@@ -1,0 +1,181 @@
+"""GPU parity of the SP2 core (gather, squarings, traces/branch, assembly) against the oracle.
+
+Partitions come from the oracle and enter libgbe through gbe_parts_import, so these tests
+isolate the SP2 kernels; the graph and partition kernels have their own parity tests.
+Tolerances: FP64 path 1e-10 (max |dD| against the FP64 oracle on the same graph and
+branch sequence); FP16X6 tensor-core path 1e-6; BF16X3 reported, bounded loosely.
+"""
+import numpy as np
+import pytest
+
+from oracle import graph, partition, sp2
+
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_helpers import (assembled_dense, device_csr, gbe, host_csr, import_parts,  # noqa: E402
+                               lattice_case, oracle_graph_sp2)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return gbe.Context(0)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    w, H, S, subs, nc = lattice_case(8, seed=0, thr=1e-5)
+    N = H.shape[0]
+    _, logd = sp2.sp2_dense(H, N // 2)
+    Dref, logr, xs = oracle_graph_sp2(H, subs, nc, seq=logd.seq)
+    return dict(w=w, H=H, subs=subs, nc=nc, seq=logd.seq, Dref=Dref, logr=logr)
+
+
+def run(ctx, case, prec, seq=None, **kw):
+    H = case["H"]
+    N = H.shape[0]
+    parts = import_parts(ctx, N, case["subs"], case["nc"])
+    p = gbe.sp2_params(N // 2, prec=prec, seq=seq, **kw)
+    X, rep = gbe.sp2_submatrices(ctx, device_csr(H), parts, p)
+    D, col, val = assembled_dense(ctx, X, parts, N)
+    return D, rep, parts, X
+
+
+def test_fp64_replay_parity(ctx, c1):
+    D, rep, _, _ = run(ctx, c1, gbe.PREC_FP64, seq=c1["seq"])
+    assert rep["iters"] == len(c1["seq"]) and rep["stop"] == "replay"
+    err = np.abs(D - c1["Dref"]).max()
+    assert err <= 1e-10, err
+    # traces recorded on the device follow the oracle's FP64 traces
+    np.testing.assert_allclose(rep["t1"], c1["logr"].t1, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(rep["t2"], c1["logr"].t2, rtol=0, atol=1e-9)
+    lo, hi = sp2.gershgorin(c1["H"])
+    assert abs(rep["eps"][0] - lo) < 1e-12 and abs(rep["eps"][1] - hi) < 1e-12
+
+
+def test_fp64_free_running_matches_oracle_decisions(ctx, c1):
+    H = c1["H"]
+    N = H.shape[0]
+    _, logo, _ = oracle_graph_sp2(H, c1["subs"], c1["nc"], seq=None)
+    _, rep, _, _ = run(ctx, c1, gbe.PREC_FP64, seq=None, n_max=60)
+    assert rep["stop"] == logo.stop
+    assert rep["seq"] == logo.seq
+
+
+def test_fp64_host_csr_e2e(ctx, c1):
+    H = c1["H"]
+    N = H.shape[0]
+    parts = import_parts(ctx, N, c1["subs"], c1["nc"])
+    p = gbe.sp2_params(N // 2, prec=gbe.PREC_FP64, seq=c1["seq"])
+    X, rep = gbe.sp2_submatrices(ctx, host_csr(H), parts, p)
+    n, width = gbe.assemble_width(ctx, X, parts)
+    col = np.zeros((n, width), dtype=np.int32)
+    val = np.zeros((n, width), dtype=np.float64)
+    gbe.assemble_D(ctx, X, parts, col, val)
+    D = gbe.ell_to_dense(col, val, N)
+    assert np.abs(D - c1["Dref"]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("tail", [0, 2])
+def test_fp16x6_replay_parity(ctx, c1, tail):
+    D, rep, _, _ = run(ctx, c1, gbe.PREC_FP16X6, seq=c1["seq"], fp64_tail=tail)
+    assert rep["iters"] == len(c1["seq"]) and rep["fp64_iters"] == tail
+    err = np.abs(D - c1["Dref"]).max()
+    assert err <= 1e-6, err
+
+
+def test_bf16x3_replay_bounded(ctx, c1):
+    D, rep, _, _ = run(ctx, c1, gbe.PREC_BF16X3, seq=c1["seq"])
+    err = np.abs(D - c1["Dref"]).max()
+    assert err <= 1e-3, err
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 3e-9), (2, 3e-4)])
+@pytest.mark.parametrize("b", [1, 0])
+def test_single_step(ctx, c1, prec, tol, b):
+    """One squaring X_1 = X_0^2 (b=1) or 2 X_0 - X_0^2 (b=0): dense per-subgraph check."""
+    H = c1["H"]
+    N = H.shape[0]
+    D, rep, parts, X = run(ctx, c1, prec, seq=[b])
+    _, _, xs = oracle_graph_sp2(H, c1["subs"], c1["nc"], seq=[b])
+    for s in (0, 17, 63):
+        m = len(c1["subs"][s])
+        got = X.export(s, m)
+        assert np.abs(got - xs[s]).max() <= tol
+        if prec == gbe.PREC_FP64:
+            np.testing.assert_array_equal(got, got.T)  # same products, same order: exact
+        else:
+            # off-diagonal tiles are mirrored (exact); inside diagonal tiles (a,b) and (b,a)
+            # accumulate their split products in different orders
+            assert np.abs(got - got.T).max() <= (1e-9 if prec == gbe.PREC_FP16X6 else 1e-7)
+
+
+def ragged_case(seed=3, thr=0.3):
+    """Uneven subgraphs (m not multiples of 128, several tiles, small ones) on an 8^3 lattice."""
+    import synth
+    from oracle import hamiltonian
+    w = synth.lattice(8, seed=seed)
+    H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
+    S = graph.h2_threshold(H, thr)
+    N = H.shape[0]
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(N)
+    sizes = [1, 3, 37, 64, 150, 2]
+    cores, k = [], 0
+    while k < N:
+        sz = sizes[len(cores) % len(sizes)]
+        cores.append(np.sort(perm[k:k + sz]))
+        k += sz
+    subs, nc = partition.subgraphs(S, cores)
+    return dict(H=H, subs=subs, nc=nc)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+def test_ragged_subgraphs(ctx, prec, tol):
+    case = ragged_case()
+    H = case["H"]
+    N = H.shape[0]
+    _, logd = sp2.sp2_dense(H, N // 2)
+    Dref, _, _ = oracle_graph_sp2(H, case["subs"], case["nc"], seq=logd.seq)
+    ms = [len(s) for s in case["subs"]]
+    assert max(ms) > 256 and min(ms) < 100 and any(c > 128 for c in case["nc"])
+    D, rep, _, _ = run(ctx, case, prec, seq=logd.seq)
+    assert np.abs(D - Dref).max() <= tol
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+def test_tiny_subgraphs(ctx, prec, tol):
+    """Very sparse graph: subgraphs of fewer than 32 vertices (a single K-chunk)."""
+    case = ragged_case(seed=5, thr=1.5)
+    H = case["H"]
+    _, logd = sp2.sp2_dense(H, H.shape[0] // 2)
+    Dref, _, _ = oracle_graph_sp2(H, case["subs"], case["nc"], seq=logd.seq)
+    assert min(len(s) for s in case["subs"]) < 32
+    D, rep, _, _ = run(ctx, case, prec, seq=logd.seq)
+    assert np.abs(D - Dref).max() <= tol
+
+
+def test_complete_graph_matches_eigh(ctx):
+    """One subgraph covering everything: graph SP2 is dense SP2, which is theta(mu - H)."""
+    from oracle import exact
+    w, H, _, _, _ = lattice_case(6, seed=4)
+    N = H.shape[0]
+    case = dict(H=H, subs=[np.arange(N)], nc=np.array([N]))
+    Dex, _ = exact.density_matrix(H, N // 2)
+    D, rep, _, _ = run(ctx, case, gbe.PREC_FP64, n_max=80, idem_tol=1e-11)
+    assert rep["stop"] == "tol"
+    assert np.abs(D - Dex).max() <= 1e-10
+
+
+def test_drop_tolerance_and_width_query(ctx, c1):
+    H = c1["H"]
+    N = H.shape[0]
+    _, rep, parts, X = run(ctx, c1, gbe.PREC_FP64, seq=c1["seq"])
+    D0, col0, _ = assembled_dense(ctx, X, parts, N)
+    D1, col1, val1 = assembled_dense(ctx, X, parts, N, drop_tol=1e-3)
+    ref = np.where(np.abs(c1["Dref"]) >= 1e-3, c1["Dref"], 0.0)
+    assert np.abs(D1 - ref).max() <= 1e-10
+    assert (col1 >= 0).sum() < (col0 >= 0).sum()
+    # packed rows: padding only after the kept entries
+    for r in range(0, N, 51):
+        k = (col1[r] >= 0).sum()
+        assert np.all(col1[r, :k] >= 0) and np.all(col1[r, k:] == -1)
