@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Benchmark: graph-partitioned SP2 density-matrix throughput on GB300.
+
+Metric (one JSON line on rank 0): SP2 density-matrix orbitals/s = N / (gather + SP2 +
+assembly time) of one D build, for the tensor-core FP16X6 path, with the FP64 GPU path,
+tensor TFLOP/s, max |dD| between the two, a live roofline figure of the dominant kernel,
+an end-to-end figure through the C ABI with host buffers, and the CPU oracle timed on a
+bounded sample of the same workload.
+
+Default workload: 32^3 jittered rock-salt lattice (N = 32768, seed 0), H_ij =
+-exp(-(r-a)/0.3a) for r < 2.5a, graph |H^2| >= 0.15 (the knob that gives the stated
+300-600 submatrix range), 512 cores of 4x4x4 sites from 8x8x8 spatial cells,
+one global SP2 with FP64 global traces deciding every branch on the device, stop on
+stalled idempotency error (n_min 10) or 1e-10.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbe|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SP2 density-matrix orbitals/s and tensor TFLOP/s, mixed vs FP64 at max|ΔD|≤1e-6"
+UNIT = "orbitals/s"
+WORKLOADS = {
+    # the configuration the metric is quoted on: 32^3 lattice, cores of 64, m_s ~ 460-480
+    "lattice32": dict(L=32, seed=0, thresh=0.15, ncell=(8, 8, 8)),
+    # small case (8^3, |H^2| >= 1e-5 graph, cores of 8, m_s ~ 470-510)
+    "lattice8": dict(L=8, seed=0, thresh=1e-5, ncell=(4, 4, 4)),
+    # 16^3 slice of the 32^3 workload (same m_s distribution, 64 subgraphs): profiling case
+    "lattice16": dict(L=16, seed=0, thresh=0.15, ncell=(4, 4, 4)),
+}
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def oracle_sample(L, seed, thresh, ncell):
+    """The oracle's graph SP2 on an L^3 sample of the same lattice model; returns
+    (orbitals, seconds of gather + SP2 + assembly, iterations)."""
+    import synth
+    from oracle import graph, hamiltonian, partition, sp2
+    w = synth.lattice(L, seed=seed)
+    H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
+    N = H.shape[0]
+    S = graph.h2_threshold(H, thresh)
+    subs, nc = partition.subgraphs(S, partition.spatial_cores(w["pos"], w["box"], ncell))
+    t0 = time.perf_counter()
+    D, log = sp2.sp2_graph(H, subs, nc, N // 2, n_max=48)
+    dt = time.perf_counter() - t0
+    return N, dt, log.iters
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    # each step: the oracle on a 12^3 sample (27 core sets of the 32^3 workload's shape)
+    L = 12
+    for _ in range(args.warmup):
+        oracle_sample(L, 0, 0.15, (3, 3, 3))
+    ts, its = [], []
+    for _ in range(args.steps):
+        N, dt, it = oracle_sample(L, 0, 0.15, (3, 3, 3))
+        ts.append(dt)
+        its.append(it)
+    value = N * len(ts) / sum(ts)
+    sample = "12^3 sample (N=1728, 27 cores of 4^3, |H^2|>=0.15 halos, m_s~430-470) of the 32^3 workload; " \
+             "oracle graph SP2 (NumPy FP64), gather+SP2+assembly timed"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(ts) / len(ts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "lattice32 (oracle on a 12^3 sample)", "iters": its[-1]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbe", choices=["gbe", "reference"])
+    ap.add_argument("--workload", default="lattice32", choices=sorted(WORKLOADS))
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--fp64-tail", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1603_00937_gb300 as gbe
+    import synth
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    wl = WORKLOADS[args.workload]
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = gbe.Context(local, stream)
+    ctx.set_profiling(True)
+
+    # ---------------------------------------------------------------- set-up (timed apart)
+    t_setup = time.perf_counter()
+    w = synth.lattice(wl["L"], seed=wl["seed"] + rank)
+    N = w["pos"].shape[0]
+    pos = torch.from_numpy(w["pos"]).cuda()
+    ons = torch.from_numpy(w["onsite"]).cuda()
+    st = gbe.sites(pos, ons, w["box"])
+    Hh = gbe.build_hamiltonian(ctx, st)
+    Hv = Hh.csr()
+    G = gbe.build_graph(ctx, Hv, gbe.GRAPH_H2_THRESH, thresh=wl["thresh"])
+    parts = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=wl["ncell"], site_struct=st)
+    P, total, max_m = parts.info()
+    cc, sptr, _ = parts.export()
+    ms = np.diff(sptr)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+
+    n, width = N, max_m
+    col_m = torch.empty((n, width), dtype=torch.int32, device="cuda")
+    val_m = torch.empty((n, width), dtype=torch.float64, device="cuda")
+    col_d = torch.empty_like(col_m)
+    val_d = torch.empty_like(val_m)
+    n_max = 48
+
+    def params(prec, seq=None):
+        return gbe.sp2_params(N / 2.0, prec=prec, n_max=n_max, n_min=10, idem_tol=1e-10,
+                              fp64_tail=args.fp64_tail if prec != gbe.PREC_FP64 else 0, seq=seq)
+
+    def timed(X, prm, col, val, steps, warmup):
+        for _ in range(warmup):
+            gbe.sp2_run(ctx, Hv, parts, prm, X)
+            gbe.assemble_D(ctx, X, parts, col, val)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            gbe.sp2_run(ctx, Hv, parts, prm, X)
+            gbe.assemble_D(ctx, X, parts, col, val)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, gbe.sp2_report_get(ctx, X).as_dict()
+
+    Xm = gbe.subs_create(ctx, parts, gbe.PREC_FP16X6)
+    pm = params(gbe.PREC_FP16X6)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_m, rep_m = timed(Xm, pm, col_m, val_m, args.steps, max(args.warmup, 3))
+    clk = clocks.stop()
+
+    out = {}
+    if not args.no_fp64:
+        Xd = gbe.subs_create(ctx, parts, gbe.PREC_FP64)
+        ms_d, rep_d = timed(Xd, params(gbe.PREC_FP64), col_d, val_d, args.fp64_steps, 1)
+        seq_equal = rep_d["seq"] == rep_m["seq"]
+        dD_free = float((val_m - val_d).abs().max().item()) if torch.equal(col_m, col_d) else float("nan")
+        # same branch sequence for the precision comparison: replay the FP64 run's sequence
+        gbe.sp2_run(ctx, Hv, parts, params(gbe.PREC_FP16X6, seq=rep_d["seq"]), Xm)
+        gbe.assemble_D(ctx, Xm, parts, col_m, val_m)
+        torch.cuda.synchronize()
+        dD = float((val_m - val_d).abs().max().item())
+        out["fp64"] = {"value": N * world / (ms_d / 1000.0), "unit": UNIT, "ms_per_step": ms_d,
+                       "steps": args.fp64_steps, "iters": rep_d["iters"], "stop": rep_d["stop"],
+                       "fp64_tflops_executed": rep_d["fp64_flops"] / (rep_d["ms_fp64"] / 1000.0) / 1e12
+                       if rep_d["ms_fp64"] else None,
+                       "alg_tflops": rep_d["alg_flops"] / (ms_d / 1000.0) / 1e12}
+        out["max_abs_dD_vs_fp64"] = dD
+        out["max_abs_dD_vs_fp64_free_running"] = dD_free
+        out["branch_sequences_equal"] = seq_equal
+        out["speedup_vs_fp64"] = ms_d / ms_m
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    def dev_to_host(ptr, count, typestr):
+        class _A:
+            pass
+        a = _A()
+        a.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr, "data": (int(ptr), False),
+                                      "version": 3}
+        return torch.as_tensor(a, device="cuda").cpu()
+
+    rp_h = dev_to_host(Hv.rowptr, N + 1, "<i8").pin_memory()
+    ci_h = dev_to_host(Hv.col, Hv.nnz, "<i4").pin_memory()
+    va_h = dev_to_host(Hv.val, Hv.nnz, "<f8").pin_memory()
+    Hhost = gbe.csr(N, rp_h.numpy(), ci_h.numpy(), va_h.numpy())
+    col_h = torch.empty((n, width), dtype=torch.int32).pin_memory()
+    val_h = torch.empty((n, width), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        gbe.sp2_submatrices(ctx, Hhost, parts, pm, Xm)
+        gbe.assemble_D(ctx, Xm, parts, col_h.numpy(), val_h.numpy())
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, args.steps)
+    for _ in range(e2e_steps):
+        gbe.sp2_submatrices(ctx, Hhost, parts, pm, Xm)
+        gbe.assemble_D(ctx, Xm, parts, col_h.numpy(), val_h.numpy())
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = (N + 1) * 8 + Hv.nnz * 12
+    d2h = n * width * 12 + 4616
+
+    # ---------------------------------------------------------------- roofline of the squaring kernel
+    peaks, peak_kind = load_peaks()
+    tc_ms = rep_m["ms_tc"] / max(1, rep_m["n_tc"])
+    tc_flops = rep_m["mma_flops"] / max(1, rep_m["iters"] - rep_m["fp64_iters"])
+    achieved = tc_flops / (tc_ms / 1000.0) / 1e12 if tc_ms > 0 else None
+    peak = float(peaks["bf16_tflops"])
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "sp2_square_tc_kernel<FP16X6>", "peak_kind": peak_kind + " dense bf16/fp16 burst",
+                "launches": rep_m["n_tc"], "ms_per_launch": tc_ms}
+
+    mixed_iters = rep_m["iters"] - rep_m["fp64_iters"]
+    launches = 1 + 1 + 1 + 1 + n_max * (2 + (2 if args.fp64_tail > 0 else 0)) + 2
+    line = {
+        "metric": METRIC, "value": N * world / (ms_m / 1000.0), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_m, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16-split(x6)/f32-acc/f64-trace", "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "L": wl["L"], "graph": "|H^2|>=%g" % wl["thresh"],
+                   "cores": int(P), "core_size": int(np.median(cc)), "m_s_min": int(ms.min()),
+                   "m_s_median": float(np.median(ms)), "m_s_max": int(ms.max()), "precision": "FP16X6",
+                   "fp64_tail": args.fp64_tail, "branch": "global FP64 trace on device, stall stop",
+                   "iters": rep_m["iters"], "stop": rep_m["stop"],
+                   "l2": "inputs larger than L2: %.2f GB of split planes (2 sides x 4 planes) vs 129 MB L2; "
+                         "no flush" % (16.0 * sum(((int(m) + 127) // 128 * 128) ** 2 for m in ms) / 1e9),
+                   "setup_s": setup_s, "parallelism": "independent system per GPU" if world > 1 else "1 GPU"},
+        "tensor_tflops": rep_m["mma_flops"] / (ms_m / 1000.0) / 1e12,
+        "tensor_tflops_in_squarings": achieved,
+        "alg_tflops": rep_m["alg_flops"] / (ms_m / 1000.0) / 1e12,
+        "phase_ms": {"gather": rep_m["ms_gather"], "sp2": rep_m["ms_sp2"], "squarings": rep_m["ms_tc"]},
+        "roofline": roofline,
+        "e2e": {"value": N * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches * args.steps,
+        "clocks": clk,
+    }
+    line.update(out)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Ns, dt, it = oracle_sample(16, 0, 0.15, (4, 4, 4))
+        line["cpu_baseline"] = {"value": Ns / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                "sample": "16^3 sample of the same lattice model (N=4096, 64 cores of 4^3, "
+                                          "|H^2|>=0.15 halos, m_s 461-481), oracle graph SP2 (NumPy FP64, %d "
+                                          "iterations), gather+SP2+assembly timed (%.1f s)" % (it, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -97,6 +97,10 @@ int gbe_create(gbe_ctx** ctx, int device, void* cuda_stream);
 int gbe_destroy(gbe_ctx* ctx);
 /* Change the stream later calls are ordered on. */
 int gbe_set_stream(gbe_ctx* ctx, void* cuda_stream);
+/* Profiling switch: when on, gbe_sp2_run records a CUDA event pair around every
+ * squaring launch on the context stream and gbe_sp2_report_get sums the durations of
+ * the launches that did work (ms_tc / n_tc, ms_fp64 / n_fp64). */
+int gbe_set_profiling(gbe_ctx* ctx, int on);
 /* Number of SMs of the context's device (grids are sized from it). */
 int gbe_device_sm_count(const gbe_ctx* ctx);
 const char* gbe_strerror(int code);
@@ -231,6 +235,11 @@ typedef struct {
     float ms_gather, ms_sp2;            /* CUDA-event times of the phases                */
     double mma_flops;      /* tensor-core flops issued (split products included)          */
     double alg_flops;      /* sum over iterations and subgraphs of 2 m_s^3                 */
+    /* per-kernel CUDA-event times of the squaring launches that did work (filled only
+       when profiling is on, see gbe_set_profiling) */
+    float ms_tc, ms_fp64;
+    int n_tc, n_fp64;
+    double fp64_flops;     /* FP64 flops issued by the FP64 squarings                      */
 } gbe_sp2_report;
 
 /* Allocate the SP2 state for a partition and precision (dense padded tiles in HBM,

@@ -28,7 +28,7 @@ SEQ_MAX = 256
 
 # Every entry point declared in include/gbe.h (checked by the CPU test suite).
 EXPORTS = [
-    "gbe_create", "gbe_destroy", "gbe_set_stream", "gbe_device_sm_count", "gbe_strerror",
+    "gbe_create", "gbe_destroy", "gbe_set_stream", "gbe_set_profiling", "gbe_device_sm_count", "gbe_strerror",
     "gbe_last_error_message", "gbe_build_hamiltonian", "gbe_hamiltonian_csr", "gbe_free_hamiltonian",
     "gbe_build_graph", "gbe_graph_size", "gbe_graph_export", "gbe_free_graph", "gbe_partition",
     "gbe_parts_info", "gbe_parts_export", "gbe_parts_import", "gbe_free_parts", "gbe_subs_create",
@@ -88,7 +88,9 @@ class Sp2Report(ctypes.Structure):
                 ("eps_max", ctypes.c_double), ("trace", ctypes.c_double), ("idem_err", ctypes.c_double),
                 ("seq", ctypes.c_uint8 * SEQ_MAX), ("t1", ctypes.c_double * (SEQ_MAX + 1)),
                 ("t2", ctypes.c_double * (SEQ_MAX + 1)), ("ms_gather", ctypes.c_float),
-                ("ms_sp2", ctypes.c_float), ("mma_flops", ctypes.c_double), ("alg_flops", ctypes.c_double)]
+                ("ms_sp2", ctypes.c_float), ("mma_flops", ctypes.c_double), ("alg_flops", ctypes.c_double),
+                ("ms_tc", ctypes.c_float), ("ms_fp64", ctypes.c_float), ("n_tc", ctypes.c_int),
+                ("n_fp64", ctypes.c_int), ("fp64_flops", ctypes.c_double)]
 
     def as_dict(self):
         n = self.iters
@@ -96,7 +98,9 @@ class Sp2Report(ctypes.Structure):
                     converged=bool(self.converged), status=self.status, eps=(self.eps_min, self.eps_max),
                     trace=self.trace, idem_err=self.idem_err, seq=list(self.seq[:n]),
                     t1=list(self.t1[:n + 1]), t2=list(self.t2[:n + 1]), ms_gather=self.ms_gather,
-                    ms_sp2=self.ms_sp2, mma_flops=self.mma_flops, alg_flops=self.alg_flops)
+                    ms_sp2=self.ms_sp2, mma_flops=self.mma_flops, alg_flops=self.alg_flops,
+                    ms_tc=self.ms_tc, n_tc=self.n_tc, ms_fp64=self.ms_fp64, n_fp64=self.n_fp64,
+                    fp64_flops=self.fp64_flops)
 
 
 _lib = None
@@ -114,7 +118,7 @@ def load_library(path=LIB_PATH):
     P, I64, I32, D, C = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_char_p
     sig = {
         "gbe_create": (I32, [P, I32, P]), "gbe_destroy": (I32, [P]), "gbe_set_stream": (I32, [P, P]),
-        "gbe_device_sm_count": (I32, [P]), "gbe_strerror": (C, [I32]), "gbe_last_error_message": (C, []),
+        "gbe_device_sm_count": (I32, [P]), "gbe_set_profiling": (I32, [P, I32]), "gbe_strerror": (C, [I32]), "gbe_last_error_message": (C, []),
         "gbe_build_hamiltonian": (I32, [P, P, P, P]), "gbe_hamiltonian_csr": (I32, [P, P]),
         "gbe_free_hamiltonian": (I32, [P]), "gbe_build_graph": (I32, [P, P, P, P]),
         "gbe_graph_size": (I32, [P, P, P, P]), "gbe_graph_export": (I32, [P, P, P, P]),
@@ -181,6 +185,9 @@ class Context:
     @property
     def handle(self):
         return self._h
+
+    def set_profiling(self, on=True):
+        check(load_library().gbe_set_profiling(self._h, 1 if on else 0), "gbe_set_profiling")
 
     def set_stream(self, stream):
         check(load_library().gbe_set_stream(self._h, ctypes.c_void_p(stream)), "gbe_set_stream")

@@ -98,4 +98,10 @@ extern "C" int gbe_set_stream(gbe_ctx* ctx, void* cuda_stream) {
     return GBE_OK;
 }
 
+extern "C" int gbe_set_profiling(gbe_ctx* ctx, int on) {
+    GBE_CHECK_ARG(ctx != nullptr, "ctx is NULL");
+    ctx->profile = on ? 1 : 0;
+    return GBE_OK;
+}
+
 extern "C" int gbe_device_sm_count(const gbe_ctx* ctx) { return ctx ? ctx->sm_count : 0; }

@@ -44,6 +44,7 @@ struct gbe_ctx {
     // small device scratch for counters and flags (4 KB), and its pinned host mirror
     void* d_scratch = nullptr;
     void* h_scratch = nullptr;
+    int profile = 0;
 };
 
 struct gbe_hamiltonian {
@@ -89,6 +90,7 @@ struct Sp2Ctrl {
     int fp64_iters;
     int switch_iter; // first FP64 iteration in mixed runs (-1 before the switch)
     int pending;     // a squaring kernel ran since the last decision
+    uint8_t slot_ran[GBE_SEQ_MAX];  // per launch slot: bit 0 tensor-core kernel worked, bit 1 FP64 kernel
     int n_min, n_max, branch_mode, seq_len, fp64_tail, prec, eps_given;
     unsigned long long eps_min_key, eps_max_key;  // order-preserving keys for atomics
     double eps_min, eps_max;
@@ -139,6 +141,9 @@ struct gbe_subs {
     bool tmap_ok = false;
     // phase timing
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    std::vector<cudaEvent_t> ev_tc, ev_64;   // [2 * slot + {0,1}] when profiling
+    int last_slots = 0;
+    bool last_prof = false;
     double alg_flops_per_iter = 0.0, mma_flops_per_iter = 0.0, fp64_flops_per_iter = 0.0;
 };
 
@@ -152,7 +157,7 @@ __host__ __device__ inline int64_t blk_index(int64_t off, int mpad, int r, int c
 // ----------------------------------------------------------------------------- launchers
 int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X);
 int gbe_tc_make_tmaps(gbe_subs* X);
-int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X);
+int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot);
 int gbe_tc_prepare(gbe_ctx* ctx);
 
 // helpers

@@ -1,20 +1,919 @@
-// Hamiltonian, graph and partition entry points (device kernels follow in this file).
+// Hamiltonian build (cell list), data-dependency graphs and core+halo partitions.
+//
+//  * gbe_build_hamiltonian: H_ij = hop exp(-(r - a)/decay) for 0 < r < rcut, minimum
+//    image, H_ii = onsite; sites binned into cells of edge >= rcut, one warp per row.
+//  * gbe_build_graph (Eq. 2, Eq. 8): a graph is a base pattern A (undirected, diagonal
+//    present) and a path length k, S = pattern(A^k).  Row sets are built per row with a
+//    shared-memory hash set, sorted, and written as CSR by a count / scan / fill pattern.
+//    |(H^2)_ij| is a merge dot product of two sorted rows in ascending k (deterministic).
+//  * gbe_partition (Sec. II.A, Fig. 1, observation vi): cores are non-empty spatial cells
+//    (ascending cell id) or index blocks; each core set is expanded by k hops over A in a
+//    shared-memory hash set, sorted, and emitted as core vertices then halo vertices.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "gbe_internal.h"
 
-extern "C" int gbe_build_hamiltonian(gbe_ctx*, const gbe_sites*, const gbe_tb_model*, gbe_hamiltonian**) {
-    gbe_set_error("gbe_build_hamiltonian: not built yet");
-    return GBE_EINVAL;
+namespace {
+
+constexpr int kHashCap = 8192;   // hash-set capacity of one row / core set (ints)
+constexpr int kSetMax = 4096;    // largest set a CTA sorts and emits
+
+// ------------------------------------------------------------------ scan (exclusive, int32 -> int64)
+constexpr int kScanThreads = 1024, kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t* sh, int64_t* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int64_t s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        sh[lane] = s;
+    }
+    __syncthreads();
+    const int64_t base = (w > 0) ? sh[w - 1] : 0;
+    if (total) *total = sh[(blockDim.x >> 5) - 1];
+    const int64_t r = base + x - v;
+    __syncthreads();
+    return r;
 }
-extern "C" int gbe_hamiltonian_csr(const gbe_hamiltonian*, gbe_csr*) { return GBE_EINVAL; }
-extern "C" int gbe_free_hamiltonian(gbe_hamiltonian*) { return GBE_OK; }
-extern "C" int gbe_build_graph(gbe_ctx*, const gbe_csr*, const gbe_graph_params*, gbe_graph**) {
-    gbe_set_error("gbe_build_graph: not built yet");
-    return GBE_EINVAL;
+
+__global__ void __launch_bounds__(kScanThreads) scan_local_kernel(const int32_t* __restrict__ in, int64_t* out,
+                                                                  int64_t n, int64_t* bsum) {
+    __shared__ int64_t sh[32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems], s = 0;
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < n) ? in[base + i] : 0;
+        s += v[i];
+    }
+    int64_t tot;
+    int64_t ex = block_exclusive_scan(s, sh, &tot);
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = ex;
+        ex += v[i];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
-extern "C" int gbe_graph_size(gbe_ctx*, gbe_graph*, int64_t*, int64_t*) { return GBE_EINVAL; }
-extern "C" int gbe_graph_export(gbe_ctx*, gbe_graph*, int64_t*, int32_t*) { return GBE_EINVAL; }
-extern "C" int gbe_free_graph(gbe_graph*) { return GBE_OK; }
-extern "C" int gbe_partition(gbe_ctx*, const gbe_graph*, const gbe_partition_params*, gbe_parts**) {
-    gbe_set_error("gbe_partition: not built yet");
+
+__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(int64_t* bsum, int nb, int64_t* total) {
+    __shared__ int64_t sh[32];
+    int64_t carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
+        const int i = b0 + threadIdx.x;
+        const int64_t v = (i < nb) ? bsum[i] : 0;
+        int64_t tot;
+        const int64_t ex = block_exclusive_scan(v, sh, &tot);
+        if (i < nb) bsum[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void scan_add_kernel(int64_t* out, int64_t n, const int64_t* bsum, const int64_t* total) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += bsum[i / kScanBlock];
+    if (i == n) out[n] = *total;
+}
+
+// ------------------------------------------------------------------ shared-memory hash set
+__device__ __forceinline__ unsigned hslot(int v) { return ((unsigned)v * 2654435761u) >> (32 - 13); }  // 8192 slots
+
+// Insert v; returns false when the table is full.
+__device__ __forceinline__ bool hset_insert(int* table, int* count, int v) {
+    unsigned h = hslot(v);
+    for (int probe = 0; probe < kHashCap; ++probe) {
+        const int cur = table[h];
+        if (cur == v) return true;
+        if (cur == -1) {
+            const int old = atomicCAS(&table[h], -1, v);
+            if (old == -1) {
+                atomicAdd(count, 1);
+                return true;
+            }
+            if (old == v) return true;
+        }
+        h = (h + 1) & (kHashCap - 1);
+    }
+    return false;
+}
+
+// Ascending bitonic sort of n <= cap ints in shared memory (cap a power of two).
+__device__ void bitonic_sort(int* a, int n, int cap) {
+    for (int i = n + threadIdx.x; i < cap; i += blockDim.x) a[i] = INT32_MAX;
+    __syncthreads();
+    int size = 1;
+    while (size < n) size <<= 1;
+    for (int k = 2; k <= size; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < size; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = ((i & k) == 0);
+                    const int x = a[i], y = a[l];
+                    if ((x > y) == up) { a[i] = y; a[l] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Move the hash-set contents into list[0..count) (unordered).
+__device__ int hset_compact(const int* table, int* list, int* cursor) {
+    if (threadIdx.x == 0) *cursor = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHashCap; i += blockDim.x) {
+        const int v = table[i];
+        if (v != -1) list[atomicAdd(cursor, 1)] = v;
+    }
+    __syncthreads();
+    return *cursor;
+}
+
+__device__ void hset_clear(int* table, int* count, int* flag) {
+    for (int i = threadIdx.x; i < kHashCap; i += blockDim.x) table[i] = -1;
+    if (threadIdx.x == 0) { *count = 0; *flag = 0; }
+    __syncthreads();
+}
+
+// Expand the set in the table by `hops` steps over CSR A.  Returns false on overflow.
+__device__ bool hset_expand(int* table, int* count, int* list, int* cursor, int* flag, const int64_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, int hops) {
+    if (threadIdx.x == 0) *flag = 0;
+    for (int h = 0; h < hops; ++h) {
+        const int n = hset_compact(table, list, cursor);
+        if (n > kSetMax) { if (threadIdx.x == 0) *flag = 1; __syncthreads(); return false; }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int t = warp; t < n; t += nw) {
+            const int v = list[t];
+            for (int64_t p = rp[v] + lane; p < rp[v + 1]; p += 32)
+                if (!hset_insert(table, count, ci[p])) *flag = 1;
+        }
+        __syncthreads();
+        if (*flag || *count > kSetMax) { if (threadIdx.x == 0) *flag = 1; __syncthreads(); return false; }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ Hamiltonian
+struct CellGrid {
+    int nc[3];
+    double box[3];
+};
+
+__device__ __forceinline__ int cell_of(const double* p, const CellGrid& g) {
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+        int v = (int)floor(p[d] / g.box[d] * g.nc[d]);
+        c[d] = min(max(v, 0), g.nc[d] - 1);
+    }
+    return (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
+}
+
+__global__ void cell_count_kernel(const double* __restrict__ pos, int64_t n, CellGrid g, int32_t* cell, int32_t* cnt) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cell_of(pos + 3 * i, g);
+    cell[i] = c;
+    atomicAdd(&cnt[c], 1);
+}
+
+__global__ void cell_fill_kernel(const int32_t* __restrict__ cell, int64_t n, const int64_t* __restrict__ start,
+                                 int32_t* cursor, int32_t* members) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c = cell[i];
+    members[start[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
+}
+
+// Sort the members of each cell ascending (cells are small; one warp per cell).
+__global__ void cell_sort_kernel(const int64_t* __restrict__ start, int ncells, int32_t* members) {
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= ncells) return;
+    int32_t* a = members + start[wid];
+    const int n = (int)(start[wid + 1] - start[wid]);
+    // odd-even transposition sort, warp-cooperative
+    for (int phase = 0; phase < n; ++phase) {
+        for (int i = 2 * lane + (phase & 1); i + 1 < n; i += 64) {
+            const int x = a[i], y = a[i + 1];
+            if (x > y) { a[i] = y; a[i + 1] = x; }
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ double min_image(double d, double L) { return __dsub_rn(d, __dmul_rn(L, rint(d / L))); }
+__device__ __forceinline__ double dist3(double x, double y, double z) {
+    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+}
+
+struct HModel {
+    double a, rcut, decay, hop;
+};
+
+constexpr int kRowCap = 1024;
+
+// One warp per row.  pass 0: count neighbours; pass 1: write sorted (col, val).
+__global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ pos, const double* __restrict__ onsite,
+                                                     int64_t n, CellGrid g, const int64_t* __restrict__ cstart,
+                                                     const int32_t* __restrict__ members, HModel mdl, int pass,
+                                                     int32_t* cnt, const int64_t* __restrict__ rowptr, int32_t* col,
+                                                     double* val, int* overflow) {
+    __shared__ int buf[8][kRowCap];
+    __shared__ int bcount[8];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 8 + w;
+    if (i >= n) return;
+    const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    const int ci = cell_of(pos + 3 * i, g);
+    int cc[3] = {ci / (g.nc[1] * g.nc[2]), (ci / g.nc[2]) % g.nc[1], ci % g.nc[2]};
+    if (lane == 0) bcount[w] = 0;
+    __syncwarp();
+    // neighbour cells: offsets -1..1, or every cell along an axis with fewer than 3 cells
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        if (g.nc[d] >= 3) { lo[d] = -1; hi[d] = 1; }
+        else { lo[d] = -cc[d]; hi[d] = g.nc[d] - 1 - cc[d]; }
+    }
+    for (int dx = lo[0]; dx <= hi[0]; ++dx)
+        for (int dy = lo[1]; dy <= hi[1]; ++dy)
+            for (int dz = lo[2]; dz <= hi[2]; ++dz) {
+                const int ax = (cc[0] + dx + g.nc[0]) % g.nc[0];
+                const int ay = (cc[1] + dy + g.nc[1]) % g.nc[1];
+                const int az = (cc[2] + dz + g.nc[2]) % g.nc[2];
+                const int cell = (ax * g.nc[1] + ay) * g.nc[2] + az;
+                for (int64_t p = cstart[cell] + lane; p < cstart[cell + 1]; p += 32) {
+                    const int j = members[p];
+                    const double r = dist3(min_image(xi - pos[3 * j], g.box[0]), min_image(yi - pos[3 * j + 1], g.box[1]),
+                                           min_image(zi - pos[3 * j + 2], g.box[2]));
+                    if (j == i || r < mdl.rcut) {
+                        const int k = atomicAdd(&bcount[w], 1);
+                        if (k < kRowCap) buf[w][k] = j;
+                    }
+                }
+            }
+    __syncwarp();
+    const int m = bcount[w];
+    if (m > kRowCap) {
+        if (lane == 0) atomicExch(overflow, 1);
+        return;
+    }
+    if (pass == 0) {
+        if (lane == 0) cnt[i] = m;
+        return;
+    }
+    // sort the row's columns (odd-even transposition within the warp)
+    for (int phase = 0; phase < m; ++phase) {
+        for (int t = 2 * lane + (phase & 1); t + 1 < m; t += 64) {
+            const int x = buf[w][t], y = buf[w][t + 1];
+            if (x > y) { buf[w][t] = y; buf[w][t + 1] = x; }
+        }
+        __syncwarp();
+    }
+    const int64_t base = rowptr[i];
+    for (int t = lane; t < m; t += 32) {
+        const int j = buf[w][t];
+        double v;
+        if (j == i) {
+            v = onsite[i];
+        } else {
+            const double r = dist3(min_image(xi - pos[3 * j], g.box[0]), min_image(yi - pos[3 * j + 1], g.box[1]),
+                                   min_image(zi - pos[3 * j + 2], g.box[2]));
+            v = mdl.hop * exp(-(r - mdl.a) / mdl.decay);
+        }
+        col[base + t] = j;
+        val[base + t] = v;
+    }
+}
+
+// ------------------------------------------------------------------ graph row sets
+// Deterministic sparse dot product of two sorted CSR rows (ascending column order,
+// separate multiply and add).
+__device__ double row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ va,
+                          int i, int j) {
+    int64_t p = rp[i], pe = rp[i + 1], q = rp[j], qe = rp[j + 1];
+    double s = 0.0;
+    while (p < pe && q < qe) {
+        const int a = ci[p], b = ci[q];
+        if (a == b) { s = __dadd_rn(s, __dmul_rn(va[p], va[q])); ++p; ++q; }
+        else if (a < b) ++p;
+        else ++q;
+    }
+    return s;
+}
+
+struct RowSetSmem {
+    int table[kHashCap];
+    int list[kHashCap];
+    int count, cursor, flag;
+};
+
+// mode 0: |(H^2)_ij| >= thresh (numeric), hops over H = 1 then filter
+// mode 1: union of sources given as CSR lists (A1 row i, A2 row i, A3 row i) + diagonal
+// mode 2: pattern of A^hops (materialisation)
+__global__ void __launch_bounds__(256) rowset_kernel(int mode, int64_t n, const int64_t* __restrict__ hrp,
+                                                     const int32_t* __restrict__ hci, const double* __restrict__ hva,
+                                                     double thresh, const int64_t* __restrict__ s1rp,
+                                                     const int32_t* __restrict__ s1ci, const int64_t* __restrict__ s2rp,
+                                                     const int32_t* __restrict__ s2ci, const int64_t* __restrict__ s3rp,
+                                                     const int32_t* __restrict__ s3ci, int hops, int pass, int32_t* cnt,
+                                                     const int64_t* __restrict__ outrp, int32_t* outci, int* overflow) {
+    extern __shared__ unsigned char smraw[];
+    RowSetSmem& S = *reinterpret_cast<RowSetSmem*>(smraw);
+    for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
+        const int i = (int)row;
+        hset_clear(S.table, &S.count, &S.flag);
+        if (threadIdx.x == 0) hset_insert(S.table, &S.count, i);
+        __syncthreads();
+        bool ok = true;
+        if (mode == 0) {
+            // candidates: union of H rows of H's neighbours of i
+            for (int64_t p = hrp[i]; p < hrp[i + 1]; ++p) {
+                const int k = hci[p];
+                for (int64_t q = hrp[k] + threadIdx.x; q < hrp[k + 1]; q += blockDim.x)
+                    if (!hset_insert(S.table, &S.count, hci[q])) S.flag = 1;
+            }
+            __syncthreads();
+        } else if (mode == 1) {
+            const int64_t* rps[3] = {s1rp, s2rp, s3rp};
+            const int32_t* cis[3] = {s1ci, s2ci, s3ci};
+            for (int s = 0; s < 3; ++s) {
+                if (!rps[s]) continue;
+                for (int64_t q = rps[s][i] + threadIdx.x; q < rps[s][i + 1]; q += blockDim.x)
+                    hset_insert(S.table, &S.count, cis[s][q]);
+            }
+            __syncthreads();
+        } else {
+            ok = hset_expand(S.table, &S.count, S.list, &S.cursor, &S.flag, s1rp, s1ci, hops);
+        }
+        if (!ok || S.flag || S.count > kSetMax) {
+            if (threadIdx.x == 0) atomicExch(overflow, 1);
+            __syncthreads();
+            continue;
+        }
+        int m = hset_compact(S.table, S.list, &S.cursor);
+        bitonic_sort(S.list, m, kHashCap);
+        if (mode == 0) {
+            // keep |(H^2)_ij| >= thresh or j == i; compact in order
+            if (threadIdx.x == 0) S.cursor = 0;
+            __syncthreads();
+            for (int t0 = 0; t0 < m; t0 += blockDim.x) {
+                const int t = t0 + threadIdx.x;
+                int keep = 0, j = 0;
+                if (t < m) {
+                    j = S.list[t];
+                    keep = (j == i) || (fabs(row_dot(hrp, hci, hva, i, j)) >= thresh);
+                }
+                // ordered compaction within the block
+                __shared__ int wsum[8];
+                const unsigned bal = __ballot_sync(0xffffffffu, keep);
+                const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+                if (lane == 0) wsum[w] = __popc(bal);
+                __syncthreads();
+                int before = 0;
+                for (int q = 0; q < w; ++q) before += wsum[q];
+                const int base = S.cursor;
+                __syncthreads();
+                if (keep) S.table[base + before + __popc(bal & ((1u << lane) - 1u))] = j;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int tot = 0;
+                    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += wsum[q];
+                    S.cursor = base + tot;
+                }
+                __syncthreads();
+            }
+            m = S.cursor;
+            for (int t = threadIdx.x; t < m; t += blockDim.x) S.list[t] = S.table[t];
+            __syncthreads();
+        }
+        if (pass == 0) {
+            if (threadIdx.x == 0) cnt[i] = m;
+        } else {
+            const int64_t base = outrp[i];
+            for (int t = threadIdx.x; t < m; t += blockDim.x) outci[base + t] = S.list[t];
+        }
+        __syncthreads();
+    }
+}
+
+// ELL D -> pattern of kept entries (|D_ki| >= tau) as CSR by ELL row (row i lists k),
+// and the transposed lists (row k lists i).
+__global__ void ell_count_kernel(const int32_t* __restrict__ col, const double* __restrict__ val, int64_t n, int64_t W,
+                                 double tau, int32_t* cnt_own, int32_t* cnt_tr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int own = 0;
+    for (int64_t t = 0; t < W; ++t) {
+        const int k = col[i * W + t];
+        if (k < 0) break;
+        if (fabs(val[i * W + t]) >= tau) {
+            ++own;
+            atomicAdd(&cnt_tr[k], 1);
+        }
+    }
+    cnt_own[i] = own;
+}
+
+__global__ void ell_fill_kernel(const int32_t* __restrict__ col, const double* __restrict__ val, int64_t n, int64_t W,
+                                double tau, const int64_t* __restrict__ rp_own, int32_t* ci_own,
+                                const int64_t* __restrict__ rp_tr, int32_t* cur_tr, int32_t* ci_tr) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t o = rp_own[i];
+    for (int64_t t = 0; t < W; ++t) {
+        const int k = col[i * W + t];
+        if (k < 0) break;
+        if (fabs(val[i * W + t]) >= tau) {
+            ci_own[o++] = k;
+            ci_tr[rp_tr[k] + atomicAdd(&cur_tr[k], 1)] = (int32_t)i;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ partition
+// Core set of subgraph s: members[core_start[s] .. core_start[s+1]) (ascending).
+// Writes m_s, c_s and the local index list (cores, then sorted halo) into a slot of
+// capacity `cap` at s * cap.
+__global__ void __launch_bounds__(256) halo_kernel(int64_t P, const int64_t* __restrict__ core_start,
+                                                   const int32_t* __restrict__ members,
+                                                   const int64_t* __restrict__ arp, const int32_t* __restrict__ aci,
+                                                   int hops, int cap, int32_t* msize, int32_t* csize, int32_t* slots,
+                                                   int* overflow) {
+    extern __shared__ unsigned char smraw[];
+    RowSetSmem& S = *reinterpret_cast<RowSetSmem*>(smraw);
+    for (int64_t s = blockIdx.x; s < P; s += gridDim.x) {
+        const int64_t c0 = core_start[s];
+        const int c = (int)(core_start[s + 1] - c0);
+        hset_clear(S.table, &S.count, &S.flag);
+        for (int t = threadIdx.x; t < c; t += blockDim.x) hset_insert(S.table, &S.count, members[c0 + t]);
+        __syncthreads();
+        const bool ok = (c <= kSetMax) && hset_expand(S.table, &S.count, S.list, &S.cursor, &S.flag, arp, aci, hops);
+        if (!ok || S.count > cap || S.count > kSetMax) {
+            if (threadIdx.x == 0) { atomicExch(overflow, max(S.count, c)); msize[s] = 0; csize[s] = c; }
+            __syncthreads();
+            continue;
+        }
+        const int m = hset_compact(S.table, S.list, &S.cursor);
+        bitonic_sort(S.list, m, kHashCap);
+        int32_t* out = slots + s * (int64_t)cap;
+        for (int t = threadIdx.x; t < c; t += blockDim.x) out[t] = members[c0 + t];
+        // halo = sorted set minus the (sorted) core members, order kept: ordered compaction
+        if (threadIdx.x == 0) S.cursor = 0;
+        __syncthreads();
+        for (int t0 = 0; t0 < m; t0 += blockDim.x) {
+            const int t = t0 + threadIdx.x;
+            int keep = 0, v = 0;
+            if (t < m) {
+                v = S.list[t];
+                int lo = 0, hi = c - 1;
+                keep = 1;
+                while (lo <= hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int x = members[c0 + mid];
+                    if (x == v) { keep = 0; break; }
+                    if (x < v) lo = mid + 1; else hi = mid - 1;
+                }
+            }
+            __shared__ int wsum[8];
+            const unsigned bal = __ballot_sync(0xffffffffu, keep);
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+            if (lane == 0) wsum[w] = __popc(bal);
+            __syncthreads();
+            int before = 0;
+            for (int q = 0; q < w; ++q) before += wsum[q];
+            const int base = S.cursor;
+            __syncthreads();
+            if (keep) out[c + base + before + __popc(bal & ((1u << lane) - 1u))] = v;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int tot = 0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) tot += wsum[q];
+                S.cursor = base + tot;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) { msize[s] = c + S.cursor; csize[s] = c; }
+        __syncthreads();
+    }
+}
+
+__global__ void compact_slots_kernel(int64_t P, const int32_t* __restrict__ slots, int cap,
+                                     const int64_t* __restrict__ sub_ptr, int32_t* sub_idx) {
+    for (int64_t s = blockIdx.x; s < P; s += gridDim.x) {
+        const int64_t b = sub_ptr[s], m = sub_ptr[s + 1] - b;
+        for (int64_t t = threadIdx.x; t < m; t += blockDim.x) sub_idx[b + t] = slots[s * (int64_t)cap + t];
+    }
+}
+
+__global__ void iota_blocks_kernel(int64_t n, int32_t* members) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) members[i] = (int32_t)i;
+}
+
+// ------------------------------------------------------------------ host helpers
+struct DevBuf {
+    void* p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+    template <class T> T* as() { return (T*)p; }
+};
+
+int scan_exclusive(gbe_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total_host) {
+    const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
+    DevBuf bs;
+    GBE_TRY(gbe_alloc(&bs.p, (size_t)(nb + 1) * 8));
+    int64_t* tot = bs.as<int64_t>() + nb;
+    if (n > 0) scan_local_kernel<<<nb, kScanThreads, 0, ctx->stream>>>(in, out, n, bs.as<int64_t>());
+    scan_top_kernel<<<1, kScanThreads, 0, ctx->stream>>>(bs.as<int64_t>(), nb, tot);
+    scan_add_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, ctx->stream>>>(out, n, bs.as<int64_t>(), tot);
+    GBE_CUDA_TRY(cudaGetLastError());
+    if (total_host) {
+        GBE_CUDA_TRY(cudaMemcpyAsync(total_host, tot, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+    return GBE_OK;
+}
+
+int read_flag(gbe_ctx* ctx, const int* d, int* h) {
+    GBE_CUDA_TRY(cudaMemcpyAsync(h, d, 4, cudaMemcpyDeviceToHost, ctx->stream));
+    GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBE_OK;
+}
+
+size_t rowset_smem() { return sizeof(RowSetSmem); }
+
+// Copy an array to the device when it is on the host.
+int to_device(gbe_ctx* ctx, const void* src, size_t bytes, int on_device, DevBuf& hold, const void** out) {
+    if (on_device) { *out = src; return GBE_OK; }
+    GBE_TRY(gbe_alloc(&hold.p, bytes));
+    GBE_CUDA_TRY(cudaMemcpyAsync(hold.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *out = hold.p;
+    return GBE_OK;
+}
+
+// Build a CSR whose row i is produced by rowset_kernel (count, scan, fill).
+int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thresh, const int64_t* s1rp,
+               const int32_t* s1ci, const int64_t* s2rp, const int32_t* s2ci, const int64_t* s3rp, const int32_t* s3ci,
+               int hops, int64_t** rp_out, int32_t** ci_out, int64_t* nnz_out) {
+    DevBuf cnt, flag;
+    GBE_TRY(gbe_alloc(&cnt.p, n * 4));
+    GBE_TRY(gbe_alloc(&flag.p, 4));
+    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 4, ctx->stream));
+    const size_t sm = rowset_smem();
+    cudaFuncSetAttribute(rowset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int grid = (int)std::min<int64_t>(n, (int64_t)ctx->sm_count * 3);
+    const int64_t* hrp = H ? H->rowptr : nullptr;
+    const int32_t* hci = H ? H->col : nullptr;
+    const double* hva = H ? H->val : nullptr;
+    rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp, s3ci,
+                                                  hops, 0, cnt.as<int32_t>(), nullptr, nullptr, flag.as<int>());
+    GBE_CUDA_TRY(cudaGetLastError());
+    int64_t* rp = nullptr;
+    GBE_TRY(gbe_alloc((void**)&rp, (n + 1) * 8));
+    int64_t nnz = 0;
+    int r = scan_exclusive(ctx, cnt.as<int32_t>(), rp, n, &nnz);
+    int ovf = 0;
+    if (r == GBE_OK) r = read_flag(ctx, flag.as<int>(), &ovf);
+    if (r == GBE_OK && ovf) {
+        gbe_set_error("graph row exceeds %d entries", kSetMax);
+        r = GBE_ECAPACITY;
+    }
+    int32_t* ci = nullptr;
+    if (r == GBE_OK) r = gbe_alloc((void**)&ci, std::max<int64_t>(nnz, 1) * 4);
+    if (r != GBE_OK) { cudaFree(rp); return r; }
+    rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp, s3ci,
+                                                  hops, 1, cnt.as<int32_t>(), rp, ci, flag.as<int>());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(rp); cudaFree(ci);
+        gbe_set_error("rowset: %s", cudaGetErrorString(e));
+        return GBE_ECUDA;
+    }
+    *rp_out = rp; *ci_out = ci; *nnz_out = nnz;
+    return GBE_OK;
+}
+
+}  // namespace
+
+// ============================================================================= Hamiltonian
+extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gbe_tb_model* model, gbe_hamiltonian** out) {
+    GBE_CHECK_ARG(ctx && st && model && out, "NULL argument");
+    GBE_CHECK_ARG(st->n > 0 && st->n < INT32_MAX && st->pos && st->onsite, "sites");
+    GBE_CHECK_ARG(model->rcut > 0 && model->decay > 0, "model");
+    for (int d = 0; d < 3; ++d) GBE_CHECK_ARG(st->box[d] > 2.0 * model->rcut, "box must exceed 2 rcut (minimum image)");
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    const int64_t n = st->n;
+    cudaStream_t s = ctx->stream;
+    DevBuf hpos, hons;
+    const double *pos, *ons;
+    GBE_TRY(to_device(ctx, st->pos, n * 24, st->on_device, hpos, (const void**)&pos));
+    GBE_TRY(to_device(ctx, st->onsite, n * 8, st->on_device, hons, (const void**)&ons));
+    CellGrid g;
+    int64_t ncells = 1;
+    for (int d = 0; d < 3; ++d) {
+        g.nc[d] = std::max(1, (int)floor(st->box[d] / model->rcut));
+        g.box[d] = st->box[d];
+        ncells *= g.nc[d];
+    }
+    DevBuf cell, ccnt, cstart, cur, mem, cnt, flag;
+    GBE_TRY(gbe_alloc(&cell.p, n * 4));
+    GBE_TRY(gbe_alloc(&ccnt.p, ncells * 4));
+    GBE_TRY(gbe_alloc(&cstart.p, (ncells + 1) * 8));
+    GBE_TRY(gbe_alloc(&cur.p, ncells * 4));
+    GBE_TRY(gbe_alloc(&mem.p, n * 4));
+    GBE_TRY(gbe_alloc(&cnt.p, n * 4));
+    GBE_TRY(gbe_alloc(&flag.p, 4));
+    GBE_CUDA_TRY(cudaMemsetAsync(ccnt.p, 0, ncells * 4, s));
+    GBE_CUDA_TRY(cudaMemsetAsync(cur.p, 0, ncells * 4, s));
+    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 4, s));
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    cell_count_kernel<<<nb, 256, 0, s>>>(pos, n, g, cell.as<int32_t>(), ccnt.as<int32_t>());
+    GBE_TRY(scan_exclusive(ctx, ccnt.as<int32_t>(), cstart.as<int64_t>(), ncells, nullptr));
+    cell_fill_kernel<<<nb, 256, 0, s>>>(cell.as<int32_t>(), n, cstart.as<int64_t>(), cur.as<int32_t>(), mem.as<int32_t>());
+    HModel mdl{model->a, model->rcut, model->decay, model->hop};
+    const unsigned rb = (unsigned)((n + 7) / 8);
+    hbuild_kernel<<<rb, 256, 0, s>>>(pos, ons, n, g, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 0, cnt.as<int32_t>(),
+                                     nullptr, nullptr, nullptr, flag.as<int>());
+    GBE_CUDA_TRY(cudaGetLastError());
+    gbe_hamiltonian* H = new gbe_hamiltonian();
+    H->n = n;
+    int r = gbe_alloc((void**)&H->rowptr, (n + 1) * 8);
+    int64_t nnz = 0;
+    if (r == GBE_OK) r = scan_exclusive(ctx, cnt.as<int32_t>(), H->rowptr, n, &nnz);
+    int ovf = 0;
+    if (r == GBE_OK) r = read_flag(ctx, flag.as<int>(), &ovf);
+    if (r == GBE_OK && ovf) { gbe_set_error("a row of H has more than %d neighbours", kRowCap); r = GBE_ECAPACITY; }
+    if (r == GBE_OK) r = gbe_alloc((void**)&H->col, nnz * 4);
+    if (r == GBE_OK) r = gbe_alloc((void**)&H->val, nnz * 8);
+    if (r != GBE_OK) { gbe_free_hamiltonian(H); return r; }
+    H->nnz = nnz;
+    hbuild_kernel<<<rb, 256, 0, s>>>(pos, ons, n, g, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 1, cnt.as<int32_t>(),
+                                     H->rowptr, H->col, H->val, flag.as<int>());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        gbe_free_hamiltonian(H);
+        gbe_set_error("hbuild: %s", cudaGetErrorString(e));
+        return GBE_ECUDA;
+    }
+    *out = H;
+    return GBE_OK;
+}
+
+extern "C" int gbe_hamiltonian_csr(const gbe_hamiltonian* H, gbe_csr* v) {
+    GBE_CHECK_ARG(H && v, "NULL argument");
+    v->n = H->n; v->nnz = H->nnz; v->rowptr = H->rowptr; v->col = H->col; v->val = H->val; v->on_device = 1;
+    return GBE_OK;
+}
+
+extern "C" int gbe_free_hamiltonian(gbe_hamiltonian* H) {
+    if (!H) return GBE_OK;
+    cudaFree(H->rowptr); cudaFree(H->col); cudaFree(H->val);
+    delete H;
+    return GBE_OK;
+}
+
+// ============================================================================= graph
+extern "C" int gbe_free_graph(gbe_graph* S) {
+    if (!S) return GBE_OK;
+    cudaFree(S->rowptr); cudaFree(S->col);
+    if (S->full_rowptr != S->rowptr) { cudaFree(S->full_rowptr); cudaFree(S->full_col); }
+    delete S;
+    return GBE_OK;
+}
+
+int gbe_graph_mlp_edges(gbe_ctx* ctx, const gbe_csr* H, const gbe_graph_params* p, int64_t** rp, int32_t** ci);
+
+extern "C" int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* Hin, const gbe_graph_params* p, gbe_graph** out) {
+    GBE_CHECK_ARG(ctx && Hin && p && out, "NULL argument");
+    GBE_CHECK_ARG(Hin->n > 0 && Hin->n < INT32_MAX, "H size");
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    const int64_t n = Hin->n;
+    // H on the device
+    DevBuf hrp, hci, hva;
+    gbe_csr H = *Hin;
+    if (!Hin->on_device) {
+        GBE_TRY(to_device(ctx, Hin->rowptr, (n + 1) * 8, 0, hrp, (const void**)&H.rowptr));
+        GBE_TRY(to_device(ctx, Hin->col, Hin->nnz * 4, 0, hci, (const void**)&H.col));
+        GBE_TRY(to_device(ctx, Hin->val, Hin->nnz * 8, 0, hva, (const void**)&H.val));
+        H.on_device = 1;
+    }
+    gbe_graph* S = new gbe_graph();
+    S->n = n;
+    int r = GBE_OK;
+    switch (p->mode) {
+        case GBE_GRAPH_H2_THRESH:
+            r = rowset_csr(ctx, 0, n, &H, p->thresh, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1,
+                           &S->rowptr, &S->col, &S->nnz);
+            S->hops = 1;
+            break;
+        case GBE_GRAPH_HK_PATTERN:
+            GBE_CHECK_ARG(p->k >= 1, "k >= 1");
+            // base A = pattern(H) with the diagonal (union with itself adds the diagonal)
+            r = rowset_csr(ctx, 1, n, nullptr, 0.0, H.rowptr, H.col, nullptr, nullptr, nullptr, nullptr, 1, &S->rowptr,
+                           &S->col, &S->nnz);
+            S->hops = p->k;
+            break;
+        case GBE_GRAPH_D_THRESH:
+        case GBE_GRAPH_EQ8_SYMBOLIC: {
+            const gbe_ell* D = p->D_prev;
+            if (!D || !D->col || !D->val || D->n != n) { delete S; gbe_set_error("D_prev missing or wrong size"); return GBE_EINVAL; }
+            DevBuf dcol, dval;
+            const int32_t* ecol;
+            const double* eval;
+            r = to_device(ctx, D->col, D->n * D->width * 4, D->on_device, dcol, (const void**)&ecol);
+            if (r == GBE_OK) r = to_device(ctx, D->val, D->n * D->width * 8, D->on_device, dval, (const void**)&eval);
+            DevBuf co, ct, rpo, rpt, cio, cit, cur;
+            if (r == GBE_OK) r = gbe_alloc(&co.p, n * 4);
+            if (r == GBE_OK) r = gbe_alloc(&ct.p, n * 4);
+            if (r == GBE_OK) r = gbe_alloc(&rpo.p, (n + 1) * 8);
+            if (r == GBE_OK) r = gbe_alloc(&rpt.p, (n + 1) * 8);
+            if (r == GBE_OK) r = gbe_alloc(&cur.p, n * 4);
+            if (r != GBE_OK) break;
+            cudaMemsetAsync(ct.p, 0, n * 4, ctx->stream);
+            cudaMemsetAsync(cur.p, 0, n * 4, ctx->stream);
+            const unsigned nb = (unsigned)((n + 255) / 256);
+            ell_count_kernel<<<nb, 256, 0, ctx->stream>>>(ecol, eval, n, D->width, p->thresh, co.as<int32_t>(), ct.as<int32_t>());
+            int64_t no = 0, nt = 0;
+            r = scan_exclusive(ctx, co.as<int32_t>(), rpo.as<int64_t>(), n, &no);
+            if (r == GBE_OK) r = scan_exclusive(ctx, ct.as<int32_t>(), rpt.as<int64_t>(), n, &nt);
+            if (r == GBE_OK) r = gbe_alloc(&cio.p, std::max<int64_t>(no, 1) * 4);
+            if (r == GBE_OK) r = gbe_alloc(&cit.p, std::max<int64_t>(nt, 1) * 4);
+            if (r != GBE_OK) break;
+            ell_fill_kernel<<<nb, 256, 0, ctx->stream>>>(ecol, eval, n, D->width, p->thresh, rpo.as<int64_t>(),
+                                                         cio.as<int32_t>(), rpt.as<int64_t>(), cur.as<int32_t>(), cit.as<int32_t>());
+            const bool eq8 = (p->mode == GBE_GRAPH_EQ8_SYMBOLIC);
+            r = rowset_csr(ctx, 1, n, nullptr, 0.0, rpo.as<int64_t>(), cio.as<int32_t>(), rpt.as<int64_t>(),
+                           cit.as<int32_t>(), eq8 ? H.rowptr : nullptr, eq8 ? H.col : nullptr, 1, &S->rowptr, &S->col,
+                           &S->nnz);
+            S->hops = eq8 ? 2 : 1;
+            break;
+        }
+        case GBE_GRAPH_MLP:
+            r = gbe_graph_mlp_edges(ctx, &H, p, &S->rowptr, &S->col);
+            if (r == GBE_OK) {
+                int64_t nnz = 0;
+                cudaMemcpy(&nnz, S->rowptr + n, 8, cudaMemcpyDeviceToHost);
+                S->nnz = nnz;
+            }
+            S->hops = 1;
+            break;
+        default:
+            gbe_set_error("unknown graph mode %d", p->mode);
+            r = GBE_EINVAL;
+    }
+    if (r != GBE_OK) { gbe_free_graph(S); return r; }
+    if (S->hops == 1) { S->full_rowptr = S->rowptr; S->full_col = S->col; S->full_nnz = S->nnz; }
+    *out = S;
+    return GBE_OK;
+}
+
+extern "C" int gbe_graph_size(gbe_ctx* ctx, gbe_graph* S, int64_t* n, int64_t* nnz) {
+    GBE_CHECK_ARG(ctx && S, "NULL argument");
+    if (S->full_nnz < 0) {
+        GBE_TRY(rowset_csr(ctx, 2, S->n, nullptr, 0.0, S->rowptr, S->col, nullptr, nullptr, nullptr, nullptr, S->hops,
+                           &S->full_rowptr, &S->full_col, &S->full_nnz));
+    }
+    if (n) *n = S->n;
+    if (nnz) *nnz = S->full_nnz;
+    return GBE_OK;
+}
+
+extern "C" int gbe_graph_export(gbe_ctx* ctx, gbe_graph* S, int64_t* rowptr, int32_t* col) {
+    GBE_CHECK_ARG(ctx && S && rowptr && col, "NULL argument");
+    GBE_TRY(gbe_graph_size(ctx, S, nullptr, nullptr));
+    GBE_CUDA_TRY(cudaMemcpyAsync(rowptr, S->full_rowptr, (S->n + 1) * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    if (S->full_nnz > 0)
+        GBE_CUDA_TRY(cudaMemcpyAsync(col, S->full_col, S->full_nnz * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    return GBE_OK;
+}
+
+// ============================================================================= partition
+extern "C" int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* p, gbe_parts** out) {
+    GBE_CHECK_ARG(ctx && S && p && out, "NULL argument");
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int64_t n = S->n;
+    const int cap = p->max_sub > 0 ? std::min(p->max_sub, kSetMax) : kSetMax;
+    DevBuf cstart, mem;
+    int64_t P = 0;
+    GBE_TRY(gbe_alloc(&mem.p, n * 4));
+    if (p->mode == GBE_PART_SPATIAL_CELLS) {
+        GBE_CHECK_ARG(p->sites && p->sites->n == n && p->sites->pos, "spatial cells need sites of the graph's size");
+        GBE_CHECK_ARG(p->ncell[0] > 0 && p->ncell[1] > 0 && p->ncell[2] > 0, "ncell");
+        DevBuf hpos;
+        const double* pos;
+        GBE_TRY(to_device(ctx, p->sites->pos, n * 24, p->sites->on_device, hpos, (const void**)&pos));
+        CellGrid g;
+        int64_t ncells = 1;
+        for (int d = 0; d < 3; ++d) { g.nc[d] = p->ncell[d]; g.box[d] = p->sites->box[d]; ncells *= g.nc[d]; }
+        GBE_CHECK_ARG(ncells < INT32_MAX, "too many cells");
+        DevBuf cell, ccnt, cst, cur;
+        GBE_TRY(gbe_alloc(&cell.p, n * 4));
+        GBE_TRY(gbe_alloc(&ccnt.p, ncells * 4));
+        GBE_TRY(gbe_alloc(&cst.p, (ncells + 1) * 8));
+        GBE_TRY(gbe_alloc(&cur.p, ncells * 4));
+        GBE_CUDA_TRY(cudaMemsetAsync(ccnt.p, 0, ncells * 4, st));
+        GBE_CUDA_TRY(cudaMemsetAsync(cur.p, 0, ncells * 4, st));
+        const unsigned nb = (unsigned)((n + 255) / 256);
+        cell_count_kernel<<<nb, 256, 0, st>>>(pos, n, g, cell.as<int32_t>(), ccnt.as<int32_t>());
+        GBE_TRY(scan_exclusive(ctx, ccnt.as<int32_t>(), cst.as<int64_t>(), ncells, nullptr));
+        cell_fill_kernel<<<nb, 256, 0, st>>>(cell.as<int32_t>(), n, cst.as<int64_t>(), cur.as<int32_t>(), mem.as<int32_t>());
+        cell_sort_kernel<<<(unsigned)((ncells * 32 + 255) / 256), 256, 0, st>>>(cst.as<int64_t>(), (int)ncells, mem.as<int32_t>());
+        // non-empty cells, ascending id -> core_start
+        std::vector<int64_t> hst(ncells + 1);
+        GBE_CUDA_TRY(cudaMemcpyAsync(hst.data(), cst.p, (ncells + 1) * 8, cudaMemcpyDeviceToHost, st));
+        GBE_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<int64_t> cs;
+        cs.reserve(ncells + 1);
+        for (int64_t c = 0; c < ncells; ++c)
+            if (hst[c + 1] > hst[c]) cs.push_back(hst[c]);
+        cs.push_back(hst[ncells]);
+        P = (int64_t)cs.size() - 1;
+        GBE_TRY(gbe_alloc(&cstart.p, (P + 1) * 8));
+        GBE_CUDA_TRY(cudaMemcpyAsync(cstart.p, cs.data(), (P + 1) * 8, cudaMemcpyHostToDevice, st));
+        GBE_CUDA_TRY(cudaStreamSynchronize(st));
+    } else if (p->mode == GBE_PART_INDEX_BLOCKS) {
+        GBE_CHECK_ARG(p->core_size > 0, "core_size");
+        P = (n + p->core_size - 1) / p->core_size;
+        std::vector<int64_t> cs(P + 1);
+        for (int64_t s = 0; s <= P; ++s) cs[s] = std::min<int64_t>(s * p->core_size, n);
+        GBE_TRY(gbe_alloc(&cstart.p, (P + 1) * 8));
+        GBE_CUDA_TRY(cudaMemcpyAsync(cstart.p, cs.data(), (P + 1) * 8, cudaMemcpyHostToDevice, st));
+        iota_blocks_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, mem.as<int32_t>());
+        GBE_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+        gbe_set_error("unknown partition mode %d", p->mode);
+        return GBE_EINVAL;
+    }
+    DevBuf msz, csz, slots, flag;
+    GBE_TRY(gbe_alloc(&msz.p, P * 4));
+    GBE_TRY(gbe_alloc(&csz.p, P * 4));
+    GBE_TRY(gbe_alloc(&slots.p, (size_t)P * cap * 4));
+    GBE_TRY(gbe_alloc(&flag.p, 4));
+    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 4, st));
+    const size_t sm = rowset_smem();
+    cudaFuncSetAttribute(halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int grid = (int)std::min<int64_t>(P, (int64_t)ctx->sm_count * 3);
+    halo_kernel<<<grid, 256, sm, st>>>(P, cstart.as<int64_t>(), mem.as<int32_t>(), S->rowptr, S->col, S->hops, cap,
+                                       msz.as<int32_t>(), csz.as<int32_t>(), slots.as<int32_t>(), flag.as<int>());
+    GBE_CUDA_TRY(cudaGetLastError());
+    int ovf = 0;
+    GBE_TRY(read_flag(ctx, flag.as<int>(), &ovf));
+    if (ovf) {
+        gbe_set_error("a core+halo subgraph exceeds capacity %d (needs >= %d)", cap, ovf);
+        return GBE_ECAPACITY;
+    }
+    gbe_parts* parts = new gbe_parts();
+    parts->n = n;
+    parts->P = P;
+    parts->h_core_count.resize(P);
+    std::vector<int32_t> hm(P);
+    cudaMemcpyAsync(hm.data(), msz.p, P * 4, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(parts->h_core_count.data(), csz.p, P * 4, cudaMemcpyDeviceToHost, st);
+    GBE_CUDA_TRY(cudaStreamSynchronize(st));
+    parts->h_sub_ptr.resize(P + 1);
+    parts->h_sub_ptr[0] = 0;
+    for (int64_t s = 0; s < P; ++s) {
+        parts->h_sub_ptr[s + 1] = parts->h_sub_ptr[s] + hm[s];
+        parts->max_m = std::max<int64_t>(parts->max_m, hm[s]);
+    }
+    parts->total = parts->h_sub_ptr[P];
+    int r = gbe_alloc((void**)&parts->d_core_count, P * 4);
+    if (r == GBE_OK) r = gbe_alloc((void**)&parts->d_sub_ptr, (P + 1) * 8);
+    if (r == GBE_OK) r = gbe_alloc((void**)&parts->d_sub_idx, parts->total * 4);
+    if (r != GBE_OK) { gbe_free_parts(parts); return r; }
+    cudaMemcpyAsync(parts->d_core_count, csz.p, P * 4, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(parts->d_sub_ptr, parts->h_sub_ptr.data(), (P + 1) * 8, cudaMemcpyHostToDevice, st);
+    compact_slots_kernel<<<grid, 256, 0, st>>>(P, slots.as<int32_t>(), cap, parts->d_sub_ptr, parts->d_sub_idx);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        gbe_free_parts(parts);
+        gbe_set_error("partition: %s", cudaGetErrorString(e));
+        return GBE_ECUDA;
+    }
+    *out = parts;
+    return GBE_OK;
+}
+
+// Learned graph proposals are built in mlp.cu; without it the mode is rejected.
+__attribute__((weak)) int gbe_graph_mlp_edges(gbe_ctx*, const gbe_csr*, const gbe_graph_params*, int64_t**, int32_t**) {
+    gbe_set_error("MLP graph mode not available in this build");
     return GBE_EINVAL;
 }

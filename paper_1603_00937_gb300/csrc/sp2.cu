@@ -158,6 +158,33 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     }
 }
 
+// ----------------------------------------------------------------------------- init
+// Control-block initialisation from parameters passed by value (no host staging, so
+// consecutive runs enqueue without synchronising).
+struct Sp2Init {
+    int mode, fmt, n_min, n_max, branch_mode, seq_len, fp64_tail, prec, eps_given;
+    double eps_min, eps_max, n_occ, idem_tol, tail_switch;
+    long long timeout_cycles;
+    uint8_t seq_in[GBE_SEQ_MAX];
+};
+
+__global__ void init_ctrl_kernel(Sp2Ctrl* C, Sp2Init in) {
+    // zero the whole block, then set the run's parameters
+    uint32_t* w = reinterpret_cast<uint32_t*>(C);
+    for (int i = threadIdx.x; i < (int)(sizeof(Sp2Ctrl) / 4); i += blockDim.x) w[i] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < GBE_SEQ_MAX; i += blockDim.x) C->seq_in[i] = in.seq_in[i];
+    if (threadIdx.x == 0) {
+        C->mode = in.mode; C->fmt = in.fmt; C->switch_iter = -1;
+        C->n_min = in.n_min; C->n_max = in.n_max; C->branch_mode = in.branch_mode; C->seq_len = in.seq_len;
+        C->fp64_tail = in.fp64_tail; C->prec = in.prec; C->eps_given = in.eps_given;
+        C->eps_min = in.eps_min; C->eps_max = in.eps_max;
+        C->eps_min_key = ~0ull; C->eps_max_key = 0ull;
+        C->n_occ = in.n_occ; C->idem_tol = in.idem_tol; C->tail_switch = in.tail_switch;
+        C->timeout_cycles = in.timeout_cycles;
+    }
+}
+
 // ----------------------------------------------------------------------------- decide
 // Global FP64 traces over core positions -> stop rule and branch of the next step.
 // kind: 0 after the gather (X_0), 1 after a tensor-core step, 2 after an FP64 step.
@@ -230,7 +257,7 @@ __global__ void __launch_bounds__(256) square_fp64_kernel(Sp2Ctrl* ctrl, SubsGeo
                                                           const TileItem* __restrict__ items, int n_items,
                                                           uint16_t* planes0, uint16_t* planes1,
                                                           int64_t plane_stride, double* f0, double* f1,
-                                                          double* partials, int max_units) {
+                                                          double* partials, int max_units, int slot) {
     __shared__ double As[2][16][64];
     __shared__ double Bs[2][16][64];
     __shared__ double red[8];
@@ -244,7 +271,7 @@ __global__ void __launch_bounds__(256) square_fp64_kernel(Sp2Ctrl* ctrl, SubsGeo
     }
     __syncthreads();
     if (!hdr[0]) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->pending = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) { ctrl->pending = 1; ctrl->slot_ran[slot] |= 2; }
     const int cur = hdr[1], fmt = hdr[2], branch = hdr[3], prec = hdr[4];
     const uint16_t* pin = cur ? planes1 : planes0;
     const double* fin = cur ? f1 : f0;
@@ -460,6 +487,8 @@ extern "C" int gbe_free_subs(gbe_subs* X) {
     cudaFree(X->d_items_tc); cudaFree(X->d_items_64); cudaFree(X->d_partials); cudaFree(X->d_ctrl);
     if (X->h_ctrl) cudaFreeHost(X->h_ctrl);
     for (int i = 0; i < 3; ++i) if (X->ev[i]) cudaEventDestroy(X->ev[i]);
+    for (auto e : X->ev_tc) cudaEventDestroy(e);
+    for (auto e : X->ev_64) cudaEventDestroy(e);
     delete X;
     return GBE_OK;
 }
@@ -579,32 +608,28 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     GBE_CHECK_ARG(parts->max_m <= 8192, "subgraph larger than 8192");
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    Sp2Ctrl* C = X->h_ctrl;
-    // the pinned block may still be read by an earlier enqueued copy
-    GBE_CUDA_TRY(cudaStreamSynchronize(st));
-    memset(C, 0, sizeof(Sp2Ctrl));
-    C->mode = (prm->prec == GBE_PREC_FP64) ? 1 : 0;
-    C->fmt = (prm->prec == GBE_PREC_FP64) ? 1 : 0;
-    C->switch_iter = -1;
-    C->n_min = prm->n_min;
-    C->n_max = prm->n_max;
-    C->branch_mode = prm->branch_mode;
-    C->seq_len = prm->branch_mode == GBE_BRANCH_REPLAY ? prm->seq_len : 0;
-    C->fp64_tail = prm->fp64_tail;
-    C->prec = prm->prec;
-    C->eps_given = prm->eps_given;
-    C->eps_min = prm->eps_min;
-    C->eps_max = prm->eps_max;
-    C->eps_min_key = ~0ull;
-    C->eps_max_key = 0ull;
-    C->n_occ = prm->n_occ;
-    C->idem_tol = prm->idem_tol;
-    C->tail_switch = prm->tail_switch;
+    Sp2Init in;
+    memset(&in, 0, sizeof(in));
+    in.mode = (prm->prec == GBE_PREC_FP64) ? 1 : 0;
+    in.fmt = (prm->prec == GBE_PREC_FP64) ? 1 : 0;
+    in.n_min = prm->n_min;
+    in.n_max = prm->n_max;
+    in.branch_mode = prm->branch_mode;
+    in.seq_len = prm->branch_mode == GBE_BRANCH_REPLAY ? prm->seq_len : 0;
+    in.fp64_tail = prm->fp64_tail;
+    in.prec = prm->prec;
+    in.eps_given = prm->eps_given;
+    in.eps_min = prm->eps_min;
+    in.eps_max = prm->eps_max;
+    in.n_occ = prm->n_occ;
+    in.idem_tol = prm->idem_tol;
+    in.tail_switch = prm->tail_switch;
     const double tmo = prm->timeout_ms > 0 ? prm->timeout_ms : 2000.0;
-    C->timeout_cycles = (long long)(tmo * 2.2e6);
-    if (C->branch_mode == GBE_BRANCH_REPLAY && C->seq_len) memcpy(C->seq_in, prm->seq_in, C->seq_len);
-    if (C->prec != GBE_PREC_FP64 && C->branch_mode == GBE_BRANCH_REPLAY && C->seq_len <= C->fp64_tail) C->mode = 1;
-    GBE_CUDA_TRY(cudaMemcpyAsync(X->d_ctrl, C, sizeof(Sp2Ctrl), cudaMemcpyHostToDevice, st));
+    in.timeout_cycles = (long long)(tmo * 2.2e6);
+    if (in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len) memcpy(in.seq_in, prm->seq_in, in.seq_len);
+    if (in.prec != GBE_PREC_FP64 && in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len <= in.fp64_tail) in.mode = 1;
+    init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
+    GBE_CUDA_TRY(cudaGetLastError());
     cudaEventRecord(X->ev[0], st);
     if (!prm->eps_given) GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
     const int64_t ps = X->total_elems;
@@ -619,18 +644,34 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, (int)X->P, 0);
     cudaEventRecord(X->ev[1], st);
     const int grid64 = std::max(1, std::min(X->n_items_64, ctx->sm_count * 4));
+    const bool prof = ctx->profile != 0;
+    if (prof && (int)X->ev_tc.size() < 2 * prm->n_max) {
+        for (int i = (int)X->ev_tc.size(); i < 2 * prm->n_max; ++i) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            X->ev_tc.push_back(a);
+            X->ev_64.push_back(b);
+        }
+    }
+    X->last_slots = prm->n_max;
     for (int slot = 0; slot < prm->n_max; ++slot) {
         if (X->prec != GBE_PREC_FP64) {
-            GBE_TRY(gbe_tc_launch_square(ctx, X));
+            if (prof) cudaEventRecord(X->ev_tc[2 * slot], st);
+            GBE_TRY(gbe_tc_launch_square(ctx, X, slot));
+            if (prof) cudaEventRecord(X->ev_tc[2 * slot + 1], st);
             decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_tc, 1);
         }
         if (X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0) {
+            if (prof) cudaEventRecord(X->ev_64[2 * slot], st);
             square_fp64_kernel<<<grid64, 256, 0, st>>>(X->d_ctrl, geom_of(X), X->d_items_64, X->n_items_64,
                                                        X->planes[0], X->planes[1], ps, X->f64[0], X->f64[1],
-                                                       X->d_partials, X->max_units);
+                                                       X->d_partials, X->max_units, slot);
+            if (prof) cudaEventRecord(X->ev_64[2 * slot + 1], st);
             decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_64, 2);
         }
     }
+    X->last_prof = prof;
     GBE_CUDA_TRY(cudaGetLastError());
     cudaEventRecord(X->ev[2], st);
     return GBE_OK;
@@ -659,6 +700,20 @@ extern "C" int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_repor
     const int mixed_iters = C->iter - C->fp64_iters;
     rep->mma_flops = X->mma_flops_per_iter * mixed_iters;
     rep->alg_flops = X->alg_flops_per_iter * C->iter;
+    rep->fp64_flops = X->fp64_flops_per_iter * C->fp64_iters;
+    if (X->last_prof) {
+        for (int slot = 0; slot < X->last_slots; ++slot) {
+            float ms = 0.f;
+            if ((C->slot_ran[slot] & 1) && cudaEventElapsedTime(&ms, X->ev_tc[2 * slot], X->ev_tc[2 * slot + 1]) == cudaSuccess) {
+                rep->ms_tc += ms;
+                rep->n_tc += 1;
+            }
+            if ((C->slot_ran[slot] & 2) && cudaEventElapsedTime(&ms, X->ev_64[2 * slot], X->ev_64[2 * slot + 1]) == cudaSuccess) {
+                rep->ms_fp64 += ms;
+                rep->n_fp64 += 1;
+            }
+        }
+    }
     return GBE_OK;
 }
 

@@ -179,6 +179,7 @@ struct TcArgs {
     int64_t ps;  // plane stride in elements
     double* partials;
     int max_units;
+    int slot;
 };
 
 // Double-float accumulation of w * (P + Q)^2 (FP64-grade traces from FP32 parts).
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     if (!hdr[0]) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctrl->pending = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) { ctrl->pending = 1; ctrl->slot_ran[args.slot] |= 1; }
     const int cur = hdr[1], branch = hdr[2];
     const long long budget = ctrl->timeout_cycles;
     const CUtensorMap* tmap = cur ? &tmap1 : &tmap0;
@@ -541,7 +542,7 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
     return GBE_OK;
 }
 
-int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X) {
+int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot) {
     if (!X->tmap_ok) {
         gbe_set_error("tensor maps missing");
         return GBE_ECUDA;
@@ -556,6 +557,7 @@ int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X) {
     a.ps = X->total_elems;
     a.partials = X->d_partials;
     a.max_units = X->max_units;
+    a.slot = slot;
     CUtensorMap m0, m1;
     memcpy(&m0, X->tmap[0], sizeof(m0));
     memcpy(&m1, X->tmap[1], sizeof(m1));

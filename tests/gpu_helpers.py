@@ -57,3 +57,15 @@ def oracle_graph_sp2(H, subs, nc, seq=None, **kw):
     N = H.shape[0]
     D, log, xs = sp2.sp2_graph(H, subs, nc, N // 2, seq=seq, return_subs=True, **kw)
     return D.toarray(), log, xs
+
+
+class _CudaArray:
+    def __init__(self, ptr, count, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(count),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3}
+
+
+def device_array(ptr, count, typestr):
+    """NumPy copy of `count` elements at a raw device pointer owned by libgbe."""
+    torch.cuda.synchronize()
+    return torch.as_tensor(_CudaArray(ptr, count, typestr), device="cuda").cpu().numpy().copy()
