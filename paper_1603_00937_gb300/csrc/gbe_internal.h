@@ -148,10 +148,16 @@ struct gbe_subs {
 };
 
 // ----------------------------------------------------------------------------- blocked layout
-// A padded m x m submatrix (mpad multiple of 128) is stored as 128 x 64 blocks, block
-// (r / 128, c / 64) at index (r / 128) * (mpad / 64) + c / 64, row-major inside a block.
+// A padded m x m submatrix (mpad a multiple of 128) is stored in row blocks of 128 rows;
+// inside a row block, column groups of 8 follow each other, and a group holds its 128
+// rows x 8 columns row by row:
+//   element (r, c) -> off + (r / 128) * 128 * mpad + (c / 8) * 1024 + (r % 128) * 8 + c % 8.
+// A 32-column K-chunk of a row block is one contiguous 8 KB run that is already the
+// canonical K-major, unswizzled operand layout of the tensor cores (8-row x 16-byte core
+// matrices: 128 B apart along rows, 2 KB apart along K), and a warp's 32 consecutive
+// rows x 8 columns are 512 contiguous bytes.
 __host__ __device__ inline int64_t blk_index(int64_t off, int mpad, int r, int c) {
-    return off + ((int64_t)((r >> 7) * (mpad >> 6) + (c >> 6)) << 13) + ((r & 127) << 6) + (c & 63);
+    return off + (int64_t)(r >> 7) * 128 * mpad + ((int64_t)(c >> 3) << 10) + ((r & 127) << 3) + (c & 7);
 }
 
 // ----------------------------------------------------------------------------- launchers

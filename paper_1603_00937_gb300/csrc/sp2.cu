@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     if (ctrl->eps_given) { emin = ctrl->eps_min; emax = ctrl->eps_max; }
     else { emin = dkey_inv(ctrl->eps_min_key); emax = dkey_inv(ctrl->eps_max_key); }
     const double range = emax - emin;
+    const double inv_range = 1.0 / range;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double t1 = 0.0, t2 = 0.0;
     for (int a = warp; a < m; a += 8) {
@@ -128,12 +129,16 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
             const int b = find_local(sidx, c, m, col[p]);
             if (b < 0) continue;
             const double h = val[p];
-            const double x = ((a == b ? emax : 0.0) - h) / range;
             const int64_t e = blk_index(off, mpad, a, b);
+            // FP64 path: the exact quotient; split paths only need ~2^-35, so one FP64
+            // multiply and an FP32 pair (FP64 is a narrow pipe on this part)
+            const double x = (prec == GBE_PREC_FP64) ? ((a == b ? emax : 0.0) - h) / range
+                                                     : ((a == b ? emax : 0.0) - h) * inv_range;
             if (prec == GBE_PREC_FP64) {
                 f[e] = x;
             } else if (prec == GBE_PREC_FP16X6) {
-                OzSplit o = oz_split_d(x);
+                const float xh = __double2float_rn(x);
+                OzSplit o = oz_split_pq(xh, __double2float_rn(x - (double)xh));
                 planes[e] = o.s0;
                 planes[e + plane_stride] = o.s1;
                 planes[e + 2 * plane_stride] = o.s2;

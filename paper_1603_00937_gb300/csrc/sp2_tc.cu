@@ -3,12 +3,16 @@
 // epilogue, next split written directly, FP64-grade core traces fused.
 //
 // One CTA per SM (persistent), 6 warps:
-//   warp 0  TMA producer      : K-chunks of 32 for every split plane an MMA needs
+//   warp 0  TMA producer      : K-chunks of 32 for every split plane an MMA needs (one
+//                               contiguous 8 KB box each, already in MMA operand order)
 //   warp 1  MMA issuer        : 128x128x16 tcgen05.mma per product and k-step into
 //                               two TMEM accumulators, double-buffered (4 x 128 cols)
-//   warps 2-5 epilogue        : TMEM -> registers, X_{n+1} = S or 2 X_n - S, split,
+//   warps 2-9 epilogue        : TMEM -> registers, X_{n+1} = S or 2 X_n - S, split,
 //                               store tile and (off-diagonal tiles) its transpose,
-//                               partial traces of core rows
+//                               partial traces of core rows; two warps per TMEM lane
+//                               quarter, each taking half of the tile's columns.  X_n
+//                               values for the next chunk are fetched ahead, and the
+//                               transpose is done with warp shuffles (no CTA barriers).
 // Work items are upper-triangular output tiles (I <= J) of every subgraph; the
 // iterate is exactly symmetric because every off-diagonal tile is mirrored.
 //
@@ -26,8 +30,9 @@
 
 namespace {
 
-constexpr int kThreads = 192;
-constexpr int kTileBytes = 128 * 32 * 2;   // 128 rows x 32 halfs (64-byte rows, 64B swizzle)
+constexpr int kEpiWarps = 8;                       // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;      // producer, MMA issuer, epilogue
+constexpr int kTileBytes = 128 * 32 * 2;   // 128 rows x 32 halfs: 4 column groups of 128 x 16 bytes
 constexpr int kTmemCols = 512;
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -100,14 +105,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-// Named barrier over the 128 epilogue threads that also ORs a flag across them.
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// Named barrier over the 256 epilogue threads that also ORs a flag across them.
 __device__ __forceinline__ bool epi_bar_any(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, 128, p;\n\t"
+        "bar.red.or.pred q, 1, 256, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(r)
         : "r"((uint32_t)v)
@@ -115,15 +120,15 @@ __device__ __forceinline__ bool epi_bar_any(bool v) {
     return r != 0;
 }
 
-// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row atoms of
-// 512 bytes (stride byte offset 512), descriptor version 1.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major operand without swizzling; core matrices of
+// 8 rows x 16 bytes, 2048 bytes apart along K (leading byte offset) and 128 bytes apart
+// along M/N (stride byte offset); descriptor version 1.
+__device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)(2048 >> 4) << 16;
+    d |= (uint64_t)(128 >> 4) << 32;
     d |= (uint64_t)1 << 46;
-    d |= (uint64_t)4 << 61;
     return d;
 }
 
@@ -144,7 +149,7 @@ template <>
 struct Recipe<GBE_PREC_FP16X6> {
     // slots: A {s0, s1, s2}, B {s0, s1, s1s, s2}; products into acc0: s0 s0^T,
     // into acc1 (units 2^-11): s0 s1^T, s1 s0^T, s1 s1s^T, s0 s2^T, s2 s0^T
-    static constexpr int kSlots = 7, kA = 3, kProducts = 6, kPlanes = 4, kStages = 3;
+    static constexpr int kSlots = 7, kA = 3, kProducts = 6, kPlanes = 4, kStages = 4;
     static constexpr uint32_t kType = 0;  // fp16
     static constexpr uint32_t kPlane = 0x2310210u, kAlias1 = 0x3021000u;
     static constexpr uint32_t kPa = 0x201100u, kPb = 0x365343u, kPacc = 0x111110u;
@@ -153,7 +158,7 @@ struct Recipe<GBE_PREC_FP16X6> {
 template <>
 struct Recipe<GBE_PREC_BF16X3> {
     // slots: A {hi, lo}, B {hi, lo}; products hi hi^T + hi lo^T + lo hi^T into acc0
-    static constexpr int kSlots = 4, kA = 2, kProducts = 3, kPlanes = 2, kStages = 4;
+    static constexpr int kSlots = 4, kA = 2, kProducts = 3, kPlanes = 2, kStages = 6;
     static constexpr uint32_t kType = 1;  // bf16
     static constexpr uint32_t kPlane = 0x1010u, kAlias1 = 0x2100u;
     static constexpr uint32_t kPa = 0x100u, kPb = 0x232u, kPacc = 0x0u;
@@ -166,9 +171,23 @@ template <class R> __device__ __forceinline__ int slot_alias(int s) { return nib
 template <int PREC>
 constexpr size_t smem_bytes() {
     using R = Recipe<PREC>;
-    return 1024 /*align slack*/ + (size_t)R::kStages * R::kSlots * kTileBytes + (size_t)R::kPlanes * 16 * 128 * 2 +
-           256 /*barriers, flags, reduction*/;
+    return 1024 /*align slack*/ + (size_t)R::kStages * R::kSlots * kTileBytes + 512 /*barriers, flags, reduction*/;
 }
+
+// Optional wait-time counters (build with -DGBE_TC_STATS): cycles each role spends in
+// barrier waits, summed over CTAs into a device array of 8 counters.
+#ifdef GBE_TC_STATS
+__device__ unsigned long long g_tc_stats[16];
+#define TC_T0() const long long _t0 = clock64()
+#define TC_ACC(i) (st_acc[i] += (unsigned long long)(clock64() - _t0))
+#define TC_FLUSH()                                                       \
+    for (int i_ = 0; i_ < 8; ++i_)                                       \
+        if (st_acc[i_]) atomicAdd(&g_tc_stats[i_], st_acc[i_])
+#else
+#define TC_T0()
+#define TC_ACC(i)
+#define TC_FLUSH()
+#endif
 
 struct TcArgs {
     Sp2Ctrl* ctrl;
@@ -204,8 +223,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* tiles = smem;                                          // NS * kSlots * 8 KB
-    uint16_t* stg = (uint16_t*)(tiles + (size_t)NS * R::kSlots * kTileBytes);  // kPlanes x 16 x 128
-    uint64_t* bars = (uint64_t*)((unsigned char*)stg + (size_t)R::kPlanes * 16 * 128 * 2);
+    uint64_t* bars = (uint64_t*)(tiles + (size_t)NS * R::kSlots * kTileBytes);
     uint64_t* full = bars;             // [NS]
     uint64_t* empty = bars + NS;       // [NS]
     uint64_t* tfull = bars + 2 * NS;   // [2]
@@ -214,17 +232,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tmem_holder = (uint32_t*)(bars + 2 * NS + 5);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
     int* hdr = (int*)(tmem_holder + 2);           // run, cur, branch
-    double* red = (double*)(bars + 2 * NS + 8);   // 8 doubles
+    double* red = (double*)(bars + 2 * NS + 8);   // 2 x 16 doubles (by tile parity)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Sp2Ctrl* ctrl = args.ctrl;
+#ifdef GBE_TC_STATS
+    const long long g_kernel_t0 = clock64();
+    unsigned long long st_acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#endif
     if (threadIdx.x == 0) {
         hdr[0] = (ctrl->stop == 0 && ctrl->mode == 0);
         hdr[1] = ctrl->cur;
         hdr[2] = ctrl->branch;
         *abort_flag = 0;
         for (int i = 0; i < NS; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 128); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 32 * kEpiWarps); }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -234,8 +256,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int cur = hdr[1], branch = hdr[2];
     const long long budget = ctrl->timeout_cycles;
     const CUtensorMap* tmap = cur ? &tmap1 : &tmap0;
-    const uint16_t* pin = args.planes[cur];
-    uint16_t* pout = args.planes[cur ^ 1];
+    const uint16_t* pin = cur ? args.planes[1] : args.planes[0];
+    uint16_t* pout = cur ? args.planes[0] : args.planes[1];
     const int64_t ps = args.ps;
 
     if (warp == 1) {
@@ -254,8 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            int issued_stage[NS], issued_parity[NS];
-            for (int i = 0; i < NS; ++i) issued_stage[i] = 0;
+            uint32_t issued_mask = 0, issued_par = 0;   // per stage: armed, and the parity it was armed with
             bool ok = true;
             for (int it = blockIdx.x; it < args.n_items && ok; it += gridDim.x) {
                 const TileItem w = args.items[it];
@@ -266,18 +287,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int nload = 0;
                 for (int sl = 0; sl < R::kSlots; ++sl) nload += !(diag && slot_alias<R>(sl) >= 0);
                 for (int kc = 0; kc < nk; ++kc) {
-                    if (!mbar_wait(&empty[stage], phase ^ 1, budget, abort_flag)) { ok = false; break; }
+                    bool got;
+                    {
+                        TC_T0();
+                        got = mbar_wait(&empty[stage], phase ^ 1, budget, abort_flag);
+                        TC_ACC(0);
+                    }
+                    if (!got) { ok = false; break; }
                     mbar_arrive_expect_tx(&full[stage], (uint32_t)(nload * kTileBytes));
-                    issued_stage[stage] = 1;
-                    issued_parity[stage] = phase;
+                    issued_mask |= 1u << stage;
+                    issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
                     unsigned char* st = tiles + (size_t)stage * R::kSlots * kTileBytes;
-                    const int x = (kc & 1) * 32;
                     for (int sl = 0; sl < R::kSlots; ++sl) {
                         if (diag && slot_alias<R>(sl) >= 0) continue;
                         const int Rt = (sl < R::kA) ? w.I : w.J;
-                        const int64_t y = (int64_t)slot_plane<R>(sl) * (ps >> 6) + (off >> 6) +
-                                          ((int64_t)(Rt * (mpad >> 6) + (kc >> 1)) << 7);
-                        tma_load_2d(st + (size_t)sl * kTileBytes, tmap, &full[stage], x, (int)y);
+                        // the chunk is 4 column groups of 1024 elements = 16 view rows of 256
+                        const int64_t y = ((int64_t)slot_plane<R>(sl) * (ps >> 10) + (off >> 10) +
+                                           (int64_t)Rt * (mpad >> 3) + 4 * kc) << 2;
+                        tma_load_2d(st + (size_t)sl * kTileBytes, tmap, &full[stage], 0, (int)y);
                     }
                     if (++stage == NS) { stage = 0; phase ^= 1; }
                 }
@@ -287,9 +314,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 atomicExch(&ctrl->status, GBE_ETIMEOUT);
                 // drain copies this thread issued so no TMA write lands after exit
                 for (int i = 0; i < NS; ++i)
-                    if (issued_stage[i]) {
+                    if (issued_mask & (1u << i)) {
                         const long long t0 = clock64();
-                        while (!mbar_try_wait(&full[i], issued_parity[i]) && clock64() - t0 < budget) {
+                        while (!mbar_try_wait(&full[i], (issued_par >> i) & 1u) && clock64() - t0 < budget) {
                         }
                     }
             }
@@ -305,15 +332,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             const uint32_t tiles_addr = smem_u32(tiles);
             for (int it = blockIdx.x; it < args.n_items && ok; it += gridDim.x) {
+#ifdef GBE_TC_STATS
+                const long long ts0 = clock64();
+#endif
                 const TileItem w = args.items[it];
                 const int m = args.g.m[w.s];
                 const int nk = (m + 31) >> 5;
                 const bool diag = (w.I == w.J);
-                if (!mbar_wait(&tempty[tb], tph ^ 1, budget, abort_flag)) { ok = false; break; }
+#ifdef GBE_TC_STATS
+                st_acc[6] += (unsigned long long)(clock64() - ts0);
+#endif
+                bool got;
+                {
+                    TC_T0();
+                    got = mbar_wait(&tempty[tb], tph ^ 1, budget, abort_flag);
+                    TC_ACC(1);
+                }
+                if (!got) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t dacc0 = tmem_base + (uint32_t)(tb * 256);
                 for (int kc = 0; kc < nk; ++kc) {
-                    if (!mbar_wait(&full[stage], phase, budget, abort_flag)) { ok = false; break; }
+                    {
+                        TC_T0();
+                        got = mbar_wait(&full[stage], phase, budget, abort_flag);
+                        TC_ACC(2);
+                    }
+                    if (!got) { ok = false; break; }
+#ifdef GBE_TC_STATS
+                    const long long ti0 = clock64();
+#endif
                     tc_fence_after();
                     const uint32_t sbase = tiles_addr + (uint32_t)(stage * R::kSlots * kTileBytes);
 #pragma unroll
@@ -323,8 +370,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const int a = nib(R::kPa, p), acc = nib(R::kPacc, p);
                             int b = nib(R::kPb, p);
                             if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);
-                            const uint64_t da = sdesc_sw64(sbase + a * kTileBytes + ks * 32);
-                            const uint64_t db = sdesc_sw64(sbase + b * kTileBytes + ks * 32);
+                            const uint64_t da = sdesc_kmajor(sbase + a * kTileBytes + ks * 4096);
+                            const uint64_t db = sdesc_kmajor(sbase + b * kTileBytes + ks * 4096);
                             // the first product into each accumulator overwrites it
                             bool first = (kc == 0 && ks == 0);
                             if (first) {
@@ -335,6 +382,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     umma_commit(&empty[stage]);
+#ifdef GBE_TC_STATS
+                    st_acc[7] += (unsigned long long)(clock64() - ti0);
+#endif
                     if (++stage == NS) { stage = 0; phase ^= 1; }
                 }
                 if (!ok) break;
@@ -353,53 +403,76 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // ------------------------------------------------------------ epilogue (warps 2..5)
-        const int q = warp & 3;
-        const int ew = warp - 2;
+        // ------------------------------------------------------------ epilogue (warps 2..9)
+        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        const int ew = warp - 2;                // 0..7
+        const int half = ew >> 2;               // column half of the tile
         const int a = 32 * q + lane;
         const uint32_t lane_addr = tmem_base + ((uint32_t)(32 * q) << 16);
+        constexpr int kXP = (R::kPlanes == 4) ? 3 : 2;   // planes of X_n the update reads
         int tb = 0;
         uint32_t tph = 0;
+        int par = 0;
         for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
             const TileItem w = args.items[it];
             const int mpad = args.g.mpad[w.s], c = args.g.c[w.s];
             const int64_t off = args.g.off[w.s];
-            const bool ok = mbar_wait(&tfull[tb], tph, budget, abort_flag);
-            // all four epilogue warps leave together, so no named barrier is left waiting
+            const int row = 128 * w.I + a;
+            const bool core_row = row < c;
+            const bool offdiag = (w.I != w.J);
+            // X_n of the first chunk, fetched before the accumulator is ready
+            uint32_t xn[kXP][8];
+            auto fetch_x = [&](int ch) {
+                const int64_t e = blk_index(off, mpad, row, 128 * w.J + 16 * ch);
+#pragma unroll
+                for (int p = 0; p < kXP; ++p) {
+                    const uint4 v0 = *reinterpret_cast<const uint4*>(pin + p * ps + e);
+                    const uint4 v1 = *reinterpret_cast<const uint4*>(pin + p * ps + e + 1024);
+                    xn[p][0] = v0.x; xn[p][1] = v0.y; xn[p][2] = v0.z; xn[p][3] = v0.w;
+                    xn[p][4] = v1.x; xn[p][5] = v1.y; xn[p][6] = v1.z; xn[p][7] = v1.w;
+                }
+            };
+            if (!branch) fetch_x(4 * half);
+            bool ok;
+            {
+                TC_T0();
+                ok = mbar_wait(&tfull[tb], tph, budget, abort_flag);
+                if (lane == 0) TC_ACC(3);
+            }
+            // all epilogue warps leave together, so no named barrier is left waiting
             if (epi_bar_any(!ok)) {
                 *abort_flag = 1;
                 atomicExch(&ctrl->status, GBE_ETIMEOUT);
                 break;
             }
             tc_fence_after();
-            const int row = 128 * w.I + a;
-            const bool core_row = row < c;
-            float sh = 0.f, sl = 0.f;
-            double t1 = 0.0;
-            for (int ch = 0; ch < 8; ++ch) {
+            float sh = 0.f, sl = 0.f, dP = 0.f, dQ = 0.f;
+            for (int cc = 0; cc < 4; ++cc) {
+                const int ch = 4 * half + cc;
                 const int col0 = 128 * w.J + 16 * ch;
                 uint32_t ra[16], rb[16];
                 tmem_ld16(lane_addr + (uint32_t)(tb * 256 + 16 * ch), ra);
                 if (R::kPlanes == 4) tmem_ld16(lane_addr + (uint32_t)(tb * 256 + 128 + 16 * ch), rb);
+                uint32_t xw[kXP][8];
+#pragma unroll
+                for (int p = 0; p < kXP; ++p)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) xw[p][k] = xn[p][k];
+                if (!branch && cc < 3) fetch_x(ch + 1);
                 tmem_wait_ld();
-                if (ch == 7) {
+                if (cc == 3) {
                     tc_fence_before();
                     mbar_arrive(&tempty[tb]);
                 }
-                const int64_t e0 = blk_index(off, mpad, row, col0);
-                uint16_t xv[3][16];
-                if (!branch) {
+                uint32_t ow[R::kPlanes][8];
 #pragma unroll
-                    for (int p = 0; p < (R::kPlanes == 4 ? 3 : 2); ++p) {
-                        const uint4* src = reinterpret_cast<const uint4*>(pin + p * ps + e0);
-                        uint4 v0 = src[0], v1 = src[1];
-                        memcpy(&xv[p][0], &v0, 16);
-                        memcpy(&xv[p][8], &v1, 16);
-                    }
-                }
-                uint16_t ov[R::kPlanes][16];
+                for (int p = 0; p < R::kPlanes; ++p)
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) ow[p][k] = 0u;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
+                    const int sh16 = 16 * (j & 1);
+#define XV(p) ((uint16_t)(xw[p][j >> 1] >> sh16))
                     const float A = __uint_as_float(ra[j]);
                     float P, Q;
                     if constexpr (PREC == GBE_PREC_FP16X6) {
@@ -408,71 +481,89 @@ __global__ void __launch_bounds__(kThreads, 1)
                             P = A;
                             Q = B * GBE_OZ_R_INV;
                         } else {
-                            const float s0 = h_val(xv[0][j]), s1 = h_val(xv[1][j]), s2 = h_val(xv[2][j]);
+                            const float s0 = h_val(XV(0)), s1 = h_val(XV(1)), s2 = h_val(XV(2));
                             P = 2.0f * s0 - A;
                             Q = (2.0f * (s1 + s2) - B) * GBE_OZ_R_INV;
                         }
                         const OzSplit o = oz_split_pq(P, Q);
-                        ov[0][j] = o.s0;
-                        ov[1][j] = o.s1;
-                        ov[2][j] = o.s2;
-                        ov[3][j] = o.s1s;
+                        ow[0][j >> 1] |= (uint32_t)o.s0 << sh16;
+                        ow[1][j >> 1] |= (uint32_t)o.s1 << sh16;
+                        ow[2][j >> 1] |= (uint32_t)o.s2 << sh16;
+                        ow[R::kPlanes - 1][j >> 1] |= (uint32_t)o.s1s << sh16;
                     } else {
-                        P = branch ? A : 2.0f * (b_val(xv[0][j]) + b_val(xv[1][j])) - A;
+                        P = branch ? A : 2.0f * (b_val(XV(0)) + b_val(XV(1))) - A;
                         Q = 0.0f;
                         const __nv_bfloat16 hi = __float2bfloat16_rn(P);
-                        ov[0][j] = b_bits(hi);
-                        ov[1][j] = b_bits(__float2bfloat16_rn(P - __bfloat162float(hi)));
+                        ow[0][j >> 1] |= (uint32_t)b_bits(hi) << sh16;
+                        ow[1][j >> 1] |= (uint32_t)b_bits(__float2bfloat16_rn(P - __bfloat162float(hi))) << sh16;
                     }
+#undef XV
                     const int colg = col0 + j;
-                    const float wgt = (float)((int)core_row + (int)((w.I != w.J) && colg < c));
+                    const float wgt = (float)((int)core_row + (int)(offdiag && colg < c));
                     if (wgt != 0.0f) df_add_sq(sh, sl, P, Q, wgt);
-                    if (colg == row && core_row) t1 += (double)P + (double)Q;
+                    const bool dg = (colg == row);
+                    dP = dg ? P : dP;
+                    dQ = dg ? Q : dQ;
                 }
+                const int64_t e0 = blk_index(off, mpad, row, col0);
 #pragma unroll
                 for (int p = 0; p < R::kPlanes; ++p) {
-                    uint4* dst = reinterpret_cast<uint4*>(pout + p * ps + e0);
-                    uint4 v0, v1;
-                    memcpy(&v0, &ov[p][0], 16);
-                    memcpy(&v1, &ov[p][8], 16);
-                    dst[0] = v0;
-                    dst[1] = v1;
+                    *reinterpret_cast<uint4*>(pout + p * ps + e0) = make_uint4(ow[p][0], ow[p][1], ow[p][2], ow[p][3]);
+                    *reinterpret_cast<uint4*>(pout + p * ps + e0 + 1024) = make_uint4(ow[p][4], ow[p][5], ow[p][6], ow[p][7]);
                 }
-                if (w.I != w.J) {
+                if (offdiag) {
+                    // mirror: lanes 2k and 2k+1 swap halves so that each writes two adjacent
+                    // rows' values (a = 2k, 2k+1) of one transposed row: even lanes take the
+                    // even column of every word, odd lanes the odd one
+                    const bool odd = lane & 1;
+                    const int64_t tbase = blk_index(off, mpad, 128 * w.J + 16 * ch, 128 * w.I + 32 * q + (lane & ~1));
 #pragma unroll
                     for (int p = 0; p < R::kPlanes; ++p)
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) stg[(p * 16 + j) * 128 + a] = ov[p][j];
-                    epi_bar();
-                    // transposed rows: (plane, j) pairs split over the 4 epilogue warps
-                    for (int pr = ew; pr < R::kPlanes * 16; pr += 4) {
-                        const int p = pr >> 4, j = pr & 15;
-                        const int trow = 128 * w.J + 16 * ch + j;
-                        const uint2 v = *reinterpret_cast<const uint2*>(&stg[(p * 16 + j) * 128 + 4 * lane]);
-                        *reinterpret_cast<uint2*>(pout + p * ps + blk_index(off, mpad, trow, 128 * w.I + 4 * lane)) = v;
-                    }
-                    epi_bar();
+                        for (int k = 0; k < 8; ++k) {
+                            const uint32_t mine = ow[p][k];
+                            const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                            // even lane: (own j=2k, partner j=2k) ; odd lane: (partner j=2k+1, own j=2k+1)
+                            const uint32_t v = odd ? ((other >> 16) | (mine & 0xffff0000u))
+                                                   : ((mine & 0xffffu) | (other << 16));
+                            const int jrow = 2 * k + (odd ? 1 : 0);
+                            *reinterpret_cast<uint32_t*>(pout + p * ps + tbase + ((int64_t)jrow << 3)) = v;
+                        }
                 }
             }
-            // partial traces of this tile: fixed-order reduction over the 128 threads
+            // partial traces of this tile: fixed-order reduction over the 256 threads
+            double t1 = (core_row && !offdiag && (row >> 7) == w.J && ((row & 127) >> 6) == half)
+                            ? (double)dP + (double)dQ : 0.0;
             double t2 = (double)sh + (double)sl;
             for (int o = 16; o > 0; o >>= 1) {
                 t1 += __shfl_xor_sync(0xffffffffu, t1, o);
                 t2 += __shfl_xor_sync(0xffffffffu, t2, o);
             }
-            if (lane == 0) { red[2 * ew] = t1; red[2 * ew + 1] = t2; }
+            double* rd = red + 16 * par;
+            if (lane == 0) { rd[2 * ew] = t1; rd[2 * ew + 1] = t2; }
             epi_bar();
             if (ew == 0 && lane == 0) {
-                args.partials[it] = ((red[0] + red[2]) + red[4]) + red[6];
-                args.partials[args.max_units + it] = ((red[1] + red[3]) + red[5]) + red[7];
+                double r1 = 0.0, r2 = 0.0;
+                for (int k = 0; k < kEpiWarps; ++k) { r1 += rd[2 * k]; r2 += rd[2 * k + 1]; }
+                args.partials[it] = r1;
+                args.partials[args.max_units + it] = r2;
             }
-            epi_bar();
+            par ^= 1;
+#ifdef GBE_TC_STATS
+            if (lane == 0) st_acc[4] += 1ull;
+#endif
             tb ^= 1;
             if (tb == 0) tph ^= 1;
         }
         tc_fence_before();
     }
+#ifdef GBE_TC_STATS
+    if (lane == 0) TC_FLUSH();
+#endif
     __syncthreads();
+#ifdef GBE_TC_STATS
+    if (threadIdx.x == 0) atomicAdd(&g_tc_stats[5], (unsigned long long)(clock64() - g_kernel_t0));
+#endif
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols) : "memory");
@@ -482,6 +573,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 PFN_cuTensorMapEncodeTiled_v12000 g_encode_tiled = nullptr;
 
 }  // namespace
+
+#ifdef GBE_TC_STATS
+extern "C" int gbe_tc_stats(unsigned long long* out, int reset) {
+    cudaMemcpyFromSymbol(out, g_tc_stats, sizeof(g_tc_stats));
+    if (reset) {
+        unsigned long long z[16] = {0};
+        cudaMemcpyToSymbol(g_tc_stats, z, sizeof(z));
+    }
+    return 0;
+}
+#endif
 
 int gbe_tc_prepare(gbe_ctx* ctx) {
     (void)ctx;
@@ -523,13 +625,15 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
     for (int side = 0; side < 2; ++side) {
         CUtensorMap m;
         memset(&m, 0, sizeof(m));
-        cuuint64_t dims[2] = {64, (cuuint64_t)(nplanes * X->total_elems / 64)};
-        cuuint64_t strides[1] = {128};
-        cuuint32_t box[2] = {32, 128};
+        // view: rows of 256 elements (512 B); a 32-column K-chunk of a row block is one
+        // contiguous 8 KB run = a 256 x 16 box, copied unchanged
+        cuuint64_t dims[2] = {256, (cuuint64_t)(nplanes * X->total_elems / 256)};
+        cuuint64_t strides[1] = {512};
+        cuuint32_t box[2] = {256, 16};
         cuuint32_t estr[2] = {1, 1};
         CUresult r = g_encode_tiled(&m, X->prec == GBE_PREC_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                                     2, X->planes[side], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             gbe_set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
