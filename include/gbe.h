@@ -275,6 +275,27 @@ int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, doub
 /* Copy the final dense x_s (m_s x m_s, row-major, FP64) of subgraph s to host. */
 int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out);
 
+/* ----------------------------------------------- allocation-free Gershgorin bounds */
+
+/* Gershgorin bounds of a device CSR H, computed without allocating any device memory.
+ * The paper has no counterpart; this is a library convenience for callers that must not
+ * call cudaMalloc -- for example code whose device memory is entirely owned by another
+ * allocator (a framework's memory pool with a fixed budget), or loops that cannot afford
+ * the implicit device synchronisation an allocation can cause.
+ *   bounds: caller-owned DEVICE memory for 2 doubles, receives {e_min, e_max} with
+ *           e_min = min_i H_ii - sum_{j!=i}|H_ij| and e_max = max_i H_ii + sum_{j!=i}|H_ij|
+ *           (the same values gbe_sp2_run uses); both NaN when H holds a NaN or Inf.
+ *   H:      device CSR (on_device = 1); 1 <= n <= 4,194,304 rows, else GBE_EINVAL with a
+ *           message naming the limit.
+ * Scratch: a fixed file-scope device array of 16384 per-block partials (about 256 KB),
+ * held by every GPU that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress, with the device
+ * current); make that first call before any stream capture.  Every call shares the one
+ * array and overwrites it, so calls that overlap on the GPU (different streams or
+ * contexts on the same device) race and must be serialised by the caller.
+ * Enqueues on the context stream and returns without synchronising. */
+int gbe_gershgorin_noalloc(gbe_ctx* ctx, const gbe_csr* H, double* bounds);
+
 #ifdef __cplusplus
 }
 #endif

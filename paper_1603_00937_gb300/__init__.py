@@ -33,7 +33,7 @@ EXPORTS = [
     "gbe_build_graph", "gbe_graph_size", "gbe_graph_export", "gbe_free_graph", "gbe_partition",
     "gbe_parts_info", "gbe_parts_export", "gbe_parts_import", "gbe_free_parts", "gbe_subs_create",
     "gbe_free_subs", "gbe_sp2_run", "gbe_sp2_report_get", "gbe_sp2_submatrices", "gbe_assemble_D",
-    "gbe_subs_export",
+    "gbe_subs_export", "gbe_gershgorin_noalloc",
 ]
 
 
@@ -128,7 +128,7 @@ def load_library(path=LIB_PATH):
         "gbe_subs_create": (I32, [P, P, I32, P]), "gbe_free_subs": (I32, [P]),
         "gbe_sp2_run": (I32, [P, P, P, P, P]), "gbe_sp2_report_get": (I32, [P, P, P]),
         "gbe_sp2_submatrices": (I32, [P, P, P, P, P, P]), "gbe_assemble_D": (I32, [P, P, P, D, P]),
-        "gbe_subs_export": (I32, [P, P, I64, P]),
+        "gbe_subs_export": (I32, [P, P, I64, P]), "gbe_gershgorin_noalloc": (I32, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -380,6 +380,13 @@ def sp2_submatrices(ctx, H, parts, params, X=None):
         X = Subs(ctx, h)
     check(code, "gbe_sp2_submatrices")
     return X, r.as_dict()
+
+
+def gershgorin_noalloc(ctx, H, bounds):
+    """Enqueue allocation-free Gershgorin bounds of device CSR H into bounds (device, 2 doubles)."""
+    check(load_library().gbe_gershgorin_noalloc(ctx.handle, ctypes.byref(H), _ptr(bounds)),
+          "gbe_gershgorin_noalloc")
+    return bounds
 
 
 def assemble_width(ctx, X, parts):
