@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(256) gershgorin_kernel(const int64_t* __restri
 }
 
 // ----------------------------------------------------------------------------- gather
-// One CTA per subgraph: row a of x_s is row idx_s[a] of H restricted to idx_s; local
-// column of a global column found by binary search in the sorted core and halo lists.
+// Local column of a global column: binary search in the sorted core list, then in the
+// sorted halo list.
 __device__ __forceinline__ int find_local(const int32_t* idx, int c, int m, int g) {
     int lo = 0, hi = c - 1;
     while (lo <= hi) {
@@ -101,19 +101,28 @@ __device__ __forceinline__ int find_local(const int32_t* idx, int c, int m, int 
     return -1;
 }
 
+// One CTA (8 warps) per subgraph, one warp per row at a time: lanes map the row's H
+// entries to local columns (binary search in the sorted core and halo lists), split them
+// and scatter them into the warp's dense row buffer in shared memory (4 split planes
+// packed in 8 bytes per column, or the FP64 value); then each lane writes whole 8-column
+// groups of the row to every plane (16 B per plane and group).  Every element of the
+// padded tile is written, zeros included, so the planes need no separate clear.
+template <int prec>
 __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_t* __restrict__ rowptr,
-                                                     const int32_t* __restrict__ col,
-                                                     const double* __restrict__ val,
+                                                     const int32_t* __restrict__ col, const double* __restrict__ val,
                                                      const int64_t* __restrict__ sub_ptr,
-                                                     const int32_t* __restrict__ sub_idx, SubsGeom g,
-                                                     int prec, uint16_t* planes, int64_t plane_stride,
-                                                     double* f, double* partials, int max_units) {
-    extern __shared__ int32_t sidx[];
-    __shared__ double red[8];
+                                                     const int32_t* __restrict__ sub_idx, SubsGeom g, int max_mpad,
+                                                     uint16_t* planes, int64_t plane_stride, double* f,
+                                                     double* partials, int max_units) {
+    extern __shared__ unsigned char gsm[];
+    __shared__ double red[16];
     const int s = blockIdx.x;
     const int m = g.m[s], c = g.c[s], mpad = g.mpad[s];
     const int64_t off = g.off[s];
     const int64_t base = sub_ptr[s];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint2* rowbuf = reinterpret_cast<uint2*>(gsm) + (size_t)warp * max_mpad;          // [8][max_mpad]
+    int32_t* sidx = reinterpret_cast<int32_t*>(gsm + (size_t)8 * max_mpad * 8);         // m_s local -> global
     for (int a = threadIdx.x; a < m; a += blockDim.x) sidx[a] = sub_idx[base + a];
     __syncthreads();
     double emin, emax;
@@ -121,41 +130,78 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     else { emin = dkey_inv(ctrl->eps_min_key); emax = dkey_inv(ctrl->eps_max_key); }
     const double range = emax - emin;
     const double inv_range = 1.0 / range;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double t1 = 0.0, t2 = 0.0;
-    for (int a = warp; a < m; a += 8) {
-        const int64_t gi = sidx[a];
-        for (int64_t p = rowptr[gi] + lane; p < rowptr[gi + 1]; p += 32) {
-            const int b = find_local(sidx, c, m, col[p]);
-            if (b < 0) continue;
-            const double h = val[p];
-            const int64_t e = blk_index(off, mpad, a, b);
-            // FP64 path: the exact quotient; split paths only need ~2^-35, so one FP64
-            // multiply and an FP32 pair (FP64 is a narrow pipe on this part)
-            const double x = (prec == GBE_PREC_FP64) ? ((a == b ? emax : 0.0) - h) / range
-                                                     : ((a == b ? emax : 0.0) - h) * inv_range;
-            if (prec == GBE_PREC_FP64) {
-                f[e] = x;
-            } else if (prec == GBE_PREC_FP16X6) {
-                const float xh = __double2float_rn(x);
-                OzSplit o = oz_split_pq(xh, __double2float_rn(x - (double)xh));
-                planes[e] = o.s0;
-                planes[e + plane_stride] = o.s1;
-                planes[e + 2 * plane_stride] = o.s2;
-                planes[e + 3 * plane_stride] = o.s1s;
-            } else {
-                __nv_bfloat16 hi = __double2bfloat16(x);
-                planes[e] = b_bits(hi);
-                planes[e + plane_stride] = b_bits(__double2bfloat16(x - (double)__bfloat162float(hi)));
-            }
-            if (a < c) {
-                t2 += x * x;
-                if (a == b) t1 += x;
+    for (int a = warp; a < mpad; a += 8) {
+        for (int b = lane; b < mpad; b += 32) rowbuf[b] = make_uint2(0u, 0u);
+        __syncwarp();
+        if (a < m) {
+            const int64_t gi = sidx[a];
+            for (int64_t p = rowptr[gi] + lane; p < rowptr[gi + 1]; p += 32) {
+                const int b = find_local(sidx, c, m, col[p]);
+                if (b < 0) continue;
+                const double h = val[p];
+                // FP64 path: the exact quotient, as the FP64 oracle computes it; split paths
+                // need ~2^-35: one FP64 multiply, then an integer-only split to FP32 pairs
+                double x;
+                if constexpr (prec == GBE_PREC_FP64) x = ((a == b ? emax : 0.0) - h) / range;
+                else x = ((a == b ? emax : 0.0) - h) * inv_range;
+                if (a < c) {
+                    t2 += x * x;
+                    if (a == b) t1 += x;
+                }
+                uint2 packed;
+                if constexpr (prec == GBE_PREC_FP64) {
+                    packed = make_uint2((uint32_t)__double2loint(x), (uint32_t)__double2hiint(x));
+                } else {
+                    float xh, xl;
+                    f64_to_f32_pair(x, xh, xl);
+                    if constexpr (prec == GBE_PREC_FP16X6) {
+                        const OzSplit o = oz_split_pq(xh, xl);
+                        packed = make_uint2((uint32_t)o.s0 | ((uint32_t)o.s1 << 16), (uint32_t)o.s2 | ((uint32_t)o.s1s << 16));
+                    } else {
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(xh);
+                        const uint16_t lo = b_bits(__float2bfloat16_rn((xh - __bfloat162float(hi)) + xl));
+                        packed = make_uint2((uint32_t)b_bits(hi) | ((uint32_t)lo << 16), 0u);
+                    }
+                }
+                rowbuf[b] = packed;
             }
         }
+        __syncwarp();
+        for (int gi8 = lane; gi8 < (mpad >> 3); gi8 += 32) {
+            const int c0 = gi8 << 3;
+            const int64_t e = blk_index(off, mpad, a, c0);
+            uint2 u[8];
+            const uint4* rb4 = reinterpret_cast<const uint4*>(rowbuf + c0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint4 v = rb4[k];
+                u[2 * k] = make_uint2(v.x, v.y);
+                u[2 * k + 1] = make_uint2(v.z, v.w);
+            }
+            if constexpr (prec == GBE_PREC_FP64) {
+                uint4* d = reinterpret_cast<uint4*>(f + e);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) d[k] = make_uint4(u[2 * k].x, u[2 * k].y, u[2 * k + 1].x, u[2 * k + 1].y);
+            } else {
+                uint32_t w[4][4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    w[0][k] = (u[2 * k].x & 0xffffu) | (u[2 * k + 1].x << 16);
+                    w[1][k] = (u[2 * k].x >> 16) | (u[2 * k + 1].x & 0xffff0000u);
+                    w[2][k] = (u[2 * k].y & 0xffffu) | (u[2 * k + 1].y << 16);
+                    w[3][k] = (u[2 * k].y >> 16) | (u[2 * k + 1].y & 0xffff0000u);
+                }
+                const int np = (prec == GBE_PREC_FP16X6) ? 4 : 2;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < np) *reinterpret_cast<uint4*>(planes + e + q * plane_stride) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            }
+        }
+        __syncwarp();
     }
     double s1 = block_sum_d<256>(t1, red);
-    double s2 = block_sum_d<256>(t2, red);
+    double s2 = block_sum_d<256>(t2, red + 8);
     if (threadIdx.x == 0) {
         partials[s] = s1;
         partials[max_units + s] = s2;
@@ -638,13 +684,13 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     cudaEventRecord(X->ev[0], st);
     if (!prm->eps_given) GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
     const int64_t ps = X->total_elems;
-    if (X->prec == GBE_PREC_FP64) GBE_CUDA_TRY(cudaMemsetAsync(X->f64[0], 0, ps * 8, st));
-    else GBE_CUDA_TRY(cudaMemsetAsync(X->planes[0], 0, 4 * ps * 2, st));
-    const size_t smem = (size_t)parts->max_m * 4;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    gather_kernel<<<(unsigned)X->P, 256, smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr,
-                                                      parts->d_sub_idx, geom_of(X), X->prec, X->planes[0], ps,
-                                                      X->f64[0], X->d_partials, X->max_units);
+    const size_t smem = (size_t)8 * X->max_mpad * 8 + (size_t)parts->max_m * 4;
+    auto gk = X->prec == GBE_PREC_FP64 ? gather_kernel<GBE_PREC_FP64>
+            : (X->prec == GBE_PREC_FP16X6 ? gather_kernel<GBE_PREC_FP16X6> : gather_kernel<GBE_PREC_BF16X3>);
+    cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    gk<<<(unsigned)X->P, 256, smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
+                                           geom_of(X), X->max_mpad, X->planes[0], ps, X->f64[0], X->d_partials,
+                                           X->max_units);
     GBE_CUDA_TRY(cudaGetLastError());
     decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, (int)X->P, 0);
     cudaEventRecord(X->ev[1], st);

@@ -201,6 +201,15 @@ struct TcArgs {
     int slot;
 };
 
+// Double-float sum (sh, sl) += (bh, bl) (TwoSum on the high parts).
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+    const float s = sh + bh;
+    const float bp = s - sh;
+    const float err = (sh - (s - bp)) + (bh - bp);
+    sh = s;
+    sl += err + bl;
+}
+
 // Double-float accumulation of w * (P + Q)^2 (FP64-grade traces from FP32 parts).
 __device__ __forceinline__ void df_add_sq(float& sh, float& sl, float P, float Q, float w) {
     const float p2 = P * P;
@@ -232,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* tmem_holder = (uint32_t*)(bars + 2 * NS + 5);
     volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
     int* hdr = (int*)(tmem_holder + 2);           // run, cur, branch
-    double* red = (double*)(bars + 2 * NS + 8);   // 2 x 16 doubles (by tile parity)
+    double* red = (double*)(bars + 2 * NS + 8);   // 2 x 32 floats (by tile parity)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Sp2Ctrl* ctrl = args.ctrl;
@@ -531,20 +540,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                 }
             }
-            // partial traces of this tile: fixed-order reduction over the 256 threads
-            double t1 = (core_row && !offdiag && (row >> 7) == w.J && ((row & 127) >> 6) == half)
-                            ? (double)dP + (double)dQ : 0.0;
-            double t2 = (double)sh + (double)sl;
+            // partial traces of this tile: FP32-pair (TwoSum) reduction in a fixed order over
+            // the warp, FP64 only for the final per-tile sum (FP64 is a narrow pipe here)
+            const bool has_diag = core_row && !offdiag && (row >> 7) == w.J && ((row & 127) >> 6) == half;
+            float d1h = has_diag ? dP : 0.f, d1l = has_diag ? dQ : 0.f;
             for (int o = 16; o > 0; o >>= 1) {
-                t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-                t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+                df_add(sh, sl, __shfl_xor_sync(0xffffffffu, sh, o), __shfl_xor_sync(0xffffffffu, sl, o));
+                df_add(d1h, d1l, __shfl_xor_sync(0xffffffffu, d1h, o), __shfl_xor_sync(0xffffffffu, d1l, o));
             }
-            double* rd = red + 16 * par;
-            if (lane == 0) { rd[2 * ew] = t1; rd[2 * ew + 1] = t2; }
+            float* rd = reinterpret_cast<float*>(red) + 32 * par;
+            if (lane == 0) { rd[4 * ew] = d1h; rd[4 * ew + 1] = d1l; rd[4 * ew + 2] = sh; rd[4 * ew + 3] = sl; }
             epi_bar();
             if (ew == 0 && lane == 0) {
                 double r1 = 0.0, r2 = 0.0;
-                for (int k = 0; k < kEpiWarps; ++k) { r1 += rd[2 * k]; r2 += rd[2 * k + 1]; }
+                for (int k = 0; k < kEpiWarps; ++k) {
+                    r1 += (double)rd[4 * k] + (double)rd[4 * k + 1];
+                    r2 += (double)rd[4 * k + 2] + (double)rd[4 * k + 3];
+                }
                 args.partials[it] = r1;
                 args.partials[args.max_units + it] = r2;
             }

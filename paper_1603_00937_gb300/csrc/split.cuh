@@ -45,19 +45,20 @@ __device__ __forceinline__ OzSplit oz_split_pq(float P, float Q) {
     return o;
 }
 
-// Split of an FP64 value (gather of X_0).
-__device__ __forceinline__ OzSplit oz_split_d(double x) {
-    double s0 = rint(x * 1024.0) * (1.0 / 1024.0);
-    double r1 = x - s0;
-    double t = r1 * 2048.0;
-    __half h1 = __double2half(t);
-    double rest = t - (double)__half2float(h1);
-    OzSplit o;
-    o.s0 = h_bits(__double2half(s0));
-    o.s1 = h_bits(h1);
-    o.s2 = h_bits(__double2half(rest));
-    o.s1s = h_bits(__double2half(r1));
-    return o;
+// x = hi + lo with hi = x truncated to a 24-bit significand (exact) and lo the remaining
+// 29 bits rounded to FP32 (|lo - (x - hi)| <= 2^-47 |x|), using integer operations only:
+// on this part FP64<->FP32 conversions run on the narrow FP64 pipe.  Values below 2^-60
+// in magnitude (irrelevant at the 2^-35 resolution of the splits) become 0.
+__device__ __forceinline__ void f64_to_f32_pair(double x, float& hi, float& lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const uint32_t sign = (uint32_t)(u >> 63) << 31;
+    const int e = (int)((u >> 52) & 0x7FF) - 1023;
+    if (e < -60) { hi = 0.0f; lo = 0.0f; return; }
+    const unsigned long long mant = u & 0xFFFFFFFFFFFFFull;
+    hi = __uint_as_float(sign | ((uint32_t)(e + 127) << 23) | (uint32_t)(mant >> 29));
+    const float l = (float)(uint32_t)(mant & 0x1FFFFFFFull);                  // units of 2^(e-52)
+    lo = l * __uint_as_float((uint32_t)(e - 52 + 127) << 23);
+    lo = sign ? -lo : lo;
 }
 
 __device__ __forceinline__ double oz_value(uint16_t s0, uint16_t s1, uint16_t s2) {
