@@ -137,7 +137,8 @@ struct gbe_subs {
     Sp2Ctrl* d_ctrl = nullptr;
     Sp2Ctrl* h_ctrl = nullptr;       // pinned
     // tensor maps for the split planes (opaque 128-byte CUtensorMap blobs)
-    alignas(64) unsigned char tmap[2][128];
+    alignas(64) unsigned char tmap[2][128];    // K-chunk view
+    alignas(64) unsigned char tmapT[2][128];   // transposed (lower-block) view
     bool tmap_ok = false;
     // phase timing
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -158,6 +159,11 @@ struct gbe_subs {
 // rows x 8 columns are 512 contiguous bytes.
 __host__ __device__ inline int64_t blk_index(int64_t off, int mpad, int r, int c) {
     return off + (int64_t)(r >> 7) * 128 * mpad + ((int64_t)(c >> 3) << 10) + ((r & 127) << 3) + (c & 7);
+}
+// Split planes hold only upper-triangular 128 x 128 blocks (the iterates are symmetric):
+// an element of a lower block is read from its mirror.
+__host__ __device__ inline int64_t sym_index(int64_t off, int mpad, int r, int c) {
+    return ((r >> 7) > (c >> 7)) ? blk_index(off, mpad, c, r) : blk_index(off, mpad, r, c);
 }
 
 // ----------------------------------------------------------------------------- launchers

@@ -168,7 +168,9 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
             }
         }
         __syncwarp();
-        for (int gi8 = lane; gi8 < (mpad >> 3); gi8 += 32) {
+        // split planes store only upper-triangular blocks; FP64 iterates are stored in full
+        const int gstart = (prec == GBE_PREC_FP64) ? 0 : 16 * (a >> 7);
+        for (int gi8 = gstart + lane; gi8 < (mpad >> 3); gi8 += 32) {
             const int c0 = gi8 << 3;
             const int64_t e = blk_index(off, mpad, a, c0);
             uint2 u[8];
@@ -298,8 +300,9 @@ __global__ void __launch_bounds__(512) decide_kernel(Sp2Ctrl* ctrl, const double
 // 64 x 64 output tiles (I <= J) of X_{n+1} = f(X_n) per subgraph, DFMA with register
 // blocking; the branch is applied in the epilogue and the tile is mirrored to (J, I).
 __device__ __forceinline__ double load_x(int fmt, int prec, const uint16_t* pl, int64_t ps, const double* f,
-                                         int64_t e) {
-    if (fmt == 1) return f[e];
+                                         int64_t off, int mpad, int r, int c) {
+    if (fmt == 1) return f[blk_index(off, mpad, r, c)];
+    const int64_t e = sym_index(off, mpad, r, c);
     if (prec == GBE_PREC_FP16X6) return oz_value(pl[e], pl[e + ps], pl[e + 2 * ps]);
     return bf_value(pl[e], pl[e + ps]);
 }
@@ -345,8 +348,8 @@ __global__ void __launch_bounds__(256) square_fp64_kernel(Sp2Ctrl* ctrl, SubsGeo
         auto fetch = [&](int k0) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                va[q] = load_x(fmt, prec, pin, plane_stride, fin, blk_index(off, mpad, ra, k0 + lk + q));
-                vb[q] = load_x(fmt, prec, pin, plane_stride, fin, blk_index(off, mpad, rb, k0 + lk + q));
+                va[q] = load_x(fmt, prec, pin, plane_stride, fin, off, mpad, ra, k0 + lk + q);
+                vb[q] = load_x(fmt, prec, pin, plane_stride, fin, off, mpad, rb, k0 + lk + q);
             }
         };
         fetch(0);
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(256) square_fp64_kernel(Sp2Ctrl* ctrl, SubsGeo
                 const int cc = w.J * 64 + tx + 16 * j;
                 const int64_t e = blk_index(off, mpad, r, cc);
                 double x = acc[i][j];
-                if (!branch) x = 2.0 * load_x(fmt, prec, pin, plane_stride, fin, e) - x;
+                if (!branch) x = 2.0 * load_x(fmt, prec, pin, plane_stride, fin, off, mpad, r, cc) - x;
                 fout[e] = x;
                 if (w.I != w.J) fout[blk_index(off, mpad, cc, r)] = x;
                 const int wgt = (r < c) + ((w.I != w.J) && (cc < c));
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
             double v = 0.0;
             int gk = -1;
             if (k < m) {
-                v = load_x(fmt, prec, pl, plane_stride, f, blk_index(off, mpad, j, k));
+                v = load_x(fmt, prec, pl, plane_stride, f, off, mpad, j, k);
                 gk = sub_idx[base + k];
             }
             const bool keep = (k < m) && !(drop_tol > 0.0 && fabs(v) < drop_tol);
@@ -461,7 +464,7 @@ __global__ void export_kernel(const Sp2Ctrl* ctrl, SubsGeom g, int s, const uint
     const double* f = cur ? f1 : f0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)m * m; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / m), cc = (int)(i % m);
-        out[i] = load_x(fmt, prec, pl, plane_stride, f, blk_index(off, mpad, r, cc));
+        out[i] = load_x(fmt, prec, pl, plane_stride, f, off, mpad, r, cc);
     }
 }
 

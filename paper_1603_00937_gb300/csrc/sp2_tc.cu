@@ -8,13 +8,13 @@
 //   warp 1  MMA issuer        : 128x128x16 tcgen05.mma per product and k-step into
 //                               two TMEM accumulators, double-buffered (4 x 128 cols)
 //   warps 2-9 epilogue        : TMEM -> registers, X_{n+1} = S or 2 X_n - S, split,
-//                               store tile and (off-diagonal tiles) its transpose,
-//                               partial traces of core rows; two warps per TMEM lane
+//                               store the tile, partial traces of core rows (counting the
+//                               implied mirror of off-diagonal tiles); two warps per TMEM lane
 //                               quarter, each taking half of the tile's columns.  X_n
-//                               values for the next chunk are fetched ahead, and the
-//                               transpose is done with warp shuffles (no CTA barriers).
-// Work items are upper-triangular output tiles (I <= J) of every subgraph; the
-// iterate is exactly symmetric because every off-diagonal tile is mirrored.
+//                               values for the next chunk are fetched ahead.
+// Only upper-triangular 128x128 blocks of each iterate are stored; a K-chunk that falls in
+// a lower block is loaded from the mirror block as a transposed (MN-major) operand tile.
+// Work items are upper-triangular output tiles (I <= J) of every subgraph.
 //
 // Every mbarrier wait is bounded by a clock budget; on expiry the CTA records
 // GBE_ETIMEOUT in the control block, stops issuing, drains what it issued (again
@@ -131,9 +131,19 @@ __device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
     d |= (uint64_t)1 << 46;
     return d;
 }
+// Same for an MN-major (transposed) operand tile [16 groups of 8 rows][32 k][8]: core
+// matrices 128 bytes apart along K (leading byte offset), 512 bytes apart along M/N.
+__device__ __forceinline__ uint64_t sdesc_mnmajor(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
 
 // Instruction descriptor of kind::f16: FP32 accumulator, A/B type (0 fp16, 1 bf16),
-// both K-major, N = 128, M = 128.
+// K-major operands (bits 15/16 select MN-major per operand), N = 128, M = 128.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type) {
     return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 }
@@ -226,6 +236,7 @@ __device__ __forceinline__ void df_add_sq(float& sh, float& sl, float P, float Q
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
     sp2_square_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1,
+                         const __grid_constant__ CUtensorMap tmapT0, const __grid_constant__ CUtensorMap tmapT1,
                          TcArgs args) {
     using R = Recipe<PREC>;
     constexpr int NS = R::kStages;
@@ -264,7 +275,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (blockIdx.x == 0 && threadIdx.x == 0) { ctrl->pending = 1; ctrl->slot_ran[args.slot] |= 1; }
     const int cur = hdr[1], branch = hdr[2];
     const long long budget = ctrl->timeout_cycles;
-    const CUtensorMap* tmap = cur ? &tmap1 : &tmap0;
+    const CUtensorMap* tmap = cur ? &tmap1 : &tmap0;      // K-chunks of stored (upper) blocks
+    const CUtensorMap* tmapT = cur ? &tmapT1 : &tmapT0;   // transposed K-chunks for lower blocks
     const uint16_t* pin = cur ? args.planes[1] : args.planes[0];
     uint16_t* pout = cur ? args.planes[0] : args.planes[1];
     const int64_t ps = args.ps;
@@ -310,10 +322,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int sl = 0; sl < R::kSlots; ++sl) {
                         if (diag && slot_alias<R>(sl) >= 0) continue;
                         const int Rt = (sl < R::kA) ? w.I : w.J;
-                        // the chunk is 4 column groups of 1024 elements = 16 view rows of 256
-                        const int64_t y = ((int64_t)slot_plane<R>(sl) * (ps >> 10) + (off >> 10) +
-                                           (int64_t)Rt * (mpad >> 3) + 4 * kc) << 2;
-                        tma_load_2d(st + (size_t)sl * kTileBytes, tmap, &full[stage], 0, (int)y);
+                        const int kb = kc >> 2;
+                        const int64_t g0 = (int64_t)slot_plane<R>(sl) * (ps >> 10) + (off >> 10);
+                        if (Rt <= kb) {
+                            // stored block (Rt, kb): 4 column groups of 1024 elements = 16 view rows of 256
+                            const int64_t y = (g0 + (int64_t)Rt * (mpad >> 3) + 4 * kc) << 2;
+                            tma_load_2d(st + (size_t)sl * kTileBytes, tmap, &full[stage], 0, (int)y);
+                        } else {
+                            // lower block: rows 32 (kc & 3).. of stored block (kb, Rt), its 16 column
+                            // groups -> [16 groups][32 rows][8], an MN-major operand tile
+                            const int64_t y = g0 + (int64_t)kb * (mpad >> 3) + 16 * Rt;
+                            tma_load_2d(st + (size_t)sl * kTileBytes, tmapT, &full[stage], 256 * (kc & 3), (int)y);
+                        }
                     }
                     if (++stage == NS) { stage = 0; phase ^= 1; }
                 }
@@ -372,6 +392,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 #endif
                     tc_fence_after();
                     const uint32_t sbase = tiles_addr + (uint32_t)(stage * R::kSlots * kTileBytes);
+                    const int kb = kc >> 2;
+                    const bool tA = w.I > kb, tB = w.J > kb;   // operand loaded transposed (MN-major)
+                    const uint32_t idesc_t = idesc | ((uint32_t)tA << 15) | ((uint32_t)tB << 16);
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
 #pragma unroll
@@ -379,15 +402,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                             const int a = nib(R::kPa, p), acc = nib(R::kPacc, p);
                             int b = nib(R::kPb, p);
                             if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);
-                            const uint64_t da = sdesc_kmajor(sbase + a * kTileBytes + ks * 4096);
-                            const uint64_t db = sdesc_kmajor(sbase + b * kTileBytes + ks * 4096);
+                            const uint32_t aa = sbase + a * kTileBytes, ba = sbase + b * kTileBytes;
+                            const uint64_t da = tA ? sdesc_mnmajor(aa + ks * 256) : sdesc_kmajor(aa + ks * 4096);
+                            const uint64_t db = tB ? sdesc_mnmajor(ba + ks * 256) : sdesc_kmajor(ba + ks * 4096);
                             // the first product into each accumulator overwrites it
                             bool first = (kc == 0 && ks == 0);
                             if (first) {
                                 for (int q = 0; q < p; ++q)
                                     if (nib(R::kPacc, q) == acc) first = false;
                             }
-                            umma_f16(dacc0 + acc * 128, da, db, idesc, first ? 0u : 1u);
+                            umma_f16(dacc0 + acc * 128, da, db, idesc_t, first ? 0u : 1u);
                         }
                     }
                     umma_commit(&empty[stage]);
@@ -520,25 +544,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     *reinterpret_cast<uint4*>(pout + p * ps + e0) = make_uint4(ow[p][0], ow[p][1], ow[p][2], ow[p][3]);
                     *reinterpret_cast<uint4*>(pout + p * ps + e0 + 1024) = make_uint4(ow[p][4], ow[p][5], ow[p][6], ow[p][7]);
                 }
-                if (offdiag) {
-                    // mirror: lanes 2k and 2k+1 swap halves so that each writes two adjacent
-                    // rows' values (a = 2k, 2k+1) of one transposed row: even lanes take the
-                    // even column of every word, odd lanes the odd one
-                    const bool odd = lane & 1;
-                    const int64_t tbase = blk_index(off, mpad, 128 * w.J + 16 * ch, 128 * w.I + 32 * q + (lane & ~1));
-#pragma unroll
-                    for (int p = 0; p < R::kPlanes; ++p)
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const uint32_t mine = ow[p][k];
-                            const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                            // even lane: (own j=2k, partner j=2k) ; odd lane: (partner j=2k+1, own j=2k+1)
-                            const uint32_t v = odd ? ((other >> 16) | (mine & 0xffff0000u))
-                                                   : ((mine & 0xffffu) | (other << 16));
-                            const int jrow = 2 * k + (odd ? 1 : 0);
-                            *reinterpret_cast<uint32_t*>(pout + p * ps + tbase + ((int64_t)jrow << 3)) = v;
-                        }
-                }
             }
             // partial traces of this tile: FP32-pair (TwoSum) reduction in a fixed order over
             // the warp, FP64 only for the final per-tile sum (FP64 is a narrow pipe here)
@@ -635,6 +640,25 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
     }
     const int nplanes = 4;
     for (int side = 0; side < 2; ++side) {
+        // transposed view: one 2 KB column group per view row; a box of 256 x 16 takes 32
+        // rows of 16 consecutive column groups
+        {
+            CUtensorMap m;
+            memset(&m, 0, sizeof(m));
+            cuuint64_t dims[2] = {1024, (cuuint64_t)(nplanes * X->total_elems / 1024)};
+            cuuint64_t strides[1] = {2048};
+            cuuint32_t box[2] = {256, 16};
+            cuuint32_t estr[2] = {1, 1};
+            CUresult r = g_encode_tiled(&m, X->prec == GBE_PREC_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                                        2, X->planes[side], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) {
+                gbe_set_error("cuTensorMapEncodeTiled (transposed view) failed (%d)", (int)r);
+                return GBE_ECUDA;
+            }
+            memcpy(X->tmapT[side], &m, sizeof(m));
+        }
         CUtensorMap m;
         memset(&m, 0, sizeof(m));
         // view: rows of 256 elements (512 B); a 32-column K-chunk of a row block is one
@@ -674,14 +698,16 @@ int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot) {
     a.partials = X->d_partials;
     a.max_units = X->max_units;
     a.slot = slot;
-    CUtensorMap m0, m1;
+    CUtensorMap m0, m1, t0, t1;
     memcpy(&m0, X->tmap[0], sizeof(m0));
     memcpy(&m1, X->tmap[1], sizeof(m1));
+    memcpy(&t0, X->tmapT[0], sizeof(t0));
+    memcpy(&t1, X->tmapT[1], sizeof(t1));
     const int grid = std::max(1, std::min(X->n_items_tc, ctx->sm_count));
     if (X->prec == GBE_PREC_FP16X6)
-        sp2_square_tc_kernel<GBE_PREC_FP16X6><<<grid, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(m0, m1, a);
+        sp2_square_tc_kernel<GBE_PREC_FP16X6><<<grid, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(m0, m1, t0, t1, a);
     else
-        sp2_square_tc_kernel<GBE_PREC_BF16X3><<<grid, kThreads, smem_bytes<GBE_PREC_BF16X3>(), ctx->stream>>>(m0, m1, a);
+        sp2_square_tc_kernel<GBE_PREC_BF16X3><<<grid, kThreads, smem_bytes<GBE_PREC_BF16X3>(), ctx->stream>>>(m0, m1, t0, t1, a);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }
