@@ -1,0 +1,68 @@
+"""Pins for the oracle's edge-classifier MLP: finite differences, closed forms, Adam."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import hamiltonian, mlp
+
+
+def small_batch(n=40, seed=0):
+    rng = np.random.default_rng(seed)
+    F = rng.normal(size=(n, mlp.NF))
+    y = (rng.uniform(size=n) < 0.4).astype(float)
+    return F, y
+
+
+def test_gradient_matches_central_differences():
+    h = 8
+    rng = np.random.default_rng(3)
+    p = rng.normal(0, 0.5, mlp.n_params(h))
+    F, y = small_batch()
+    _, g = mlp.loss_and_grad(p, F, y, h=h, rounded=False)
+    eps = 1e-6
+    for k in rng.choice(len(p), 40, replace=False):
+        d = np.zeros_like(p); d[k] = eps
+        lp = mlp.bce_loss(mlp.forward(p + d, F, h, rounded=False), y)
+        lm = mlp.bce_loss(mlp.forward(p - d, F, h, rounded=False), y)
+        assert abs((lp - lm) / (2 * eps) - g[k]) < 1e-7 * max(1.0, abs(g[k]))
+
+
+def test_bias_only_network_closed_form():
+    h = 8
+    p = np.zeros(mlp.n_params(h))
+    p[-1] = 0.7                       # b3
+    F, y = small_batch()
+    z = mlp.forward(p, F, h, rounded=False)
+    assert np.all(z == 0.7)
+    loss, g = mlp.loss_and_grad(p, F, y, h=h, rounded=False)
+    assert loss == pytest.approx(np.log1p(np.exp(0.7)) - 0.7 * y.mean(), rel=1e-14)
+    assert g[-1] == pytest.approx(1 / (1 + np.exp(-0.7)) - y.mean(), rel=1e-14)
+    assert np.all(g[:-1] == 0.0)
+    assert mlp.bce_loss(np.zeros(5), np.array([0, 1, 0, 1, 1.0])) == pytest.approx(np.log(2.0), rel=1e-15)
+
+
+def test_first_adam_step_is_sign_step():
+    g = np.array([3.0, -2e-3, 0.5, -7.0])
+    p, m, v = mlp.adam_step(np.zeros(4), g, np.zeros(4), np.zeros(4), 1, lr=0.01, eps=0.0)
+    np.testing.assert_allclose(p, -0.01 * np.sign(g), rtol=1e-12)
+
+
+def test_fp16_rounding_of_weights():
+    p = np.array([1.0 + 2 ** -11, 0.1, 65504.0], dtype=np.float32)
+    r = mlp.fp16_round(p)
+    assert r[0] == 1.0 and r[2] == 65504.0 and abs(r[1] - 0.1) < 1e-4
+
+
+def test_pairs_and_features_symmetric():
+    w = synth.disordered(300, seed=4)
+    H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
+    I, J, R = mlp.candidate_pairs(w["pos"], w["box"], 2.0)
+    assert np.all(I != J) and np.all(R < 2.0)
+    fwd = dict(zip(zip(I, J), range(len(I))))
+    assert all((j, i) in fwd for i, j in zip(I, J))
+    F = mlp.features(H, w["onsite"], I, J, R, 2.0)
+    back = np.array([fwd[(j, i)] for i, j in zip(I, J)])
+    np.testing.assert_allclose(F, F[back], rtol=1e-14, atol=0)
+    # a pair inside the 2.5 a hopping range has its hopping as first feature
+    k = np.argmin(R)
+    assert F[k, 0] == pytest.approx(-np.log10(abs(H[I[k], J[k]])) / 12.0, rel=1e-12)
