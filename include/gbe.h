@@ -275,6 +275,53 @@ int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, doub
 /* Copy the final dense x_s (m_s x m_s, row-major, FP64) of subgraph s to host. */
 int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out);
 
+/* ------------------------------------------------ learned graph proposal (a9) */
+
+/* A small classifier proposes the data-dependency graph when no prior density matrix
+ * exists (not in the paper, whose graphs come from a prior D, Sec. II.A/II.C).
+ * Candidate pairs are all i != j with minimum-image distance r_ij < rcand; each pair has
+ * features f = [-log10(max(|H_ij|,1e-12))/12, -log10(max(|(H^2)_ij|,1e-12))/12,
+ * r_ij/rcand, min(e_i,e_j), max(e_i,e_j)] (float32, symmetric in i and j; e = onsite).
+ * Network: h1 = relu(W1 f + b1), h2 = relu(W2 h1 + b2), logit = w3.h2 + b3, width 64,
+ * fp16-rounded weights and FP32 arithmetic.  Parameters (4609 float32): W1[64x5],
+ * b1[64], W2[64x64] (row = output), b2[64], w3[64], b3.  Training minimises the mean
+ * binary cross-entropy with logits (label 1 when |D_ij| >= tau) with Adam on the fp32
+ * master copy; gradients are reduced in a fixed order (run-to-run identical). */
+typedef struct gbe_pairs gbe_pairs;
+
+/* Candidate pairs and features on the device (rows ordered by i, then j ascending).
+ * sites and H may be host or device.  GBE_ECAPACITY above 1024 candidates per site;
+ * GBE_EINVAL unless box > 2 rcand.  Synchronises. */
+int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* sites, const gbe_csr* H, double rcand, gbe_pairs** pairs);
+int gbe_pairs_info(const gbe_pairs* pairs, int64_t* n, int64_t* npairs);
+/* Host copies: rowptr[n+1] (int64), j[npairs] (int32), features[npairs*5] (float32); NULL skips. */
+int gbe_pairs_export(gbe_ctx* ctx, const gbe_pairs* pairs, int64_t* rowptr, int32_t* j, float* features);
+/* Library-owned device arrays of the pairs (valid until gbe_free_pairs); NULL skips. */
+int gbe_pairs_device(const gbe_pairs* pairs, const int64_t** rowptr, const int32_t** j, const float** features);
+int gbe_free_pairs(gbe_pairs* pairs);
+
+/* Network with zero parameters (hidden must be 64); set them with gbe_mlp_set_params. */
+int gbe_mlp_create(gbe_ctx* ctx, int hidden, gbe_mlp** mlp);
+int gbe_mlp_param_count(const gbe_mlp* mlp);
+/* host_params: gbe_mlp_param_count floats; also resets the Adam moments and step count. */
+int gbe_mlp_set_params(gbe_ctx* ctx, gbe_mlp* mlp, const float* host_params);
+int gbe_mlp_get_params(gbe_ctx* ctx, const gbe_mlp* mlp, float* host_params);
+/* logits: device float[npairs].  Enqueue only. */
+int gbe_mlp_forward(gbe_ctx* ctx, const gbe_mlp* mlp, const gbe_pairs* pairs, float* logits);
+/* Mean BCE loss and its gradient at the current parameters; labels: device uint8[npairs]
+ * (0/1).  loss (host, nullable) and grad_host (host float[param_count], nullable) are
+ * written after a synchronisation.  The gradient stays on the device for the next
+ * gbe_mlp_adam_step. */
+int gbe_mlp_gradient(gbe_ctx* ctx, gbe_mlp* mlp, const gbe_pairs* pairs, const uint8_t* labels, double* loss,
+                     float* grad_host);
+/* One bias-corrected Adam step with the last gradient.  Enqueue only. */
+int gbe_mlp_adam_step(gbe_ctx* ctx, gbe_mlp* mlp, float lr, float beta1, float beta2, float eps);
+/* epochs x (gradient + Adam(lr, 0.9, 0.999, 1e-8)) on the device; final_loss (host,
+ * nullable) is the mean loss of the last epoch before its update.  Synchronises. */
+int gbe_mlp_train(gbe_ctx* ctx, gbe_mlp* mlp, const gbe_pairs* pairs, const uint8_t* labels, int epochs, float lr,
+                  double* final_loss);
+int gbe_free_mlp(gbe_mlp* mlp);
+
 /* ----------------------------------------------- allocation-free Gershgorin bounds */
 
 /* Gershgorin bounds of a device CSR H, computed without allocating any device memory.

@@ -15,12 +15,16 @@ the graph.  This module is the plain FP64 statement of that network:
   loss        mean binary cross-entropy with logits, label y = 1 when |D_ij| >= tau
   optimiser   Adam (bias-corrected), applied to the fp32 master parameters with the
               gradient taken at the fp16-rounded weights
+  graph       pairs with logit >= cut, united with the pattern of H, symmetrised, plus the
+              diagonal
 
 Parameter vector layout (4609 for width 64): W1 [64x5] row-major, b1 [64], W2 [64x64]
 row-major (out x in), b2 [64], w3 [64], b3 [1].
 """
 import numpy as np
 import scipy.sparse as sp
+
+from . import graph
 
 NF = 5
 HIDDEN = 64
@@ -56,11 +60,13 @@ def fp16_round(p):
     return np.asarray(p, dtype=np.float32).astype(np.float16).astype(np.float64)
 
 
-def candidate_pairs(pos, box, rcand):
-    """All ordered pairs (i, j), i != j, with minimum-image distance < rcand; sorted by (i, j)."""
+def candidate_pairs(pos, box, rcand, rows=None):
+    """All ordered pairs (i, j), i != j, with minimum-image distance < rcand; sorted by (i, j).
+
+    rows: optional ascending subset of i (all rows by default)."""
     N = len(pos)
     I, J, R = [], [], []
-    for i in range(N):
+    for i in (range(N) if rows is None else rows):
         d = pos[i][None, :] - pos
         d = d - box * np.round(d / box)
         r = np.sqrt(np.einsum("ij,ij->i", d, d))
@@ -70,11 +76,13 @@ def candidate_pairs(pos, box, rcand):
 
 
 def features(H, onsite, I, J, R, rcand):
-    """Feature matrix [npairs, 5] (FP64)."""
+    """Feature matrix [npairs, 5] (FP64).
+
+    (H^2)_ij = sum_k H_ik H_kj is taken as the dot product of rows i and j (H is
+    symmetric), so H may hold only the rows of the sites the pairs touch."""
     H = sp.csr_matrix(H)
-    H2 = (H @ H).tocsr()
     hij = np.asarray(H[I, J]).ravel()
-    h2ij = np.asarray(H2[I, J]).ravel()
+    h2ij = np.asarray(H[I].multiply(H[J]).sum(axis=1)).ravel()
     f = np.empty((len(I), NF))
     f[:, 0] = -np.log10(np.maximum(np.abs(hij), 1e-12)) / 12.0
     f[:, 1] = -np.log10(np.maximum(np.abs(h2ij), 1e-12)) / 12.0
@@ -130,3 +138,12 @@ def labels(D, I, J, tau):
     """y = 1 where |D_ij| >= tau (D dense or sparse)."""
     D = sp.csr_matrix(D)
     return (np.abs(np.asarray(D[I, J]).ravel()) >= tau).astype(np.float64)
+
+
+def graph_from_logits(H, I, J, z, cut):
+    """Proposed graph: candidate pairs with logit z >= cut, united with the pattern of H,
+    symmetrised, with the diagonal (boolean CSR)."""
+    N = H.shape[0]
+    keep = np.asarray(z) >= cut
+    E = sp.csr_matrix((np.ones(int(keep.sum()), dtype=bool), (I[keep], J[keep])), shape=(N, N))
+    return graph._finish(E + graph.pattern(H))

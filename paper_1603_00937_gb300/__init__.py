@@ -33,7 +33,9 @@ EXPORTS = [
     "gbe_build_graph", "gbe_graph_size", "gbe_graph_export", "gbe_free_graph", "gbe_partition",
     "gbe_parts_info", "gbe_parts_export", "gbe_parts_import", "gbe_free_parts", "gbe_subs_create",
     "gbe_free_subs", "gbe_sp2_run", "gbe_sp2_report_get", "gbe_sp2_submatrices", "gbe_assemble_D",
-    "gbe_subs_export", "gbe_gershgorin_noalloc",
+    "gbe_subs_export", "gbe_gershgorin_noalloc", "gbe_pairs_build", "gbe_pairs_info", "gbe_pairs_export", "gbe_pairs_device",
+    "gbe_free_pairs", "gbe_mlp_create", "gbe_mlp_param_count", "gbe_mlp_set_params", "gbe_mlp_get_params",
+    "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_free_mlp",
 ]
 
 
@@ -129,6 +131,14 @@ def load_library(path=LIB_PATH):
         "gbe_sp2_run": (I32, [P, P, P, P, P]), "gbe_sp2_report_get": (I32, [P, P, P]),
         "gbe_sp2_submatrices": (I32, [P, P, P, P, P, P]), "gbe_assemble_D": (I32, [P, P, P, D, P]),
         "gbe_subs_export": (I32, [P, P, I64, P]), "gbe_gershgorin_noalloc": (I32, [P, P, P]),
+        "gbe_pairs_build": (I32, [P, P, P, D, P]), "gbe_pairs_info": (I32, [P, P, P]),
+        "gbe_pairs_export": (I32, [P, P, P, P, P]), "gbe_free_pairs": (I32, [P]),
+        "gbe_pairs_device": (I32, [P, P, P, P]),
+        "gbe_mlp_create": (I32, [P, I32, P]), "gbe_mlp_param_count": (I32, [P]),
+        "gbe_mlp_set_params": (I32, [P, P, P]), "gbe_mlp_get_params": (I32, [P, P, P]),
+        "gbe_mlp_forward": (I32, [P, P, P, P]), "gbe_mlp_gradient": (I32, [P, P, P, P, P, P]),
+        "gbe_mlp_adam_step": (I32, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+        "gbe_mlp_train": (I32, [P, P, P, P, I32, ctypes.c_float, P]), "gbe_free_mlp": (I32, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -420,3 +430,80 @@ def ell_to_dense(col, val, n):
     m = col >= 0
     D[col[m], rows[m]] = val[m]
     return D
+
+
+# ----------------------------------------------------------------------------- learned graph proposal
+class Pairs(_Owned):
+    _free = "gbe_free_pairs"
+
+    def info(self):
+        n, npairs = ctypes.c_int64(), ctypes.c_int64()
+        check(load_library().gbe_pairs_info(self._h, ctypes.byref(n), ctypes.byref(npairs)), "gbe_pairs_info")
+        return n.value, npairs.value
+
+    def export(self):
+        """(rowptr[n+1], j[npairs], features[npairs, 5]) as NumPy arrays."""
+        n, npairs = self.info()
+        rp = np.zeros(n + 1, dtype=np.int64)
+        j = np.zeros(max(npairs, 1), dtype=np.int32)
+        f = np.zeros((max(npairs, 1), 5), dtype=np.float32)
+        check(load_library().gbe_pairs_export(self.ctx.handle, self._h, _ptr(rp), _ptr(j), _ptr(f)), "gbe_pairs_export")
+        return rp, j[:npairs], f[:npairs]
+
+    def device(self):
+        """(rowptr, j, features) device addresses (library-owned, valid while this object lives)."""
+        rp, j, f = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        check(load_library().gbe_pairs_device(self._h, ctypes.byref(rp), ctypes.byref(j), ctypes.byref(f)),
+              "gbe_pairs_device")
+        return rp.value, j.value, f.value
+
+
+class Mlp(_Owned):
+    _free = "gbe_free_mlp"
+
+    @property
+    def param_count(self):
+        return load_library().gbe_mlp_param_count(self._h)
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.param_count
+        check(load_library().gbe_mlp_set_params(self.ctx.handle, self._h, _ptr(p)), "gbe_mlp_set_params")
+
+    def get_params(self):
+        p = np.zeros(self.param_count, dtype=np.float32)
+        check(load_library().gbe_mlp_get_params(self.ctx.handle, self._h, _ptr(p)), "gbe_mlp_get_params")
+        return p
+
+    def forward(self, pairs, logits):
+        check(load_library().gbe_mlp_forward(self.ctx.handle, self._h, pairs.handle, _ptr(logits)), "gbe_mlp_forward")
+        return logits
+
+    def gradient(self, pairs, labels):
+        loss = ctypes.c_double()
+        g = np.zeros(self.param_count, dtype=np.float32)
+        check(load_library().gbe_mlp_gradient(self.ctx.handle, self._h, pairs.handle, _ptr(labels), ctypes.byref(loss),
+                                              _ptr(g)), "gbe_mlp_gradient")
+        return loss.value, g
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        check(load_library().gbe_mlp_adam_step(self.ctx.handle, self._h, lr, beta1, beta2, eps), "gbe_mlp_adam_step")
+
+    def train(self, pairs, labels, epochs, lr):
+        loss = ctypes.c_double()
+        check(load_library().gbe_mlp_train(self.ctx.handle, self._h, pairs.handle, _ptr(labels), int(epochs),
+                                           float(lr), ctypes.byref(loss)), "gbe_mlp_train")
+        return loss.value
+
+
+def pairs_build(ctx, site_struct, H, rcand):
+    h = ctypes.c_void_p()
+    check(load_library().gbe_pairs_build(ctx.handle, ctypes.byref(site_struct), ctypes.byref(H), float(rcand),
+                                         ctypes.byref(h)), "gbe_pairs_build")
+    return Pairs(ctx, h)
+
+
+def mlp_create(ctx, hidden=64):
+    h = ctypes.c_void_p()
+    check(load_library().gbe_mlp_create(ctx.handle, int(hidden), ctypes.byref(h)), "gbe_mlp_create")
+    return Mlp(ctx, h)

@@ -14,78 +14,14 @@
 #include <cstring>
 
 #include "gbe_internal.h"
+#include "devutil.cuh"
+
+using namespace gbe_dev;
 
 namespace {
 
 constexpr int kHashCap = 8192;   // hash-set capacity of one row / core set (ints)
 constexpr int kSetMax = 4096;    // largest set a CTA sorts and emits
-
-// ------------------------------------------------------------------ scan (exclusive, int32 -> int64)
-constexpr int kScanThreads = 1024, kScanItems = 4;
-constexpr int kScanBlock = kScanThreads * kScanItems;
-
-__device__ int64_t block_exclusive_scan(int64_t v, int64_t* sh, int64_t* total) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    int64_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) sh[w] = x;
-    __syncthreads();
-    if (w == 0) {
-        int64_t s = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0;
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t y = __shfl_up_sync(0xffffffffu, s, o);
-            if (lane >= o) s += y;
-        }
-        sh[lane] = s;
-    }
-    __syncthreads();
-    const int64_t base = (w > 0) ? sh[w - 1] : 0;
-    if (total) *total = sh[(blockDim.x >> 5) - 1];
-    const int64_t r = base + x - v;
-    __syncthreads();
-    return r;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_local_kernel(const int32_t* __restrict__ in, int64_t* out,
-                                                                  int64_t n, int64_t* bsum) {
-    __shared__ int64_t sh[32];
-    const int64_t base = (int64_t)blockIdx.x * kScanBlock + (int64_t)threadIdx.x * kScanItems;
-    int64_t v[kScanItems], s = 0;
-    for (int i = 0; i < kScanItems; ++i) {
-        v[i] = (base + i < n) ? in[base + i] : 0;
-        s += v[i];
-    }
-    int64_t tot;
-    int64_t ex = block_exclusive_scan(s, sh, &tot);
-    for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < n) out[base + i] = ex;
-        ex += v[i];
-    }
-    if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_top_kernel(int64_t* bsum, int nb, int64_t* total) {
-    __shared__ int64_t sh[32];
-    int64_t carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += kScanThreads) {
-        const int i = b0 + threadIdx.x;
-        const int64_t v = (i < nb) ? bsum[i] : 0;
-        int64_t tot;
-        const int64_t ex = block_exclusive_scan(v, sh, &tot);
-        if (i < nb) bsum[i] = carry + ex;
-        carry += tot;
-    }
-    if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void scan_add_kernel(int64_t* out, int64_t n, const int64_t* bsum, const int64_t* total) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] += bsum[i / kScanBlock];
-    if (i == n) out[n] = *total;
-}
 
 // ------------------------------------------------------------------ shared-memory hash set
 __device__ __forceinline__ unsigned hslot(int v) { return ((unsigned)v * 2654435761u) >> (32 - 13); }  // 8192 slots
@@ -168,36 +104,6 @@ __device__ bool hset_expand(int* table, int* count, int* list, int* cursor, int*
 }
 
 // ------------------------------------------------------------------ Hamiltonian
-struct CellGrid {
-    int nc[3];
-    double box[3];
-};
-
-__device__ __forceinline__ int cell_of(const double* p, const CellGrid& g) {
-    int c[3];
-    for (int d = 0; d < 3; ++d) {
-        int v = (int)floor(p[d] / g.box[d] * g.nc[d]);
-        c[d] = min(max(v, 0), g.nc[d] - 1);
-    }
-    return (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
-}
-
-__global__ void cell_count_kernel(const double* __restrict__ pos, int64_t n, CellGrid g, int32_t* cell, int32_t* cnt) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = cell_of(pos + 3 * i, g);
-    cell[i] = c;
-    atomicAdd(&cnt[c], 1);
-}
-
-__global__ void cell_fill_kernel(const int32_t* __restrict__ cell, int64_t n, const int64_t* __restrict__ start,
-                                 int32_t* cursor, int32_t* members) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int c = cell[i];
-    members[start[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
-}
-
 // Sort the members of each cell ascending (cells are small; one warp per cell).
 __global__ void cell_sort_kernel(const int64_t* __restrict__ start, int ncells, int32_t* members) {
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -213,11 +119,6 @@ __global__ void cell_sort_kernel(const int64_t* __restrict__ start, int ncells, 
         }
         __syncwarp();
     }
-}
-
-__device__ __forceinline__ double min_image(double d, double L) { return __dsub_rn(d, __dmul_rn(L, rint(d / L))); }
-__device__ __forceinline__ double dist3(double x, double y, double z) {
-    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
 }
 
 struct HModel {
@@ -300,21 +201,6 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
 }
 
 // ------------------------------------------------------------------ graph row sets
-// Deterministic sparse dot product of two sorted CSR rows (ascending column order,
-// separate multiply and add).
-__device__ double row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ va,
-                          int i, int j) {
-    int64_t p = rp[i], pe = rp[i + 1], q = rp[j], qe = rp[j + 1];
-    double s = 0.0;
-    while (p < pe && q < qe) {
-        const int a = ci[p], b = ci[q];
-        if (a == b) { s = __dadd_rn(s, __dmul_rn(va[p], va[q])); ++p; ++q; }
-        else if (a < b) ++p;
-        else ++q;
-    }
-    return s;
-}
-
 struct RowSetSmem {
     int table[kHashCap];
     int list[kHashCap];
@@ -525,44 +411,7 @@ __global__ void iota_blocks_kernel(int64_t n, int32_t* members) {
 }
 
 // ------------------------------------------------------------------ host helpers
-struct DevBuf {
-    void* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
-    template <class T> T* as() { return (T*)p; }
-};
-
-int scan_exclusive(gbe_ctx* ctx, const int32_t* in, int64_t* out, int64_t n, int64_t* total_host) {
-    const int nb = (int)((n + kScanBlock - 1) / kScanBlock);
-    DevBuf bs;
-    GBE_TRY(gbe_alloc(&bs.p, (size_t)(nb + 1) * 8));
-    int64_t* tot = bs.as<int64_t>() + nb;
-    if (n > 0) scan_local_kernel<<<nb, kScanThreads, 0, ctx->stream>>>(in, out, n, bs.as<int64_t>());
-    scan_top_kernel<<<1, kScanThreads, 0, ctx->stream>>>(bs.as<int64_t>(), nb, tot);
-    scan_add_kernel<<<(unsigned)((n + 1 + 255) / 256), 256, 0, ctx->stream>>>(out, n, bs.as<int64_t>(), tot);
-    GBE_CUDA_TRY(cudaGetLastError());
-    if (total_host) {
-        GBE_CUDA_TRY(cudaMemcpyAsync(total_host, tot, 8, cudaMemcpyDeviceToHost, ctx->stream));
-        GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    }
-    return GBE_OK;
-}
-
-int read_flag(gbe_ctx* ctx, const int* d, int* h) {
-    GBE_CUDA_TRY(cudaMemcpyAsync(h, d, 4, cudaMemcpyDeviceToHost, ctx->stream));
-    GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-    return GBE_OK;
-}
-
 size_t rowset_smem() { return sizeof(RowSetSmem); }
-
-// Copy an array to the device when it is on the host.
-int to_device(gbe_ctx* ctx, const void* src, size_t bytes, int on_device, DevBuf& hold, const void** out) {
-    if (on_device) { *out = src; return GBE_OK; }
-    GBE_TRY(gbe_alloc(&hold.p, bytes));
-    GBE_CUDA_TRY(cudaMemcpyAsync(hold.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
-    *out = hold.p;
-    return GBE_OK;
-}
 
 // Build a CSR whose row i is produced by rowset_kernel (count, scan, fill).
 int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thresh, const int64_t* s1rp,
@@ -696,7 +545,7 @@ extern "C" int gbe_free_graph(gbe_graph* S) {
     return GBE_OK;
 }
 
-int gbe_graph_mlp_edges(gbe_ctx* ctx, const gbe_csr* H, const gbe_graph_params* p, int64_t** rp, int32_t** ci);
+int gbe_graph_mlp_select(gbe_ctx* ctx, const gbe_csr* H, const gbe_graph_params* p, int64_t** rp, int32_t** ci);
 
 extern "C" int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* Hin, const gbe_graph_params* p, gbe_graph** out) {
     GBE_CHECK_ARG(ctx && Hin && p && out, "NULL argument");
@@ -763,15 +612,20 @@ extern "C" int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* Hin, const gbe_graph
             S->hops = eq8 ? 2 : 1;
             break;
         }
-        case GBE_GRAPH_MLP:
-            r = gbe_graph_mlp_edges(ctx, &H, p, &S->rowptr, &S->col);
-            if (r == GBE_OK) {
-                int64_t nnz = 0;
-                cudaMemcpy(&nnz, S->rowptr + n, 8, cudaMemcpyDeviceToHost);
-                S->nnz = nnz;
-            }
+        case GBE_GRAPH_MLP: {
+            // pairs the network keeps (a symmetric set: features are symmetric in i, j),
+            // united with the pattern of H and the diagonal
+            int64_t* srp = nullptr;
+            int32_t* sci = nullptr;
+            r = gbe_graph_mlp_select(ctx, &H, p, &srp, &sci);
+            if (r == GBE_OK)
+                r = rowset_csr(ctx, 1, n, nullptr, 0.0, srp, sci, H.rowptr, H.col, nullptr, nullptr, 1, &S->rowptr,
+                               &S->col, &S->nnz);
+            cudaFree(srp);
+            cudaFree(sci);
             S->hops = 1;
             break;
+        }
         default:
             gbe_set_error("unknown graph mode %d", p->mode);
             r = GBE_EINVAL;
@@ -912,8 +766,3 @@ extern "C" int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partiti
     return GBE_OK;
 }
 
-// Learned graph proposals are built in mlp.cu; without it the mode is rejected.
-__attribute__((weak)) int gbe_graph_mlp_edges(gbe_ctx*, const gbe_csr*, const gbe_graph_params*, int64_t**, int32_t**) {
-    gbe_set_error("MLP graph mode not available in this build");
-    return GBE_EINVAL;
-}

@@ -1,6 +1,7 @@
 """Pins for the oracle's edge-classifier MLP: finite differences, closed forms, Adam."""
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import synth
 from oracle import hamiltonian, mlp
@@ -66,3 +67,61 @@ def test_pairs_and_features_symmetric():
     # a pair inside the 2.5 a hopping range has its hopping as first feature
     k = np.argmin(R)
     assert F[k, 0] == pytest.approx(-np.log10(abs(H[I[k], J[k]])) / 12.0, rel=1e-12)
+
+
+@pytest.mark.parametrize("rcand,count", [(1.5, 18), (1.9, 26), (2.1, 32), (2.3, 56)])
+def test_candidate_pairs_simple_cubic_shells(rcand, count):
+    # unjittered simple-cubic lattice: neighbour shells at 1, sqrt2, sqrt3, 2, sqrt5 hold
+    # 6, 12, 8, 6, 24 sites
+    w = synth.lattice(6, jitter=0.0)
+    I, J, R = mlp.candidate_pairs(w["pos"], w["box"], rcand)
+    assert np.all(np.bincount(I, minlength=216) == count)
+
+
+def test_candidate_pairs_row_subset():
+    w = synth.disordered(400, seed=9)
+    I, J, R = mlp.candidate_pairs(w["pos"], w["box"], 2.2)
+    rows = np.array([0, 17, 18, 250, 399])
+    Is, Js, Rs = mlp.candidate_pairs(w["pos"], w["box"], 2.2, rows=rows)
+    m = np.isin(I, rows)
+    np.testing.assert_array_equal(Is, I[m])
+    np.testing.assert_array_equal(Js, J[m])
+    np.testing.assert_array_equal(Rs, R[m])
+
+
+def test_graph_from_logits_limits_and_example():
+    w = synth.disordered(300, seed=4)
+    H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
+    I, J, R = mlp.candidate_pairs(w["pos"], w["box"], 3.0)
+    z = np.linspace(-1.0, 1.0, len(I))
+    # nothing kept: the pattern of H (which stores its diagonal)
+    G = mlp.graph_from_logits(H, I, J, z, np.inf)
+    assert (G != (H != 0)).nnz == 0
+    # everything kept: the whole candidate ball (a superset of the 2.5 a hopping range)
+    G = mlp.graph_from_logits(H, I, J, z, -np.inf)
+    ball = np.zeros((300, 300), dtype=bool)
+    ball[I, J] = True
+    np.fill_diagonal(ball, True)
+    np.testing.assert_array_equal(G.toarray(), ball)
+    # a single kept pair (i, j) outside the hopping range adds both (i, j) and (j, i)
+    k = int(np.argmax(R))
+    zk = np.full(len(I), -5.0)
+    zk[k] = 0.5
+    G = mlp.graph_from_logits(H, I, J, zk, 0.0)
+    extra = G.toarray() & ~(H != 0).toarray()
+    assert set(zip(*np.nonzero(extra))) == {(I[k], J[k]), (J[k], I[k])}
+
+
+def test_h2_feature_equals_matrix_square():
+    # the row-dot-product form of (H^2)_ij against the explicit sparse product, and
+    # against rows-only H (all other rows empty)
+    w = synth.disordered(500, seed=11)
+    H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
+    I, J, R = mlp.candidate_pairs(w["pos"], w["box"], 3.5, rows=np.arange(0, 500, 7))
+    F = mlp.features(H, w["onsite"], I, J, R, 3.5)
+    H2 = (H @ H).toarray()
+    h2 = H2[I, J]
+    np.testing.assert_allclose(F[:, 1], -np.log10(np.maximum(np.abs(h2), 1e-12)) / 12.0, rtol=1e-13, atol=1e-15)
+    keep = np.union1d(I, J)
+    Hr = sp.csr_matrix(H.toarray() * np.isin(np.arange(500), keep)[:, None])
+    np.testing.assert_array_equal(mlp.features(Hr, w["onsite"], I, J, R, 3.5), F)
