@@ -275,6 +275,30 @@ int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, doub
 /* Copy the final dense x_s (m_s x m_s, row-major, FP64) of subgraph s to host. */
 int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out);
 
+/* ------------------------------------------------ pre-determined branch sequences */
+
+/* Sec. II.C: in an MD run the SP2 sequence (shared by every subgraph) is fixed in advance
+ * from a HOMO-LUMO gap estimated at the previous step, so that the expansions exchange no
+ * traces.  Host-only functions (no context, no GPU).
+ *
+ * gbe_sp2_gap_estimate: HOMO/LUMO estimates (energy units of H) from a finished run's report
+ * (its traces t1/t2, branch sequence and spectral bounds).  The last step k with idempotency
+ * error t1[k]-t2[k] in [e_lo, e_hi] is modelled as two unconverged levels, the HOMO image
+ * x_h and the LUMO image x_l (t1-t2 = x_h(1-x_h) + x_l(1-x_l), t1-n_occ = x_l-(1-x_h)), which
+ * the inverse branch maps carry back to step 0.  Needs 0 < e_lo < e_hi < 0.5.  GBE_EINVAL when
+ * no step lies in the window; GBE_ENUMERIC when the traces admit no such pair.  Reliable only
+ * when the run reaches that two-level regime (dense or well-converged graph runs). */
+int gbe_sp2_gap_estimate(const gbe_sp2_report* rep, double n_occ, double e_lo, double e_hi, double* homo,
+                         double* lumo);
+
+/* Branch sequence (seq[i] = 1 for X^2, 0 for 2X-X^2; *len entries written) that drives every
+ * eigenvalue <= homo within tol of 1 and every eigenvalue >= lumo within tol of 0 in the
+ * scaled variable x = (eps_max - e)/(eps_max - eps_min): the branch rule applied to the
+ * two-level matrix diag(x_homo, x_lumo) with one occupied level.  seq: caller-owned, n_max
+ * (<= GBE_SEQ_MAX) bytes.  GBE_ENOCONV when n_max steps do not suffice. */
+int gbe_sp2_sequence(double eps_min, double eps_max, double homo, double lumo, double tol, int n_max, uint8_t* seq,
+                     int* len);
+
 /* ------------------------------------------------ learned graph proposal (a9) */
 
 /* A small classifier proposes the data-dependency graph when no prior density matrix

@@ -199,3 +199,48 @@ def chebyshev_graph(X, subs, coeffs):
         p = chebyshev_dense(x, coeffs)[:, 0]
         rows.append(idx); cols.append(np.full(len(idx), idx[0])); vals.append(p)
     return sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
+
+
+# ---------------------------------------------------------------- pre-determined sequences
+# Sec. II.C: in the MD run every step's branch sequence is fixed beforehand from a HOMO-LUMO
+# gap estimated at the previous step.  Readings (the cited estimator is not printed):
+#  * the estimate models a late SP2 step as two unconverged levels, the HOMO image x_h (near
+#    1) and the LUMO image x_l (near 0), every other level being converged:
+#        Tr X_k - Tr X_k^2 = x_h (1 - x_h) + x_l (1 - x_l),   Tr X_k - N_occ = (x_h - 1) + x_l,
+#    solved for (x_h, x_l) and mapped back through the inverse branch maps to eigenvalues;
+#  * the sequence applies the branch rule above to the two-level matrix diag(x_h, x_l) with
+#    one occupied level, until both are within tol of 1 and 0.
+def gap_estimate(t1, t2, seq, n_occ, eps, e_lo, e_hi):
+    """(homo, lumo) from the traces of a finished run; uses the last step whose idempotency
+    error lies in [e_lo, e_hi]."""
+    ks = [k for k in range(min(len(t1), len(t2))) if e_lo <= t1[k] - t2[k] <= e_hi]
+    if not ks:
+        raise ValueError("no step with idempotency error in range")
+    k = ks[-1]
+    e, d = t1[k] - t2[k], t1[k] - n_occ
+    # substitute x_l = d + 1 - x_h into the first equation: a quadratic in x_h
+    c = d + 1.0
+    roots = np.roots([-2.0, 2.0 * c, c - c * c - e])
+    xh = float(max(r.real for r in roots if abs(r.imag) < 1e-12))
+    xl = c - xh
+    for b in reversed(seq[:k]):
+        if b:
+            xh, xl = np.sqrt(xh), np.sqrt(xl)
+        else:
+            xh, xl = 1.0 - np.sqrt(1.0 - xh), 1.0 - np.sqrt(1.0 - xl)
+    e_min, e_max = eps
+    return e_max - xh * (e_max - e_min), e_max - xl * (e_max - e_min)
+
+
+def sequence_from_gap(eps, homo, lumo, tol, n_max=256):
+    e_min, e_max = eps
+    xh = (e_max - homo) / (e_max - e_min)
+    xl = (e_max - lumo) / (e_max - e_min)
+    seq = []
+    while not (1.0 - xh <= tol and xl <= tol):
+        if len(seq) == n_max:
+            raise RuntimeError("sequence longer than n_max")
+        b = choose_square(xh + xl, xh * xh + xl * xl, 1.0)
+        xh, xl = (xh * xh, xl * xl) if b else (2 * xh - xh * xh, 2 * xl - xl * xl)
+        seq.append(int(b))
+    return seq

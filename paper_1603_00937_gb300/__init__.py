@@ -36,6 +36,7 @@ EXPORTS = [
     "gbe_subs_export", "gbe_gershgorin_noalloc", "gbe_pairs_build", "gbe_pairs_info", "gbe_pairs_export", "gbe_pairs_device",
     "gbe_free_pairs", "gbe_mlp_create", "gbe_mlp_param_count", "gbe_mlp_set_params", "gbe_mlp_get_params",
     "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_free_mlp",
+    "gbe_sp2_gap_estimate", "gbe_sp2_sequence",
 ]
 
 
@@ -139,6 +140,7 @@ def load_library(path=LIB_PATH):
         "gbe_mlp_forward": (I32, [P, P, P, P]), "gbe_mlp_gradient": (I32, [P, P, P, P, P, P]),
         "gbe_mlp_adam_step": (I32, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
         "gbe_mlp_train": (I32, [P, P, P, P, I32, ctypes.c_float, P]), "gbe_free_mlp": (I32, [P]),
+        "gbe_sp2_gap_estimate": (I32, [P, D, D, D, P, P]), "gbe_sp2_sequence": (I32, [D, D, D, D, D, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -390,6 +392,30 @@ def sp2_submatrices(ctx, H, parts, params, X=None):
         X = Subs(ctx, h)
     check(code, "gbe_sp2_submatrices")
     return X, r.as_dict()
+
+
+def sp2_gap_estimate(report, n_occ, e_lo=1e-6, e_hi=1e-2):
+    """(homo, lumo) from a report dict (iters, eps, seq, t1, t2) of a finished run."""
+    r = Sp2Report()
+    r.iters = int(report["iters"])
+    r.eps_min, r.eps_max = report["eps"]
+    for i, b in enumerate(report["seq"]):
+        r.seq[i] = int(b)
+    for i, (a, b) in enumerate(zip(report["t1"], report["t2"])):
+        r.t1[i], r.t2[i] = a, b
+    homo, lumo = ctypes.c_double(), ctypes.c_double()
+    check(load_library().gbe_sp2_gap_estimate(ctypes.byref(r), float(n_occ), float(e_lo), float(e_hi),
+                                              ctypes.byref(homo), ctypes.byref(lumo)), "gbe_sp2_gap_estimate")
+    return homo.value, lumo.value
+
+
+def sp2_sequence(eps, homo, lumo, tol, n_max=SEQ_MAX):
+    """Branch sequence (list of 0/1) that converges a gap [homo, lumo] within tol."""
+    buf = (ctypes.c_uint8 * SEQ_MAX)()
+    n = ctypes.c_int()
+    check(load_library().gbe_sp2_sequence(float(eps[0]), float(eps[1]), float(homo), float(lumo), float(tol),
+                                          int(n_max), ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(n)), "gbe_sp2_sequence")
+    return list(buf[:n.value])
 
 
 def gershgorin_noalloc(ctx, H, bounds):
