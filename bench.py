@@ -34,12 +34,30 @@ METRIC = "SP2 density-matrix orbitals/s and tensor TFLOP/s, mixed vs FP64 at max
 UNIT = "orbitals/s"
 WORKLOADS = {
     # the configuration the metric is quoted on: 32^3 lattice, cores of 64, m_s ~ 460-480
-    "lattice32": dict(L=32, seed=0, thresh=0.15, ncell=(8, 8, 8)),
+    "lattice32": dict(kind="lattice", L=32, seed=0, thresh=0.15, ncell=(8, 8, 8)),
     # small case (8^3, |H^2| >= 1e-5 graph, cores of 8, m_s ~ 470-510)
-    "lattice8": dict(L=8, seed=0, thresh=1e-5, ncell=(4, 4, 4)),
+    "lattice8": dict(kind="lattice", L=8, seed=0, thresh=1e-5, ncell=(4, 4, 4)),
     # 16^3 slice of the 32^3 workload (same m_s distribution, 64 subgraphs): profiling case
-    "lattice16": dict(L=16, seed=0, thresh=0.15, ncell=(4, 4, 4)),
+    "lattice16": dict(kind="lattice", L=16, seed=0, thresh=0.15, ncell=(4, 4, 4)),
+    # disordered liquid-like system: 131072 uniform random sites (box 50.8a), cores of ~60
+    # sites from 13^3 cells, |H^2| >= 0.1 halos: uneven m_s over several 128-wide buckets
+    "disordered131k": dict(kind="disordered", N=131072, seed=0, thresh=0.1, ncell=(13, 13, 13), n_max=80),
+    # 4096-site sample of the same model (box 16a, 4^3 cells): profiling / oracle sample
+    "disordered4k": dict(kind="disordered", N=4096, seed=0, thresh=0.1, ncell=(4, 4, 4), n_max=80),
+    # QMD-like run on the 32^3 lattice: positions advance by N(0, 0.01a) per step, the graph
+    # comes from the previous step's |D| >= 1e-2 (first step: |H^2| >= 0.15), the SP2
+    # sequence is the previous step's, replayed (no trace exchange during a step)
+    "qmd32": dict(kind="lattice", L=32, seed=0, thresh=0.15, ncell=(8, 8, 8), qmd=True, tau=1e-2),
 }
+PRECS = {"fp16x6": ("FP16X6", "f16-split(x6)/f32-acc/f64-trace"),
+         "bf16x3": ("BF16X3", "bf16-split(x3)/f32-acc/f64-trace")}
+
+
+def make_system(wl, seed):
+    import synth
+    if wl["kind"] == "lattice":
+        return synth.lattice(wl["L"], seed=seed)
+    return synth.disordered(wl["N"], seed=seed)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -110,12 +128,12 @@ def dist_env():
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
-def oracle_sample(L, seed, thresh, ncell):
-    """The oracle's graph SP2 on an L^3 sample of the same lattice model; returns
-    (orbitals, seconds of gather + SP2 + assembly, iterations)."""
-    import synth
+def oracle_sample(wl):
+    """The oracle's graph SP2 on a sample workload; returns (orbitals, seconds of gather +
+    SP2 + assembly, iterations)."""
     from oracle import graph, hamiltonian, partition, sp2
-    w = synth.lattice(L, seed=seed)
+    w = make_system(wl, wl["seed"])
+    thresh, ncell = wl["thresh"], wl["ncell"]
     H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
     N = H.shape[0]
     S = graph.h2_threshold(H, thresh)
@@ -138,12 +156,12 @@ def run_reference(args):
     if rank != 0:
         return
     # each step: the oracle on a 12^3 sample (27 core sets of the 32^3 workload's shape)
-    L = 12
+    wl = dict(kind="lattice", L=12, seed=0, thresh=0.15, ncell=(3, 3, 3))
     for _ in range(args.warmup):
-        oracle_sample(L, 0, 0.15, (3, 3, 3))
+        oracle_sample(wl)
     ts, its = [], []
     for _ in range(args.steps):
-        N, dt, it = oracle_sample(L, 0, 0.15, (3, 3, 3))
+        N, dt, it = oracle_sample(wl)
         ts.append(dt)
         its.append(it)
     value = N * len(ts) / sum(ts)
@@ -158,6 +176,117 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- QMD-like run
+def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
+    """MD steps of the lattice: every step rebuilds H from the new positions, the graph from
+    the previous step's D, the partition, the SP2 state, runs SP2 with the previous step's
+    branch sequence replayed, and assembles D (the next step's graph input).  A step's
+    inputs are the positions, copied in from pinned host memory; its output read back is
+    the SP2 report.  Timed: the whole step, wall clock, K steps after W warm-up steps."""
+    import synth
+    prec_name, dtype_name = PRECS[args.prec]
+    PREC = getattr(gbe, "PREC_" + prec_name)
+    w = make_system(wl, wl["seed"] + rank)
+    N = w["pos"].shape[0]
+    vel = synth.velocities(N, seed=1 + rank)
+    box = w["box"]
+    ons = torch.from_numpy(w["onsite"]).cuda()
+    pos_h = torch.empty((N, 3), dtype=torch.float64).pin_memory()
+    pos_d = torch.empty((N, 3), dtype=torch.float64, device="cuda")
+    state = {"D": None, "seq": None}
+    phase = {k: 0.0 for k in ("h_build", "graph", "partition", "sp2_state", "sp2", "assemble")}
+    last = {}
+
+    def step(t, timed):
+        def mark(name, t0):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if timed:
+                phase[name] += t1 - t0
+            return t1
+        t0 = time.perf_counter()
+        pos_h.numpy()[:] = synth.advance(w["pos"], vel, box, t)
+        pos_d.copy_(pos_h, non_blocking=True)
+        st = gbe.sites(pos_d, ons, box)
+        Hg = gbe.build_hamiltonian(ctx, st)
+        t0 = mark("h_build", t0)
+        if state["D"] is None:
+            G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_H2_THRESH, thresh=wl["thresh"])
+        else:
+            G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_D_THRESH, thresh=wl["tau"], D_prev=state["D"])
+        t0 = mark("graph", t0)
+        parts = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=wl["ncell"], site_struct=st)
+        P, total, max_m = parts.info()
+        t0 = mark("partition", t0)
+        X = gbe.subs_create(ctx, parts, PREC)
+        col = torch.empty((N, max_m), dtype=torch.int32, device="cuda")
+        val = torch.empty((N, max_m), dtype=torch.float64, device="cuda")
+        t0 = mark("sp2_state", t0)
+        prm = gbe.sp2_params(N / 2.0, prec=PREC, n_max=64, n_min=10, idem_tol=1e-10, seq=state["seq"],
+                             fp64_tail=args.fp64_tail)
+        gbe.sp2_run(ctx, Hg.csr(), parts, prm, X)
+        rep = gbe.sp2_report_get(ctx, X).as_dict()
+        t0 = mark("sp2", t0)
+        gbe.assemble_D(ctx, X, parts, col, val)
+        mark("assemble", t0)
+        if state["seq"] is None:
+            state["seq"] = rep["seq"]
+        state["D"] = gbe.ell_struct(col, val)
+        cc, sptr, _ = parts.export()
+        last.update(rep=rep, ms=np.diff(sptr), P=P, cc=cc)
+
+    W = max(args.warmup, 3)
+    for t in range(W):
+        step(t, False)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_start = time.perf_counter()
+    for t in range(W, W + args.steps):
+        step(t, True)
+    torch.cuda.synchronize()
+    total = time.perf_counter() - t_start
+    clk = clocks.stop()
+    if world > 1:
+        tt = torch.tensor([total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total = float(tt.item())
+    rep, ms = last["rep"], last["ms"]
+    peaks, peak_kind = load_peaks()
+    tc_ms = rep["ms_tc"] / max(1, rep["n_tc"])
+    mixed = max(1, rep["iters"] - rep["fp64_iters"])
+    achieved = rep["mma_flops"] / mixed / (tc_ms / 1000.0) / 1e12 if tc_ms > 0 else None
+    peak = float(peaks["bf16_tflops"])
+    value = N * world * args.steps / total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": W,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, "L": wl["L"], "md_steps_timed": args.steps,
+                   "graph": "first step |H^2|>=%g, then |D_prev|>=%g" % (wl["thresh"], wl["tau"]),
+                   "branch": "previous step's sequence replayed", "sp2_iters": rep["iters"],
+                   "precision": prec_name, "fp64_tail": args.fp64_tail, "cores": int(last["P"]),
+                   "m_s_min": int(ms.min()), "m_s_median": float(np.median(ms)), "m_s_max": int(ms.max()),
+                   "l2": "inputs larger than L2 (GB-scale split planes); no flush",
+                   "timing": "wall clock over whole MD steps (H build, graph, partition, SP2 state, SP2, "
+                             "assembly), positions copied in from pinned host memory each step"},
+        "phase_ms_per_step": {k: 1000.0 * v / args.steps for k, v in phase.items()},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "kernel": "sp2_square_tc_kernel<%s>" % prec_name,
+                     "peak_kind": peak_kind + " dense bf16/fp16 burst", "ms_per_launch": tc_ms},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": N * 24, "d2h_bytes_per_step": 4616},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
 # ----------------------------------------------------------------------------- GPU leg
 def main():
     ap = argparse.ArgumentParser()
@@ -170,6 +299,7 @@ def main():
     ap.add_argument("--fp64-tail", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--prec", default="fp16x6", choices=sorted(PRECS))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -179,7 +309,6 @@ def main():
     import torch.distributed as dist
 
     import paper_1603_00937_gb300 as gbe
-    import synth
 
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -189,10 +318,13 @@ def main():
     stream = torch.cuda.current_stream().cuda_stream
     ctx = gbe.Context(local, stream)
     ctx.set_profiling(True)
+    if wl.get("qmd"):
+        run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world)
+        return
 
     # ---------------------------------------------------------------- set-up (timed apart)
     t_setup = time.perf_counter()
-    w = synth.lattice(wl["L"], seed=wl["seed"] + rank)
+    w = make_system(wl, wl["seed"] + rank)
     N = w["pos"].shape[0]
     pos = torch.from_numpy(w["pos"]).cuda()
     ons = torch.from_numpy(w["onsite"]).cuda()
@@ -212,7 +344,7 @@ def main():
     val_m = torch.empty((n, width), dtype=torch.float64, device="cuda")
     col_d = torch.empty_like(col_m)
     val_d = torch.empty_like(val_m)
-    n_max = 48
+    n_max = wl.get("n_max", 48)
 
     def params(prec, seq=None):
         return gbe.sp2_params(N / 2.0, prec=prec, n_max=n_max, n_min=10, idem_tol=1e-10,
@@ -239,8 +371,10 @@ def main():
             ms = float(t.item())
         return ms, gbe.sp2_report_get(ctx, X).as_dict()
 
-    Xm = gbe.subs_create(ctx, parts, gbe.PREC_FP16X6)
-    pm = params(gbe.PREC_FP16X6)
+    prec_name, dtype_name = PRECS[args.prec]
+    PREC = getattr(gbe, "PREC_" + prec_name)
+    Xm = gbe.subs_create(ctx, parts, PREC)
+    pm = params(PREC)
     clocks = ClockSampler(local)
     clocks.start()
     ms_m, rep_m = timed(Xm, pm, col_m, val_m, args.steps, max(args.warmup, 3))
@@ -253,7 +387,7 @@ def main():
         seq_equal = rep_d["seq"] == rep_m["seq"]
         dD_free = float((val_m - val_d).abs().max().item()) if torch.equal(col_m, col_d) else float("nan")
         # same branch sequence for the precision comparison: replay the FP64 run's sequence
-        gbe.sp2_run(ctx, Hv, parts, params(gbe.PREC_FP16X6, seq=rep_d["seq"]), Xm)
+        gbe.sp2_run(ctx, Hv, parts, params(PREC, seq=rep_d["seq"]), Xm)
         gbe.assemble_D(ctx, Xm, parts, col_m, val_m)
         torch.cuda.synchronize()
         dD = float((val_m - val_d).abs().max().item())
@@ -308,22 +442,25 @@ def main():
     peak = float(peaks["bf16_tflops"])
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "sp2_square_tc_kernel<FP16X6>", "peak_kind": peak_kind + " dense bf16/fp16 burst",
+                "kernel": "sp2_square_tc_kernel<%s>" % prec_name, "peak_kind": peak_kind + " dense bf16/fp16 burst",
                 "launches": rep_m["n_tc"], "ms_per_launch": tc_ms}
 
     mixed_iters = rep_m["iters"] - rep_m["fp64_iters"]
     launches = 1 + 1 + 1 + 1 + n_max * (2 + (2 if args.fp64_tail > 0 else 0)) + 2
+    tiles = [(int(m) + 127) // 128 for m in ms]
+    plane_gb = 2 * (4 if prec_name == "FP16X6" else 2) * 2 * 128 * 128 * sum(t * (t + 1) // 2 for t in tiles) / 1e9
+    geometry = {"L": wl["L"]} if wl["kind"] == "lattice" else {"box_a": float(w["box"][0])}
     line = {
         "metric": METRIC, "value": N * world / (ms_m / 1000.0), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_m, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16-split(x6)/f32-acc/f64-trace", "data": "synthetic",
-        "config": {"workload": args.workload, "N": N, "L": wl["L"], "graph": "|H^2|>=%g" % wl["thresh"],
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
+        "config": {"workload": args.workload, "N": N, **geometry, "graph": "|H^2|>=%g" % wl["thresh"],
                    "cores": int(P), "core_size": int(np.median(cc)), "m_s_min": int(ms.min()),
-                   "m_s_median": float(np.median(ms)), "m_s_max": int(ms.max()), "precision": "FP16X6",
+                   "m_s_median": float(np.median(ms)), "m_s_max": int(ms.max()), "precision": prec_name,
                    "fp64_tail": args.fp64_tail, "branch": "global FP64 trace on device, stall stop",
                    "iters": rep_m["iters"], "stop": rep_m["stop"],
-                   "l2": "inputs larger than L2: %.2f GB of split planes (2 sides x 4 planes) vs 129 MB L2; "
-                         "no flush" % (16.0 * sum(((int(m) + 127) // 128 * 128) ** 2 for m in ms) / 1e9),
+                   "l2": "inputs larger than L2: %.2f GB of split planes (2 sides, upper 128-blocks) vs 129 MB "
+                         "L2; no flush" % plane_gb,
                    "setup_s": setup_s, "parallelism": "independent system per GPU" if world > 1 else "1 GPU"},
         "tensor_tflops": rep_m["mma_flops"] / (ms_m / 1000.0) / 1e12,
         "tensor_tflops_in_squarings": achieved,
@@ -336,11 +473,16 @@ def main():
     }
     line.update(out)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        Ns, dt, it = oracle_sample(16, 0, 0.15, (4, 4, 4))
+        if wl["kind"] == "lattice":
+            swl = dict(kind="lattice", L=16, seed=0, thresh=0.15, ncell=(4, 4, 4))
+            what = "16^3 sample of the same lattice model (N=4096, 64 cores of 4^3, |H^2|>=0.15 halos, m_s 461-481)"
+        else:
+            swl = WORKLOADS["disordered4k"]
+            what = "4096-site sample of the same disordered model (box 16a, 64 cells, |H^2|>=0.1 halos)"
+        Ns, dt, it = oracle_sample(swl)
         line["cpu_baseline"] = {"value": Ns / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                "sample": "16^3 sample of the same lattice model (N=4096, 64 cores of 4^3, "
-                                          "|H^2|>=0.15 halos, m_s 461-481), oracle graph SP2 (NumPy FP64, %d "
-                                          "iterations), gather+SP2+assembly timed (%.1f s)" % (it, dt)}
+                                "sample": what + ", oracle graph SP2 (NumPy FP64, %d iterations), "
+                                          "gather+SP2+assembly timed (%.1f s)" % (it, dt)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -82,3 +82,20 @@ def complete_blocks(labels):
     A = sp.csr_matrix((np.ones(sum(len(r) for r in rows), dtype=bool),
                        (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
     return _finish(A)
+
+
+def h2_threshold_rows(H, thresh, rows):
+    """Rows `rows` of h2_threshold(H, thresh), computed from those rows of H^2 alone
+    (H^2 is symmetric, so the symmetrisation adds nothing beyond rounding ties); returns
+    an N x N boolean CSR whose other rows are empty."""
+    H = sp.csr_matrix(H, dtype=np.float64)
+    rows = np.asarray(rows)
+    R = (H[rows] @ H).tocsr()
+    R = sp.csr_matrix((np.abs(R.data) >= thresh, R.indices, R.indptr), shape=R.shape)
+    R.eliminate_zeros()
+    E = sp.csr_matrix((np.ones(len(rows), dtype=bool), (rows, np.arange(len(rows)))), shape=(H.shape[0], len(rows)))
+    A = (E.astype(np.int64) @ R.astype(np.int64)).tocsr()
+    A = A + sp.csr_matrix((np.ones(len(rows), dtype=np.int64), (rows, rows)), shape=H.shape)
+    A = sp.csr_matrix(A, dtype=bool)
+    A.sort_indices()
+    return A

@@ -52,3 +52,30 @@ def build_h(pos, box, onsite, a=1.0, rcut=RCUT, rows=None, chunk=1024):
                       shape=(len(rows), N))
     H.sort_indices()
     return H
+
+
+def build_h_tree(pos, box, onsite, a=1.0, rcut=RCUT):
+    """The same H as build_h for systems too large for its O(N^2) scan.
+
+    Candidate neighbours come from scipy's periodic k-d tree (a library search, queried
+    with a radius slightly above the cutoff); every candidate's distance and hopping are
+    then evaluated with the same minimum-image formula as build_h and cut at r < rcut a.
+    """
+    from scipy.spatial import cKDTree
+    pos = np.asarray(pos, dtype=np.float64)
+    box = np.asarray(box, dtype=np.float64)
+    N = pos.shape[0]
+    tree = cKDTree(pos, boxsize=box)
+    pr = tree.query_pairs(rcut * a * (1.0 + 1e-9), output_type="ndarray")
+    i, j = pr[:, 0], pr[:, 1]
+    d = pos[i] - pos[j]
+    d = d - box * np.round(d / box)
+    r = np.sqrt(np.einsum("ij,ij->i", d, d))
+    keep = r < rcut * a
+    i, j, v = i[keep], j[keep], hopping(r[keep], a)
+    rows = np.concatenate([i, j, np.arange(N)])
+    cols = np.concatenate([j, i, np.arange(N)])
+    vals = np.concatenate([v, v, np.asarray(onsite, dtype=np.float64)])
+    H = sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+    H.sort_indices()
+    return H

@@ -71,3 +71,15 @@ def test_halo_brute_force():
         np.testing.assert_array_equal(idx[:c], C)
         halo = sorted(set(np.nonzero(Sd[C].any(0))[0]) - set(C))
         np.testing.assert_array_equal(idx[c:], halo)
+
+
+def test_h2_threshold_rows_equals_full():
+    w = synth.disordered(1200, seed=8)
+    H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
+    full = graph.h2_threshold(H, 0.1).tocsr()
+    rows = np.array([0, 5, 6, 400, 1199])
+    part = graph.h2_threshold_rows(H, 0.1, rows)
+    for i in rows:
+        np.testing.assert_array_equal(part[i].indices, full[i].indices)
+    others = np.setdiff1d(np.arange(1200), rows)
+    assert part[others].nnz == 0

@@ -50,3 +50,13 @@ def test_rows_subset_matches_full():
     rows = np.array([0, 17, 99, 124])
     Hr = hamiltonian.build_h(w["pos"], w["box"], w["onsite"], rows=rows)
     np.testing.assert_array_equal(Hr.toarray(), H[rows].toarray())
+
+
+@pytest.mark.parametrize("kind", ["lattice", "disordered"])
+def test_tree_build_equals_brute_force(kind):
+    w = synth.lattice(10, seed=3) if kind == "lattice" else synth.disordered(3000, seed=5)
+    Hb = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
+    Ht = hamiltonian.build_h_tree(w["pos"], w["box"], w["onsite"])
+    np.testing.assert_array_equal(Ht.indptr, Hb.indptr)
+    np.testing.assert_array_equal(Ht.indices, Hb.indices)
+    np.testing.assert_allclose(Ht.data, Hb.data, rtol=1e-15, atol=0)
