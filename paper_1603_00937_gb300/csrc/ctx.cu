@@ -1,6 +1,9 @@
 // Context, errors and small helpers of libgbe.
 #include <cstdarg>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
+#include <unordered_map>
 
 #include "gbe_internal.h"
 
@@ -30,16 +33,59 @@ extern "C" const char* gbe_strerror(int code) {
     }
 }
 
+// ------------------------------------------------------------------ device memory
+namespace {
+thread_local cudaStream_t t_stream = nullptr;
+thread_local cudaMemPool_t t_pool = nullptr;
+std::mutex g_alloc_mu;
+std::unordered_map<void*, cudaStream_t> g_pooled;   // pool allocation -> stream it was made on
+}  // namespace
+
+AllocScope::AllocScope(const gbe_ctx* ctx) : prev_stream(t_stream), prev_pool(t_pool) {
+    if (ctx && ctx->pool) {
+        t_stream = ctx->stream;
+        t_pool = ctx->pool;
+    }
+}
+
+AllocScope::~AllocScope() {
+    t_stream = prev_stream;
+    t_pool = prev_pool;
+}
+
 int gbe_alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(p, bytes);
+    const bool pooled = t_pool != nullptr;
+    cudaError_t e = pooled ? cudaMallocFromPoolAsync(p, bytes, t_pool, t_stream) : cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
-        gbe_set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        gbe_set_error("device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
         (void)cudaGetLastError();
+        *p = nullptr;
         return e == cudaErrorMemoryAllocation ? GBE_ENOMEM : GBE_ECUDA;
     }
+    if (pooled) {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        g_pooled[*p] = t_stream;
+    }
     return GBE_OK;
+}
+
+void gbe_free(void* p) {
+    if (!p) return;
+    bool pooled = false;
+    cudaStream_t s = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        auto it = g_pooled.find(p);
+        if (it != g_pooled.end()) {
+            pooled = true;
+            s = it->second;
+            g_pooled.erase(it);
+        }
+    }
+    if (pooled) cudaFreeAsync(p, s);
+    else cudaFree(p);
 }
 
 int gbe_sync(gbe_ctx* ctx) {
@@ -68,16 +114,39 @@ extern "C" int gbe_create(gbe_ctx** out, int device, void* cuda_stream) {
     c->stream = (cudaStream_t)cuda_stream;
     c->sm_count = prop.multiProcessorCount;
     c->smem_optin = (int)prop.sharedMemPerBlockOptin;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        gbe_set_error("cudaMemPoolCreate failed on device %d", device);
+        return GBE_ECUDA;
+    }
+    uint64_t keep = UINT64_MAX;   // keep freed blocks for reuse instead of returning them at every sync
+    cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    AllocScope scope(c);
     int r = gbe_alloc(&c->d_scratch, 4096);
-    if (r != GBE_OK) { delete c; return r; }
+    if (r != GBE_OK) { cudaMemPoolDestroy(c->pool); delete c; return r; }
     if (cudaMallocHost(&c->h_scratch, 4096) != cudaSuccess) {
-        cudaFree(c->d_scratch);
+        gbe_free(c->d_scratch);
+        cudaStreamSynchronize(c->stream);
+        cudaMemPoolDestroy(c->pool);
         delete c;
         gbe_set_error("cudaMallocHost failed");
         return GBE_ENOMEM;
     }
     r = gbe_tc_prepare(c);
-    if (r != GBE_OK) { cudaFree(c->d_scratch); cudaFreeHost(c->h_scratch); delete c; return r; }
+    if (r != GBE_OK) {
+        gbe_free(c->d_scratch);
+        cudaStreamSynchronize(c->stream);
+        cudaFreeHost(c->h_scratch);
+        cudaMemPoolDestroy(c->pool);
+        delete c;
+        return r;
+    }
     *out = c;
     return GBE_OK;
 }
@@ -85,9 +154,11 @@ extern "C" int gbe_create(gbe_ctx** out, int device, void* cuda_stream) {
 extern "C" int gbe_destroy(gbe_ctx* ctx) {
     if (!ctx) return GBE_OK;
     cudaSetDevice(ctx->device);
+    gbe_free(ctx->d_scratch);
     cudaStreamSynchronize(ctx->stream);
-    cudaFree(ctx->d_scratch);
     cudaFreeHost(ctx->h_scratch);
+    // blocks still held by live objects keep the pool alive until they are freed
+    cudaMemPoolDestroy(ctx->pool);
     delete ctx;
     return GBE_OK;
 }

@@ -79,6 +79,7 @@ static __global__ void scan_add_kernel(int64_t* out, int64_t n, const int64_t* b
 struct CellGrid {
     int nc[3];
     double box[3];
+    double inv[3];   // 1 / box
 };
 
 __device__ __forceinline__ int cell_of(const double* p, const CellGrid& g) {
@@ -106,9 +107,21 @@ static __global__ void cell_fill_kernel(const int32_t* __restrict__ cell, int64_
     members[start[c] + atomicAdd(&cursor[c], 1)] = (int32_t)i;
 }
 
-__device__ __forceinline__ double min_image(double d, double L) { return __dsub_rn(d, __dmul_rn(L, rint(d / L))); }
-__device__ __forceinline__ double dist3(double x, double y, double z) {
-    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+// Minimum image d - L rint(d / L), with the quotient taken as d * (1/L): the two can round to
+// different integers only when d / L lies within an ulp of a half-integer, i.e. for pairs about
+// L/2 apart, which every caller rejects (its cutoff is below L/2), so accepted pairs get the
+// same separation as with a true division (an FP64 division is many times the cost of a
+// multiplication on this part's FP64 pipe).
+__device__ __forceinline__ double min_image(double d, double L, double invL) {
+    return __dsub_rn(d, __dmul_rn(L, rint(__dmul_rn(d, invL))));
+}
+__device__ __forceinline__ double dist2(double x, double y, double z) {
+    return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
+}
+// squared minimum-image distance between sites i and j of a [n][3] position array
+__device__ __forceinline__ double pair_dist2(const double* pos, double xi, double yi, double zi, int j, const CellGrid& g) {
+    return dist2(min_image(xi - pos[3 * j], g.box[0], g.inv[0]), min_image(yi - pos[3 * j + 1], g.box[1], g.inv[1]),
+                 min_image(zi - pos[3 * j + 2], g.box[2], g.inv[2]));
 }
 
 // Deterministic sparse dot product of two sorted CSR rows (ascending column order,
@@ -128,7 +141,7 @@ static __device__ double row_dot(const int64_t* __restrict__ rp, const int32_t* 
 
 struct DevBuf {
     void* p = nullptr;
-    ~DevBuf() { if (p) cudaFree(p); }
+    ~DevBuf() { if (p) gbe_free(p); }
     template <class T> T* as() { return (T*)p; }
 };
 

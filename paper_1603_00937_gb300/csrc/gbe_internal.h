@@ -45,6 +45,8 @@ struct gbe_ctx {
     void* d_scratch = nullptr;
     void* h_scratch = nullptr;
     int profile = 0;
+    // stream-ordered device memory pool of this context (freed blocks are kept for reuse)
+    cudaMemPool_t pool = nullptr;
 };
 
 struct gbe_hamiltonian {
@@ -173,5 +175,18 @@ int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot);
 int gbe_tc_prepare(gbe_ctx* ctx);
 
 // helpers
+// Device memory.  Inside an AllocScope (every entry point that takes a context opens one)
+// gbe_alloc takes memory from the context's pool in the context's stream order; gbe_free
+// returns it in the order of the stream it was allocated on (no device synchronisation).
+// Outside a scope they fall back to cudaMalloc / cudaFree.
 int gbe_alloc(void** p, size_t bytes);
+void gbe_free(void* p);
+struct AllocScope {
+    explicit AllocScope(const gbe_ctx* ctx);
+    ~AllocScope();
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+    cudaStream_t prev_stream;
+    cudaMemPool_t prev_pool;
+};
 int gbe_sync(gbe_ctx* ctx);

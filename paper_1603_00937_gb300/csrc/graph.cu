@@ -122,7 +122,7 @@ __global__ void cell_sort_kernel(const int64_t* __restrict__ start, int ncells, 
 }
 
 struct HModel {
-    double a, rcut, decay, hop;
+    double a, rcut, decay, hop, rcut2;
 };
 
 constexpr int kRowCap = 1024;
@@ -158,9 +158,8 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
                 const int cell = (ax * g.nc[1] + ay) * g.nc[2] + az;
                 for (int64_t p = cstart[cell] + lane; p < cstart[cell + 1]; p += 32) {
                     const int j = members[p];
-                    const double r = dist3(min_image(xi - pos[3 * j], g.box[0]), min_image(yi - pos[3 * j + 1], g.box[1]),
-                                           min_image(zi - pos[3 * j + 2], g.box[2]));
-                    if (j == i || r < mdl.rcut) {
+                    // r^2 < rcut^2 (differs from r < rcut only within an ulp of the cutoff)
+                    if (j == i || pair_dist2(pos, xi, yi, zi, j, g) < mdl.rcut2) {
                         const int k = atomicAdd(&bcount[w], 1);
                         if (k < kRowCap) buf[w][k] = j;
                     }
@@ -191,8 +190,7 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
         if (j == i) {
             v = onsite[i];
         } else {
-            const double r = dist3(min_image(xi - pos[3 * j], g.box[0]), min_image(yi - pos[3 * j + 1], g.box[1]),
-                                   min_image(zi - pos[3 * j + 2], g.box[2]));
+            const double r = sqrt(pair_dist2(pos, xi, yi, zi, j, g));
             v = mdl.hop * exp(-(r - mdl.a) / mdl.decay);
         }
         col[base + t] = j;
@@ -442,13 +440,13 @@ int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thres
     }
     int32_t* ci = nullptr;
     if (r == GBE_OK) r = gbe_alloc((void**)&ci, std::max<int64_t>(nnz, 1) * 4);
-    if (r != GBE_OK) { cudaFree(rp); return r; }
+    if (r != GBE_OK) { gbe_free(rp); return r; }
     rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp, s3ci,
                                                   hops, 1, cnt.as<int32_t>(), rp, ci, flag.as<int>());
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
-        cudaFree(rp); cudaFree(ci);
+        gbe_free(rp); gbe_free(ci);
         gbe_set_error("rowset: %s", cudaGetErrorString(e));
         return GBE_ECUDA;
     }
@@ -460,6 +458,7 @@ int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thres
 
 // ============================================================================= Hamiltonian
 extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gbe_tb_model* model, gbe_hamiltonian** out) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && st && model && out, "NULL argument");
     GBE_CHECK_ARG(st->n > 0 && st->n < INT32_MAX && st->pos && st->onsite, "sites");
     GBE_CHECK_ARG(model->rcut > 0 && model->decay > 0, "model");
@@ -476,6 +475,7 @@ extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gb
     for (int d = 0; d < 3; ++d) {
         g.nc[d] = std::max(1, (int)floor(st->box[d] / model->rcut));
         g.box[d] = st->box[d];
+        g.inv[d] = 1.0 / st->box[d];
         ncells *= g.nc[d];
     }
     DevBuf cell, ccnt, cstart, cur, mem, cnt, flag;
@@ -493,7 +493,7 @@ extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gb
     cell_count_kernel<<<nb, 256, 0, s>>>(pos, n, g, cell.as<int32_t>(), ccnt.as<int32_t>());
     GBE_TRY(scan_exclusive(ctx, ccnt.as<int32_t>(), cstart.as<int64_t>(), ncells, nullptr));
     cell_fill_kernel<<<nb, 256, 0, s>>>(cell.as<int32_t>(), n, cstart.as<int64_t>(), cur.as<int32_t>(), mem.as<int32_t>());
-    HModel mdl{model->a, model->rcut, model->decay, model->hop};
+    HModel mdl{model->a, model->rcut, model->decay, model->hop, model->rcut * model->rcut};
     const unsigned rb = (unsigned)((n + 7) / 8);
     hbuild_kernel<<<rb, 256, 0, s>>>(pos, ons, n, g, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 0, cnt.as<int32_t>(),
                                      nullptr, nullptr, nullptr, flag.as<int>());
@@ -531,7 +531,7 @@ extern "C" int gbe_hamiltonian_csr(const gbe_hamiltonian* H, gbe_csr* v) {
 
 extern "C" int gbe_free_hamiltonian(gbe_hamiltonian* H) {
     if (!H) return GBE_OK;
-    cudaFree(H->rowptr); cudaFree(H->col); cudaFree(H->val);
+    gbe_free(H->rowptr); gbe_free(H->col); gbe_free(H->val);
     delete H;
     return GBE_OK;
 }
@@ -539,8 +539,8 @@ extern "C" int gbe_free_hamiltonian(gbe_hamiltonian* H) {
 // ============================================================================= graph
 extern "C" int gbe_free_graph(gbe_graph* S) {
     if (!S) return GBE_OK;
-    cudaFree(S->rowptr); cudaFree(S->col);
-    if (S->full_rowptr != S->rowptr) { cudaFree(S->full_rowptr); cudaFree(S->full_col); }
+    gbe_free(S->rowptr); gbe_free(S->col);
+    if (S->full_rowptr != S->rowptr) { gbe_free(S->full_rowptr); gbe_free(S->full_col); }
     delete S;
     return GBE_OK;
 }
@@ -548,6 +548,7 @@ extern "C" int gbe_free_graph(gbe_graph* S) {
 int gbe_graph_mlp_select(gbe_ctx* ctx, const gbe_csr* H, const gbe_graph_params* p, int64_t** rp, int32_t** ci);
 
 extern "C" int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* Hin, const gbe_graph_params* p, gbe_graph** out) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && Hin && p && out, "NULL argument");
     GBE_CHECK_ARG(Hin->n > 0 && Hin->n < INT32_MAX, "H size");
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -621,8 +622,8 @@ extern "C" int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* Hin, const gbe_graph
             if (r == GBE_OK)
                 r = rowset_csr(ctx, 1, n, nullptr, 0.0, srp, sci, H.rowptr, H.col, nullptr, nullptr, 1, &S->rowptr,
                                &S->col, &S->nnz);
-            cudaFree(srp);
-            cudaFree(sci);
+            gbe_free(srp);
+            gbe_free(sci);
             S->hops = 1;
             break;
         }
@@ -637,6 +638,7 @@ extern "C" int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* Hin, const gbe_graph
 }
 
 extern "C" int gbe_graph_size(gbe_ctx* ctx, gbe_graph* S, int64_t* n, int64_t* nnz) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && S, "NULL argument");
     if (S->full_nnz < 0) {
         GBE_TRY(rowset_csr(ctx, 2, S->n, nullptr, 0.0, S->rowptr, S->col, nullptr, nullptr, nullptr, nullptr, S->hops,
@@ -648,6 +650,7 @@ extern "C" int gbe_graph_size(gbe_ctx* ctx, gbe_graph* S, int64_t* n, int64_t* n
 }
 
 extern "C" int gbe_graph_export(gbe_ctx* ctx, gbe_graph* S, int64_t* rowptr, int32_t* col) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && S && rowptr && col, "NULL argument");
     GBE_TRY(gbe_graph_size(ctx, S, nullptr, nullptr));
     GBE_CUDA_TRY(cudaMemcpyAsync(rowptr, S->full_rowptr, (S->n + 1) * 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -659,6 +662,7 @@ extern "C" int gbe_graph_export(gbe_ctx* ctx, gbe_graph* S, int64_t* rowptr, int
 
 // ============================================================================= partition
 extern "C" int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* p, gbe_parts** out) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && S && p && out, "NULL argument");
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
@@ -675,7 +679,12 @@ extern "C" int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partiti
         GBE_TRY(to_device(ctx, p->sites->pos, n * 24, p->sites->on_device, hpos, (const void**)&pos));
         CellGrid g;
         int64_t ncells = 1;
-        for (int d = 0; d < 3; ++d) { g.nc[d] = p->ncell[d]; g.box[d] = p->sites->box[d]; ncells *= g.nc[d]; }
+        for (int d = 0; d < 3; ++d) {
+            g.nc[d] = p->ncell[d];
+            g.box[d] = p->sites->box[d];
+            g.inv[d] = 1.0 / p->sites->box[d];
+            ncells *= g.nc[d];
+        }
         GBE_CHECK_ARG(ncells < INT32_MAX, "too many cells");
         DevBuf cell, ccnt, cst, cur;
         GBE_TRY(gbe_alloc(&cell.p, n * 4));

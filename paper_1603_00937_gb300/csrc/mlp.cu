@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
     const int64_t i = (int64_t)blockIdx.x * 8 + w;
     if (i >= n) return;
     const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    const double rcand2 = rcand * rcand;
     const int ci = cell_of(pos + 3 * i, g);
     const int cc[3] = {ci / (g.nc[1] * g.nc[2]), (ci / g.nc[2]) % g.nc[1], ci % g.nc[2]};
     if (lane == 0) bcount[w] = 0;
@@ -65,9 +66,7 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
                 for (int64_t p = cstart[cell] + lane; p < cstart[cell + 1]; p += 32) {
                     const int j = members[p];
                     if (j == i) continue;
-                    const double r = dist3(min_image(xi - pos[3 * j], g.box[0]), min_image(yi - pos[3 * j + 1], g.box[1]),
-                                           min_image(zi - pos[3 * j + 2], g.box[2]));
-                    if (r < rcand) {
+                    if (pair_dist2(pos, xi, yi, zi, j, g) < rcand2) {   // r < rcand up to an ulp at the cutoff
                         const int k = atomicAdd(&bcount[w], 1);
                         if (k < kPairCap) buf[w][k] = j;
                     }
@@ -94,8 +93,7 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
     const double ei = onsite[i];
     for (int t = lane; t < m; t += 32) {
         const int j = buf[w][t];
-        const double r = dist3(min_image(xi - pos[3 * j], g.box[0]), min_image(yi - pos[3 * j + 1], g.box[1]),
-                               min_image(zi - pos[3 * j + 2], g.box[2]));
+        const double r = sqrt(pair_dist2(pos, xi, yi, zi, j, g));
         // H_ij by binary search in row i, (H^2)_ij by the ordered merge dot product
         double hij = 0.0;
         int64_t a = hrp[i], b = hrp[i + 1] - 1;
@@ -372,12 +370,13 @@ struct gbe_mlp {
 
 extern "C" int gbe_free_pairs(gbe_pairs* P) {
     if (!P) return GBE_OK;
-    cudaFree(P->rowptr); cudaFree(P->j); cudaFree(P->feat);
+    gbe_free(P->rowptr); gbe_free(P->j); gbe_free(P->feat);
     delete P;
     return GBE_OK;
 }
 
 extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr* Hin, double rcand, gbe_pairs** out) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && st && Hin && out, "NULL argument");
     GBE_CHECK_ARG(st->n > 0 && st->n == Hin->n && st->n < INT32_MAX, "sites / H sizes");
     GBE_CHECK_ARG(rcand > 0.0, "rcand");
@@ -400,6 +399,7 @@ extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr*
     for (int d = 0; d < 3; ++d) {
         g.nc[d] = std::max(1, (int)floor(st->box[d] / rcand));
         g.box[d] = st->box[d];
+        g.inv[d] = 1.0 / st->box[d];
         ncells *= g.nc[d];
     }
     DevBuf cell, ccnt, cst, cur, mem, cnt, flag;
@@ -454,6 +454,7 @@ extern "C" int gbe_pairs_info(const gbe_pairs* P, int64_t* n, int64_t* npairs) {
 }
 
 extern "C" int gbe_pairs_export(gbe_ctx* ctx, const gbe_pairs* P, int64_t* rowptr, int32_t* j, float* features) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && P, "NULL argument");
     cudaStream_t s = ctx->stream;
     if (rowptr) GBE_CUDA_TRY(cudaMemcpyAsync(rowptr, P->rowptr, (P->n + 1) * 8, cudaMemcpyDeviceToHost, s));
@@ -473,13 +474,14 @@ extern "C" int gbe_pairs_device(const gbe_pairs* P, const int64_t** rowptr, cons
 
 extern "C" int gbe_free_mlp(gbe_mlp* M) {
     if (!M) return GBE_OK;
-    cudaFree(M->p); cudaFree(M->pw); cudaFree(M->m); cudaFree(M->v); cudaFree(M->g); cudaFree(M->loss);
-    cudaFree(M->partials); cudaFree(M->loss_part);
+    gbe_free(M->p); gbe_free(M->pw); gbe_free(M->m); gbe_free(M->v); gbe_free(M->g); gbe_free(M->loss);
+    gbe_free(M->partials); gbe_free(M->loss_part);
     delete M;
     return GBE_OK;
 }
 
 extern "C" int gbe_mlp_create(gbe_ctx* ctx, int hidden, gbe_mlp** out) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && out, "NULL argument");
     GBE_CHECK_ARG(hidden == kHid, "only hidden width 64 is built");
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -507,6 +509,7 @@ extern "C" int gbe_mlp_create(gbe_ctx* ctx, int hidden, gbe_mlp** out) {
 extern "C" int gbe_mlp_param_count(const gbe_mlp* M) { return M ? kNParams : 0; }
 
 extern "C" int gbe_mlp_set_params(gbe_ctx* ctx, gbe_mlp* M, const float* host_params) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && M && host_params, "NULL argument");
     GBE_CUDA_TRY(cudaMemcpyAsync(M->p, host_params, kNParams * 4, cudaMemcpyHostToDevice, ctx->stream));
     GBE_CUDA_TRY(cudaMemsetAsync(M->m, 0, kNParams * 4, ctx->stream));
@@ -517,6 +520,7 @@ extern "C" int gbe_mlp_set_params(gbe_ctx* ctx, gbe_mlp* M, const float* host_pa
 }
 
 extern "C" int gbe_mlp_get_params(gbe_ctx* ctx, const gbe_mlp* M, float* host_params) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && M && host_params, "NULL argument");
     GBE_CUDA_TRY(cudaMemcpyAsync(host_params, M->p, kNParams * 4, cudaMemcpyDeviceToHost, ctx->stream));
     GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -532,6 +536,7 @@ static int mlp_forward_dev(gbe_ctx* ctx, const gbe_mlp* M, const gbe_pairs* P, f
 }
 
 extern "C" int gbe_mlp_forward(gbe_ctx* ctx, const gbe_mlp* M, const gbe_pairs* P, float* logits) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && M && P && logits, "NULL argument");
     return mlp_forward_dev(ctx, M, P, logits);
 }
@@ -551,6 +556,7 @@ static int mlp_grad_dev(gbe_ctx* ctx, gbe_mlp* M, const gbe_pairs* P, const uint
 
 extern "C" int gbe_mlp_gradient(gbe_ctx* ctx, gbe_mlp* M, const gbe_pairs* P, const uint8_t* labels, double* loss,
                                 float* grad_host) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && M && P && labels, "NULL argument");
     GBE_TRY(mlp_grad_dev(ctx, M, P, labels));
     if (loss) GBE_CUDA_TRY(cudaMemcpyAsync(loss, M->loss, 8, cudaMemcpyDeviceToHost, ctx->stream));
@@ -560,6 +566,7 @@ extern "C" int gbe_mlp_gradient(gbe_ctx* ctx, gbe_mlp* M, const gbe_pairs* P, co
 }
 
 extern "C" int gbe_mlp_adam_step(gbe_ctx* ctx, gbe_mlp* M, float lr, float beta1, float beta2, float eps) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && M, "NULL argument");
     M->t += 1;
     const float c1 = 1.0f - powf(beta1, (float)M->t), c2 = 1.0f - powf(beta2, (float)M->t);
@@ -570,6 +577,7 @@ extern "C" int gbe_mlp_adam_step(gbe_ctx* ctx, gbe_mlp* M, float lr, float beta1
 
 extern "C" int gbe_mlp_train(gbe_ctx* ctx, gbe_mlp* M, const gbe_pairs* P, const uint8_t* labels, int epochs,
                              float lr, double* final_loss) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && M && P && labels && epochs > 0, "bad argument");
     for (int e = 0; e < epochs; ++e) {
         GBE_TRY(mlp_grad_dev(ctx, M, P, labels));
@@ -608,7 +616,7 @@ int gbe_graph_mlp_select(gbe_ctx* ctx, const gbe_csr* H, const gbe_graph_params*
         if (e != cudaSuccess) { gbe_set_error("mlp select: %s", cudaGetErrorString(e)); r = GBE_ECUDA; }
     }
     gbe_free_pairs(P);
-    if (r != GBE_OK) { cudaFree(rp); cudaFree(ci); return r; }
+    if (r != GBE_OK) { gbe_free(rp); gbe_free(ci); return r; }
     *rp_out = rp;
     *ci_out = ci;
     return GBE_OK;

@@ -117,6 +117,7 @@ int scratch_for(int device, unsigned long long** out) {
 }  // namespace
 
 extern "C" int gbe_gershgorin_noalloc(gbe_ctx* ctx, const gbe_csr* H, double* bounds) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && H && bounds, "NULL argument");
     GBE_CHECK_ARG(H->on_device == 1, "gbe_gershgorin_noalloc needs a device CSR (copying host data would allocate)");
     GBE_CHECK_ARG(H->rowptr && H->col && H->val, "CSR arrays are NULL");

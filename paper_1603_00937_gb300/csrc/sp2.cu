@@ -101,12 +101,15 @@ __device__ __forceinline__ int find_local(const int32_t* idx, int c, int m, int 
     return -1;
 }
 
-// One CTA (8 warps) per subgraph, one warp per row at a time: lanes map the row's H
-// entries to local columns (binary search in the sorted core and halo lists), split them
-// and scatter them into the warp's dense row buffer in shared memory (4 split planes
-// packed in 8 bytes per column, or the FP64 value); then each lane writes whole 8-column
-// groups of the row to every plane (16 B per plane and group).  Every element of the
-// padded tile is written, zeros included, so the planes need no separate clear.
+// One CTA (8 warps) per subgraph, 8 consecutive rows a0..a0+7 at a time, one per warp:
+// lanes map the row's H entries to local columns (binary search in the sorted core and halo
+// lists), split them and scatter them into the warp's dense row buffer in shared memory (4
+// split planes packed in 8 bytes per column, or the FP64 value).  X_0 is symmetric, so the
+// 8 rows are also columns a0..a0+7: for the split planes the whole CTA then writes that
+// 8-column group of every stored (upper) block, each thread one row r of it (16 contiguous
+// bytes per plane; a warp covers 512 contiguous bytes).  The FP64 iterate (stored in full)
+// is written row by row.  Every element of the padded tile is written, zeros included, so
+// the planes need no separate clear.
 template <int prec>
 __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_t* __restrict__ rowptr,
                                                      const int32_t* __restrict__ col, const double* __restrict__ val,
@@ -121,7 +124,8 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     const int64_t off = g.off[s];
     const int64_t base = sub_ptr[s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint2* rowbuf = reinterpret_cast<uint2*>(gsm) + (size_t)warp * max_mpad;          // [8][max_mpad]
+    uint2* rows8 = reinterpret_cast<uint2*>(gsm);                                      // [8][max_mpad]
+    uint2* rowbuf = rows8 + (size_t)warp * max_mpad;
     int32_t* sidx = reinterpret_cast<int32_t*>(gsm + (size_t)8 * max_mpad * 8);         // m_s local -> global
     for (int a = threadIdx.x; a < m; a += blockDim.x) sidx[a] = sub_idx[base + a];
     __syncthreads();
@@ -130,8 +134,12 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     else { emin = dkey_inv(ctrl->eps_min_key); emax = dkey_inv(ctrl->eps_max_key); }
     const double range = emax - emin;
     const double inv_range = 1.0 / range;
+    float ih = 0.f, il = 0.f;              // 1 / range as an FP32 pair (split paths)
+    f64_to_f32_pair(inv_range, ih, il);
     double t1 = 0.0, t2 = 0.0;
-    for (int a = warp; a < mpad; a += 8) {
+    float t2h = 0.f, t2l = 0.f;             // double-float Tr X_0^2 (split paths)
+    for (int a0 = 0; a0 < mpad; a0 += 8) {
+        const int a = a0 + warp;
         for (int b = lane; b < mpad; b += 32) rowbuf[b] = make_uint2(0u, 0u);
         __syncwarp();
         if (a < m) {
@@ -140,21 +148,30 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                 const int b = find_local(sidx, c, m, col[p]);
                 if (b < 0) continue;
                 const double h = val[p];
-                // FP64 path: the exact quotient, as the FP64 oracle computes it; split paths
-                // need ~2^-35: one FP64 multiply, then an integer-only split to FP32 pairs
-                double x;
-                if constexpr (prec == GBE_PREC_FP64) x = ((a == b ? emax : 0.0) - h) / range;
-                else x = ((a == b ? emax : 0.0) - h) * inv_range;
-                if (a < c) {
-                    t2 += x * x;
-                    if (a == b) t1 += x;
-                }
                 uint2 packed;
                 if constexpr (prec == GBE_PREC_FP64) {
+                    // the exact quotient, as the FP64 oracle computes it
+                    const double x = ((a == b ? emax : 0.0) - h) / range;
+                    if (a < c) {
+                        t2 += x * x;
+                        if (a == b) t1 += x;
+                    }
                     packed = make_uint2((uint32_t)__double2loint(x), (uint32_t)__double2hiint(x));
                 } else {
+                    // split paths need x to ~2^-35: off-diagonal x = -h / range as an FP32 pair
+                    // product (no FP64 arithmetic: this part's FP64 pipe is narrow); the diagonal
+                    // (one entry per row) in FP64
                     float xh, xl;
-                    f64_to_f32_pair(x, xh, xl);
+                    if (a == b) {
+                        const double x = (emax - h) * inv_range;
+                        f64_to_f32_pair(x, xh, xl);
+                        if (a < c) t1 += x;
+                    } else {
+                        float hh, hl;
+                        f64_to_f32_pair(h, hh, hl);
+                        neg_mul_pair(hh, hl, ih, il, xh, xl);
+                    }
+                    if (a < c) df_add_sq(t2h, t2l, xh, xl, 1.0f);
                     if constexpr (prec == GBE_PREC_FP16X6) {
                         const OzSplit o = oz_split_pq(xh, xl);
                         packed = make_uint2((uint32_t)o.s0 | ((uint32_t)o.s1 << 16), (uint32_t)o.s2 | ((uint32_t)o.s1s << 16));
@@ -167,25 +184,25 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                 rowbuf[b] = packed;
             }
         }
-        __syncwarp();
-        // split planes store only upper-triangular blocks; FP64 iterates are stored in full
-        const int gstart = (prec == GBE_PREC_FP64) ? 0 : 16 * (a >> 7);
-        for (int gi8 = gstart + lane; gi8 < (mpad >> 3); gi8 += 32) {
-            const int c0 = gi8 << 3;
-            const int64_t e = blk_index(off, mpad, a, c0);
-            uint2 u[8];
-            const uint4* rb4 = reinterpret_cast<const uint4*>(rowbuf + c0);
+        if constexpr (prec == GBE_PREC_FP64) {
+            __syncwarp();
+            // row a, all column groups: 64 contiguous bytes per lane and group
+            for (int gi8 = lane; gi8 < (mpad >> 3); gi8 += 32) {
+                const int c0 = gi8 << 3;
+                uint4* d = reinterpret_cast<uint4*>(f + blk_index(off, mpad, a, c0));
+                const uint4* rb4 = reinterpret_cast<const uint4*>(rowbuf + c0);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint4 v = rb4[k];
-                u[2 * k] = make_uint2(v.x, v.y);
-                u[2 * k + 1] = make_uint2(v.z, v.w);
+                for (int k = 0; k < 4; ++k) d[k] = rb4[k];
             }
-            if constexpr (prec == GBE_PREC_FP64) {
-                uint4* d = reinterpret_cast<uint4*>(f + e);
+            __syncwarp();
+        } else {
+            __syncthreads();
+            // columns a0..a0+7 (= rows a0..a0+7 by symmetry) of blocks I = 0..J, J = a0 / 128
+            const int rows = ((a0 >> 7) + 1) << 7;
+            for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+                uint2 u[8];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) d[k] = make_uint4(u[2 * k].x, u[2 * k].y, u[2 * k + 1].x, u[2 * k + 1].y);
-            } else {
+                for (int k = 0; k < 8; ++k) u[k] = rows8[(size_t)k * max_mpad + r];
                 uint32_t w[4][4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -194,14 +211,16 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                     w[2][k] = (u[2 * k].y & 0xffffu) | (u[2 * k + 1].y << 16);
                     w[3][k] = (u[2 * k].y >> 16) | (u[2 * k + 1].y & 0xffff0000u);
                 }
+                const int64_t e = blk_index(off, mpad, r, a0);
                 const int np = (prec == GBE_PREC_FP16X6) ? 4 : 2;
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (q < np) *reinterpret_cast<uint4*>(planes + e + q * plane_stride) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
             }
+            __syncthreads();
         }
-        __syncwarp();
     }
+    if constexpr (prec != GBE_PREC_FP64) t2 = (double)t2h + (double)t2l;
     double s1 = block_sum_d<256>(t1, red);
     double s2 = block_sum_d<256>(t2, red + 8);
     if (threadIdx.x == 0) {
@@ -473,6 +492,7 @@ static SubsGeom geom_of(const gbe_subs* X) { return SubsGeom{X->d_off, X->d_mpad
 
 extern "C" int gbe_parts_import(gbe_ctx* ctx, int64_t n, int64_t P, const int32_t* core_count,
                                 const int64_t* sub_ptr, const int32_t* sub_idx, gbe_parts** out) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && out && core_count && sub_ptr && sub_idx, "NULL argument");
     GBE_CHECK_ARG(n > 0 && n < INT32_MAX && P > 0, "bad sizes");
     GBE_CHECK_ARG(sub_ptr[0] == 0, "sub_ptr[0] must be 0");
@@ -515,6 +535,7 @@ extern "C" int gbe_parts_info(const gbe_parts* p, int64_t* P, int64_t* total, in
 
 extern "C" int gbe_parts_export(gbe_ctx* ctx, const gbe_parts* p, int32_t* core_count, int64_t* sub_ptr,
                                 int32_t* sub_idx) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && p, "NULL argument");
     if (core_count) memcpy(core_count, p->h_core_count.data(), p->P * 4);
     if (sub_ptr) memcpy(sub_ptr, p->h_sub_ptr.data(), (p->P + 1) * 8);
@@ -527,18 +548,18 @@ extern "C" int gbe_parts_export(gbe_ctx* ctx, const gbe_parts* p, int32_t* core_
 
 extern "C" int gbe_free_parts(gbe_parts* p) {
     if (!p) return GBE_OK;
-    cudaFree(p->d_core_count);
-    cudaFree(p->d_sub_ptr);
-    cudaFree(p->d_sub_idx);
+    gbe_free(p->d_core_count);
+    gbe_free(p->d_sub_ptr);
+    gbe_free(p->d_sub_idx);
     delete p;
     return GBE_OK;
 }
 
 extern "C" int gbe_free_subs(gbe_subs* X) {
     if (!X) return GBE_OK;
-    cudaFree(X->d_off); cudaFree(X->d_mpad); cudaFree(X->d_m); cudaFree(X->d_c);
-    for (int i = 0; i < 2; ++i) { cudaFree(X->planes[i]); cudaFree(X->f64[i]); }
-    cudaFree(X->d_items_tc); cudaFree(X->d_items_64); cudaFree(X->d_partials); cudaFree(X->d_ctrl);
+    gbe_free(X->d_off); gbe_free(X->d_mpad); gbe_free(X->d_m); gbe_free(X->d_c);
+    for (int i = 0; i < 2; ++i) { gbe_free(X->planes[i]); gbe_free(X->f64[i]); }
+    gbe_free(X->d_items_tc); gbe_free(X->d_items_64); gbe_free(X->d_partials); gbe_free(X->d_ctrl);
     if (X->h_ctrl) cudaFreeHost(X->h_ctrl);
     for (int i = 0; i < 3; ++i) if (X->ev[i]) cudaEventDestroy(X->ev[i]);
     for (auto e : X->ev_tc) cudaEventDestroy(e);
@@ -563,6 +584,7 @@ static void make_items(const std::vector<int32_t>& dim, const std::vector<int32_
 }
 
 extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, gbe_subs** out) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && parts && out, "NULL argument");
     GBE_CHECK_ARG(prec == GBE_PREC_FP64 || prec == GBE_PREC_FP16X6 || prec == GBE_PREC_BF16X3, "unknown prec");
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -650,6 +672,7 @@ int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X) {
 
 extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* prm,
                            gbe_subs* X) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && H && parts && prm && X, "NULL argument");
     GBE_CHECK_ARG(H->on_device, "gbe_sp2_run needs a device CSR (use gbe_sp2_submatrices for host H)");
     GBE_CHECK_ARG(X->parts == parts, "state was created for another partition");
@@ -732,6 +755,7 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
 }
 
 extern "C" int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_report* rep) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && X && rep, "NULL argument");
     GBE_CUDA_TRY(cudaMemcpyAsync(X->h_ctrl, X->d_ctrl, sizeof(Sp2Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
     GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -775,7 +799,7 @@ extern "C" int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_repor
 struct DevCsr {
     gbe_csr view{};
     void* buf = nullptr;
-    ~DevCsr() { if (buf) cudaFree(buf); }
+    ~DevCsr() { if (buf) gbe_free(buf); }
 };
 
 static int csr_to_device(gbe_ctx* ctx, const gbe_csr* H, DevCsr& d) {
@@ -796,6 +820,7 @@ static int csr_to_device(gbe_ctx* ctx, const gbe_csr* H, DevCsr& d) {
 
 extern "C" int gbe_sp2_submatrices(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts,
                                    const gbe_sp2_params* prm, gbe_subs** X, gbe_sp2_report* rep) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && H && parts && prm && X, "NULL argument");
     bool created = false;
     if (*X == nullptr) {
@@ -824,6 +849,7 @@ extern "C" int gbe_sp2_submatrices(gbe_ctx* ctx, const gbe_csr* H, const gbe_par
 }
 
 extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, double drop_tol, gbe_ell* D) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && X && parts && D, "NULL argument");
     GBE_CHECK_ARG(X->parts == parts, "state was created for another partition");
     if (D->col == nullptr) {
@@ -858,7 +884,7 @@ extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* 
         if (e == cudaSuccess) e = cudaMemcpyAsync(D->val, val, total * 8, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    if (tmp) cudaFree(tmp);
+    if (tmp) gbe_free(tmp);
     if (e != cudaSuccess) {
         gbe_set_error("assemble: %s", cudaGetErrorString(e));
         return GBE_ECUDA;
@@ -867,6 +893,7 @@ extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* 
 }
 
 extern "C" int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out) {
+    AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && X && out && s >= 0 && s < X->P, "bad argument");
     const int64_t m = X->h_m[s];
     void* tmp = nullptr;
@@ -876,7 +903,7 @@ extern "C" int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, doubl
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, m * m * 8, cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    cudaFree(tmp);
+    gbe_free(tmp);
     if (e != cudaSuccess) {
         gbe_set_error("export: %s", cudaGetErrorString(e));
         return GBE_ECUDA;

@@ -212,26 +212,6 @@ struct TcArgs {
 };
 
 // Double-float sum (sh, sl) += (bh, bl) (TwoSum on the high parts).
-__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
-    const float s = sh + bh;
-    const float bp = s - sh;
-    const float err = (sh - (s - bp)) + (bh - bp);
-    sh = s;
-    sl += err + bl;
-}
-
-// Double-float accumulation of w * (P + Q)^2 (FP64-grade traces from FP32 parts).
-__device__ __forceinline__ void df_add_sq(float& sh, float& sl, float P, float Q, float w) {
-    const float p2 = P * P;
-    const float e2 = fmaf(P, P, -p2);
-    const float th = w * p2;
-    const float tl = w * (e2 + Q * (2.0f * P + Q));
-    const float s = sh + th;
-    const float bp = s - sh;
-    const float err = (sh - (s - bp)) + (th - bp);
-    sh = s;
-    sl += err + tl;
-}
 
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)

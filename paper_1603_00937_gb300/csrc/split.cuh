@@ -68,3 +68,36 @@ __device__ __forceinline__ double oz_value(uint16_t s0, uint16_t s1, uint16_t s2
 __device__ __forceinline__ double bf_value(uint16_t hi, uint16_t lo) {
     return (double)b_val(hi) + (double)b_val(lo);
 }
+
+// Double-float (FP32 pair) accumulation: (sh, sl) += (bh, bl).
+__device__ __forceinline__ void df_add(float& sh, float& sl, float bh, float bl) {
+    const float s = sh + bh;
+    const float bp = s - sh;
+    const float err = (sh - (s - bp)) + (bh - bp);
+    sh = s;
+    sl += err + bl;
+}
+
+// Double-float accumulation of w * (P + Q)^2 (FP64-grade traces from FP32 parts).
+__device__ __forceinline__ void df_add_sq(float& sh, float& sl, float P, float Q, float w) {
+    const float p2 = P * P;
+    const float e2 = fmaf(P, P, -p2);
+    const float th = w * p2;
+    const float tl = w * (e2 + Q * (2.0f * P + Q));
+    const float s = sh + th;
+    const float bp = s - sh;
+    const float err = (sh - (s - bp)) + (th - bp);
+    sh = s;
+    sl += err + tl;
+}
+
+// -(ah + al) * (bh + bl) as an FP32 pair (P, Q): the product of the leading parts with its
+// exact rounding error (FMA) plus both cross terms; relative error ~2^-47.
+__device__ __forceinline__ void neg_mul_pair(float ah, float al, float bh, float bl, float& P, float& Q) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    P = -p;
+    Q = -e;
+}
