@@ -139,8 +139,8 @@ struct gbe_subs {
     Sp2Ctrl* d_ctrl = nullptr;
     Sp2Ctrl* h_ctrl = nullptr;       // pinned
     // tensor maps for the split planes (opaque 128-byte CUtensorMap blobs)
-    alignas(64) unsigned char tmap[2][128];    // K-chunk view
-    alignas(64) unsigned char tmapT[2][128];   // transposed (lower-block) view
+    // TMA descriptors [side][view: K-chunk, transposed][box: A planes, B planes, diagonal B]
+    alignas(64) unsigned char tmap[2][2][3][128];
     bool tmap_ok = false;
     // phase timing
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};

@@ -77,6 +77,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// 3-D box (x, y, plane z): the planes of one operand side in a single copy.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -149,26 +158,28 @@ __host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type) {
 }
 
 // ------------------------------------------------------------------ recipes
-// Operand slots of a stage: A slots first, then B slots; `plane` is the storage plane,
-// `alias` the A slot holding the same plane on diagonal tiles (-1: always loaded).
+// Operand slots of a stage: A slots first, then B slots, each side in storage-plane order
+// so that one 3-D TMA box (planes as its third dimension) fills a side's slots; `plane` is
+// the storage plane, `alias` the A slot holding the same plane on diagonal tiles (-1: always
+// loaded).  On a diagonal tile B's non-aliased slots are the planes kA.. (kDiag of them).
 template <int PREC>
 struct Recipe;
 
 // Tables are packed 4-bit fields indexed by slot / product number.
 template <>
 struct Recipe<GBE_PREC_FP16X6> {
-    // slots: A {s0, s1, s2}, B {s0, s1, s1s, s2}; products into acc0: s0 s0^T,
+    // slots: A {s0, s1, s2}, B {s0, s1, s2, s1s}; products into acc0: s0 s0^T,
     // into acc1 (units 2^-11): s0 s1^T, s1 s0^T, s1 s1s^T, s0 s2^T, s2 s0^T
-    static constexpr int kSlots = 7, kA = 3, kProducts = 6, kPlanes = 4, kStages = 4;
+    static constexpr int kSlots = 7, kA = 3, kProducts = 6, kPlanes = 4, kStages = 4, kDiag = 1;
     static constexpr uint32_t kType = 0;  // fp16
-    static constexpr uint32_t kPlane = 0x2310210u, kAlias1 = 0x3021000u;
-    static constexpr uint32_t kPa = 0x201100u, kPb = 0x365343u, kPacc = 0x111110u;
+    static constexpr uint32_t kPlane = 0x3210210u, kAlias1 = 0x0321000u;
+    static constexpr uint32_t kPa = 0x201100u, kPb = 0x356343u, kPacc = 0x111110u;
 };
 
 template <>
 struct Recipe<GBE_PREC_BF16X3> {
     // slots: A {hi, lo}, B {hi, lo}; products hi hi^T + hi lo^T + lo hi^T into acc0
-    static constexpr int kSlots = 4, kA = 2, kProducts = 3, kPlanes = 2, kStages = 6;
+    static constexpr int kSlots = 4, kA = 2, kProducts = 3, kPlanes = 2, kStages = 6, kDiag = 0;
     static constexpr uint32_t kType = 1;  // bf16
     static constexpr uint32_t kPlane = 0x1010u, kAlias1 = 0x2100u;
     static constexpr uint32_t kPa = 0x100u, kPb = 0x232u, kPacc = 0x0u;
@@ -199,6 +210,13 @@ __device__ unsigned long long g_tc_stats[16];
 #define TC_FLUSH()
 #endif
 
+// 3-D tensor maps [side][view][box]: view 0 = K-chunk view of stored blocks, view 1 =
+// transposed view (lower blocks); box 0 = A planes (depth kA), 1 = B planes (depth kSlots-kA),
+// 2 = B planes of a diagonal tile (depth kDiag, from plane kA).
+struct TcMaps {
+    CUtensorMap m[2][2][3];
+};
+
 struct TcArgs {
     Sp2Ctrl* ctrl;
     SubsGeom g;
@@ -211,13 +229,9 @@ struct TcArgs {
     int slot;
 };
 
-// Double-float sum (sh, sl) += (bh, bl) (TwoSum on the high parts).
-
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1)
-    sp2_square_tc_kernel(const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1,
-                         const __grid_constant__ CUtensorMap tmapT0, const __grid_constant__ CUtensorMap tmapT1,
-                         TcArgs args) {
+    sp2_square_tc_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     using R = Recipe<PREC>;
     constexpr int NS = R::kStages;
     extern __shared__ unsigned char smem_raw[];
@@ -255,8 +269,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (blockIdx.x == 0 && threadIdx.x == 0) { ctrl->pending = 1; ctrl->slot_ran[args.slot] |= 1; }
     const int cur = hdr[1], branch = hdr[2];
     const long long budget = ctrl->timeout_cycles;
-    const CUtensorMap* tmap = cur ? &tmap1 : &tmap0;      // K-chunks of stored (upper) blocks
-    const CUtensorMap* tmapT = cur ? &tmapT1 : &tmapT0;   // transposed K-chunks for lower blocks
+    const CUtensorMap(*tm)[3] = maps.m[cur];              // [view][box] of the current side
     const uint16_t* pin = cur ? args.planes[1] : args.planes[0];
     uint16_t* pout = cur ? args.planes[0] : args.planes[1];
     const int64_t ps = args.ps;
@@ -285,8 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int64_t off = args.g.off[w.s];
                 const int nk = (m + 31) >> 5;
                 const bool diag = (w.I == w.J);
-                int nload = 0;
-                for (int sl = 0; sl < R::kSlots; ++sl) nload += !(diag && slot_alias<R>(sl) >= 0);
+                const int nload = R::kA + (diag ? R::kDiag : R::kSlots - R::kA);
                 for (int kc = 0; kc < nk; ++kc) {
                     bool got;
                     {
@@ -299,20 +311,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                     issued_mask |= 1u << stage;
                     issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
                     unsigned char* st = tiles + (size_t)stage * R::kSlots * kTileBytes;
-                    for (int sl = 0; sl < R::kSlots; ++sl) {
-                        if (diag && slot_alias<R>(sl) >= 0) continue;
-                        const int Rt = (sl < R::kA) ? w.I : w.J;
-                        const int kb = kc >> 2;
-                        const int64_t g0 = (int64_t)slot_plane<R>(sl) * (ps >> 10) + (off >> 10);
+                    const int kb = kc >> 2;
+                    const int64_t g0 = off >> 10;
+                    // side A (row block I), then side B (column block J): one box per side
+#pragma unroll
+                    for (int side = 0; side < 2; ++side) {
+                        const int Rt = side == 0 ? w.I : w.J;
+                        const int bx = side == 0 ? 0 : (diag ? 2 : 1);
+                        if (side == 1 && diag && R::kDiag == 0) continue;
+                        const int slot0 = side == 0 ? 0 : (diag ? R::kA + R::kA : R::kA);
+                        const int z = side == 1 && diag ? R::kA : 0;
+                        unsigned char* dst = st + (size_t)slot0 * kTileBytes;
                         if (Rt <= kb) {
                             // stored block (Rt, kb): 4 column groups of 1024 elements = 16 view rows of 256
                             const int64_t y = (g0 + (int64_t)Rt * (mpad >> 3) + 4 * kc) << 2;
-                            tma_load_2d(st + (size_t)sl * kTileBytes, tmap, &full[stage], 0, (int)y);
+                            tma_load_3d(dst, &tm[0][bx], &full[stage], 0, (int)y, z);
                         } else {
                             // lower block: rows 32 (kc & 3).. of stored block (kb, Rt), its 16 column
                             // groups -> [16 groups][32 rows][8], an MN-major operand tile
                             const int64_t y = g0 + (int64_t)kb * (mpad >> 3) + 16 * Rt;
-                            tma_load_2d(st + (size_t)sl * kTileBytes, tmapT, &full[stage], 256 * (kc & 3), (int)y);
+                            tma_load_3d(dst, &tm[1][bx], &full[stage], 256 * (kc & 3), (int)y, z);
                         }
                     }
                     if (++stage == NS) { stage = 0; phase ^= 1; }
@@ -618,46 +636,34 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
         gbe_set_error("tensor maps requested before gbe_tc_prepare");
         return GBE_ECUDA;
     }
-    const int nplanes = 4;
-    for (int side = 0; side < 2; ++side) {
-        // transposed view: one 2 KB column group per view row; a box of 256 x 16 takes 32
-        // rows of 16 consecutive column groups
-        {
-            CUtensorMap m;
-            memset(&m, 0, sizeof(m));
-            cuuint64_t dims[2] = {1024, (cuuint64_t)(nplanes * X->total_elems / 1024)};
-            cuuint64_t strides[1] = {2048};
-            cuuint32_t box[2] = {256, 16};
-            cuuint32_t estr[2] = {1, 1};
-            CUresult r = g_encode_tiled(&m, X->prec == GBE_PREC_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-                                        2, X->planes[side], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) {
-                gbe_set_error("cuTensorMapEncodeTiled (transposed view) failed (%d)", (int)r);
-                return GBE_ECUDA;
+    const int nplanes = 4;   // plane buffers hold 4 planes of total_elems for every split format
+    const bool fp16 = X->prec != GBE_PREC_BF16X3;
+    const int depth[3] = {fp16 ? 3 : 2, fp16 ? 4 : 2, fp16 ? 1 : 1};
+    for (int side = 0; side < 2; ++side)
+        for (int view = 0; view < 2; ++view)
+            for (int bx = 0; bx < 3; ++bx) {
+                CUtensorMap m;
+                memset(&m, 0, sizeof(m));
+                // view 0: rows of 256 elements (512 B); a 32-column K-chunk of a row block is one
+                // contiguous 8 KB run = a 256 x 16 box per plane, copied unchanged.
+                // view 1 (transposed): one 2 KB column group per row; a 256 x 16 box takes 32 rows
+                // of 16 consecutive column groups.  Planes are the third dimension.
+                const cuuint64_t inner = view == 0 ? 256 : 1024;
+                cuuint64_t dims[3] = {inner, (cuuint64_t)(X->total_elems / inner), (cuuint64_t)nplanes};
+                cuuint64_t strides[2] = {inner * 2, (cuuint64_t)X->total_elems * 2};
+                cuuint32_t box[3] = {256, 16, (cuuint32_t)depth[bx]};
+                cuuint32_t estr[3] = {1, 1, 1};
+                CUresult r = g_encode_tiled(&m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                                            X->planes[side], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS) {
+                    gbe_set_error("cuTensorMapEncodeTiled (view %d, box %d) failed (%d)", view, bx, (int)r);
+                    return GBE_ECUDA;
+                }
+                static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
+                memcpy(X->tmap[side][view][bx], &m, sizeof(m));
             }
-            memcpy(X->tmapT[side], &m, sizeof(m));
-        }
-        CUtensorMap m;
-        memset(&m, 0, sizeof(m));
-        // view: rows of 256 elements (512 B); a 32-column K-chunk of a row block is one
-        // contiguous 8 KB run = a 256 x 16 box, copied unchanged
-        cuuint64_t dims[2] = {256, (cuuint64_t)(nplanes * X->total_elems / 256)};
-        cuuint64_t strides[1] = {512};
-        cuuint32_t box[2] = {256, 16};
-        cuuint32_t estr[2] = {1, 1};
-        CUresult r = g_encode_tiled(&m, X->prec == GBE_PREC_BF16X3 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-                                    2, X->planes[side], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            gbe_set_error("cuTensorMapEncodeTiled failed (%d)", (int)r);
-            return GBE_ECUDA;
-        }
-        static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
-        memcpy(X->tmap[side], &m, sizeof(m));
-    }
     X->tmap_ok = true;
     return GBE_OK;
 }
@@ -678,16 +684,14 @@ int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot) {
     a.partials = X->d_partials;
     a.max_units = X->max_units;
     a.slot = slot;
-    CUtensorMap m0, m1, t0, t1;
-    memcpy(&m0, X->tmap[0], sizeof(m0));
-    memcpy(&m1, X->tmap[1], sizeof(m1));
-    memcpy(&t0, X->tmapT[0], sizeof(t0));
-    memcpy(&t1, X->tmapT[1], sizeof(t1));
+    TcMaps maps;
+    static_assert(sizeof(maps) == sizeof(X->tmap), "tensor map set size");
+    memcpy(&maps, X->tmap, sizeof(maps));
     const int grid = std::max(1, std::min(X->n_items_tc, ctx->sm_count));
     if (X->prec == GBE_PREC_FP16X6)
-        sp2_square_tc_kernel<GBE_PREC_FP16X6><<<grid, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(m0, m1, t0, t1, a);
+        sp2_square_tc_kernel<GBE_PREC_FP16X6><<<grid, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(maps, a);
     else
-        sp2_square_tc_kernel<GBE_PREC_BF16X3><<<grid, kThreads, smem_bytes<GBE_PREC_BF16X3>(), ctx->stream>>>(m0, m1, t0, t1, a);
+        sp2_square_tc_kernel<GBE_PREC_BF16X3><<<grid, kThreads, smem_bytes<GBE_PREC_BF16X3>(), ctx->stream>>>(maps, a);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }
