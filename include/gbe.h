@@ -101,6 +101,13 @@ int gbe_set_stream(gbe_ctx* ctx, void* cuda_stream);
  * squaring launch on the context stream and gbe_sp2_report_get sums the durations of
  * the launches that did work (ms_tc / n_tc, ms_fp64 / n_fp64). */
 int gbe_set_profiling(gbe_ctx* ctx, int on);
+/* Launch each SP2 run as two CUDA graphs (default on): the prologue (control block,
+ * spectral bounds, gather, first decision) and a loop node whose body is one SP2 step,
+ * repeated on the device while the run's own decision says continue, so exactly the steps
+ * a run needs are executed and no host round trip is involved.  The graphs are captured on
+ * the first run and relaunched while parameters and inputs (pointers, sizes) are unchanged.
+ * Profiling (gbe_set_profiling) launches step by step instead, to time every squaring. */
+int gbe_set_graph_launch(gbe_ctx* ctx, int on);
 /* Number of SMs of the context's device (grids are sized from it). */
 int gbe_device_sm_count(const gbe_ctx* ctx);
 const char* gbe_strerror(int code);

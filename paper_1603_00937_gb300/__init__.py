@@ -28,7 +28,7 @@ SEQ_MAX = 256
 
 # Every entry point declared in include/gbe.h (checked by the CPU test suite).
 EXPORTS = [
-    "gbe_create", "gbe_destroy", "gbe_set_stream", "gbe_set_profiling", "gbe_device_sm_count", "gbe_strerror",
+    "gbe_create", "gbe_destroy", "gbe_set_stream", "gbe_set_profiling", "gbe_set_graph_launch", "gbe_device_sm_count", "gbe_strerror",
     "gbe_last_error_message", "gbe_build_hamiltonian", "gbe_hamiltonian_csr", "gbe_free_hamiltonian",
     "gbe_build_graph", "gbe_graph_size", "gbe_graph_export", "gbe_free_graph", "gbe_partition",
     "gbe_parts_info", "gbe_parts_export", "gbe_parts_import", "gbe_free_parts", "gbe_subs_create",
@@ -121,7 +121,7 @@ def load_library(path=LIB_PATH):
     P, I64, I32, D, C = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_char_p
     sig = {
         "gbe_create": (I32, [P, I32, P]), "gbe_destroy": (I32, [P]), "gbe_set_stream": (I32, [P, P]),
-        "gbe_device_sm_count": (I32, [P]), "gbe_set_profiling": (I32, [P, I32]), "gbe_strerror": (C, [I32]), "gbe_last_error_message": (C, []),
+        "gbe_device_sm_count": (I32, [P]), "gbe_set_profiling": (I32, [P, I32]), "gbe_set_graph_launch": (I32, [P, I32]), "gbe_strerror": (C, [I32]), "gbe_last_error_message": (C, []),
         "gbe_build_hamiltonian": (I32, [P, P, P, P]), "gbe_hamiltonian_csr": (I32, [P, P]),
         "gbe_free_hamiltonian": (I32, [P]), "gbe_build_graph": (I32, [P, P, P, P]),
         "gbe_graph_size": (I32, [P, P, P, P]), "gbe_graph_export": (I32, [P, P, P, P]),
@@ -200,6 +200,9 @@ class Context:
 
     def set_profiling(self, on=True):
         check(load_library().gbe_set_profiling(self._h, 1 if on else 0), "gbe_set_profiling")
+
+    def set_graph_launch(self, on=True):
+        check(load_library().gbe_set_graph_launch(self._h, 1 if on else 0), "gbe_set_graph_launch")
 
     def set_stream(self, stream):
         check(load_library().gbe_set_stream(self._h, ctypes.c_void_p(stream)), "gbe_set_stream")

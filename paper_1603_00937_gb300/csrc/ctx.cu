@@ -175,4 +175,10 @@ extern "C" int gbe_set_profiling(gbe_ctx* ctx, int on) {
     return GBE_OK;
 }
 
+extern "C" int gbe_set_graph_launch(gbe_ctx* ctx, int on) {
+    GBE_CHECK_ARG(ctx != nullptr, "ctx is NULL");
+    ctx->graphs = on ? 1 : 0;
+    return GBE_OK;
+}
+
 extern "C" int gbe_device_sm_count(const gbe_ctx* ctx) { return ctx ? ctx->sm_count : 0; }

@@ -45,6 +45,7 @@ struct gbe_ctx {
     void* d_scratch = nullptr;
     void* h_scratch = nullptr;
     int profile = 0;
+    int graphs = 1;   // SP2 runs launched as CUDA graphs (when per-kernel profiling is off)
     // stream-ordered device memory pool of this context (freed blocks are kept for reuse)
     cudaMemPool_t pool = nullptr;
 };
@@ -92,6 +93,7 @@ struct Sp2Ctrl {
     int fp64_iters;
     int switch_iter; // first FP64 iteration in mixed runs (-1 before the switch)
     int pending;     // a squaring kernel ran since the last decision
+    int loops;       // iterations of the graph's device-driven loop (guard)
     uint8_t slot_ran[GBE_SEQ_MAX];  // per launch slot: bit 0 tensor-core kernel worked, bit 1 FP64 kernel
     int n_min, n_max, branch_mode, seq_len, fp64_tail, prec, eps_given;
     unsigned long long eps_min_key, eps_max_key;  // order-preserving keys for atomics
@@ -147,6 +149,12 @@ struct gbe_subs {
     std::vector<cudaEvent_t> ev_tc, ev_64;   // [2 * slot + {0,1}] when profiling
     int last_slots = 0;
     bool last_prof = false;
+    // CUDA graphs of a run: [0] control init, bounds, gather, first decision; [1] a loop node
+    // whose body is one SP2 step, repeated while the device's decision says continue.
+    // Reused while a run's parameters and inputs match the key they were captured with.
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    std::vector<unsigned char> gkey;
+    cudaStream_t cap_stream = nullptr;
     double alg_flops_per_iter = 0.0, mma_flops_per_iter = 0.0, fp64_flops_per_iter = 0.0;
 };
 

@@ -260,10 +260,29 @@ __global__ void init_ctrl_kernel(Sp2Ctrl* C, Sp2Init in) {
 // ----------------------------------------------------------------------------- decide
 // Global FP64 traces over core positions -> stop rule and branch of the next step.
 // kind: 0 after the gather (X_0), 1 after a tensor-core step, 2 after an FP64 step.
+// In a graph-launched run the last decision of a loop iteration (set_cond) also sets the
+// loop node's condition: continue while the run has not stopped, and never beyond
+// n_max + 8 iterations of the loop.
+__device__ void decide_body(Sp2Ctrl* ctrl, const double* __restrict__ partials, int max_units, int n_units, int kind,
+                            double* red, int* run);
+
 __global__ void __launch_bounds__(512) decide_kernel(Sp2Ctrl* ctrl, const double* __restrict__ partials,
-                                                     int max_units, int n_units, int kind) {
+                                                     int max_units, int n_units, int kind,
+                                                     cudaGraphConditionalHandle cond, int set_cond) {
     __shared__ double red[16];
     __shared__ int run;
+    decide_body(ctrl, partials, max_units, n_units, kind, red, &run);
+    if (set_cond && threadIdx.x == 0) {
+        __threadfence_block();
+        Sp2Ctrl* C = ctrl;
+        if (++C->loops > C->n_max + 8 && C->stop == 0) C->stop = GBE_STOP_NMAX;
+        cudaGraphSetConditional(cond, C->stop == 0 ? 1u : 0u);
+    }
+}
+
+__device__ void decide_body(Sp2Ctrl* ctrl, const double* __restrict__ partials, int max_units, int n_units, int kind,
+                            double* red, int* run_flag) {
+    int& run = *run_flag;
     if (threadIdx.x == 0) run = (kind == 0) ? 1 : ctrl->pending;
     __syncthreads();
     if (!run) return;
@@ -344,7 +363,10 @@ __global__ void __launch_bounds__(256) square_fp64_kernel(Sp2Ctrl* ctrl, SubsGeo
     }
     __syncthreads();
     if (!hdr[0]) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) { ctrl->pending = 1; ctrl->slot_ran[slot] |= 2; }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->pending = 1;
+        if (slot >= 0) ctrl->slot_ran[slot] |= 2;   // launch slots (profiled runs) only
+    }
     const int cur = hdr[1], fmt = hdr[2], branch = hdr[3], prec = hdr[4];
     const uint16_t* pin = cur ? planes1 : planes0;
     const double* fin = cur ? f1 : f0;
@@ -555,6 +577,8 @@ extern "C" int gbe_free_parts(gbe_parts* p) {
     return GBE_OK;
 }
 
+static void drop_graphs(gbe_subs* X);
+
 extern "C" int gbe_free_subs(gbe_subs* X) {
     if (!X) return GBE_OK;
     gbe_free(X->d_off); gbe_free(X->d_mpad); gbe_free(X->d_m); gbe_free(X->d_c);
@@ -564,6 +588,8 @@ extern "C" int gbe_free_subs(gbe_subs* X) {
     for (int i = 0; i < 3; ++i) if (X->ev[i]) cudaEventDestroy(X->ev[i]);
     for (auto e : X->ev_tc) cudaEventDestroy(e);
     for (auto e : X->ev_64) cudaEventDestroy(e);
+    drop_graphs(X);
+    if (X->cap_stream) cudaStreamDestroy(X->cap_stream);
     delete X;
     return GBE_OK;
 }
@@ -670,6 +696,110 @@ int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X) {
     return GBE_OK;
 }
 
+// Control init, spectral bounds, gather and the first decision of a run (on ctx->stream).
+static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, gbe_subs* X) {
+    cudaStream_t st = ctx->stream;
+    init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
+    GBE_CUDA_TRY(cudaGetLastError());
+    if (!in.eps_given) GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
+    const gbe_parts* parts = X->parts;
+    const size_t smem = (size_t)8 * X->max_mpad * 8 + (size_t)parts->max_m * 4;
+    auto gk = X->prec == GBE_PREC_FP64 ? gather_kernel<GBE_PREC_FP64>
+            : (X->prec == GBE_PREC_FP16X6 ? gather_kernel<GBE_PREC_FP16X6> : gather_kernel<GBE_PREC_BF16X3>);
+    gk<<<(unsigned)X->P, 256, smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
+                                           geom_of(X), X->max_mpad, X->planes[0], X->total_elems, X->f64[0],
+                                           X->d_partials, X->max_units);
+    GBE_CUDA_TRY(cudaGetLastError());
+    decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, (int)X->P, 0, 0, 0);
+    GBE_CUDA_TRY(cudaGetLastError());
+    return GBE_OK;
+}
+
+// One SP2 step: the tensor-core squaring and/or the FP64 squaring, each followed by its
+// decision (kernels whose turn it is not exit at once).  slot >= 0 records profiling
+// events; in a graph body slot = -1 and the last decision sets the loop condition.
+static int enqueue_step(gbe_ctx* ctx, gbe_subs* X, bool fp64_steps, int slot, cudaGraphConditionalHandle cond,
+                        bool set_cond) {
+    cudaStream_t st = ctx->stream;
+    const bool prof = slot >= 0 && ctx->profile != 0;
+    const bool has_tc = X->prec != GBE_PREC_FP64;
+    if (has_tc) {
+        if (prof) cudaEventRecord(X->ev_tc[2 * slot], st);
+        GBE_TRY(gbe_tc_launch_square(ctx, X, slot));
+        if (prof) cudaEventRecord(X->ev_tc[2 * slot + 1], st);
+        decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_tc, 1, cond,
+                                         set_cond && !fp64_steps ? 1 : 0);
+    }
+    if (fp64_steps) {
+        const int grid64 = std::max(1, std::min(X->n_items_64, ctx->sm_count * 4));
+        if (prof) cudaEventRecord(X->ev_64[2 * slot], st);
+        square_fp64_kernel<<<grid64, 256, 0, st>>>(X->d_ctrl, geom_of(X), X->d_items_64, X->n_items_64, X->planes[0],
+                                                   X->planes[1], X->total_elems, X->f64[0], X->f64[1], X->d_partials,
+                                                   X->max_units, slot);
+        if (prof) cudaEventRecord(X->ev_64[2 * slot + 1], st);
+        decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_64, 2, cond,
+                                         set_cond ? 1 : 0);
+    }
+    GBE_CUDA_TRY(cudaGetLastError());
+    return GBE_OK;
+}
+
+static void drop_graphs(gbe_subs* X) {
+    for (int i = 0; i < 2; ++i)
+        if (X->gexec[i]) { cudaGraphExecDestroy(X->gexec[i]); X->gexec[i] = nullptr; }
+    X->gkey.clear();
+}
+
+// Capture the two graphs of a run on the state's own capture stream (capture is not
+// possible on the legacy default stream) and instantiate them.
+static int build_graphs(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, gbe_subs* X, bool fp64_steps) {
+    drop_graphs(X);
+    if (!X->cap_stream) GBE_CUDA_TRY(cudaStreamCreateWithFlags(&X->cap_stream, cudaStreamNonBlocking));
+    const cudaStream_t saved = ctx->stream;
+    ctx->stream = X->cap_stream;
+    int r = GBE_OK;
+    cudaGraph_t g0 = nullptr, g1 = nullptr, tmp = nullptr;
+    // graph 0: prologue
+    cudaError_t e = cudaStreamBeginCapture(X->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        r = enqueue_prologue(ctx, H, in, X);
+        e = cudaStreamEndCapture(X->cap_stream, &g0);
+    }
+    // graph 1: while (the last decision says continue) { one SP2 step }
+    cudaGraphConditionalHandle cond = 0;
+    if (e == cudaSuccess && r == GBE_OK) e = cudaGraphCreate(&g1, 0);
+    if (e == cudaSuccess && r == GBE_OK) e = cudaGraphConditionalHandleCreate(&cond, g1, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    if (e == cudaSuccess && r == GBE_OK) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = cond;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        cudaGraphNode_t node;
+        e = cudaGraphAddNode(&node, g1, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess && r == GBE_OK) {
+        e = cudaStreamBeginCaptureToGraph(X->cap_stream, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            r = enqueue_step(ctx, X, fp64_steps, -1, cond, true);
+            e = cudaStreamEndCapture(X->cap_stream, &tmp);
+        }
+    }
+    if (e == cudaSuccess && r == GBE_OK) e = cudaGraphInstantiate(&X->gexec[0], g0, 0);
+    if (e == cudaSuccess && r == GBE_OK) e = cudaGraphInstantiate(&X->gexec[1], g1, 0);
+    ctx->stream = saved;
+    if (g0) cudaGraphDestroy(g0);
+    if (g1) cudaGraphDestroy(g1);
+    if (r == GBE_OK && e != cudaSuccess) {
+        gbe_set_error("SP2 graph capture: %s", cudaGetErrorString(e));
+        (void)cudaGetLastError();
+        r = GBE_ECUDA;
+    }
+    if (r != GBE_OK) drop_graphs(X);
+    return r;
+}
+
 extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* prm,
                            gbe_subs* X) {
     AllocScope alloc_scope_(ctx);
@@ -705,23 +835,40 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     in.timeout_cycles = (long long)(tmo * 2.2e6);
     if (in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len) memcpy(in.seq_in, prm->seq_in, in.seq_len);
     if (in.prec != GBE_PREC_FP64 && in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len <= in.fp64_tail) in.mode = 1;
-    init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
-    GBE_CUDA_TRY(cudaGetLastError());
-    cudaEventRecord(X->ev[0], st);
-    if (!prm->eps_given) GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
-    const int64_t ps = X->total_elems;
-    const size_t smem = (size_t)8 * X->max_mpad * 8 + (size_t)parts->max_m * 4;
-    auto gk = X->prec == GBE_PREC_FP64 ? gather_kernel<GBE_PREC_FP64>
-            : (X->prec == GBE_PREC_FP16X6 ? gather_kernel<GBE_PREC_FP16X6> : gather_kernel<GBE_PREC_BF16X3>);
-    cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    gk<<<(unsigned)X->P, 256, smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
-                                           geom_of(X), X->max_mpad, X->planes[0], ps, X->f64[0], X->d_partials,
-                                           X->max_units);
-    GBE_CUDA_TRY(cudaGetLastError());
-    decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, (int)X->P, 0);
-    cudaEventRecord(X->ev[1], st);
-    const int grid64 = std::max(1, std::min(X->n_items_64, ctx->sm_count * 4));
+    const bool fp64_steps = X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0;
+    // kernel attributes are set outside any capture
+    {
+        const size_t smem = (size_t)8 * X->max_mpad * 8 + (size_t)parts->max_m * 4;
+        auto gk = X->prec == GBE_PREC_FP64 ? gather_kernel<GBE_PREC_FP64>
+                : (X->prec == GBE_PREC_FP16X6 ? gather_kernel<GBE_PREC_FP16X6> : gather_kernel<GBE_PREC_BF16X3>);
+        GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     const bool prof = ctx->profile != 0;
+    if (ctx->graphs && !prof) {
+        // graph launch: the loop runs exactly as many steps as the device decides
+        std::vector<unsigned char> key(sizeof(in) + 5 * sizeof(int64_t) + 1);
+        unsigned char* k = key.data();
+        memcpy(k, &in, sizeof(in));
+        const int64_t ptrs[5] = {(int64_t)(uintptr_t)H->rowptr, (int64_t)(uintptr_t)H->col, (int64_t)(uintptr_t)H->val,
+                                 H->n, H->nnz};
+        memcpy(k + sizeof(in), ptrs, sizeof(ptrs));
+        k[sizeof(in) + sizeof(ptrs)] = fp64_steps ? 1 : 0;
+        if (!X->gexec[0] || key != X->gkey) {
+            GBE_TRY(build_graphs(ctx, H, in, X, fp64_steps));
+            X->gkey = key;
+        }
+        cudaEventRecord(X->ev[0], st);
+        GBE_CUDA_TRY(cudaGraphLaunch(X->gexec[0], st));
+        cudaEventRecord(X->ev[1], st);
+        GBE_CUDA_TRY(cudaGraphLaunch(X->gexec[1], st));
+        cudaEventRecord(X->ev[2], st);
+        X->last_slots = 0;
+        X->last_prof = false;
+        return GBE_OK;
+    }
+    cudaEventRecord(X->ev[0], st);
+    GBE_TRY(enqueue_prologue(ctx, H, in, X));
+    cudaEventRecord(X->ev[1], st);
     if (prof && (int)X->ev_tc.size() < 2 * prm->n_max) {
         for (int i = (int)X->ev_tc.size(); i < 2 * prm->n_max; ++i) {
             cudaEvent_t a, b;
@@ -732,22 +879,7 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
         }
     }
     X->last_slots = prm->n_max;
-    for (int slot = 0; slot < prm->n_max; ++slot) {
-        if (X->prec != GBE_PREC_FP64) {
-            if (prof) cudaEventRecord(X->ev_tc[2 * slot], st);
-            GBE_TRY(gbe_tc_launch_square(ctx, X, slot));
-            if (prof) cudaEventRecord(X->ev_tc[2 * slot + 1], st);
-            decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_tc, 1);
-        }
-        if (X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0) {
-            if (prof) cudaEventRecord(X->ev_64[2 * slot], st);
-            square_fp64_kernel<<<grid64, 256, 0, st>>>(X->d_ctrl, geom_of(X), X->d_items_64, X->n_items_64,
-                                                       X->planes[0], X->planes[1], ps, X->f64[0], X->f64[1],
-                                                       X->d_partials, X->max_units, slot);
-            if (prof) cudaEventRecord(X->ev_64[2 * slot + 1], st);
-            decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_64, 2);
-        }
-    }
+    for (int slot = 0; slot < prm->n_max; ++slot) GBE_TRY(enqueue_step(ctx, X, fp64_steps, slot, 0, false));
     X->last_prof = prof;
     GBE_CUDA_TRY(cudaGetLastError());
     cudaEventRecord(X->ev[2], st);

@@ -266,7 +266,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     __syncthreads();
     if (!hdr[0]) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) { ctrl->pending = 1; ctrl->slot_ran[args.slot] |= 1; }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctrl->pending = 1;
+        if (args.slot >= 0) ctrl->slot_ran[args.slot] |= 1;   // launch slots (profiled runs) only
+    }
     const int cur = hdr[1], branch = hdr[2];
     const long long budget = ctrl->timeout_cycles;
     const CUtensorMap(*tm)[3] = maps.m[cur];              // [view][box] of the current side

@@ -179,3 +179,33 @@ def test_drop_tolerance_and_width_query(ctx, c1):
     for r in range(0, N, 51):
         k = (col1[r] >= 0).sum()
         assert np.all(col1[r, :k] >= 0) and np.all(col1[r, k:] == -1)
+
+
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6])
+def test_graph_launch_matches_step_launch(prec):
+    """The CUDA-graph path (device-driven loop) and the step-by-step launch path run the same
+    kernels: identical decisions and bit-identical D; the captured graphs are reused while
+    inputs and parameters are unchanged and recaptured when they change."""
+    case = ragged_case()
+    H = case["H"]
+    N = H.shape[0]
+    outs = []
+    for mode in ("graph", "steps", "profiled", "graph-again"):
+        ctx = gbe.Context(0)
+        ctx.set_graph_launch(mode != "steps")
+        ctx.set_profiling(mode == "profiled")
+        parts = import_parts(ctx, N, case["subs"], case["nc"])
+        Hd = device_csr(H)
+        p = gbe.sp2_params(N // 2, prec=prec, n_max=60)
+        X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p)
+        if mode == "graph-again":
+            # relaunch (reuse), then a changed parameter set (replay) forces a recapture
+            X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p, X)
+            X2, rep2 = gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=prec, seq=rep["seq"][:5]), X)
+            assert rep2["iters"] == 5
+            X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p, X)
+        D, _, _ = assembled_dense(ctx, X, parts, N)
+        outs.append((rep["seq"], rep["stop"], D))
+    for seq, stop, D in outs[1:]:
+        assert seq == outs[0][0] and stop == outs[0][1]
+        np.testing.assert_array_equal(D, outs[0][2])
