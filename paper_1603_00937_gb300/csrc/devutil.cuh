@@ -118,6 +118,31 @@ __device__ __forceinline__ double min_image(double d, double L, double invL) {
 __device__ __forceinline__ double dist2(double x, double y, double z) {
     return __dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z));
 }
+// FP32 copies of the positions, one float4 per site (a 16-byte load per candidate).
+static __global__ void pos_f32_kernel(const double* __restrict__ pos, int64_t n, float4* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float4((float)pos[3 * i], (float)pos[3 * i + 1], (float)pos[3 * i + 2], 0.f);
+}
+
+// Cheap pre-filter of a candidate pair in FP32: rejects only pairs whose FP32 minimum-image
+// distance exceeds the cutoff plus a margin larger than the FP32 error of the positions and
+// of the box (see filter_lim2), so every pair the exact FP64 test accepts passes.
+__device__ __forceinline__ bool near_f32(float4 a, float4 b, float bx, float by, float bz, float ix, float iy, float iz,
+                                         float lim2) {
+    float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    dx -= bx * rintf(dx * ix);
+    dy -= by * rintf(dy * iy);
+    dz -= bz * rintf(dz * iz);
+    return dx * dx + dy * dy + dz * dz < lim2;
+}
+// (cutoff + margin)^2 with margin = 1e-3 + 2^-16 * box: FP32 positions and box lengths are
+// off by at most 2^-24 * box each, so the FP32 separation is within ~2^-21 * box of the exact one
+static inline float filter_lim2(double cutoff, const double box[3]) {
+    const double bmax = std::max(box[0], std::max(box[1], box[2]));
+    const double lim = cutoff + 1e-3 + bmax * (1.0 / 65536.0);
+    return (float)(lim * lim);
+}
+
 // squared minimum-image distance between sites i and j of a [n][3] position array
 __device__ __forceinline__ double pair_dist2(const double* pos, double xi, double yi, double zi, int j, const CellGrid& g) {
     return dist2(min_image(xi - pos[3 * j], g.box[0], g.inv[0]), min_image(yi - pos[3 * j + 1], g.box[1], g.inv[1]),

@@ -128,8 +128,9 @@ struct HModel {
 constexpr int kRowCap = 1024;
 
 // One warp per row.  pass 0: count neighbours; pass 1: write sorted (col, val).
-__global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ pos, const double* __restrict__ onsite,
-                                                     int64_t n, CellGrid g, const int64_t* __restrict__ cstart,
+__global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ pos, const float4* __restrict__ pos4,
+                                                     const double* __restrict__ onsite, int64_t n, CellGrid g,
+                                                     float lim2, const int64_t* __restrict__ cstart,
                                                      const int32_t* __restrict__ members, HModel mdl, int pass,
                                                      int32_t* cnt, const int64_t* __restrict__ rowptr, int32_t* col,
                                                      double* val, int* overflow) {
@@ -139,6 +140,9 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
     const int64_t i = (int64_t)blockIdx.x * 8 + w;
     if (i >= n) return;
     const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    const float4 pi = pos4[i];
+    const float bx = (float)g.box[0], by = (float)g.box[1], bz = (float)g.box[2];
+    const float ix = (float)g.inv[0], iy = (float)g.inv[1], iz = (float)g.inv[2];
     const int ci = cell_of(pos + 3 * i, g);
     int cc[3] = {ci / (g.nc[1] * g.nc[2]), (ci / g.nc[2]) % g.nc[1], ci % g.nc[2]};
     if (lane == 0) bcount[w] = 0;
@@ -158,8 +162,10 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
                 const int cell = (ax * g.nc[1] + ay) * g.nc[2] + az;
                 for (int64_t p = cstart[cell] + lane; p < cstart[cell + 1]; p += 32) {
                     const int j = members[p];
-                    // r^2 < rcut^2 (differs from r < rcut only within an ulp of the cutoff)
-                    if (j == i || pair_dist2(pos, xi, yi, zi, j, g) < mdl.rcut2) {
+                    // FP32 pre-filter, then r^2 < rcut^2 in FP64 (differs from r < rcut only within
+                    // an ulp of the cutoff)
+                    if (j == i || (near_f32(pi, pos4[j], bx, by, bz, ix, iy, iz, lim2) &&
+                                   pair_dist2(pos, xi, yi, zi, j, g) < mdl.rcut2)) {
                         const int k = atomicAdd(&bcount[w], 1);
                         if (k < kRowCap) buf[w][k] = j;
                     }
@@ -494,8 +500,13 @@ extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gb
     GBE_TRY(scan_exclusive(ctx, ccnt.as<int32_t>(), cstart.as<int64_t>(), ncells, nullptr));
     cell_fill_kernel<<<nb, 256, 0, s>>>(cell.as<int32_t>(), n, cstart.as<int64_t>(), cur.as<int32_t>(), mem.as<int32_t>());
     HModel mdl{model->a, model->rcut, model->decay, model->hop, model->rcut * model->rcut};
+    DevBuf p4;
+    GBE_TRY(gbe_alloc(&p4.p, n * 16));
+    pos_f32_kernel<<<nb, 256, 0, s>>>(pos, n, p4.as<float4>());
+    const float lim2 = filter_lim2(model->rcut, st->box);
     const unsigned rb = (unsigned)((n + 7) / 8);
-    hbuild_kernel<<<rb, 256, 0, s>>>(pos, ons, n, g, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 0, cnt.as<int32_t>(),
+    hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 0,
+                                     cnt.as<int32_t>(),
                                      nullptr, nullptr, nullptr, flag.as<int>());
     GBE_CUDA_TRY(cudaGetLastError());
     gbe_hamiltonian* H = new gbe_hamiltonian();
@@ -510,7 +521,8 @@ extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gb
     if (r == GBE_OK) r = gbe_alloc((void**)&H->val, nnz * 8);
     if (r != GBE_OK) { gbe_free_hamiltonian(H); return r; }
     H->nnz = nnz;
-    hbuild_kernel<<<rb, 256, 0, s>>>(pos, ons, n, g, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 1, cnt.as<int32_t>(),
+    hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 1,
+                                     cnt.as<int32_t>(),
                                      H->rowptr, H->col, H->val, flag.as<int>());
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

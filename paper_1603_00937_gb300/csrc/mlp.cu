@@ -33,8 +33,9 @@ constexpr int kBatch = 128;        // pairs per training batch (one per thread)
 constexpr int kLd = 68;            // padded row length of the batch activations (floats)
 
 // ------------------------------------------------------------------ candidate pairs + features
-__global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ pos, const double* __restrict__ onsite,
-                                                    int64_t n, CellGrid g, const int64_t* __restrict__ cstart,
+__global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ pos, const float4* __restrict__ pos4,
+                                                    const double* __restrict__ onsite, int64_t n, CellGrid g, float lim2,
+                                                    const int64_t* __restrict__ cstart,
                                                     const int32_t* __restrict__ members, double rcand, int pass,
                                                     int32_t* cnt, const int64_t* __restrict__ rowptr, int32_t* pj,
                                                     float* feat, const int64_t* __restrict__ hrp,
@@ -47,6 +48,9 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
     if (i >= n) return;
     const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
     const double rcand2 = rcand * rcand;
+    const float4 pi = pos4[i];
+    const float bx = (float)g.box[0], by = (float)g.box[1], bz = (float)g.box[2];
+    const float ix = (float)g.inv[0], iy = (float)g.inv[1], iz = (float)g.inv[2];
     const int ci = cell_of(pos + 3 * i, g);
     const int cc[3] = {ci / (g.nc[1] * g.nc[2]), (ci / g.nc[2]) % g.nc[1], ci % g.nc[2]};
     if (lane == 0) bcount[w] = 0;
@@ -66,7 +70,8 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
                 for (int64_t p = cstart[cell] + lane; p < cstart[cell + 1]; p += 32) {
                     const int j = members[p];
                     if (j == i) continue;
-                    if (pair_dist2(pos, xi, yi, zi, j, g) < rcand2) {   // r < rcand up to an ulp at the cutoff
+                    // FP32 pre-filter, then r < rcand in FP64 (up to an ulp at the cutoff)
+                    if (near_f32(pi, pos4[j], bx, by, bz, ix, iy, iz, lim2) && pair_dist2(pos, xi, yi, zi, j, g) < rcand2) {
                         const int k = atomicAdd(&bcount[w], 1);
                         if (k < kPairCap) buf[w][k] = j;
                     }
@@ -418,7 +423,12 @@ extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr*
     GBE_TRY(scan_exclusive(ctx, ccnt.as<int32_t>(), cst.as<int64_t>(), ncells, nullptr));
     cell_fill_kernel<<<nb, 256, 0, s>>>(cell.as<int32_t>(), n, cst.as<int64_t>(), cur.as<int32_t>(), mem.as<int32_t>());
     const unsigned rb = (unsigned)((n + 7) / 8);
-    pairs_kernel<<<rb, 256, 0, s>>>(pos, ons, n, g, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 0, cnt.as<int32_t>(),
+    DevBuf p4;
+    GBE_TRY(gbe_alloc(&p4.p, n * 16));
+    pos_f32_kernel<<<nb, 256, 0, s>>>(pos, n, p4.as<float4>());
+    const float lim2 = filter_lim2(rcand, st->box);
+    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 0,
+                                    cnt.as<int32_t>(),
                                     nullptr, nullptr, nullptr, rp, ci, va, flag.as<int>());
     GBE_CUDA_TRY(cudaGetLastError());
     gbe_pairs* P = new gbe_pairs();
@@ -433,7 +443,8 @@ extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr*
     if (r == GBE_OK) r = gbe_alloc((void**)&P->feat, std::max<int64_t>(np, 1) * kNF * 4);
     if (r != GBE_OK) { gbe_free_pairs(P); return r; }
     P->npairs = np;
-    pairs_kernel<<<rb, 256, 0, s>>>(pos, ons, n, g, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 1, cnt.as<int32_t>(),
+    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 1,
+                                    cnt.as<int32_t>(),
                                     P->rowptr, P->j, P->feat, rp, ci, va, flag.as<int>());
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
