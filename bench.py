@@ -138,6 +138,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, world):
+    """The largest of every rank's value (the whole job's time), via an all-reduce on the
+    process group's device (CUDA tensors for NCCL, host tensors for gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -267,10 +280,7 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
     torch.cuda.synchronize()
     total = time.perf_counter() - t_start
     clk = clocks.stop()
-    if world > 1:
-        tt = torch.tensor([total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total = float(tt.item())
+    total = max_over_ranks(total, world)
     rep, ms = last["rep"], last["ms"]
     peaks, peak_kind = load_peaks()
     tc_ms = rep["ms_tc"] / max(1, rep["n_tc"])
@@ -387,10 +397,7 @@ def main():
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, world)
         return ms, gbe.sp2_report_get(ctx, X).as_dict()
 
     prec_name, dtype_name = PRECS[args.prec]
@@ -457,10 +464,7 @@ def main():
         gbe.sp2_submatrices(ctx, Hhost, parts, pm, Xm)
         gbe.assemble_D(ctx, Xm, parts, col_h.numpy(), val_h.numpy())
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world)
     h2d = (N + 1) * 8 + Hv.nnz * 12
     d2h = n * width * 12 + 4616
 
