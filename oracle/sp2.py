@@ -244,3 +244,53 @@ def sequence_from_gap(eps, homo, lumo, tol, n_max=256):
         xh, xl = (xh * xh, xl * xl) if b else (2 * xh - xh * xh, 2 * xl - xl * xl)
         seq.append(int(b))
     return seq
+
+
+# ---------------------------------------------------------------- finite temperature (Eq. 7)
+# D = [exp(beta (H - mu)) + 1]^-1 ~ sum_n c_n T_n(x), x = (H - a I) / b on the Gershgorin
+# interval [e_min, e_max] (a its centre, b its half-width).  Readings: the coefficients are
+# the Chebyshev interpolant of the Fermi function at K = 2 (order + 1) Chebyshev-Gauss
+# nodes (c_n = (2 - delta_n0) / K sum_j f(a + b cos t_j) cos(n t_j), t_j = pi (j + 1/2) / K);
+# the series is evaluated per subgraph with Clenshaw's recurrence
+#   b_k = c_k I + 2 x b_{k+1} - b_{k+2} (k = order .. 1, b_{order+1} = b_{order+2} = 0),
+#   P = c_0 I + x b_1 - b_2,
+# which is the same polynomial as the forward sum of c_n T_n (Eqs. 4-5) in another order.
+def fermi(e, beta, mu):
+    """Fermi function [exp(beta (e - mu)) + 1]^-1 without overflow."""
+    z = beta * (np.asarray(e, dtype=np.float64) - mu)
+    return 0.5 * (1.0 - np.tanh(0.5 * z))
+
+
+def fermi_chebyshev_coeffs(beta, mu, eps, order):
+    e_min, e_max = eps
+    a, b = 0.5 * (e_max + e_min), 0.5 * (e_max - e_min)
+    K = 2 * (order + 1)
+    t = np.pi * (np.arange(K) + 0.5) / K
+    f = fermi(a + b * np.cos(t), beta, mu)
+    n = np.arange(order + 1)
+    c = (2.0 / K) * (np.cos(np.outer(n, t)) @ f)
+    c[0] *= 0.5
+    return c
+
+
+def clenshaw_dense(x, coeffs):
+    m = x.shape[0]
+    b1 = np.zeros((m, m))
+    b2 = np.zeros((m, m))
+    for c in coeffs[:0:-1]:          # c_order .. c_1
+        b1, b2 = c * np.eye(m) + 2.0 * x @ b1 - b2, b1
+    return coeffs[0] * np.eye(m) + x @ b1 - b2
+
+
+def foe_graph(H, subs, ncore, beta, mu, order, eps=None, coeffs=None, return_subs=False):
+    """Graph-partitioned finite-temperature D (Eq. 7 per subgraph, assembled by Eq. 6)."""
+    H = sp.csr_matrix(H, dtype=np.float64)
+    eps = gershgorin(H) if eps is None else eps
+    coeffs = fermi_chebyshev_coeffs(beta, mu, eps, order) if coeffs is None else coeffs
+    a, b = 0.5 * (eps[1] + eps[0]), 0.5 * (eps[1] - eps[0])
+    xs = []
+    for idx in subs:
+        h = H[idx][:, idx].toarray()
+        xs.append(clenshaw_dense((h - a * np.eye(len(idx))) / b, coeffs))
+    D = assemble(xs, subs, ncore, H.shape[0])
+    return (D, coeffs, xs) if return_subs else (D, coeffs)
