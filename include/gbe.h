@@ -282,6 +282,46 @@ int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, doub
 /* Copy the final dense x_s (m_s x m_s, row-major, FP64) of subgraph s to host. */
 int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out);
 
+/* ------------------------------------------------ finite temperature (Chebyshev expansion) */
+
+/* D = [exp(beta (H - mu)) + 1]^-1 (Eq. 7) on every subgraph, assembled by Eq. 6: x_s =
+ * (H_s - a I) / b with a, b the centre and half-width of the spectral bounds, and the
+ * Chebyshev series of the Fermi function evaluated by Clenshaw's recurrence
+ * b_k = c_k I + 2 x b_{k+1} - b_{k+2} (k = order..1), D_s = c_0 I + x b_1 - b_2
+ * (order + 1 products of x with the current iterate).  The iterates are carried divided by
+ * B >= max_k ||b_k|| (the scalar recurrence maximised over [-1, 1]) so that the tensor-core
+ * split applies; gbe_assemble_D / gbe_subs_export multiply by B.
+ *   beta, mu  inverse temperature (1/energy) and chemical potential (energy units of H)
+ *   order     highest Chebyshev degree (1..100000)
+ *   coeffs    NULL: the Fermi function's Chebyshev interpolant (gbe_fermi_coefficients); or
+ *             order + 1 caller coefficients on [eps_min, eps_max]
+ *   prec      GBE_PREC_FP64 or GBE_PREC_FP16X6 (must equal the state's)
+ *   eps_given 0: Gershgorin bounds of H (computed on the device, read back once)
+ * gbe_foe_run synchronises once (for the bounds when not given) and enqueues the rest. */
+typedef struct {
+    double beta, mu;
+    int order;
+    const double* coeffs;
+    int prec;
+    int eps_given;
+    double eps_min, eps_max;
+    double timeout_ms;
+} gbe_foe_params;
+
+typedef struct {
+    int order, status;
+    double scale;              /* B */
+    double eps_min, eps_max;
+    float ms_gather, ms_steps; /* gather (and clearing) / all order + 1 steps */
+    double mma_flops, alg_flops;
+} gbe_foe_report;
+
+/* Chebyshev interpolant of the Fermi function on [eps_min, eps_max] at 2 (order + 1)
+ * Chebyshev-Gauss nodes: c_n = (2 - delta_n0) / K sum_j f(a + b cos t_j) cos(n t_j).  Host only. */
+int gbe_fermi_coefficients(double beta, double mu, double eps_min, double eps_max, int order, double* coeffs);
+int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_foe_params* params, gbe_subs* X);
+int gbe_foe_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_foe_report* rep);
+
 /* ------------------------------------------------ pre-determined branch sequences */
 
 /* Sec. II.C: in an MD run the SP2 sequence (shared by every subgraph) is fixed in advance

@@ -36,7 +36,7 @@ EXPORTS = [
     "gbe_subs_export", "gbe_gershgorin_noalloc", "gbe_pairs_build", "gbe_pairs_info", "gbe_pairs_export", "gbe_pairs_device",
     "gbe_free_pairs", "gbe_mlp_create", "gbe_mlp_param_count", "gbe_mlp_set_params", "gbe_mlp_get_params",
     "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_free_mlp",
-    "gbe_sp2_gap_estimate", "gbe_sp2_sequence",
+    "gbe_sp2_gap_estimate", "gbe_sp2_sequence", "gbe_fermi_coefficients", "gbe_foe_run", "gbe_foe_report_get",
 ]
 
 
@@ -141,6 +141,8 @@ def load_library(path=LIB_PATH):
         "gbe_mlp_adam_step": (I32, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
         "gbe_mlp_train": (I32, [P, P, P, P, I32, ctypes.c_float, P]), "gbe_free_mlp": (I32, [P]),
         "gbe_sp2_gap_estimate": (I32, [P, D, D, D, P, P]), "gbe_sp2_sequence": (I32, [D, D, D, D, D, I32, P, P]),
+        "gbe_fermi_coefficients": (I32, [D, D, D, D, I32, P]), "gbe_foe_run": (I32, [P, P, P, P, P]),
+        "gbe_foe_report_get": (I32, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -419,6 +421,41 @@ def sp2_sequence(eps, homo, lumo, tol, n_max=SEQ_MAX):
     check(load_library().gbe_sp2_sequence(float(eps[0]), float(eps[1]), float(homo), float(lumo), float(tol),
                                           int(n_max), ctypes.cast(buf, ctypes.c_void_p), ctypes.byref(n)), "gbe_sp2_sequence")
     return list(buf[:n.value])
+
+
+class FoeParams(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("mu", ctypes.c_double), ("order", ctypes.c_int),
+                ("coeffs", ctypes.c_void_p), ("prec", ctypes.c_int), ("eps_given", ctypes.c_int),
+                ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double), ("timeout_ms", ctypes.c_double)]
+
+
+class FoeReport(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int), ("status", ctypes.c_int), ("scale", ctypes.c_double),
+                ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double), ("ms_gather", ctypes.c_float),
+                ("ms_steps", ctypes.c_float), ("mma_flops", ctypes.c_double), ("alg_flops", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+def fermi_coefficients(beta, mu, eps, order):
+    c = np.zeros(order + 1)
+    check(load_library().gbe_fermi_coefficients(float(beta), float(mu), float(eps[0]), float(eps[1]), int(order),
+                                                _ptr(c)), "gbe_fermi_coefficients")
+    return c
+
+
+def foe_run(ctx, H, parts, X, beta, mu, order, prec=PREC_FP64, coeffs=None, eps=None, timeout_ms=0.0):
+    """Enqueue a finite-temperature Chebyshev expansion into the state X; returns its report."""
+    cbuf = None if coeffs is None else np.ascontiguousarray(coeffs, dtype=np.float64)
+    p = FoeParams(float(beta), float(mu), int(order), _ptr(cbuf) if cbuf is not None else None, int(prec),
+                  1 if eps is not None else 0, eps[0] if eps is not None else 0.0,
+                  eps[1] if eps is not None else 0.0, float(timeout_ms))
+    check(load_library().gbe_foe_run(ctx.handle, ctypes.byref(H), parts.handle, ctypes.byref(p), X.handle),
+          "gbe_foe_run")
+    r = FoeReport()
+    check(load_library().gbe_foe_report_get(ctx.handle, X.handle, ctypes.byref(r)), "gbe_foe_report_get")
+    return r.as_dict()
 
 
 def gershgorin_noalloc(ctx, H, bounds):

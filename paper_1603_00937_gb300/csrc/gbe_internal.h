@@ -94,6 +94,8 @@ struct Sp2Ctrl {
     int switch_iter; // first FP64 iteration in mixed runs (-1 before the switch)
     int pending;     // a squaring kernel ran since the last decision
     int loops;       // iterations of the graph's device-driven loop (guard)
+    int foe;         // 1: a Chebyshev expansion (Eq. 7) instead of SP2
+    double out_scale;  // factor applied by assembly / export (Chebyshev: the iterates' scale)
     uint8_t slot_ran[GBE_SEQ_MAX];  // per launch slot: bit 0 tensor-core kernel worked, bit 1 FP64 kernel
     int n_min, n_max, branch_mode, seq_len, fp64_tail, prec, eps_given;
     unsigned long long eps_min_key, eps_max_key;  // order-preserving keys for atomics
@@ -132,23 +134,30 @@ struct gbe_subs {
     int32_t* d_m = nullptr;
     int32_t* d_c = nullptr;
     // storage
-    uint16_t* planes[2] = {nullptr, nullptr};  // tensor-core path: 4 planes x total_elems, fp16/bf16 bits
-    double* f64[2] = {nullptr, nullptr};       // FP64 iterates
+    // sides 0/1: ping-pong iterates; side 2: the fixed x of a Chebyshev expansion (allocated
+    // by its first run)
+    uint16_t* planes[3] = {nullptr, nullptr, nullptr};  // tensor-core path: 4 planes x total_elems
+    double* f64[3] = {nullptr, nullptr, nullptr};       // FP64 iterates
     // work lists
     TileItem* d_items_tc = nullptr;  int n_items_tc = 0;   // 128x128 tiles
     TileItem* d_items_64 = nullptr;  int n_items_64 = 0;   // 64x64 tiles
+    TileItem* d_items_tc_full = nullptr;  int n_items_tc_full = 0;   // all (I, J), for products x b
+    TileItem* d_items_64_full = nullptr;  int n_items_64_full = 0;
     double* d_partials = nullptr;    int max_units = 0;    // [2][max_units] (t1, t2)
     Sp2Ctrl* d_ctrl = nullptr;
     Sp2Ctrl* h_ctrl = nullptr;       // pinned
     // tensor maps for the split planes (opaque 128-byte CUtensorMap blobs)
     // TMA descriptors [side][view: K-chunk, transposed][box: A planes, B planes, diagonal B]
-    alignas(64) unsigned char tmap[2][2][3][128];
+    alignas(64) unsigned char tmap[3][2][3][128];
     bool tmap_ok = false;
     // phase timing
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::vector<cudaEvent_t> ev_tc, ev_64;   // [2 * slot + {0,1}] when profiling
     int last_slots = 0;
     bool last_prof = false;
+    // last Chebyshev expansion: order, scale of the iterates, run time (events ev[0..2])
+    int foe_order = 0;
+    double foe_scale = 0.0;
     // CUDA graphs of a run: [0] control init, bounds, gather, first decision; [1] a loop node
     // whose body is one SP2 step, repeated while the device's decision says continue.
     // Reused while a run's parameters and inputs match the key they were captured with.
@@ -156,6 +165,7 @@ struct gbe_subs {
     std::vector<unsigned char> gkey;
     cudaStream_t cap_stream = nullptr;
     double alg_flops_per_iter = 0.0, mma_flops_per_iter = 0.0, fp64_flops_per_iter = 0.0;
+    double mma_flops_full = 0.0, fp64_flops_full = 0.0;   // per product over all tiles
 };
 
 // ----------------------------------------------------------------------------- blocked layout
@@ -180,6 +190,7 @@ __host__ __device__ inline int64_t sym_index(int64_t off, int mpad, int r, int c
 int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X);
 int gbe_tc_make_tmaps(gbe_subs* X);
 int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot);
+int gbe_tc_launch_foe(gbe_ctx* ctx, gbe_subs* X, int a_side, int b_side, int c_side, float alpha, double gamma);
 int gbe_tc_prepare(gbe_ctx* ctx);
 
 // helpers

@@ -26,6 +26,13 @@ __device__ __forceinline__ double dkey_inv(unsigned long long k) {
     return __longlong_as_double((long long)b);
 }
 
+static double dkey_inv_host(unsigned long long k) {
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    double d;
+    memcpy(&d, &b, sizeof(d));
+    return d;
+}
+
 __device__ __forceinline__ double warp_sum_d(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -133,9 +140,14 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     if (ctrl->eps_given) { emin = ctrl->eps_min; emax = ctrl->eps_max; }
     else { emin = dkey_inv(ctrl->eps_min_key); emax = dkey_inv(ctrl->eps_max_key); }
     const double range = emax - emin;
-    const double inv_range = 1.0 / range;
-    float ih = 0.f, il = 0.f;              // 1 / range as an FP32 pair (split paths)
-    f64_to_f32_pair(inv_range, ih, il);
+    // SP2: X_0 = (emax I - H) / (emax - emin); Chebyshev: x = (H - a I) / b with a, b the
+    // centre and half-width of [emin, emax]; both as x = (shift I - H) * gsc
+    const bool foe = ctrl->foe != 0;
+    const double half = 0.5 * range, centre = 0.5 * (emax + emin);
+    const double shift = foe ? centre : emax;
+    const double gsc = foe ? -1.0 / half : 1.0 / range;
+    float ih = 0.f, il = 0.f;              // gsc as an FP32 pair (split paths)
+    f64_to_f32_pair(gsc, ih, il);
     double t1 = 0.0, t2 = 0.0;
     float t2h = 0.f, t2l = 0.f;             // double-float Tr X_0^2 (split paths)
     for (int a0 = 0; a0 < mpad; a0 += 8) {
@@ -150,8 +162,8 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                 const double h = val[p];
                 uint2 packed;
                 if constexpr (prec == GBE_PREC_FP64) {
-                    // the exact quotient, as the FP64 oracle computes it
-                    const double x = ((a == b ? emax : 0.0) - h) / range;
+                    // the exact quotients, as the FP64 oracle computes them
+                    const double x = foe ? (h - (a == b ? centre : 0.0)) / half : ((a == b ? emax : 0.0) - h) / range;
                     if (a < c) {
                         t2 += x * x;
                         if (a == b) t1 += x;
@@ -163,7 +175,7 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                     // (one entry per row) in FP64
                     float xh, xl;
                     if (a == b) {
-                        const double x = (emax - h) * inv_range;
+                        const double x = (shift - h) * gsc;
                         f64_to_f32_pair(x, xh, xl);
                         if (a < c) t1 += x;
                     } else {
@@ -234,8 +246,8 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
 // Control-block initialisation from parameters passed by value (no host staging, so
 // consecutive runs enqueue without synchronising).
 struct Sp2Init {
-    int mode, fmt, n_min, n_max, branch_mode, seq_len, fp64_tail, prec, eps_given;
-    double eps_min, eps_max, n_occ, idem_tol, tail_switch;
+    int mode, fmt, n_min, n_max, branch_mode, seq_len, fp64_tail, prec, eps_given, foe, cur;
+    double eps_min, eps_max, n_occ, idem_tol, tail_switch, out_scale;
     long long timeout_cycles;
     uint8_t seq_in[GBE_SEQ_MAX];
 };
@@ -254,6 +266,9 @@ __global__ void init_ctrl_kernel(Sp2Ctrl* C, Sp2Init in) {
         C->eps_min_key = ~0ull; C->eps_max_key = 0ull;
         C->n_occ = in.n_occ; C->idem_tol = in.idem_tol; C->tail_switch = in.tail_switch;
         C->timeout_cycles = in.timeout_cycles;
+        C->foe = in.foe;
+        C->cur = in.cur;
+        C->out_scale = in.out_scale;
     }
 }
 
@@ -444,6 +459,76 @@ __global__ void __launch_bounds__(256) square_fp64_kernel(Sp2Ctrl* ctrl, SubsGeo
     }
 }
 
+// ----------------------------------------------------------------------------- Chebyshev step (FP64)
+// Every 64 x 64 output tile (I, J) of out = alpha x b - c + gamma I with x (side fx,
+// symmetric) and b (side fb) multiplied as they are: x and b commute only up to rounding,
+// and computing upper tiles and mirroring them would turn that rounding into a growing
+// error of the recurrence.  c is read from and overwritten in fc (each tile only its own
+// elements, so the update is in place).
+__global__ void __launch_bounds__(256) cheb_fp64_kernel(SubsGeom g, const TileItem* __restrict__ items, int n_items,
+                                                        const double* __restrict__ fx, const double* __restrict__ fb,
+                                                        double* fc, double alpha, double gamma) {
+    __shared__ double As[2][16][64];
+    __shared__ double Bs[2][16][64];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int lr = threadIdx.x >> 2, lk = (threadIdx.x & 3) * 4;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const TileItem w = items[it];
+        const int mpad = g.mpad[w.s], m = g.m[w.s];
+        const int64_t off = g.off[w.s];
+        const int kend = (m + 15) & ~15;
+        double acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        const int ra = w.I * 64 + lr, rb = w.J * 64 + lr;
+        double va[4], vb[4];
+        auto fetch = [&](int k0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                va[q] = fx[blk_index(off, mpad, ra, k0 + lk + q)];
+                vb[q] = fb[blk_index(off, mpad, k0 + lk + q, rb)];   // b[k][column rb]
+            }
+        };
+        fetch(0);
+        int buf = 0;
+        for (int k0 = 0; k0 < kend; k0 += 16) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                As[buf][lk + q][lr] = va[q];
+                Bs[buf][lk + q][lr] = vb[q];
+            }
+            __syncthreads();
+            if (k0 + 16 < kend) fetch(k0 + 16);
+#pragma unroll
+            for (int kk = 0; kk < 16; ++kk) {
+                double a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = Bs[buf][kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            buf ^= 1;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = w.I * 64 + ty + 16 * i;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cc = w.J * 64 + tx + 16 * j;
+                const int64_t e = blk_index(off, mpad, r, cc);
+                fc[e] = alpha * acc[i][j] - fc[e] + (r == cc ? gamma : 0.0);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ----------------------------------------------------------------------------- assembly
 // One CTA per subgraph, one warp per core column j: ELL row idx_s[j] <- (idx_s[k], x_s[j,k]).
 __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, const int64_t* __restrict__ sub_ptr,
@@ -456,6 +541,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
     const int m = g.m[s], c = g.c[s], mpad = g.mpad[s];
     const int64_t off = g.off[s], base = sub_ptr[s];
     const int cur = ctrl->cur, fmt = ctrl->fmt, prec = ctrl->prec;
+    const double scale = ctrl->out_scale;
     const uint16_t* pl = cur ? planes1 : planes0;
     const double* f = cur ? f1 : f0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -469,7 +555,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
             double v = 0.0;
             int gk = -1;
             if (k < m) {
-                v = load_x(fmt, prec, pl, plane_stride, f, off, mpad, j, k);
+                v = load_x(fmt, prec, pl, plane_stride, f, off, mpad, j, k) * scale;
                 gk = sub_idx[base + k];
             }
             const bool keep = (k < m) && !(drop_tol > 0.0 && fabs(v) < drop_tol);
@@ -505,7 +591,7 @@ __global__ void export_kernel(const Sp2Ctrl* ctrl, SubsGeom g, int s, const uint
     const double* f = cur ? f1 : f0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)m * m; i += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / m), cc = (int)(i % m);
-        out[i] = load_x(fmt, prec, pl, plane_stride, f, off, mpad, r, cc);
+        out[i] = load_x(fmt, prec, pl, plane_stride, f, off, mpad, r, cc) * ctrl->out_scale;
     }
 }
 
@@ -582,8 +668,9 @@ static void drop_graphs(gbe_subs* X);
 extern "C" int gbe_free_subs(gbe_subs* X) {
     if (!X) return GBE_OK;
     gbe_free(X->d_off); gbe_free(X->d_mpad); gbe_free(X->d_m); gbe_free(X->d_c);
-    for (int i = 0; i < 2; ++i) { gbe_free(X->planes[i]); gbe_free(X->f64[i]); }
+    for (int i = 0; i < 3; ++i) { gbe_free(X->planes[i]); gbe_free(X->f64[i]); }
     gbe_free(X->d_items_tc); gbe_free(X->d_items_64); gbe_free(X->d_partials); gbe_free(X->d_ctrl);
+    gbe_free(X->d_items_tc_full); gbe_free(X->d_items_64_full);
     if (X->h_ctrl) cudaFreeHost(X->h_ctrl);
     for (int i = 0; i < 3; ++i) if (X->ev[i]) cudaEventDestroy(X->ev[i]);
     for (auto e : X->ev_tc) cudaEventDestroy(e);
@@ -595,7 +682,7 @@ extern "C" int gbe_free_subs(gbe_subs* X) {
 }
 
 static void make_items(const std::vector<int32_t>& dim, const std::vector<int32_t>& cost, int tile,
-                       std::vector<TileItem>& items) {
+                       std::vector<TileItem>& items, bool full = false) {
     items.clear();
     const int64_t P = (int64_t)dim.size();
     std::vector<int64_t> order(P);
@@ -605,7 +692,7 @@ static void make_items(const std::vector<int32_t>& dim, const std::vector<int32_
     for (int64_t s : order) {
         const int T = (dim[s] + tile - 1) / tile;
         for (int I = 0; I < T; ++I)
-            for (int J = I; J < T; ++J) items.push_back(TileItem{(int)s, I, J, 0});
+            for (int J = full ? 0 : I; J < T; ++J) items.push_back(TileItem{(int)s, I, J, 0});
     }
 }
 
@@ -620,7 +707,7 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     X->P = parts->P;
     X->h_off.resize(X->P); X->h_mpad.resize(X->P); X->h_m.resize(X->P); X->h_c.resize(X->P);
     int64_t total = 0;
-    double alg = 0.0, mma = 0.0, f64 = 0.0;
+    double alg = 0.0, mma = 0.0, f64 = 0.0, mma_full = 0.0, f64_full = 0.0;
     const int nprod = (prec == GBE_PREC_FP16X6) ? 6 : 3;
     for (int64_t s = 0; s < X->P; ++s) {
         const int m = (int)(parts->h_sub_ptr[s + 1] - parts->h_sub_ptr[s]);
@@ -632,13 +719,17 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
         alg += 2.0 * (double)m * m * m;
         const int T = mpad / 128, kk = (m + 31) & ~31;
         mma += (double)nprod * 2.0 * 128.0 * 128.0 * kk * (T * (T + 1) / 2);
+        mma_full += (double)nprod * 2.0 * 128.0 * 128.0 * kk * (T * T);
         const int T64 = (m + 63) / 64, k16 = (m + 15) & ~15;
         f64 += 2.0 * 64.0 * 64.0 * k16 * (T64 * (T64 + 1) / 2);
+        f64_full += 2.0 * 64.0 * 64.0 * k16 * (T64 * T64);
     }
     X->total_elems = total;
     X->alg_flops_per_iter = alg;
     X->mma_flops_per_iter = mma;
     X->fp64_flops_per_iter = f64;
+    X->mma_flops_full = mma_full;
+    X->fp64_flops_full = f64_full;
     std::vector<TileItem> it_tc, it_64;
     std::vector<int32_t> m64(X->P);
     for (int64_t s = 0; s < X->P; ++s) m64[s] = X->h_m[s];
@@ -646,7 +737,13 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     make_items(m64, X->h_mpad, 64, it_64);
     X->n_items_tc = (int)it_tc.size();
     X->n_items_64 = (int)it_64.size();
-    X->max_units = (int)std::max<int64_t>(X->P, std::max(X->n_items_tc, X->n_items_64));
+    // every tile (I, J) for products of two different matrices (Chebyshev expansion)
+    std::vector<TileItem> ft_tc, ft_64;
+    make_items(X->h_mpad, X->h_mpad, 128, ft_tc, true);
+    make_items(m64, X->h_mpad, 64, ft_64, true);
+    X->n_items_tc_full = (int)ft_tc.size();
+    X->n_items_64_full = (int)ft_64.size();
+    X->max_units = (int)std::max<int64_t>(X->P, std::max(X->n_items_tc_full, X->n_items_64_full));
     int r = GBE_OK;
 #define ALLOC(ptr, bytes) if (r == GBE_OK) r = gbe_alloc((void**)&(ptr), (bytes))
     ALLOC(X->d_off, X->P * 8);
@@ -655,6 +752,8 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     ALLOC(X->d_c, X->P * 4);
     ALLOC(X->d_items_tc, std::max<int64_t>(1, X->n_items_tc) * sizeof(TileItem));
     ALLOC(X->d_items_64, std::max<int64_t>(1, X->n_items_64) * sizeof(TileItem));
+    ALLOC(X->d_items_tc_full, std::max<int64_t>(1, X->n_items_tc_full) * sizeof(TileItem));
+    ALLOC(X->d_items_64_full, std::max<int64_t>(1, X->n_items_64_full) * sizeof(TileItem));
     ALLOC(X->d_partials, 2 * (int64_t)X->max_units * 8);
     ALLOC(X->d_ctrl, sizeof(Sp2Ctrl));
     for (int i = 0; i < 2; ++i) {
@@ -676,6 +775,10 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     cudaMemcpyAsync(X->d_c, X->h_c.data(), X->P * 4, cudaMemcpyHostToDevice, st);
     if (X->n_items_tc) cudaMemcpyAsync(X->d_items_tc, it_tc.data(), it_tc.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
     if (X->n_items_64) cudaMemcpyAsync(X->d_items_64, it_64.data(), it_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
+    if (X->n_items_tc_full)
+        cudaMemcpyAsync(X->d_items_tc_full, ft_tc.data(), ft_tc.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
+    if (X->n_items_64_full)
+        cudaMemcpyAsync(X->d_items_64_full, ft_64.data(), ft_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
     for (int i = 0; i < 2; ++i) {
         cudaMemsetAsync(X->f64[i], 0, total * 8, st);
         if (X->planes[i]) cudaMemsetAsync(X->planes[i], 0, 4 * total * 2, st);
@@ -833,6 +936,7 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     in.tail_switch = prm->tail_switch;
     const double tmo = prm->timeout_ms > 0 ? prm->timeout_ms : 2000.0;
     in.timeout_cycles = (long long)(tmo * 2.2e6);
+    in.out_scale = 1.0;
     if (in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len) memcpy(in.seq_in, prm->seq_in, in.seq_len);
     if (in.prec != GBE_PREC_FP64 && in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len <= in.fp64_tail) in.mode = 1;
     const bool fp64_steps = X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0;
@@ -1040,5 +1144,161 @@ extern "C" int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, doubl
         gbe_set_error("export: %s", cudaGetErrorString(e));
         return GBE_ECUDA;
     }
+    return GBE_OK;
+}
+
+// ============================================================================= Chebyshev expansion
+// Finite-temperature D = [exp(beta (H - mu)) + 1]^-1 (Eq. 7) per subgraph: x = (H_s - a I) / b
+// on the Gershgorin interval, the Chebyshev series of the Fermi function evaluated by
+// Clenshaw's recurrence b_k = c_k I + 2 x b_{k+1} - b_{k+2}, D_s = c_0 I + x b_1 - b_2, and
+// the core columns assembled by Eq. 6.  The iterates are carried divided by B, a bound on
+// max_k ||b_k|| (the scalar recurrence maximised over [-1, 1]), so that they have spectral
+// norm <= 1 as the tensor-core split requires; assembly multiplies by B.
+
+extern "C" int gbe_fermi_coefficients(double beta, double mu, double eps_min, double eps_max, int order, double* c) {
+    GBE_CHECK_ARG(c && order >= 1 && eps_max > eps_min && beta > 0.0, "bad argument");
+    const double a = 0.5 * (eps_max + eps_min), b = 0.5 * (eps_max - eps_min);
+    const int K = 2 * (order + 1);
+    const double pi = 3.14159265358979323846;
+    std::vector<double> f(K), t(K);
+    for (int j = 0; j < K; ++j) {
+        t[j] = pi * (j + 0.5) / K;
+        const double z = beta * (a + b * std::cos(t[j]) - mu);
+        f[j] = 0.5 * (1.0 - std::tanh(0.5 * z));   // Fermi function without overflow
+    }
+    for (int n = 0; n <= order; ++n) {
+        double s = 0.0;
+        for (int j = 0; j < K; ++j) s += std::cos(n * t[j]) * f[j];
+        c[n] = (n == 0 ? 1.0 : 2.0) * s / K;
+    }
+    return GBE_OK;
+}
+
+// max over k and x in [-1, 1] of |b_k(x)| for the scalar recurrence, on a fine grid
+// (Chebyshev-Lobatto points, at least 4 per degree), with a 5% margin.
+static double clenshaw_bound(const double* c, int order) {
+    const int npts = std::max(4096, 4 * order);
+    const double pi = 3.14159265358979323846;
+    double mx = 0.0;
+    for (int i = 0; i <= npts; ++i) {
+        const double x = std::cos(pi * i / npts);
+        double b1 = 0.0, b2 = 0.0;
+        for (int k = order; k >= 1; --k) {
+            const double b0 = c[k] + 2.0 * x * b1 - b2;
+            b2 = b1;
+            b1 = b0;
+            mx = std::max(mx, std::fabs(b0));
+        }
+        mx = std::max(mx, std::fabs(c[0] + x * b1 - b2));
+    }
+    return 1.05 * std::max(mx, 1e-300);
+}
+
+extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_foe_params* prm,
+                           gbe_subs* X) {
+    AllocScope alloc_scope_(ctx);
+    GBE_CHECK_ARG(ctx && H && parts && prm && X, "NULL argument");
+    GBE_CHECK_ARG(H->on_device, "gbe_foe_run needs a device CSR");
+    GBE_CHECK_ARG(X->parts == parts && H->n == parts->n, "state / partition / H mismatch");
+    GBE_CHECK_ARG(X->prec == GBE_PREC_FP64 || X->prec == GBE_PREC_FP16X6, "Chebyshev expansion supports FP64 and FP16X6");
+    GBE_CHECK_ARG(prm->order >= 1 && prm->order <= 100000, "order out of range");
+    GBE_CHECK_ARG(prm->coeffs || prm->beta > 0.0, "beta must be positive (or coefficients given)");
+    GBE_CHECK_ARG(parts->max_m <= 8192, "subgraph larger than 8192");
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const bool fp64 = X->prec == GBE_PREC_FP64;
+    // the fixed x lives on side 2
+    if (fp64 && !X->f64[2]) GBE_TRY(gbe_alloc((void**)&X->f64[2], X->total_elems * 8));
+    if (!fp64 && !X->planes[2]) {
+        GBE_TRY(gbe_alloc((void**)&X->planes[2], 4 * X->total_elems * 2));
+        GBE_TRY(gbe_tc_make_tmaps(X));
+    }
+    Sp2Init in;
+    memset(&in, 0, sizeof(in));
+    in.mode = fp64 ? 1 : 0;
+    in.fmt = fp64 ? 1 : 0;
+    in.prec = X->prec;
+    in.n_max = 1;
+    in.branch_mode = GBE_BRANCH_REPLAY;
+    in.foe = 1;
+    const double tmo = prm->timeout_ms > 0 ? prm->timeout_ms : 2000.0;
+    in.timeout_cycles = (long long)(tmo * 2.2e6);
+    // spectral bounds on the host (the coefficients depend on them)
+    double emin = prm->eps_min, emax = prm->eps_max;
+    if (!prm->eps_given) {
+        in.out_scale = 1.0;
+        init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
+        GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
+        GBE_CUDA_TRY(cudaMemcpyAsync(X->h_ctrl, X->d_ctrl, sizeof(Sp2Ctrl), cudaMemcpyDeviceToHost, st));
+        GBE_CUDA_TRY(cudaStreamSynchronize(st));
+        emin = dkey_inv_host(X->h_ctrl->eps_min_key);
+        emax = dkey_inv_host(X->h_ctrl->eps_max_key);
+    }
+    GBE_CHECK_ARG(std::isfinite(emin) && std::isfinite(emax) && emax > emin, "spectral bounds");
+    const int M = prm->order;
+    std::vector<double> c(M + 1);
+    if (prm->coeffs) std::copy(prm->coeffs, prm->coeffs + M + 1, c.begin());
+    else GBE_TRY(gbe_fermi_coefficients(prm->beta, prm->mu, emin, emax, M, c.data()));
+    const double B = clenshaw_bound(c.data(), M);
+    // sides: b_{k+1} on p, b_{k+2} on q (overwritten by b_k), then swap
+    int p = 0, q = 1;
+    for (int k = M; k >= 1; --k) std::swap(p, q);
+    in.cur = q;   // the final step writes side q
+    in.eps_given = 1;
+    in.eps_min = emin;
+    in.eps_max = emax;
+    in.out_scale = B;
+    const size_t smem = (size_t)8 * X->max_mpad * 8 + (size_t)parts->max_m * 4;
+    auto gk = fp64 ? gather_kernel<GBE_PREC_FP64> : gather_kernel<GBE_PREC_FP16X6>;
+    GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    cudaEventRecord(X->ev[0], st);
+    init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
+    gk<<<(unsigned)X->P, 256, smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
+                                           geom_of(X), X->max_mpad, X->planes[2], X->total_elems, X->f64[2],
+                                           X->d_partials, X->max_units);
+    GBE_CUDA_TRY(cudaGetLastError());
+    for (int s = 0; s < 2; ++s) {
+        if (fp64) GBE_CUDA_TRY(cudaMemsetAsync(X->f64[s], 0, X->total_elems * 8, st));
+        else GBE_CUDA_TRY(cudaMemsetAsync(X->planes[s], 0, 4 * X->total_elems * 2, st));
+    }
+    cudaEventRecord(X->ev[1], st);
+    p = 0;
+    q = 1;
+    const int grid64 = std::max(1, std::min(X->n_items_64_full, ctx->sm_count * 4));
+    for (int k = M; k >= 0; --k) {
+        const double alpha = k > 0 ? 2.0 : 1.0;   // k = 0: the final combination c_0 I + x b_1 - b_2
+        const double gamma = c[k] / B;
+        if (fp64)
+            cheb_fp64_kernel<<<grid64, 256, 0, st>>>(geom_of(X), X->d_items_64_full, X->n_items_64_full, X->f64[2], X->f64[p],
+                                                     X->f64[q], alpha, gamma);
+        else
+            GBE_TRY(gbe_tc_launch_foe(ctx, X, 2, p, q, (float)alpha, gamma));
+        GBE_CUDA_TRY(cudaGetLastError());
+        if (k > 0) std::swap(p, q);
+    }
+    cudaEventRecord(X->ev[2], st);
+    X->foe_order = M;
+    X->foe_scale = B;
+    X->last_slots = 0;
+    X->last_prof = false;
+    return GBE_OK;
+}
+
+extern "C" int gbe_foe_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_foe_report* rep) {
+    AllocScope alloc_scope_(ctx);
+    GBE_CHECK_ARG(ctx && X && rep, "NULL argument");
+    GBE_CUDA_TRY(cudaMemcpyAsync(X->h_ctrl, X->d_ctrl, sizeof(Sp2Ctrl), cudaMemcpyDeviceToHost, ctx->stream));
+    GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    memset(rep, 0, sizeof(*rep));
+    rep->order = X->foe_order;
+    rep->scale = X->foe_scale;
+    rep->status = X->h_ctrl->status;
+    rep->eps_min = X->h_ctrl->eps_min;
+    rep->eps_max = X->h_ctrl->eps_max;
+    cudaEventElapsedTime(&rep->ms_gather, X->ev[0], X->ev[1]);
+    cudaEventElapsedTime(&rep->ms_steps, X->ev[1], X->ev[2]);
+    const double steps = X->foe_order + 1;
+    rep->mma_flops = (X->prec == GBE_PREC_FP64 ? X->fp64_flops_full : X->mma_flops_full) * steps;
+    rep->alg_flops = X->alg_flops_per_iter * steps;
     return GBE_OK;
 }

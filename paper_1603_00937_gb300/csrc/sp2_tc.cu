@@ -210,11 +210,12 @@ __device__ unsigned long long g_tc_stats[16];
 #define TC_FLUSH()
 #endif
 
-// 3-D tensor maps [side][view][box]: view 0 = K-chunk view of stored blocks, view 1 =
+// 3-D tensor maps [side][view][box] (sides 0/1: ping-pong iterates, 2: the fixed x of a
+// Chebyshev expansion): view 0 = K-chunk view of stored blocks, view 1 =
 // transposed view (lower blocks); box 0 = A planes (depth kA), 1 = B planes (depth kSlots-kA),
 // 2 = B planes of a diagonal tile (depth kDiag, from plane kA).
 struct TcMaps {
-    CUtensorMap m[2][2][3];
+    CUtensorMap m[3][2][3];
 };
 
 struct TcArgs {
@@ -222,14 +223,21 @@ struct TcArgs {
     SubsGeom g;
     const TileItem* items;
     int n_items;
-    uint16_t* planes[2];
+    uint16_t* planes[3];
     int64_t ps;  // plane stride in elements
+    // Chebyshev step (FOE kernels): out = alpha (x b) - c + gamma I with x on side a_side,
+    // b on side b_side, c read from and the result written to side c_side; gamma is split
+    // into its 2^-20-grid part (added to the exact leading term) and the remainder
+    int a_side, b_side, c_side;
+    float alpha, gamma_g, gamma_r;
     double* partials;
     int max_units;
     int slot;
 };
 
-template <int PREC>
+// FOE = false: one SP2 squaring X_{n+1} = X_n^2 or 2 X_n - X_n^2 (branch from the device).
+// FOE = true: one step of a Chebyshev expansion, out = alpha x b - c + gamma I (arguments).
+template <int PREC, bool FOE>
 __global__ void __launch_bounds__(kThreads, 1)
     sp2_square_tc_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     using R = Recipe<PREC>;
@@ -272,9 +280,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const int cur = hdr[1], branch = hdr[2];
     const long long budget = ctrl->timeout_cycles;
-    const CUtensorMap(*tm)[3] = maps.m[cur];              // [view][box] of the current side
-    const uint16_t* pin = cur ? args.planes[1] : args.planes[0];
-    uint16_t* pout = cur ? args.planes[0] : args.planes[1];
+    // [view][box] maps of the A and B operand sides; planes the epilogue reads and writes
+    const CUtensorMap(*tmA)[3] = maps.m[FOE ? args.a_side : cur];
+    const CUtensorMap(*tmB)[3] = maps.m[FOE ? args.b_side : cur];
+    const uint16_t* pin = FOE ? args.planes[args.c_side] : (cur ? args.planes[1] : args.planes[0]);
+    uint16_t* pout = FOE ? args.planes[args.c_side] : (cur ? args.planes[0] : args.planes[1]);
+    const bool use_c = FOE || !branch;   // the update reads the stored planes at its own tile
     const int64_t ps = args.ps;
 
     if (warp == 1) {
@@ -300,7 +311,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int mpad = args.g.mpad[w.s], m = args.g.m[w.s];
                 const int64_t off = args.g.off[w.s];
                 const int nk = (m + 31) >> 5;
-                const bool diag = (w.I == w.J);
+                // a diagonal tile of a squaring takes B's planes s0..s2 from A's slots
+                const bool diag = (w.I == w.J) && !FOE;
                 const int nload = R::kA + (diag ? R::kDiag : R::kSlots - R::kA);
                 for (int kc = 0; kc < nk; ++kc) {
                     bool got;
@@ -325,7 +337,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int slot0 = side == 0 ? 0 : (diag ? R::kA + R::kA : R::kA);
                         const int z = side == 1 && diag ? R::kA : 0;
                         unsigned char* dst = st + (size_t)slot0 * kTileBytes;
-                        if (Rt <= kb) {
+                        const CUtensorMap(*tm)[3] = side == 0 ? tmA : tmB;
+                        // a Chebyshev step's b is not symmetric to the last bit: its block (kb, J)
+                        // itself, as an MN-major tile, whatever kb and J are
+                        if (Rt <= kb && !(FOE && side == 1)) {
                             // stored block (Rt, kb): 4 column groups of 1024 elements = 16 view rows of 256
                             const int64_t y = (g0 + (int64_t)Rt * (mpad >> 3) + 4 * kc) << 2;
                             tma_load_3d(dst, &tm[0][bx], &full[stage], 0, (int)y, z);
@@ -368,7 +383,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const TileItem w = args.items[it];
                 const int m = args.g.m[w.s];
                 const int nk = (m + 31) >> 5;
-                const bool diag = (w.I == w.J);
+                const bool diag = (w.I == w.J) && !FOE;
 #ifdef GBE_TC_STATS
                 st_acc[6] += (unsigned long long)(clock64() - ts0);
 #endif
@@ -394,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t sbase = tiles_addr + (uint32_t)(stage * R::kSlots * kTileBytes);
                     const int kb = kc >> 2;
-                    const bool tA = w.I > kb, tB = w.J > kb;   // operand loaded transposed (MN-major)
+                    const bool tA = w.I > kb, tB = FOE || w.J > kb;   // operand loaded transposed (MN-major)
                     const uint32_t idesc_t = idesc | ((uint32_t)tA << 15) | ((uint32_t)tB << 16);
 #pragma unroll
                     for (int ks = 0; ks < 2; ++ks) {
@@ -402,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int p = 0; p < R::kProducts; ++p) {
                             const int a = nib(R::kPa, p), acc = nib(R::kPacc, p);
                             int b = nib(R::kPb, p);
-                            if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);
+                            if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);   // never for FOE
                             const uint32_t aa = sbase + a * kTileBytes, ba = sbase + b * kTileBytes;
                             const uint64_t da = tA ? sdesc_mnmajor(aa + ks * 256) : sdesc_kmajor(aa + ks * 4096);
                             const uint64_t db = tB ? sdesc_mnmajor(ba + ks * 256) : sdesc_kmajor(ba + ks * 4096);
@@ -466,7 +481,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     xn[p][4] = v1.x; xn[p][5] = v1.y; xn[p][6] = v1.z; xn[p][7] = v1.w;
                 }
             };
-            if (!branch) fetch_x(4 * half);
+            if (use_c) fetch_x(4 * half);
             bool ok;
             {
                 TC_T0();
@@ -492,7 +507,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int p = 0; p < kXP; ++p)
 #pragma unroll
                     for (int k = 0; k < 8; ++k) xw[p][k] = xn[p][k];
-                if (!branch && cc < 3) fetch_x(ch + 1);
+                if (use_c && cc < 3) fetch_x(ch + 1);
                 tmem_wait_ld();
                 if (cc == 3) {
                     tc_fence_before();
@@ -509,7 +524,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 #define XV(p) ((uint16_t)(xw[p][j >> 1] >> sh16))
                     const float A = __uint_as_float(ra[j]);
                     float P, Q;
-                    if constexpr (PREC == GBE_PREC_FP16X6) {
+                    if constexpr (FOE) {
+                        // alpha x b - c + gamma I: every term but gamma_r is a multiple of 2^-20
+                        // (exact in FP32), gamma_r joins the small correction
+                        const float B = __uint_as_float(rb[j]);
+                        const float s0 = h_val(XV(0)), s1 = h_val(XV(1)), s2 = h_val(XV(2));
+                        const bool dgl = (col0 + j == row);
+                        P = args.alpha * A - s0 + (dgl ? args.gamma_g : 0.0f);
+                        Q = (args.alpha * B - (s1 + s2)) * GBE_OZ_R_INV + (dgl ? args.gamma_r : 0.0f);
+                        const OzSplit o = oz_split_pq(P, Q);
+                        ow[0][j >> 1] |= (uint32_t)o.s0 << sh16;
+                        ow[1][j >> 1] |= (uint32_t)o.s1 << sh16;
+                        ow[2][j >> 1] |= (uint32_t)o.s2 << sh16;
+                        ow[R::kPlanes - 1][j >> 1] |= (uint32_t)o.s1s << sh16;
+                    } else if constexpr (PREC == GBE_PREC_FP16X6) {
                         const float B = __uint_as_float(rb[j]);
                         if (branch) {
                             P = A;
@@ -622,10 +650,13 @@ int gbe_tc_prepare(gbe_ctx* ctx) {
             return GBE_ENODEV;
         }
     }
-    e = cudaFuncSetAttribute(sp2_square_tc_kernel<GBE_PREC_FP16X6>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(sp2_square_tc_kernel<GBE_PREC_FP16X6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes<GBE_PREC_FP16X6>());
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sp2_square_tc_kernel<GBE_PREC_BF16X3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(sp2_square_tc_kernel<GBE_PREC_FP16X6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes<GBE_PREC_FP16X6>());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(sp2_square_tc_kernel<GBE_PREC_BF16X3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_bytes<GBE_PREC_BF16X3>());
     if (e != cudaSuccess) {
         gbe_set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
@@ -642,7 +673,7 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
     const int nplanes = 4;   // plane buffers hold 4 planes of total_elems for every split format
     const bool fp16 = X->prec != GBE_PREC_BF16X3;
     const int depth[3] = {fp16 ? 3 : 2, fp16 ? 4 : 2, fp16 ? 1 : 1};
-    for (int side = 0; side < 2; ++side)
+    for (int side = 0; side < 3; ++side)
         for (int view = 0; view < 2; ++view)
             for (int bx = 0; bx < 3; ++bx) {
                 CUtensorMap m;
@@ -656,6 +687,10 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
                 cuuint64_t strides[2] = {inner * 2, (cuuint64_t)X->total_elems * 2};
                 cuuint32_t box[3] = {256, 16, (cuuint32_t)depth[bx]};
                 cuuint32_t estr[3] = {1, 1, 1};
+                if (!X->planes[side]) {   // side 2 exists only once a Chebyshev expansion ran
+                    memset(X->tmap[side][view][bx], 0, 128);
+                    continue;
+                }
                 CUresult r = g_encode_tiled(&m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
                                             X->planes[side], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -671,30 +706,59 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
     return GBE_OK;
 }
 
+static TcArgs tc_args(gbe_subs* X, int slot) {
+    TcArgs a;
+    memset(&a, 0, sizeof(a));
+    a.ctrl = X->d_ctrl;
+    a.g = SubsGeom{X->d_off, X->d_mpad, X->d_m, X->d_c};
+    a.items = X->d_items_tc;
+    a.n_items = X->n_items_tc;
+    for (int i = 0; i < 3; ++i) a.planes[i] = X->planes[i];
+    a.ps = X->total_elems;
+    a.partials = X->d_partials;
+    a.max_units = X->max_units;
+    a.slot = slot;
+    return a;
+}
+
 int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot) {
     if (!X->tmap_ok) {
         gbe_set_error("tensor maps missing");
         return GBE_ECUDA;
     }
-    TcArgs a;
-    a.ctrl = X->d_ctrl;
-    a.g = SubsGeom{X->d_off, X->d_mpad, X->d_m, X->d_c};
-    a.items = X->d_items_tc;
-    a.n_items = X->n_items_tc;
-    a.planes[0] = X->planes[0];
-    a.planes[1] = X->planes[1];
-    a.ps = X->total_elems;
-    a.partials = X->d_partials;
-    a.max_units = X->max_units;
-    a.slot = slot;
+    TcArgs a = tc_args(X, slot);
     TcMaps maps;
     static_assert(sizeof(maps) == sizeof(X->tmap), "tensor map set size");
     memcpy(&maps, X->tmap, sizeof(maps));
     const int grid = std::max(1, std::min(X->n_items_tc, ctx->sm_count));
     if (X->prec == GBE_PREC_FP16X6)
-        sp2_square_tc_kernel<GBE_PREC_FP16X6><<<grid, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(maps, a);
+        sp2_square_tc_kernel<GBE_PREC_FP16X6, false><<<grid, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(maps, a);
     else
-        sp2_square_tc_kernel<GBE_PREC_BF16X3><<<grid, kThreads, smem_bytes<GBE_PREC_BF16X3>(), ctx->stream>>>(maps, a);
+        sp2_square_tc_kernel<GBE_PREC_BF16X3, false><<<grid, kThreads, smem_bytes<GBE_PREC_BF16X3>(), ctx->stream>>>(maps, a);
+    GBE_CUDA_TRY(cudaGetLastError());
+    return GBE_OK;
+}
+
+int gbe_tc_launch_foe(gbe_ctx* ctx, gbe_subs* X, int a_side, int b_side, int c_side, float alpha, double gamma) {
+    if (!X->tmap_ok || !X->planes[2] || X->prec != GBE_PREC_FP16X6) {
+        gbe_set_error("Chebyshev tensor-core step needs FP16X6 planes on three sides");
+        return GBE_ECUDA;
+    }
+    TcArgs a = tc_args(X, -1);
+    a.items = X->d_items_tc_full;   // every tile: x b is computed as it is, not mirrored
+    a.n_items = X->n_items_tc_full;
+    a.a_side = a_side;
+    a.b_side = b_side;
+    a.c_side = c_side;
+    a.alpha = alpha;
+    const double gg = rint(gamma * 1048576.0) / 1048576.0;   // 2^-20 grid
+    a.gamma_g = (float)gg;
+    a.gamma_r = (float)(gamma - gg);
+    TcMaps maps;
+    memcpy(&maps, X->tmap, sizeof(maps));
+    const int grid = std::max(1, std::min(X->n_items_tc, ctx->sm_count));
+    const int gridf = std::max(1, std::min(X->n_items_tc_full, ctx->sm_count));
+    sp2_square_tc_kernel<GBE_PREC_FP16X6, true><<<gridf, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(maps, a);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }

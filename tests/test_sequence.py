@@ -103,3 +103,10 @@ def test_library_gap_estimate_matches_oracle(lib):
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-8)
     with pytest.raises(gbe.GbeError):
         gbe.sp2_gap_estimate(rep, N // 2, 1e-30, 1e-29)
+
+
+@pytest.mark.parametrize("beta,mu,order", [(2.0, 0.0, 60), (10.0, -0.3, 400), (0.5, 1.2, 7)])
+def test_library_fermi_coefficients_match_oracle(lib, beta, mu, order):
+    eps = (-13.2, 12.9)
+    np.testing.assert_allclose(gbe.fermi_coefficients(beta, mu, eps, order),
+                               sp2.fermi_chebyshev_coeffs(beta, mu, eps, order), rtol=0, atol=1e-14)
