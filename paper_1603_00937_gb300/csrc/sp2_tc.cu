@@ -283,8 +283,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     // [view][box] maps of the A and B operand sides; planes the epilogue reads and writes
     const CUtensorMap(*tmA)[3] = maps.m[FOE ? args.a_side : cur];
     const CUtensorMap(*tmB)[3] = maps.m[FOE ? args.b_side : cur];
-    const uint16_t* pin = FOE ? args.planes[args.c_side] : (cur ? args.planes[1] : args.planes[0]);
-    uint16_t* pout = FOE ? args.planes[args.c_side] : (cur ? args.planes[0] : args.planes[1]);
+    // (selects, not an indexed parameter array, which would be copied to local memory)
+    uint16_t* const pc = args.c_side == 0 ? args.planes[0] : (args.c_side == 1 ? args.planes[1] : args.planes[2]);
+    const uint16_t* pin = FOE ? pc : (cur ? args.planes[1] : args.planes[0]);
+    uint16_t* pout = FOE ? pc : (cur ? args.planes[0] : args.planes[1]);
     const bool use_c = FOE || !branch;   // the update reads the stored planes at its own tile
     const int64_t ps = args.ps;
 
@@ -514,58 +516,73 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mbar_arrive(&tempty[tb]);
                 }
                 uint32_t ow[R::kPlanes][8];
+                if constexpr (PREC == GBE_PREC_FP16X6) {
+                    // adjacent column pairs: packed half conversions, words written whole
 #pragma unroll
-                for (int p = 0; p < R::kPlanes; ++p)
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) ow[p][k] = 0u;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int sh16 = 16 * (j & 1);
-#define XV(p) ((uint16_t)(xw[p][j >> 1] >> sh16))
-                    const float A = __uint_as_float(ra[j]);
-                    float P, Q;
-                    if constexpr (FOE) {
-                        // alpha x b - c + gamma I: every term but gamma_r is a multiple of 2^-20
-                        // (exact in FP32), gamma_r joins the small correction
-                        const float B = __uint_as_float(rb[j]);
-                        const float s0 = h_val(XV(0)), s1 = h_val(XV(1)), s2 = h_val(XV(2));
-                        const bool dgl = (col0 + j == row);
-                        P = args.alpha * A - s0 + (dgl ? args.gamma_g : 0.0f);
-                        Q = (args.alpha * B - (s1 + s2)) * GBE_OZ_R_INV + (dgl ? args.gamma_r : 0.0f);
-                        const OzSplit o = oz_split_pq(P, Q);
-                        ow[0][j >> 1] |= (uint32_t)o.s0 << sh16;
-                        ow[1][j >> 1] |= (uint32_t)o.s1 << sh16;
-                        ow[2][j >> 1] |= (uint32_t)o.s2 << sh16;
-                        ow[R::kPlanes - 1][j >> 1] |= (uint32_t)o.s1s << sh16;
-                    } else if constexpr (PREC == GBE_PREC_FP16X6) {
-                        const float B = __uint_as_float(rb[j]);
-                        if (branch) {
-                            P = A;
-                            Q = B * GBE_OZ_R_INV;
+                    for (int jj = 0; jj < 8; ++jj) {
+                        float P[2], Q[2];
+                        const float A0 = __uint_as_float(ra[2 * jj]), A1 = __uint_as_float(ra[2 * jj + 1]);
+                        const float B0 = __uint_as_float(rb[2 * jj]), B1 = __uint_as_float(rb[2 * jj + 1]);
+                        if (use_c) {
+                            const float2 c0 = h2_val(xw[0][jj]), c1 = h2_val(xw[1][jj]), c2 = h2_val(xw[2][jj]);
+                            if constexpr (FOE) {
+                                // alpha x b - c + gamma I: every term but gamma_r is a multiple of
+                                // 2^-20 (exact in FP32), gamma_r joins the small correction
+                                const bool g0 = (col0 + 2 * jj == row), g1 = (col0 + 2 * jj + 1 == row);
+                                P[0] = args.alpha * A0 - c0.x + (g0 ? args.gamma_g : 0.0f);
+                                Q[0] = (args.alpha * B0 - (c1.x + c2.x)) * GBE_OZ_R_INV + (g0 ? args.gamma_r : 0.0f);
+                                P[1] = args.alpha * A1 - c0.y + (g1 ? args.gamma_g : 0.0f);
+                                Q[1] = (args.alpha * B1 - (c1.y + c2.y)) * GBE_OZ_R_INV + (g1 ? args.gamma_r : 0.0f);
+                            } else {
+                                P[0] = 2.0f * c0.x - A0;
+                                Q[0] = (2.0f * (c1.x + c2.x) - B0) * GBE_OZ_R_INV;
+                                P[1] = 2.0f * c0.y - A1;
+                                Q[1] = (2.0f * (c1.y + c2.y) - B1) * GBE_OZ_R_INV;
+                            }
                         } else {
-                            const float s0 = h_val(XV(0)), s1 = h_val(XV(1)), s2 = h_val(XV(2));
-                            P = 2.0f * s0 - A;
-                            Q = (2.0f * (s1 + s2) - B) * GBE_OZ_R_INV;
+                            P[0] = A0;
+                            Q[0] = B0 * GBE_OZ_R_INV;
+                            P[1] = A1;
+                            Q[1] = B1 * GBE_OZ_R_INV;
                         }
-                        const OzSplit o = oz_split_pq(P, Q);
-                        ow[0][j >> 1] |= (uint32_t)o.s0 << sh16;
-                        ow[1][j >> 1] |= (uint32_t)o.s1 << sh16;
-                        ow[2][j >> 1] |= (uint32_t)o.s2 << sh16;
-                        ow[R::kPlanes - 1][j >> 1] |= (uint32_t)o.s1s << sh16;
-                    } else {
-                        P = branch ? A : 2.0f * (b_val(XV(0)) + b_val(XV(1))) - A;
-                        Q = 0.0f;
+                        const OzSplit2 o = oz_split_pq2(P[0], Q[0], P[1], Q[1]);
+                        ow[0][jj] = o.s0;
+                        ow[1][jj] = o.s1;
+                        ow[2][jj] = o.s2;
+                        ow[R::kPlanes - 1][jj] = o.s1s;
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int colg = col0 + 2 * jj + e;
+                            const float wgt = (float)((int)core_row + (int)(offdiag && colg < c));
+                            if (wgt != 0.0f) df_add_sq(sh, sl, P[e], Q[e], wgt);
+                            const bool dg = (colg == row);
+                            dP = dg ? P[e] : dP;
+                            dQ = dg ? Q[e] : dQ;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int p = 0; p < R::kPlanes; ++p)
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) ow[p][k] = 0u;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int sh16 = 16 * (j & 1);
+#define XV(p) ((uint16_t)(xw[p][j >> 1] >> sh16))
+                        const float A = __uint_as_float(ra[j]);
+                        const float P = branch ? A : 2.0f * (b_val(XV(0)) + b_val(XV(1))) - A;
+                        const float Q = 0.0f;
                         const __nv_bfloat16 hi = __float2bfloat16_rn(P);
                         ow[0][j >> 1] |= (uint32_t)b_bits(hi) << sh16;
                         ow[1][j >> 1] |= (uint32_t)b_bits(__float2bfloat16_rn(P - __bfloat162float(hi))) << sh16;
-                    }
 #undef XV
-                    const int colg = col0 + j;
-                    const float wgt = (float)((int)core_row + (int)(offdiag && colg < c));
-                    if (wgt != 0.0f) df_add_sq(sh, sl, P, Q, wgt);
-                    const bool dg = (colg == row);
-                    dP = dg ? P : dP;
-                    dQ = dg ? Q : dQ;
+                        const int colg = col0 + j;
+                        const float wgt = (float)((int)core_row + (int)(offdiag && colg < c));
+                        if (wgt != 0.0f) df_add_sq(sh, sl, P, Q, wgt);
+                        const bool dg = (colg == row);
+                        dP = dg ? P : dP;
+                        dQ = dg ? Q : dQ;
+                    }
                 }
                 const int64_t e0 = blk_index(off, mpad, row, col0);
 #pragma unroll

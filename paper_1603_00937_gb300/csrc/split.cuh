@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <cstring>
 
 #define GBE_OZ_S0_SCALE 1024.0f          // 2^10
 #define GBE_OZ_R_SCALE 2048.0f           // 2^11
@@ -59,6 +60,39 @@ __device__ __forceinline__ void f64_to_f32_pair(double x, float& hi, float& lo) 
     const float l = (float)(uint32_t)(mant & 0x1FFFFFFFull);                  // units of 2^(e-52)
     lo = l * __uint_as_float((uint32_t)(e - 52 + 127) << 23);
     lo = sign ? -lo : lo;
+}
+
+// Two adjacent elements at once (the first in the low 16 bits of every word): the same
+// rounding as oz_split_pq, with packed conversions.
+struct OzSplit2 {
+    uint32_t s0, s1, s2, s1s;
+};
+
+__device__ __forceinline__ uint32_t h2_bits(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+__device__ __forceinline__ float2 h2_val(uint32_t u) {
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return __half22float2(h);
+}
+
+__device__ __forceinline__ OzSplit2 oz_split_pq2(float P0, float Q0, float P1, float Q1) {
+    const float y0 = P0 + Q0, y1 = P1 + Q1;
+    const float s00 = rintf(y0 * GBE_OZ_S0_SCALE) * (1.0f / GBE_OZ_S0_SCALE);
+    const float s01 = rintf(y1 * GBE_OZ_S0_SCALE) * (1.0f / GBE_OZ_S0_SCALE);
+    const float r10 = (P0 - s00) + Q0, r11 = (P1 - s01) + Q1;
+    const float t0 = r10 * GBE_OZ_R_SCALE, t1 = r11 * GBE_OZ_R_SCALE;
+    const __half2 h1 = __floats2half2_rn(t0, t1);
+    const float2 f1 = __half22float2(h1);
+    OzSplit2 o;
+    o.s0 = h2_bits(__floats2half2_rn(s00, s01));
+    o.s1 = h2_bits(h1);
+    o.s2 = h2_bits(__floats2half2_rn(t0 - f1.x, t1 - f1.y));
+    o.s1s = h2_bits(__floats2half2_rn(r10, r11));
+    return o;
 }
 
 __device__ __forceinline__ double oz_value(uint16_t s0, uint16_t s1, uint16_t s2) {
