@@ -88,29 +88,22 @@ __global__ void __launch_bounds__(256) gershgorin_kernel(const int64_t* __restri
 }
 
 // ----------------------------------------------------------------------------- gather
-// Local column of a global column: binary search in the sorted core list, then in the
-// sorted halo list.
-__device__ __forceinline__ int find_local(const int32_t* idx, int c, int m, int g) {
-    int lo = 0, hi = c - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int v = idx[mid];
-        if (v == g) return mid;
-        if (v < g) lo = mid + 1; else hi = mid - 1;
+// Local index of a global site: open-addressing hash table (key = global index, value =
+// local index; at most half full, so every probe sequence ends at an empty slot).
+__device__ __forceinline__ unsigned gidx_hash(int g, int hbits) { return ((unsigned)g * 2654435761u) >> (32 - hbits); }
+
+__device__ __forceinline__ int hash_local(const int2* htab, int hbits, int g) {
+    const unsigned mask = (1u << hbits) - 1u;
+    for (unsigned h = gidx_hash(g, hbits);; h = (h + 1u) & mask) {
+        const int2 e = htab[h];
+        if (e.x == g) return e.y;
+        if (e.x == -1) return -1;
     }
-    lo = c; hi = m - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int v = idx[mid];
-        if (v == g) return mid;
-        if (v < g) lo = mid + 1; else hi = mid - 1;
-    }
-    return -1;
 }
 
 // One CTA (8 warps) per subgraph, 8 consecutive rows a0..a0+7 at a time, one per warp:
-// lanes map the row's H entries to local columns (binary search in the sorted core and halo
-// lists), split them and scatter them into the warp's dense row buffer in shared memory (4
+// lanes map the row's H entries to local columns (a shared-memory hash table of the
+// subgraph's sites), split them and scatter them into the warp's dense row buffer in shared memory (4
 // split planes packed in 8 bytes per column, or the FP64 value).  X_0 is symmetric, so the
 // 8 rows are also columns a0..a0+7: for the split planes the whole CTA then writes that
 // 8-column group of every stored (upper) block, each thread one row r of it (16 contiguous
@@ -123,7 +116,7 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                                                      const int64_t* __restrict__ sub_ptr,
                                                      const int32_t* __restrict__ sub_idx, SubsGeom g, int max_mpad,
                                                      uint16_t* planes, int64_t plane_stride, double* f,
-                                                     double* partials, int max_units) {
+                                                     double* partials, int max_units, int htab_off, int hbits) {
     extern __shared__ unsigned char gsm[];
     __shared__ double red[16];
     const int s = blockIdx.x;
@@ -134,7 +127,20 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     uint2* rows8 = reinterpret_cast<uint2*>(gsm);                                      // [8][max_mpad]
     uint2* rowbuf = rows8 + (size_t)warp * max_mpad;
     int32_t* sidx = reinterpret_cast<int32_t*>(gsm + (size_t)8 * max_mpad * 8);         // m_s local -> global
-    for (int a = threadIdx.x; a < m; a += blockDim.x) sidx[a] = sub_idx[base + a];
+    int2* htab = reinterpret_cast<int2*>(gsm + htab_off);
+    for (int i = threadIdx.x; i < (1 << hbits); i += blockDim.x) htab[i] = make_int2(-1, 0);
+    __syncthreads();
+    for (int a = threadIdx.x; a < m; a += blockDim.x) {
+        const int gi = sub_idx[base + a];
+        sidx[a] = gi;
+        // the sites of a subgraph are distinct, so an empty slot is always found
+        for (unsigned h = gidx_hash(gi, hbits);; h = (h + 1u) & ((1u << hbits) - 1u)) {
+            if (atomicCAS(&htab[h].x, -1, gi) == -1) {
+                htab[h].y = a;
+                break;
+            }
+        }
+    }
     __syncthreads();
     double emin, emax;
     if (ctrl->eps_given) { emin = ctrl->eps_min; emax = ctrl->eps_max; }
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
         if (a < m) {
             const int64_t gi = sidx[a];
             for (int64_t p = rowptr[gi] + lane; p < rowptr[gi + 1]; p += 32) {
-                const int b = find_local(sidx, c, m, col[p]);
+                const int b = hash_local(htab, hbits, col[p]);
                 if (b < 0) continue;
                 const double h = val[p];
                 uint2 packed;
@@ -799,6 +805,22 @@ int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X) {
     return GBE_OK;
 }
 
+// Dynamic shared memory of the gather: 8 dense rows, the local->global list, and a hash
+// table of >= 2 m slots (global -> local).
+struct GatherLayout {
+    size_t smem;
+    int htab_off, hbits;
+};
+static GatherLayout gather_layout(const gbe_subs* X) {
+    GatherLayout L;
+    const int64_t max_m = X->parts->max_m;
+    L.hbits = 6;
+    while ((1ll << L.hbits) < 2 * max_m) ++L.hbits;
+    L.htab_off = (int)((((size_t)8 * X->max_mpad * 8 + (size_t)max_m * 4) + 7) & ~(size_t)7);
+    L.smem = (size_t)L.htab_off + ((size_t)8 << L.hbits);
+    return L;
+}
+
 // Control init, spectral bounds, gather and the first decision of a run (on ctx->stream).
 static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, gbe_subs* X) {
     cudaStream_t st = ctx->stream;
@@ -806,12 +828,12 @@ static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, g
     GBE_CUDA_TRY(cudaGetLastError());
     if (!in.eps_given) GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
     const gbe_parts* parts = X->parts;
-    const size_t smem = (size_t)8 * X->max_mpad * 8 + (size_t)parts->max_m * 4;
+    const GatherLayout L = gather_layout(X);
     auto gk = X->prec == GBE_PREC_FP64 ? gather_kernel<GBE_PREC_FP64>
             : (X->prec == GBE_PREC_FP16X6 ? gather_kernel<GBE_PREC_FP16X6> : gather_kernel<GBE_PREC_BF16X3>);
-    gk<<<(unsigned)X->P, 256, smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
-                                           geom_of(X), X->max_mpad, X->planes[0], X->total_elems, X->f64[0],
-                                           X->d_partials, X->max_units);
+    gk<<<(unsigned)X->P, 256, L.smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
+                                             geom_of(X), X->max_mpad, X->planes[0], X->total_elems, X->f64[0],
+                                             X->d_partials, X->max_units, L.htab_off, L.hbits);
     GBE_CUDA_TRY(cudaGetLastError());
     decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, (int)X->P, 0, 0, 0);
     GBE_CUDA_TRY(cudaGetLastError());
@@ -942,10 +964,10 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     const bool fp64_steps = X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0;
     // kernel attributes are set outside any capture
     {
-        const size_t smem = (size_t)8 * X->max_mpad * 8 + (size_t)parts->max_m * 4;
+        const GatherLayout L = gather_layout(X);
         auto gk = X->prec == GBE_PREC_FP64 ? gather_kernel<GBE_PREC_FP64>
                 : (X->prec == GBE_PREC_FP16X6 ? gather_kernel<GBE_PREC_FP16X6> : gather_kernel<GBE_PREC_BF16X3>);
-        GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     }
     const bool prof = ctx->profile != 0;
     if (ctx->graphs && !prof) {
@@ -1248,14 +1270,14 @@ extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     in.eps_min = emin;
     in.eps_max = emax;
     in.out_scale = B;
-    const size_t smem = (size_t)8 * X->max_mpad * 8 + (size_t)parts->max_m * 4;
+    const GatherLayout L = gather_layout(X);
     auto gk = fp64 ? gather_kernel<GBE_PREC_FP64> : gather_kernel<GBE_PREC_FP16X6>;
-    GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     cudaEventRecord(X->ev[0], st);
     init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
-    gk<<<(unsigned)X->P, 256, smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
-                                           geom_of(X), X->max_mpad, X->planes[2], X->total_elems, X->f64[2],
-                                           X->d_partials, X->max_units);
+    gk<<<(unsigned)X->P, 256, L.smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
+                                             geom_of(X), X->max_mpad, X->planes[2], X->total_elems, X->f64[2],
+                                             X->d_partials, X->max_units, L.htab_off, L.hbits);
     GBE_CUDA_TRY(cudaGetLastError());
     for (int s = 0; s < 2; ++s) {
         if (fp64) GBE_CUDA_TRY(cudaMemsetAsync(X->f64[s], 0, X->total_elems * 8, st));
