@@ -51,6 +51,9 @@ WORKLOADS = {
     # finite temperature on the 32^3 workload: Fermi function at kT = 0.25 eV (beta = 4/eV),
     # mu = 0, Chebyshev order 300 (coefficients below 1e-8 beyond it for this spectral width)
     "foe32": dict(kind="lattice", L=32, seed=0, thresh=0.15, ncell=(8, 8, 8), foe=dict(beta=4.0, mu=0.0, order=300)),
+    # learned graph proposal at 1,048,576 disordered sites (box 101.6a): candidate pairs
+    # r < 4a with features, the width-64 network over every pair, selection + union with H
+    "mlp1m": dict(kind="disordered", N=1 << 20, seed=2024, mlp=dict(rcand=4.0, cut=0.0)),
 }
 PRECS = {"fp16x6": ("FP16X6", "f16-split(x6)/f32-acc/f64-trace"),
          "bf16x3": ("BF16X3", "bf16-split(x3)/f32-acc/f64-trace")}
@@ -386,6 +389,72 @@ def run_foe(args, wl, gbe, torch, ctx, local, rank, world):
         print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- learned graph proposal
+def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
+    """Graph proposal by the edge classifier at full size: per step the candidate pairs and
+    their features, the network's logits for every pair, and the selected graph (union
+    with H).  Reported: sites/s and pairs/s of the whole proposal; the phases apart."""
+    import numpy as np
+    w = make_system(wl, wl["seed"] + rank)
+    N = w["pos"].shape[0]
+    st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
+    Hh = gbe.build_hamiltonian(ctx, st)
+    Hv = Hh.csr()
+    cfg = wl["mlp"]
+    M = gbe.mlp_create(ctx)
+    rng = np.random.default_rng(0)
+    M.set_params((rng.normal(0, 0.2, M.param_count)).astype(np.float32))
+    phases = {"pairs_features": 0.0, "forward": 0.0, "graph": 0.0}
+    npairs = 0
+
+    def step(timed):
+        nonlocal npairs
+        t0 = time.perf_counter()
+        P = gbe.pairs_build(ctx, st, Hv, cfg["rcand"])
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        npairs = P.info()[1]
+        z = torch.empty(npairs, dtype=torch.float32, device="cuda")
+        M.forward(P, z)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        del P, z
+        G = gbe.build_graph(ctx, Hv, gbe.GRAPH_MLP, site_struct=st, mlp=M, rcand=cfg["rcand"], logit_cut=cfg["cut"])
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        if timed:
+            phases["pairs_features"] += t1 - t0
+            phases["forward"] += t2 - t1
+            phases["graph"] += t3 - t2
+        return G
+
+    for _ in range(max(args.warmup, 3)):
+        step(False)
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.steps):
+        G = step(True)
+    clk = clocks.stop()
+    edges = G.size()[1]
+    sec = max_over_ranks(phases["graph"] / args.steps, world)
+    fwd = phases["forward"] / args.steps
+    flops = 2.0 * npairs * (5 * 64 + 64 * 64 + 64)
+    line = {
+        "metric": "learned graph proposal: sites/s (candidate pairs, features, network, selection)",
+        "value": N * world / sec, "unit": "sites/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * sec, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (fp16-rounded weights)", "data": "synthetic (random weights)",
+        "config": {"workload": args.workload, "N": N, "box_a": float(w["box"][0]), "rcand_a": cfg["rcand"],
+                   "pairs": int(npairs), "graph_edges_per_site": edges / N,
+                   "timing": "wall clock of gbe_build_graph(GBE_GRAPH_MLP); pairs and forward timed apart"},
+        "phase_ms": {k: 1000.0 * v / args.steps for k, v in phases.items()},
+        "pairs_per_s_forward": npairs / fwd, "forward_tflops_fp32": flops / fwd / 1e12,
+        "e2e": None, "gpu_launches": None, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 # ----------------------------------------------------------------------------- GPU leg
 def main():
     ap = argparse.ArgumentParser()
@@ -426,6 +495,9 @@ def main():
         return
     if wl.get("foe"):
         run_foe(args, wl, gbe, torch, ctx, local, rank, world)
+        return
+    if wl.get("mlp"):
+        run_mlp(args, wl, gbe, torch, ctx, local, rank, world)
         return
 
     # ---------------------------------------------------------------- set-up (timed apart)
