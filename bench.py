@@ -85,6 +85,49 @@ def captured_traffic(kernel, workload):
     return sum(d["dram_bytes_per_launch"]) / len(d["dram_bytes_per_launch"])
 
 
+TRAFFIC_SOURCES = {
+    "sp2_square_tc_fp16x6": ["paper_1603_00937_gb300/csrc/sp2_tc.cu", "paper_1603_00937_gb300/csrc/split.cuh",
+                             "paper_1603_00937_gb300/csrc/gbe_internal.h"],
+}
+TRAFFIC_KERNEL_RE = {"sp2_square_tc_fp16x6": r"sp2_square_tc_kernel<1, (0|false)>"}   # <PREC = FP16X6, FOE = false>
+
+
+def record_traffic(report, kernel, workload, capture_md):
+    """Write profiles/traffic_<kernel>_<workload>.json from an ncu report of that workload:
+    dram__bytes_read.sum + dram__bytes_write.sum of every captured launch of the kernel, with
+    the hash of its sources (a later change of them voids the record)."""
+    import csv
+    import hashlib
+    import re
+    import subprocess
+    out = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv", "--print-units", "base"],
+                         capture_output=True, text=True, check=True).stdout
+    rows = list(csv.reader(out.splitlines()))
+    hdr = rows[0]
+    kn, rd, wr = hdr.index("Kernel Name"), hdr.index("dram__bytes_read.sum"), hdr.index("dram__bytes_write.sum")
+    pat = re.compile(TRAFFIC_KERNEL_RE[kernel])
+    per_launch = []
+    for r in rows[1:]:
+        if len(r) > max(kn, rd, wr) and pat.search(r[kn]):
+            try:
+                per_launch.append(int(round(float(r[rd].replace(",", "")) + float(r[wr].replace(",", "")))))
+            except ValueError:
+                continue   # the units row
+    if not per_launch:
+        raise SystemExit("no launch of %s in %s" % (kernel, report))
+    h = hashlib.sha256()
+    for src in TRAFFIC_SOURCES[kernel]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    rec = {"kernel": kernel, "workload": workload, "dram_bytes_per_launch": per_launch,
+           "sources": TRAFFIC_SOURCES[kernel], "sha256": h.hexdigest(), "capture": capture_md}
+    path = os.path.join(ROOT, "profiles", "traffic_%s_%s.json" % (kernel, workload))
+    with open(path, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    print(path, per_launch)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -471,7 +514,14 @@ def main():
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch SP2 runs step by step instead of as CUDA graphs (profilers do not see "
                          "kernels inside conditional graph nodes)")
+    ap.add_argument("--record-traffic", metavar="REPORT",
+                    help="write the DRAM traffic record of the FP16X6 squaring kernel for --workload "
+                         "from this ncu report (no GPU needed), then exit")
     args = ap.parse_args()
+    if args.record_traffic:
+        record_traffic(args.record_traffic, "sp2_square_tc_fp16x6", args.workload,
+                       "profiles/sp2_square_tc_%s_%s.md" % (args.prec, args.workload))
+        return
     if args.impl == "reference":
         run_reference(args)
         return
