@@ -74,6 +74,7 @@ struct gbe_parts {
     int64_t P = 0;        // subgraphs
     int64_t total = 0;    // sum of m_s
     int64_t max_m = 0;
+    int cores_cover = 0;  // every vertex is a core vertex of exactly one subgraph
     int32_t* d_core_count = nullptr;  // [P]
     int64_t* d_sub_ptr = nullptr;     // [P+1]
     int32_t* d_sub_idx = nullptr;     // [total]

@@ -757,6 +757,7 @@ extern "C" int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partiti
     gbe_parts* parts = new gbe_parts();
     parts->n = n;
     parts->P = P;
+    parts->cores_cover = 1;   // cells and index blocks both partition the vertices
     parts->h_core_count.resize(P);
     std::vector<int32_t> hm(P);
     cudaMemcpyAsync(hm.data(), msz.p, P * 4, cudaMemcpyDeviceToHost, st);

@@ -620,8 +620,22 @@ extern "C" int gbe_parts_import(gbe_ctx* ctx, int64_t n, int64_t P, const int32_
     const int64_t total = sub_ptr[P];
     for (int64_t i = 0; i < total; ++i) GBE_CHECK_ARG(sub_idx[i] >= 0 && sub_idx[i] < n, "sub_idx out of range");
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    // do the cores partition the vertices (then every row of D is written by one subgraph)?
+    int cover = 1;
+    {
+        std::vector<uint8_t> seen((size_t)n, 0);
+        int64_t cores = 0;
+        for (int64_t s = 0; s < P && cover; ++s)
+            for (int64_t i = sub_ptr[s]; i < sub_ptr[s] + core_count[s]; ++i) {
+                if (seen[sub_idx[i]]) { cover = 0; break; }
+                seen[sub_idx[i]] = 1;
+                ++cores;
+            }
+        if (cores != n) cover = 0;
+    }
     gbe_parts* p = new gbe_parts();
     p->n = n; p->P = P; p->total = total; p->max_m = max_m;
+    p->cores_cover = cover;
     p->h_core_count.assign(core_count, core_count + P);
     p->h_sub_ptr.assign(sub_ptr, sub_ptr + P + 1);
     int r = GBE_OK;
@@ -1126,22 +1140,26 @@ extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* 
     int32_t* col = D->col;
     double* val = D->val;
     void* tmp = nullptr;
-    if (!D->on_device) {
+    // host D: assembled on the device and copied out (the copy engines move it over the host
+    // link faster than the kernels' own stores to page-locked host memory)
+    const bool staged = !D->on_device;
+    if (staged) {
         const int64_t col_bytes = ((total * 4 + 15) / 16) * 16;
         GBE_TRY(gbe_alloc(&tmp, col_bytes + total * 8));
         col = (int32_t*)tmp;
         val = (double*)((char*)tmp + col_bytes);
     }
-    fill_ell_kernel<<<ctx->sm_count * 4, 256, 0, st>>>(total, col, val);
+    // rows outside every core keep the empty entry (the assembly pads the rows it writes)
+    if (!parts->cores_cover) fill_ell_kernel<<<ctx->sm_count * 4, 256, 0, st>>>(total, col, val);
     assemble_kernel<<<(unsigned)X->P, 256, 0, st>>>(X->d_ctrl, parts->d_sub_ptr, parts->d_sub_idx, geom_of(X),
                                                       X->planes[0], X->planes[1], X->total_elems, X->f64[0],
                                                       X->f64[1], D->width, col, val, drop_tol);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && !D->on_device) {
+    if (e == cudaSuccess && staged) {
         e = cudaMemcpyAsync(D->col, col, total * 4, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(D->val, val, total * 8, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
+    if (e == cudaSuccess && !D->on_device) e = cudaStreamSynchronize(st);
     if (tmp) gbe_free(tmp);
     if (e != cudaSuccess) {
         gbe_set_error("assemble: %s", cudaGetErrorString(e));

@@ -13,7 +13,7 @@ from oracle import graph, partition, sp2
 pytestmark = pytest.mark.gpu
 
 from tests.gpu_helpers import (assembled_dense, device_csr, gbe, host_csr, import_parts,  # noqa: E402
-                               lattice_case, oracle_graph_sp2)
+                               lattice_case, oracle_graph_sp2, torch)
 
 
 @pytest.fixture(scope="module")
@@ -209,3 +209,47 @@ def test_graph_launch_matches_step_launch(prec):
     for seq, stop, D in outs[1:]:
         assert seq == outs[0][0] and stop == outs[0][1]
         np.testing.assert_array_equal(D, outs[0][2])
+
+
+@pytest.mark.parametrize("cover", [True, False])
+def test_assembly_into_host_buffers(ctx, c1, cover):
+    """Device buffers, page-locked host buffers and pageable host arrays receive the same ELL
+    D, every entry written; with cores that leave vertices out (no padding pass can be
+    skipped then), those rows stay empty in all three."""
+    H = c1["H"]
+    N = H.shape[0]
+    subs, nc = list(c1["subs"]), list(c1["nc"])
+    left_out = np.asarray(subs[0][:nc[0]])
+    if not cover:
+        subs, nc = subs[1:], nc[1:]    # the first subgraph's core vertices are in no core
+    parts = import_parts(ctx, N, subs, nc)
+    X, rep = gbe.sp2_submatrices(ctx, device_csr(H), parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP64, seq=c1["seq"]))
+    n, width = gbe.assemble_width(ctx, X, parts)
+    outs = []
+    for kind in ("device", "pinned", "pageable"):
+        if kind == "device":
+            col = torch.full((n, width), 7, dtype=torch.int32, device="cuda")
+            val = torch.full((n, width), float("nan"), dtype=torch.float64, device="cuda")
+        elif kind == "pinned":
+            col = torch.full((n, width), 7, dtype=torch.int32).pin_memory()
+            val = torch.full((n, width), float("nan"), dtype=torch.float64).pin_memory()
+        else:
+            col = np.full((n, width), 7, dtype=np.int32)
+            val = np.full((n, width), np.nan)
+        gbe.assemble_D(ctx, X, parts, col, val)
+        torch.cuda.synchronize()
+        c = col.cpu().numpy() if torch.is_tensor(col) else col
+        v = val.cpu().numpy() if torch.is_tensor(val) else val
+        outs.append((c.copy(), v.copy()))
+    for c, v in outs[1:]:
+        np.testing.assert_array_equal(c, outs[0][0])
+        np.testing.assert_array_equal(v, outs[0][1])
+    c, v = outs[0]
+    assert not np.isnan(v).any() and not (c == 7).all(axis=1).any()
+    D = gbe.ell_to_dense(c, v, N)
+    if cover:
+        assert np.abs(D - c1["Dref"]).max() <= 1e-10
+    else:
+        assert np.all(c[left_out] == -1) and np.all(v[left_out] == 0.0)
+        kept = np.setdiff1d(np.arange(N), left_out)
+        assert np.abs(D[:, kept] - c1["Dref"][:, kept]).max() <= 1e-10
