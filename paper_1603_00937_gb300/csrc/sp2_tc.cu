@@ -89,18 +89,24 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// MMA and commit, executed by a whole warp with warp-uniform operands: one elected lane
+// issues the instruction (tcgen05.mma is a single-thread instruction).
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accum) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
+        "{\n\t.reg .pred p, e;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -370,89 +376,97 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t idesc = idesc_f16(R::kType);
-            int stage = 0;
-            uint32_t phase = 0;
-            int tb = 0;
-            uint32_t tph = 0;
-            bool ok = true;
-            const uint32_t tiles_addr = smem_u32(tiles);
-            for (int it = blockIdx.x; it < args.n_items && ok; it += gridDim.x) {
+        // The whole warp runs the loop (every operand is warp-uniform); one elected lane
+        // issues each tcgen05 instruction and lane 0 waits on the barriers for the warp.
+        constexpr uint32_t idesc = idesc_f16(R::kType);
+        int stage = 0;
+        uint32_t phase = 0;
+        int tb = 0;
+        uint32_t tph = 0;
+        bool ok = true;
+        const uint32_t tiles_addr = smem_u32(tiles);
+        auto wait_warp = [&](uint64_t* bar, uint32_t par) {
+            int g = 1;
+            if (lane == 0) g = mbar_wait(bar, par, budget, abort_flag) ? 1 : 0;
+            return __shfl_sync(0xffffffffu, g, 0) != 0;
+        };
+        for (int it = blockIdx.x; it < args.n_items && ok; it += gridDim.x) {
 #ifdef GBE_TC_STATS
-                const long long ts0 = clock64();
+            const long long ts0 = clock64();
 #endif
-                const TileItem w = args.items[it];
-                const int m = args.g.m[w.s];
-                const int nk = (m + 31) >> 5;
-                const bool diag = (w.I == w.J) && !FOE;
+            const TileItem w = args.items[it];
+            const int m = args.g.m[w.s];
+            const int nk = (m + 31) >> 5;
+            const bool diag = (w.I == w.J) && !FOE;
 #ifdef GBE_TC_STATS
-                st_acc[6] += (unsigned long long)(clock64() - ts0);
+            st_acc[6] += (unsigned long long)(clock64() - ts0);
 #endif
-                bool got;
+            bool got;
+            {
+                TC_T0();
+                got = wait_warp(&tempty[tb], tph ^ 1);
+                TC_ACC(1);
+            }
+            if (!got) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t dacc0 = tmem_base + (uint32_t)(tb * 256);
+            for (int kc = 0; kc < nk; ++kc) {
                 {
                     TC_T0();
-                    got = mbar_wait(&tempty[tb], tph ^ 1, budget, abort_flag);
-                    TC_ACC(1);
+                    got = wait_warp(&full[stage], phase);
+                    TC_ACC(2);
                 }
                 if (!got) { ok = false; break; }
+#ifdef GBE_TC_STATS
+                const long long ti0 = clock64();
+#endif
                 tc_fence_after();
-                const uint32_t dacc0 = tmem_base + (uint32_t)(tb * 256);
-                for (int kc = 0; kc < nk; ++kc) {
-                    {
-                        TC_T0();
-                        got = mbar_wait(&full[stage], phase, budget, abort_flag);
-                        TC_ACC(2);
-                    }
-                    if (!got) { ok = false; break; }
-#ifdef GBE_TC_STATS
-                    const long long ti0 = clock64();
-#endif
-                    tc_fence_after();
-                    const uint32_t sbase = tiles_addr + (uint32_t)(stage * R::kSlots * kTileBytes);
-                    const int kb = kc >> 2;
-                    const bool tA = w.I > kb, tB = FOE || w.J > kb;   // operand loaded transposed (MN-major)
-                    const uint32_t idesc_t = idesc | ((uint32_t)tA << 15) | ((uint32_t)tB << 16);
+                const uint32_t sbase = tiles_addr + (uint32_t)(stage * R::kSlots * kTileBytes);
+                const int kb = kc >> 2;
+                const bool tA = w.I > kb, tB = FOE || w.J > kb;   // operand loaded transposed (MN-major)
+                const uint32_t idesc_t = idesc | ((uint32_t)tA << 15) | ((uint32_t)tB << 16);
 #pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
+                for (int ks = 0; ks < 2; ++ks) {
 #pragma unroll
-                        for (int p = 0; p < R::kProducts; ++p) {
-                            const int a = nib(R::kPa, p), acc = nib(R::kPacc, p);
-                            int b = nib(R::kPb, p);
-                            if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);   // never for FOE
-                            const uint32_t aa = sbase + a * kTileBytes, ba = sbase + b * kTileBytes;
-                            const uint64_t da = tA ? sdesc_mnmajor(aa + ks * 256) : sdesc_kmajor(aa + ks * 4096);
-                            const uint64_t db = tB ? sdesc_mnmajor(ba + ks * 256) : sdesc_kmajor(ba + ks * 4096);
-                            // the first product into each accumulator overwrites it
-                            bool first = (kc == 0 && ks == 0);
-                            if (first) {
-                                for (int q = 0; q < p; ++q)
-                                    if (nib(R::kPacc, q) == acc) first = false;
-                            }
-                            umma_f16(dacc0 + acc * 128, da, db, idesc_t, first ? 0u : 1u);
+                    for (int p = 0; p < R::kProducts; ++p) {
+                        const int a = nib(R::kPa, p), acc = nib(R::kPacc, p);
+                        int b = nib(R::kPb, p);
+                        if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);   // never for FOE
+                        const uint32_t aa = sbase + a * kTileBytes, ba = sbase + b * kTileBytes;
+                        const uint64_t da = tA ? sdesc_mnmajor(aa + ks * 256) : sdesc_kmajor(aa + ks * 4096);
+                        const uint64_t db = tB ? sdesc_mnmajor(ba + ks * 256) : sdesc_kmajor(ba + ks * 4096);
+                        // the first product into each accumulator overwrites it
+                        bool first = (kc == 0 && ks == 0);
+                        if (first) {
+                            for (int q = 0; q < p; ++q)
+                                if (nib(R::kPacc, q) == acc) first = false;
                         }
+                        umma_f16(dacc0 + acc * 128, da, db, idesc_t, first ? 0u : 1u);
                     }
-                    umma_commit(&empty[stage]);
-#ifdef GBE_TC_STATS
-                    st_acc[7] += (unsigned long long)(clock64() - ti0);
-#endif
-                    if (++stage == NS) { stage = 0; phase ^= 1; }
                 }
-                if (!ok) break;
-                umma_commit(&tfull[tb]);
-                tb ^= 1;
-                if (tb == 0) tph ^= 1;
+                umma_commit(&empty[stage]);
+#ifdef GBE_TC_STATS
+                st_acc[7] += (unsigned long long)(clock64() - ti0);
+#endif
+                if (++stage == NS) { stage = 0; phase ^= 1; }
             }
-            if (!ok) {
-                *abort_flag = 1;
-                atomicExch(&ctrl->status, GBE_ETIMEOUT);
-            }
-            // all issued MMAs complete before TMEM is released
-            umma_commit(drain);
+            if (!ok) break;
+            umma_commit(&tfull[tb]);
+            tb ^= 1;
+            if (tb == 0) tph ^= 1;
+        }
+        if (!ok && lane == 0) {
+            *abort_flag = 1;
+            atomicExch(&ctrl->status, GBE_ETIMEOUT);
+        }
+        // all issued MMAs complete before TMEM is released
+        umma_commit(drain);
+        if (lane == 0) {
             const long long t0 = clock64();
             while (!mbar_try_wait(drain, 0) && clock64() - t0 < budget) {
             }
         }
+        __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..9)
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
