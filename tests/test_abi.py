@@ -51,3 +51,86 @@ def test_create_without_gpu_fails_loudly(lib):
     with pytest.raises(gbe.GbeError) as e:
         gbe.Context(0)
     assert e.value.code == gbe.GBE_ENODEV
+
+
+def declared_prototypes():
+    """name -> (return type, [argument types]) of every gbe_* prototype in include/*.h."""
+    protos = {}
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        for m in re.finditer(r"^\s*((?:const\s+)?\w+\s*\*?)\s*(gbe_\w+)\s*\(([^)]*)\)\s*;", text, re.M):
+            args = [a.strip() for a in m.group(3).split(",") if a.strip() and a.strip() != "void"]
+            protos[m.group(2)] = (m.group(1).strip(), args)
+    return protos
+
+
+def _ctype_of(decl):
+    """The ctypes type a C parameter or return type needs (pointer, int32, int64, double, float)."""
+    import ctypes
+    if "*" in decl:
+        return ctypes.c_char_p if re.match(r"^const\s+char\s*\*", decl) else ctypes.c_void_p
+    t = decl.replace("const", "").split()[0]
+    return {"int": ctypes.c_int, "int32_t": ctypes.c_int, "int64_t": ctypes.c_int64, "double": ctypes.c_double,
+            "float": ctypes.c_float, "uint8_t": ctypes.c_ubyte}[t]
+
+
+def test_binding_signatures_match_header(lib):
+    """Every ctypes signature the binding installs has the header's argument count and types:
+    a mismatch (an int64_t passed as int, a float as double) corrupts arguments silently."""
+    import ctypes
+    protos = declared_prototypes()
+    checked = 0
+    for name, (ret, args) in protos.items():
+        f = getattr(lib, name)
+        if f.argtypes is None:
+            continue
+        want = [_ctype_of(a) for a in args]
+        got = list(f.argtypes)
+        assert len(got) == len(want), (name, got, want)
+        for g, w in zip(got, want):
+            if w is ctypes.c_char_p:
+                assert g in (ctypes.c_char_p, ctypes.c_void_p), (name, g, w)
+            else:
+                assert g is w, (name, args, got)
+        if ret != "void":
+            assert f.restype is _ctype_of(ret) or (_ctype_of(ret) is ctypes.c_char_p and f.restype is ctypes.c_char_p), \
+                (name, ret, f.restype)
+        checked += 1
+    assert checked >= 40, checked
+
+
+STRUCTS = {"Csr": "gbe_csr", "Ell": "gbe_ell", "Sites": "gbe_sites", "TbModel": "gbe_tb_model",
+           "GraphParams": "gbe_graph_params", "PartitionParams": "gbe_partition_params",
+           "Sp2Params": "gbe_sp2_params", "Sp2Report": "gbe_sp2_report", "FoeParams": "gbe_foe_params",
+           "FoeReport": "gbe_foe_report"}
+
+
+def test_binding_structs_match_header(tmp_path):
+    """Every struct the binding passes by pointer has the header's size and field offsets
+    (a smaller ctypes struct would be overrun by the library's writes)."""
+    import ctypes
+    import shutil
+    import paper_1603_00937_gb300 as gbe
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gbe.h"', "int main(void) {"]
+    for py, c in STRUCTS.items():
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (py, c))
+        for f in getattr(gbe, py)._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (py, f[0], c, f[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    for py in STRUCTS:
+        S = getattr(gbe, py)
+        assert int(got["%s size" % py]) == ctypes.sizeof(S), py
+        for f in S._fields_:
+            assert int(got["%s.%s" % (py, f[0])]) == getattr(S, f[0]).offset, (py, f[0])
