@@ -257,6 +257,24 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- QMD-like run
+def configure(args, gbe, ctx, H, parts, prm, X):
+    """Launch configuration of the squaring kernel before the timed region: forced by
+    --config, the default with --no-autotune, else chosen by the library's autotuner
+    (every built configuration timed on this problem, untimed here)."""
+    if prm.prec == gbe.PREC_FP64:
+        return None
+    if args.config:
+        stages, sched = (int(v) for v in args.config.split(","))
+        gbe.subs_set_config(ctx, X, stages, sched)
+        return {"forced": gbe.subs_get_config(X)}
+    if args.no_autotune:
+        return {"default": gbe.subs_get_config(X)}
+    t0 = time.perf_counter()
+    rep = gbe.sp2_autotune(ctx, H, parts, prm, X, reps=3)
+    rep["tuning_s"] = time.perf_counter() - t0
+    return rep
+
+
 def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
     """MD steps of the lattice: every step rebuilds H from the new positions, the graph from
     the previous step's D, the partition, the SP2 state, runs SP2 with the previous step's
@@ -304,6 +322,10 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
         t0 = mark("sp2_state", t0)
         prm = gbe.sp2_params(N / 2.0, prec=PREC, n_max=64, n_min=10, idem_tol=1e-10, seq=state["seq"],
                              fp64_tail=args.fp64_tail)
+        if not timed and "tune" not in last:
+            # first warm-up step: tune once; later states of the same shape start with the choice
+            last["tune"] = configure(args, gbe, ctx, Hg.csr(), parts, prm, X)
+            t0 = time.perf_counter()
         gbe.sp2_run(ctx, Hg.csr(), parts, prm, X)
         rep = gbe.sp2_report_get(ctx, X).as_dict()
         t0 = mark("sp2", t0)
@@ -355,6 +377,7 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
                      "kernel": "sp2_square_tc_kernel<%s>" % prec_name,
                      "peak_kind": peak_kind + " dense bf16/fp16 burst", "ms_per_launch": tc_ms},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": N * 24, "d2h_bytes_per_step": 4616},
+        "autotune": last.get("tune"),
         "gpu_launches": None,
         "clocks": clk,
     }
@@ -514,6 +537,11 @@ def main():
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch SP2 runs step by step instead of as CUDA graphs (profilers do not see "
                          "kernels inside conditional graph nodes)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip the squaring kernel's autotuner (default launch configuration)")
+    ap.add_argument("--config", metavar="STAGES,SCHEDULE",
+                    help="force the squaring kernel's launch configuration instead of autotuning, e.g. 4,0 "
+                         "(schedule 0 round-robin, 1 balanced ranges); used to profile the tuned choice")
     ap.add_argument("--record-traffic", metavar="REPORT",
                     help="write the DRAM traffic record of the FP16X6 squaring kernel for --workload "
                          "from this ncu report (no GPU needed), then exit")
@@ -600,6 +628,7 @@ def main():
     PREC = getattr(gbe, "PREC_" + prec_name)
     Xm = gbe.subs_create(ctx, parts, PREC)
     pm = params(PREC)
+    tune = configure(args, gbe, ctx, Hv, parts, pm, Xm)
     clocks = ClockSampler(local)
     clocks.start()
     ms_m, rep_m = timed(Xm, pm, col_m, val_m, args.steps, max(args.warmup, 3))
@@ -705,6 +734,7 @@ def main():
         "e2e": {"value": N * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches * args.steps,
         "clocks": clk,
+        "autotune": tune,
     }
     line.update(out)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

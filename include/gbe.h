@@ -270,6 +270,58 @@ int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_report* rep);
 int gbe_sp2_submatrices(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts,
                         const gbe_sp2_params* params, gbe_subs** X, gbe_sp2_report* rep);
 
+/* ------------------------------------------- launch configuration and autotuner */
+
+/* Launch configuration of the tensor-core squaring that runs every submatrix of an SP2
+ * step in one persistent launch (one CTA per SM):
+ *   stages    depth of the TMA operand ring in 32-column K-chunks (0: the precision's
+ *             default; FP16X6 is built with 3 and 4, BF16X3 with 4, 6 and 7)
+ *   schedule  how the upper-triangular 128 x 128 output tiles of all subgraphs (ordered
+ *             subgraph by subgraph, largest first) are dealt to the CTAs:
+ *             GBE_SCHED_ROUND_ROBIN    CTA b takes tiles b, b + grid, ... (the tiles of one
+ *                                      subgraph run side by side on neighbouring CTAs)
+ *             GBE_SCHED_BALANCED_RANGES CTA b takes one contiguous run of tiles, the runs
+ *                                      cut so that every CTA gets the same number of
+ *                                      K-chunks (sum over its tiles of ceil(m_s / 32))
+ * The configuration changes no result: every tile is computed by the same instructions
+ * in the same order whichever CTA runs it, and the trace partials are summed in tile
+ * order.  It applies to GBE_PREC_FP16X6 / GBE_PREC_BF16X3 states (FP64 states ignore it).
+ * This knob is not in the paper; the paper's GPU runs call a dense GEMM per submatrix. */
+enum { GBE_SCHED_ROUND_ROBIN = 0, GBE_SCHED_BALANCED_RANGES = 1 };
+typedef struct {
+    int stages;
+    int schedule;
+} gbe_tc_config;
+
+#define GBE_TUNE_MAX 16
+typedef struct {
+    int n;                            /* candidates timed                                    */
+    gbe_tc_config cand[GBE_TUNE_MAX];
+    float ms[GBE_TUNE_MAX];           /* mean CUDA-event time of one SP2 run (gather + loop) */
+    int best;                         /* index of the configuration installed               */
+    int iters;                        /* squarings per timed run (replayed sequence)         */
+    int cached;                       /* 1: taken from the context's cache, nothing timed    */
+} gbe_tune_report;
+
+/* Read / install the configuration of a state.  Installing one rebuilds the tile schedule
+ * on the device and drops the state's captured SP2 graphs (recaptured on the next run).
+ * GBE_EINVAL for a depth the precision is not built with or an unknown schedule. */
+int gbe_subs_get_config(const gbe_subs* X, gbe_tc_config* cfg);
+int gbe_subs_set_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config* cfg);
+
+/* Autotuner (spec batching requirement, not in the paper): time every built
+ * configuration of X's precision on the caller's own problem and install the fastest.
+ * One SP2 run with `params` (its branch decisions as given) fixes the branch sequence;
+ * every candidate then replays that sequence without FP64 tail steps, once untimed and
+ * `reps` times timed with CUDA events on the context stream, so all candidates do the
+ * same work.  The choice is cached in the context under the state's shape (precision,
+ * SM count, subgraph sizes): states created later with the same shape start with it, and
+ * a later autotune of such a state returns the cached choice without timing (rep->cached).
+ * Afterwards X holds the last candidate's iterates: run gbe_sp2_run again for a result.
+ * H must be device CSR.  Synchronises.  FP64 states: nothing to tune (one candidate). */
+int gbe_sp2_autotune(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* params,
+                     gbe_subs* X, int reps, gbe_tune_report* rep);
+
 /* --------------------------------------------------------- assembly (a8) */
 
 /* Collect the core columns of every final x[s] into ELL D (Eq. 6): row C_s[j] of the

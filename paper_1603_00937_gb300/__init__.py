@@ -23,6 +23,9 @@ GRAPH_H2_THRESH, GRAPH_D_THRESH, GRAPH_EQ8_SYMBOLIC, GRAPH_HK_PATTERN, GRAPH_MLP
 PART_SPATIAL_CELLS, PART_INDEX_BLOCKS = 0, 1
 PREC_FP64, PREC_FP16X6, PREC_BF16X3 = 0, 1, 2
 BRANCH_GLOBAL_TRACE, BRANCH_REPLAY = 0, 1
+SCHED_ROUND_ROBIN, SCHED_BALANCED_RANGES = 0, 1
+SCHED_NAMES = {0: "round_robin", 1: "balanced_ranges"}
+TUNE_MAX = 16
 STOP_NAMES = {0: "none", 1: "tol", 2: "stall", 3: "nmax", 4: "replay", 5: "error"}
 SEQ_MAX = 256
 
@@ -37,6 +40,7 @@ EXPORTS = [
     "gbe_free_pairs", "gbe_mlp_create", "gbe_mlp_param_count", "gbe_mlp_set_params", "gbe_mlp_get_params",
     "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_free_mlp",
     "gbe_sp2_gap_estimate", "gbe_sp2_sequence", "gbe_fermi_coefficients", "gbe_foe_run", "gbe_foe_report_get",
+    "gbe_subs_get_config", "gbe_subs_set_config", "gbe_sp2_autotune",
 ]
 
 
@@ -106,6 +110,21 @@ class Sp2Report(ctypes.Structure):
                     fp64_flops=self.fp64_flops)
 
 
+class TcConfig(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_int), ("schedule", ctypes.c_int)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("cand", TcConfig * TUNE_MAX), ("ms", ctypes.c_float * TUNE_MAX),
+                ("best", ctypes.c_int), ("iters", ctypes.c_int), ("cached", ctypes.c_int)]
+
+    def as_dict(self):
+        cands = [dict(stages=self.cand[i].stages, schedule=SCHED_NAMES.get(self.cand[i].schedule, "?"),
+                      ms_per_run=self.ms[i]) for i in range(self.n)]
+        return dict(candidates=cands, best=cands[self.best] if self.n else None, iters=self.iters,
+                    cached=bool(self.cached))
+
+
 _lib = None
 
 
@@ -143,6 +162,8 @@ def load_library(path=LIB_PATH):
         "gbe_sp2_gap_estimate": (I32, [P, D, D, D, P, P]), "gbe_sp2_sequence": (I32, [D, D, D, D, D, I32, P, P]),
         "gbe_fermi_coefficients": (I32, [D, D, D, D, I32, P]), "gbe_foe_run": (I32, [P, P, P, P, P]),
         "gbe_foe_report_get": (I32, [P, P, P]),
+        "gbe_subs_get_config": (I32, [P, P]), "gbe_subs_set_config": (I32, [P, P, P]),
+        "gbe_sp2_autotune": (I32, [P, P, P, P, P, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -385,6 +406,25 @@ def sp2_report_get(ctx, X):
     r = Sp2Report()
     check(load_library().gbe_sp2_report_get(ctx.handle, X.handle, ctypes.byref(r)), "gbe_sp2_report_get")
     return r
+
+
+def subs_get_config(X):
+    c = TcConfig()
+    check(load_library().gbe_subs_get_config(X.handle, ctypes.byref(c)), "gbe_subs_get_config")
+    return dict(stages=c.stages, schedule=c.schedule)
+
+
+def subs_set_config(ctx, X, stages=0, schedule=SCHED_ROUND_ROBIN):
+    c = TcConfig(stages, schedule)
+    check(load_library().gbe_subs_set_config(ctx.handle, X.handle, ctypes.byref(c)), "gbe_subs_set_config")
+
+
+def sp2_autotune(ctx, H, parts, params, X, reps=3):
+    """Time every built squaring configuration on this problem, install the fastest; returns the report dict."""
+    r = TuneReport()
+    check(load_library().gbe_sp2_autotune(ctx.handle, ctypes.byref(H), parts.handle, ctypes.byref(params), X.handle,
+                                          reps, ctypes.byref(r)), "gbe_sp2_autotune")
+    return r.as_dict()
 
 
 def sp2_submatrices(ctx, H, parts, params, X=None):

@@ -48,6 +48,8 @@ struct gbe_ctx {
     int graphs = 1;   // SP2 runs launched as CUDA graphs (when per-kernel profiling is off)
     // stream-ordered device memory pool of this context (freed blocks are kept for reuse)
     cudaMemPool_t pool = nullptr;
+    // autotuned squaring configurations by state shape (precision, SM count, subgraph sizes)
+    std::vector<std::pair<std::vector<int64_t>, gbe_tc_config>> tune_cache;
 };
 
 struct gbe_hamiltonian {
@@ -167,6 +169,11 @@ struct gbe_subs {
     cudaStream_t cap_stream = nullptr;
     double alg_flops_per_iter = 0.0, mma_flops_per_iter = 0.0, fp64_flops_per_iter = 0.0;
     double mma_flops_full = 0.0, fp64_flops_full = 0.0;   // per product over all tiles
+    // launch configuration of the tensor-core squaring (ring depth, work schedule); with the
+    // balanced-range schedule CTA b takes items [d_cta_ptr[b], d_cta_ptr[b + 1])
+    gbe_tc_config tc_cfg{0, GBE_SCHED_ROUND_ROBIN};
+    int32_t* d_cta_ptr = nullptr;
+    int cta_grid = 0;
 };
 
 // ----------------------------------------------------------------------------- blocked layout
@@ -193,6 +200,12 @@ int gbe_tc_make_tmaps(gbe_subs* X);
 int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot);
 int gbe_tc_launch_foe(gbe_ctx* ctx, gbe_subs* X, int a_side, int b_side, int c_side, float alpha, double gamma);
 int gbe_tc_prepare(gbe_ctx* ctx);
+// ring depths the SP2 squaring kernel of a precision is built with (returns their count)
+int gbe_tc_stage_options(int prec, int* stages, int cap);
+// install a launch configuration on a state (work schedule rebuilt, SP2 graphs dropped)
+int gbe_subs_apply_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config& cfg);
+// shape key of a state for the context's tuning cache
+std::vector<int64_t> gbe_subs_shape_key(const gbe_ctx* ctx, const gbe_subs* X);
 
 // helpers
 // Device memory.  Inside an AllocScope (every entry point that takes a context opens one)

@@ -691,6 +691,7 @@ extern "C" int gbe_free_subs(gbe_subs* X) {
     for (int i = 0; i < 3; ++i) { gbe_free(X->planes[i]); gbe_free(X->f64[i]); }
     gbe_free(X->d_items_tc); gbe_free(X->d_items_64); gbe_free(X->d_partials); gbe_free(X->d_ctrl);
     gbe_free(X->d_items_tc_full); gbe_free(X->d_items_64_full);
+    gbe_free(X->d_cta_ptr);
     if (X->h_ctrl) cudaFreeHost(X->h_ctrl);
     for (int i = 0; i < 3; ++i) if (X->ev[i]) cudaEventDestroy(X->ev[i]);
     for (auto e : X->ev_tc) cudaEventDestroy(e);
@@ -807,9 +808,92 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     if (prec != GBE_PREC_FP64) {
         r = gbe_tc_make_tmaps(X);
         if (r != GBE_OK) { gbe_free_subs(X); return r; }
+        // a configuration the autotuner chose for a state of this shape
+        const std::vector<int64_t> key = gbe_subs_shape_key(ctx, X);
+        for (const auto& kv : ctx->tune_cache)
+            if (kv.first == key) {
+                r = gbe_subs_apply_config(ctx, X, kv.second);
+                if (r != GBE_OK) { gbe_free_subs(X); return r; }
+                break;
+            }
     }
     *out = X;
     return GBE_OK;
+}
+
+std::vector<int64_t> gbe_subs_shape_key(const gbe_ctx* ctx, const gbe_subs* X) {
+    // precision, SM count, number of subgraphs, then (padded size, count) per size bucket
+    std::vector<int64_t> key = {X->prec, ctx->sm_count, X->P};
+    std::vector<int32_t> mp(X->h_mpad);
+    std::sort(mp.begin(), mp.end());
+    for (size_t i = 0; i < mp.size();) {
+        size_t j = i;
+        while (j < mp.size() && mp[j] == mp[i]) ++j;
+        key.push_back(mp[i]);
+        key.push_back((int64_t)(j - i));
+        i = j;
+    }
+    return key;
+}
+
+int gbe_subs_apply_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config& cfg) {
+    GBE_CHECK_ARG(cfg.schedule == GBE_SCHED_ROUND_ROBIN || cfg.schedule == GBE_SCHED_BALANCED_RANGES, "schedule");
+    if (X->prec != GBE_PREC_FP64 && cfg.stages != 0) {
+        int opt[8];
+        const int n = gbe_tc_stage_options(X->prec, opt, 8);
+        bool found = false;
+        for (int i = 0; i < n; ++i) found = found || opt[i] == cfg.stages;
+        GBE_CHECK_ARG(found, "the squaring kernel of this precision is not built with that many stages");
+    }
+    drop_graphs(X);
+    gbe_free(X->d_cta_ptr);
+    X->d_cta_ptr = nullptr;
+    X->cta_grid = 0;
+    if (cfg.schedule == GBE_SCHED_BALANCED_RANGES && X->n_items_tc > 0) {
+        // the items in launch order (as built by gbe_subs_create), cost = K-chunks of the tile
+        std::vector<TileItem> items;
+        make_items(X->h_mpad, X->h_mpad, 128, items);
+        const int n = (int)items.size();
+        const int grid = std::max(1, std::min(n, ctx->sm_count));
+        std::vector<double> cost(n);
+        double total = 0.0;
+        for (int i = 0; i < n; ++i) {
+            cost[i] = (double)((X->h_m[items[i].s] + 31) / 32);
+            total += cost[i];
+        }
+        // contiguous runs of nearly equal cost, at least one item each
+        std::vector<int32_t> ptr(grid + 1, 0);
+        double acc = 0.0;
+        int j = 0;
+        for (int b = 0; b < grid - 1; ++b) {
+            const double target = total * (double)(b + 1) / grid;
+            const int lo = ptr[b] + 1, hi = n - (grid - 1 - b);
+            while (j < lo) acc += cost[j++];
+            while (j < hi && acc + 0.5 * cost[j] < target) acc += cost[j++];
+            ptr[b + 1] = j;
+        }
+        ptr[grid] = n;
+        GBE_TRY(gbe_alloc((void**)&X->d_cta_ptr, (grid + 1) * sizeof(int32_t)));
+        GBE_CUDA_TRY(cudaMemcpyAsync(X->d_cta_ptr, ptr.data(), (grid + 1) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+        GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        X->cta_grid = grid;
+    }
+    X->tc_cfg = cfg;
+    return GBE_OK;
+}
+
+extern "C" int gbe_subs_get_config(const gbe_subs* X, gbe_tc_config* cfg) {
+    GBE_CHECK_ARG(X && cfg, "NULL argument");
+    *cfg = X->tc_cfg;
+    return GBE_OK;
+}
+
+extern "C" int gbe_subs_set_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config* cfg) {
+    AllocScope alloc_scope_(ctx);
+    GBE_CHECK_ARG(ctx && X && cfg, "NULL argument");
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    return gbe_subs_apply_config(ctx, X, *cfg);
 }
 
 int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X) {

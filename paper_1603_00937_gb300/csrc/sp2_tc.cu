@@ -195,10 +195,12 @@ __host__ __device__ constexpr int nib(uint32_t v, int i) { return (int)((v >> (4
 template <class R> __device__ __forceinline__ int slot_plane(int s) { return nib(R::kPlane, s); }
 template <class R> __device__ __forceinline__ int slot_alias(int s) { return nib(R::kAlias1, s) - 1; }
 
-template <int PREC>
+// Shared memory of a CTA with an NS-deep operand ring (NS = 0: the recipe's default depth).
+template <int PREC, int NS = 0>
 constexpr size_t smem_bytes() {
     using R = Recipe<PREC>;
-    return 1024 /*align slack*/ + (size_t)R::kStages * R::kSlots * kTileBytes + 512 /*barriers, flags, reduction*/;
+    constexpr int ns = NS ? NS : R::kStages;
+    return 1024 /*align slack*/ + (size_t)ns * R::kSlots * kTileBytes + 512 /*barriers, flags, reduction*/;
 }
 
 // Optional wait-time counters (build with -DGBE_TC_STATS): cycles each role spends in
@@ -239,15 +241,19 @@ struct TcArgs {
     double* partials;
     int max_units;
     int slot;
+    // work schedule: NULL = round-robin over items (CTA b takes b, b + grid, ...);
+    // otherwise CTA b takes the contiguous range [cta_ptr[b], cta_ptr[b + 1])
+    const int32_t* cta_ptr;
 };
 
 // FOE = false: one SP2 squaring X_{n+1} = X_n^2 or 2 X_n - X_n^2 (branch from the device).
 // FOE = true: one step of a Chebyshev expansion, out = alpha x b - c + gamma I (arguments).
-template <int PREC, bool FOE>
+// NS_: depth of the operand ring in K-chunks (0: the recipe's default).
+template <int PREC, bool FOE, int NS_>
 __global__ void __launch_bounds__(kThreads, 1)
     sp2_square_tc_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     using R = Recipe<PREC>;
-    constexpr int NS = R::kStages;
+    constexpr int NS = NS_ ? NS_ : R::kStages;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* tiles = smem;                                          // NS * kSlots * 8 KB
@@ -295,6 +301,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint16_t* pout = FOE ? pc : (cur ? args.planes[0] : args.planes[1]);
     const bool use_c = FOE || !branch;   // the update reads the stored planes at its own tile
     const int64_t ps = args.ps;
+    // the same item sequence for the producer, the MMA issuer and the epilogue
+    int it_first = blockIdx.x, it_end = args.n_items, it_step = gridDim.x;
+    if (args.cta_ptr) {
+        it_first = args.cta_ptr[blockIdx.x];
+        it_end = args.cta_ptr[blockIdx.x + 1];
+        it_step = 1;
+    }
 
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
@@ -314,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t issued_mask = 0, issued_par = 0;   // per stage: armed, and the parity it was armed with
             bool ok = true;
-            for (int it = blockIdx.x; it < args.n_items && ok; it += gridDim.x) {
+            for (int it = it_first; it < it_end && ok; it += it_step) {
                 const TileItem w = args.items[it];
                 const int mpad = args.g.mpad[w.s], m = args.g.m[w.s];
                 const int64_t off = args.g.off[w.s];
@@ -390,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (lane == 0) g = mbar_wait(bar, par, budget, abort_flag) ? 1 : 0;
             return __shfl_sync(0xffffffffu, g, 0) != 0;
         };
-        for (int it = blockIdx.x; it < args.n_items && ok; it += gridDim.x) {
+        for (int it = it_first; it < it_end && ok; it += it_step) {
 #ifdef GBE_TC_STATS
             const long long ts0 = clock64();
 #endif
@@ -478,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         int tb = 0;
         uint32_t tph = 0;
         int par = 0;
-        for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+        for (int it = it_first; it < it_end; it += it_step) {
             const TileItem w = args.items[it];
             const int mpad = args.g.mpad[w.s], c = args.g.c[w.s];
             const int64_t off = args.g.off[w.s];
@@ -662,8 +675,34 @@ extern "C" int gbe_tc_stats(unsigned long long* out, int reset) {
 }
 #endif
 
+// Every launchable variant of the squaring kernel: precision, Chebyshev step or not, ring
+// depth.  The autotuner chooses among the SP2 variants of a precision.
+struct TcVariant {
+    int prec;
+    bool foe;
+    int stages;
+    const void* fn;
+    size_t smem;
+};
+#define GBE_TC_VARIANT(P, F, N) \
+    TcVariant { P, F, N ? N : Recipe<P>::kStages, (const void*)sp2_square_tc_kernel<P, F, N>, smem_bytes<P, N>() }
+static const TcVariant kVariants[] = {
+    GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 0), GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 3),
+    GBE_TC_VARIANT(GBE_PREC_FP16X6, true, 0),  GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 0),
+    GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 4), GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 7),
+};
+#undef GBE_TC_VARIANT
+
+// stages = 0: the recipe's default depth
+static const TcVariant* find_variant(int prec, bool foe, int stages) {
+    if (stages == 0)
+        stages = prec == GBE_PREC_FP16X6 ? Recipe<GBE_PREC_FP16X6>::kStages : Recipe<GBE_PREC_BF16X3>::kStages;
+    for (const TcVariant& v : kVariants)
+        if (v.prec == prec && v.foe == foe && v.stages == stages) return &v;
+    return nullptr;
+}
+
 int gbe_tc_prepare(gbe_ctx* ctx) {
-    (void)ctx;
     if (g_encode_tiled) return GBE_OK;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
@@ -672,28 +711,27 @@ int gbe_tc_prepare(gbe_ctx* ctx) {
         gbe_set_error("cuTensorMapEncodeTiled not available: %s", cudaGetErrorString(e));
         return GBE_ECUDA;
     }
-    g_encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-    int prec_list[2] = {GBE_PREC_FP16X6, GBE_PREC_BF16X3};
-    for (int p : prec_list) {
-        const size_t bytes = p == GBE_PREC_FP16X6 ? smem_bytes<GBE_PREC_FP16X6>() : smem_bytes<GBE_PREC_BF16X3>();
-        if ((int)bytes > ctx->smem_optin) {
-            gbe_set_error("tensor-core kernel needs %zu bytes of shared memory, device allows %d", bytes, ctx->smem_optin);
+    for (const TcVariant& v : kVariants) {
+        if ((int)v.smem > ctx->smem_optin) {
+            gbe_set_error("tensor-core kernel (%d stages) needs %zu bytes of shared memory, device allows %d", v.stages,
+                          v.smem, ctx->smem_optin);
             return GBE_ENODEV;
         }
+        e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem);
+        if (e != cudaSuccess) {
+            gbe_set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+            return GBE_ECUDA;
+        }
     }
-    e = cudaFuncSetAttribute(sp2_square_tc_kernel<GBE_PREC_FP16X6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem_bytes<GBE_PREC_FP16X6>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sp2_square_tc_kernel<GBE_PREC_FP16X6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes<GBE_PREC_FP16X6>());
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(sp2_square_tc_kernel<GBE_PREC_BF16X3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes<GBE_PREC_BF16X3>());
-    if (e != cudaSuccess) {
-        gbe_set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        return GBE_ECUDA;
-    }
+    g_encode_tiled = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     return GBE_OK;
+}
+
+int gbe_tc_stage_options(int prec, int* stages, int cap) {
+    int n = 0;
+    for (const TcVariant& v : kVariants)
+        if (v.prec == prec && !v.foe && n < cap) stages[n++] = v.stages;
+    return n;
 }
 
 int gbe_tc_make_tmaps(gbe_subs* X) {
@@ -757,16 +795,22 @@ int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot) {
         gbe_set_error("tensor maps missing");
         return GBE_ECUDA;
     }
+    const TcVariant* v = find_variant(X->prec, false, X->tc_cfg.stages);
+    if (!v) {
+        gbe_set_error("no tensor-core kernel with %d stages for precision %d", X->tc_cfg.stages, X->prec);
+        return GBE_EINVAL;
+    }
     TcArgs a = tc_args(X, slot);
+    int grid = std::max(1, std::min(X->n_items_tc, ctx->sm_count));
+    if (X->d_cta_ptr) {
+        a.cta_ptr = X->d_cta_ptr;
+        grid = X->cta_grid;
+    }
     TcMaps maps;
     static_assert(sizeof(maps) == sizeof(X->tmap), "tensor map set size");
     memcpy(&maps, X->tmap, sizeof(maps));
-    const int grid = std::max(1, std::min(X->n_items_tc, ctx->sm_count));
-    if (X->prec == GBE_PREC_FP16X6)
-        sp2_square_tc_kernel<GBE_PREC_FP16X6, false><<<grid, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(maps, a);
-    else
-        sp2_square_tc_kernel<GBE_PREC_BF16X3, false><<<grid, kThreads, smem_bytes<GBE_PREC_BF16X3>(), ctx->stream>>>(maps, a);
-    GBE_CUDA_TRY(cudaGetLastError());
+    void* kargs[2] = {&maps, &a};
+    GBE_CUDA_TRY(cudaLaunchKernel(v->fn, dim3(grid), dim3(kThreads), kargs, v->smem, ctx->stream));
     return GBE_OK;
 }
 
@@ -787,9 +831,8 @@ int gbe_tc_launch_foe(gbe_ctx* ctx, gbe_subs* X, int a_side, int b_side, int c_s
     a.gamma_r = (float)(gamma - gg);
     TcMaps maps;
     memcpy(&maps, X->tmap, sizeof(maps));
-    const int grid = std::max(1, std::min(X->n_items_tc, ctx->sm_count));
     const int gridf = std::max(1, std::min(X->n_items_tc_full, ctx->sm_count));
-    sp2_square_tc_kernel<GBE_PREC_FP16X6, true><<<gridf, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(maps, a);
+    sp2_square_tc_kernel<GBE_PREC_FP16X6, true, 0><<<gridf, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(maps, a);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }

@@ -105,7 +105,7 @@ def test_binding_signatures_match_header(lib):
 STRUCTS = {"Csr": "gbe_csr", "Ell": "gbe_ell", "Sites": "gbe_sites", "TbModel": "gbe_tb_model",
            "GraphParams": "gbe_graph_params", "PartitionParams": "gbe_partition_params",
            "Sp2Params": "gbe_sp2_params", "Sp2Report": "gbe_sp2_report", "FoeParams": "gbe_foe_params",
-           "FoeReport": "gbe_foe_report"}
+           "FoeReport": "gbe_foe_report", "TcConfig": "gbe_tc_config", "TuneReport": "gbe_tune_report"}
 
 
 def test_binding_structs_match_header(tmp_path):
