@@ -13,6 +13,17 @@ import synth
 from oracle import exact, graph, hamiltonian, partition, sp2
 
 
+def golden(name):
+    """Values printed in the paper (tests/golden/paper_values.txt, each line cited there)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_values.txt")
+    for line in open(path):
+        f = line.split()
+        if f and f[0] == name:
+            return [float(v) for v in f[1:]]
+    raise KeyError(name)
+
+
 @pytest.fixture(scope="module")
 def c1():
     w = synth.lattice(8, seed=0)
@@ -83,13 +94,15 @@ def test_dimers_closed_form():
 
 
 def test_expansion_order_doubles():
-    """Each SP2 step is quadratic, so n steps give degree 2^n (30 steps: > 1e9)."""
+    """Each SP2 step is quadratic, so n steps give degree 2^n; the paper's 30 iterations
+    give an order above one billion (Sec. II.B)."""
     p = np.array([0.0, 1.0])
     for n, b in enumerate([1, 0, 1, 1, 0, 0, 1, 0]):
         sq = npoly.polymul(p, p)
         p = sq if b else npoly.polysub(2 * np.pad(p, (0, len(sq) - len(p))), sq)
         assert len(np.trim_zeros(p, "b")) - 1 == 2 ** (n + 1)
-    assert 2 ** 30 > 1e9
+    (iters,), (order,) = golden("sp2_iterations"), golden("sp2_min_order")
+    assert 2 ** int(iters) > order
 
 
 def test_complete_graph_equals_dense(c1):
@@ -148,7 +161,9 @@ def test_graph_sp2_error_falls_with_tau(c1):
     _, logd = sp2.sp2_dense(H, N // 2)
     cores = partition.spatial_cores(w["pos"], w["box"], (4, 4, 4))
     errs = []
-    for tau in (1e-1, 3e-2, 1e-2):
+    taus = sorted({t for t in golden("fig5_thresholds") if t >= 1e-2} | {3e-2}, reverse=True)
+    assert taus == [1e-1, 3e-2, 1e-2]
+    for tau in taus:
         S = graph.d_threshold(sp.csr_matrix(Dex), tau)
         subs, nc = partition.subgraphs(S, cores)
         D, _ = sp2.sp2_graph(H, subs, nc, N // 2, seq=logd.seq)
