@@ -89,7 +89,7 @@ TRAFFIC_SOURCES = {
     "sp2_square_tc_fp16x6": ["paper_1603_00937_gb300/csrc/sp2_tc.cu", "paper_1603_00937_gb300/csrc/split.cuh",
                              "paper_1603_00937_gb300/csrc/gbe_internal.h"],
 }
-TRAFFIC_KERNEL_RE = {"sp2_square_tc_fp16x6": r"sp2_square_tc_kernel<1, (0|false)>"}   # <PREC = FP16X6, FOE = false>
+TRAFFIC_KERNEL_RE = {"sp2_square_tc_fp16x6": r"sp2_square_tc_kernel<1, (0|false)(, \d+)?>"}   # <PREC = FP16X6, FOE = false, ring depth>
 
 
 def record_traffic(report, kernel, workload, capture_md):

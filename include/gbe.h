@@ -257,7 +257,10 @@ int gbe_free_subs(gbe_subs* X);
 /* Enqueue one density-matrix build on the stream without synchronising:
  * Gershgorin bounds of H (FP64, a4), gather + scale of every x[s] (a4), and the SP2
  * loop (a5 squarings, a6 global FP64 trace + branch, a7 branch apply in the squaring
- * epilogue), with convergence decided on the device.  `H` must be device CSR. */
+ * epilogue), with convergence decided on the device.  `H` must be device CSR.
+ * GBE_ECAPACITY (before any launch) when a subgraph has more than 2432 vertices: the
+ * gather stages whole dense rows and an index hash table in one CTA's 227 KB of shared
+ * memory (the same bound applies to gbe_foe_run). */
 int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* params,
                 gbe_subs* X);
 /* Synchronise and read the report of the last run on X. */

@@ -919,6 +919,18 @@ static GatherLayout gather_layout(const gbe_subs* X) {
     return L;
 }
 
+// The gather stages whole dense rows and the subgraph's index hash table in shared memory:
+// subgraphs up to 2432 vertices fit the 227 KB of a GB300 CTA.
+static int check_gather_fits(const gbe_ctx* ctx, const gbe_subs* X) {
+    const GatherLayout L = gather_layout(X);
+    if ((int64_t)L.smem > (int64_t)ctx->smem_optin) {
+        gbe_set_error("a subgraph of %lld vertices needs %zu bytes of gather shared memory, the device allows %d",
+                      (long long)X->parts->max_m, L.smem, ctx->smem_optin);
+        return GBE_ECAPACITY;
+    }
+    return GBE_OK;
+}
+
 // Control init, spectral bounds, gather and the first decision of a run (on ctx->stream).
 static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, gbe_subs* X) {
     cudaStream_t st = ctx->stream;
@@ -1060,6 +1072,7 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     if (in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len) memcpy(in.seq_in, prm->seq_in, in.seq_len);
     if (in.prec != GBE_PREC_FP64 && in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len <= in.fp64_tail) in.mode = 1;
     const bool fp64_steps = X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0;
+    GBE_TRY(check_gather_fits(ctx, X));
     // kernel attributes are set outside any capture
     {
         const GatherLayout L = gather_layout(X);
@@ -1372,6 +1385,7 @@ extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     in.eps_min = emin;
     in.eps_max = emax;
     in.out_scale = B;
+    GBE_TRY(check_gather_fits(ctx, X));
     const GatherLayout L = gather_layout(X);
     auto gk = fp64 ? gather_kernel<GBE_PREC_FP64> : gather_kernel<GBE_PREC_FP16X6>;
     GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));

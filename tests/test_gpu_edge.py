@@ -1,0 +1,75 @@
+"""Degenerate and out-of-range inputs of the SP2 path, through the C ABI.
+
+- Partitions that cannot be imported (no subgraph, an empty subgraph, no core vertex, an
+  index outside H) are rejected on the host with GBE_EINVAL, before any device work.
+- Singleton subgraphs (m_s = 1, every vertex its own core and no halo): the graph SP2
+  reduces to the scalar recursion on each diagonal entry of X0, compared with the oracle.
+- A subgraph larger than the gather's shared memory holds (2433 vertices) is rejected with
+  GBE_ECAPACITY before any kernel runs, and the context stays usable.
+"""
+import numpy as np
+import pytest
+
+from oracle import sp2
+
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_helpers import assembled_dense, device_csr, gbe, import_parts, lattice_case, oracle_graph_sp2  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return gbe.Context(0)
+
+
+def test_bad_partitions_rejected(ctx):
+    lib = gbe.load_library()
+    import ctypes
+    def imp(n, cc, sp, si):
+        cc = np.asarray(cc, np.int32); sp = np.asarray(sp, np.int64); si = np.asarray(si if len(si) else [0], np.int32)
+        h = ctypes.c_void_p()
+        return lib.gbe_parts_import(ctx.handle, n, len(cc), gbe._ptr(cc), gbe._ptr(sp), gbe._ptr(si), ctypes.byref(h))
+    assert imp(4, [], [0], []) == gbe.GBE_EINVAL                 # no subgraph
+    assert imp(0, [1], [0, 1], [0]) == gbe.GBE_EINVAL            # no vertex
+    assert imp(4, [1, 1], [0, 2, 2], [0, 1]) == gbe.GBE_EINVAL   # empty subgraph
+    assert imp(4, [0], [0, 2], [0, 1]) == gbe.GBE_EINVAL         # no core vertex
+    assert imp(4, [3], [0, 2], [0, 1]) == gbe.GBE_EINVAL         # more cores than vertices
+    assert imp(4, [1], [0, 2], [0, 4]) == gbe.GBE_EINVAL         # index outside H
+    assert imp(4, [1], [0, 2], [-1, 0]) == gbe.GBE_EINVAL
+
+
+@pytest.mark.parametrize("prec,tol", [(gbe.PREC_FP64, 1e-12), (gbe.PREC_FP16X6, 1e-6), (gbe.PREC_BF16X3, 2e-4)])
+def test_singleton_subgraphs(ctx, prec, tol):
+    w, H, _, _, _ = lattice_case(6, seed=2)
+    N = H.shape[0]
+    subs = [np.array([i]) for i in range(N)]
+    nc = np.ones(N, dtype=np.int32)
+    _, logd = sp2.sp2_dense(H, N // 2)
+    seq = logd.seq[:12]
+    Dref, _, _ = oracle_graph_sp2(H, subs, nc, seq=seq)
+    parts = import_parts(ctx, N, subs, nc)
+    X, rep = gbe.sp2_submatrices(ctx, device_csr(H), parts, gbe.sp2_params(N // 2, prec=prec, seq=seq))
+    assert rep["iters"] == len(seq)
+    D, col, _ = assembled_dense(ctx, X, parts, N)
+    assert col.shape[1] == 1 and np.array_equal(col[:, 0], np.arange(N))
+    assert np.count_nonzero(D - np.diag(np.diag(D))) == 0
+    assert np.abs(D - Dref).max() <= tol
+
+
+def test_oversized_subgraph_rejected(ctx):
+    w, H, _, _, _ = lattice_case(16, seed=0, thr=0.15)
+    N = H.shape[0]
+    big = np.arange(2433)
+    subs = [big] + [np.array([i]) for i in range(2433, N)]
+    nc = np.array([2433] + [1] * (N - 2433), dtype=np.int32)
+    parts = import_parts(ctx, N, subs, nc)
+    Hd = device_csr(H)
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP64, n_max=4))
+    assert e.value.code == gbe.GBE_ECAPACITY
+    # the context still works: a partition at the bound runs
+    ok = [np.arange(2432)] + [np.array([i]) for i in range(2432, N)]
+    nc2 = np.array([2432] + [1] * (N - 2432), dtype=np.int32)
+    parts2 = import_parts(ctx, N, ok, nc2)
+    X, rep = gbe.sp2_submatrices(ctx, Hd, parts2, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=[1, 0]))
+    assert rep["iters"] == 2 and rep["status"] == 0
