@@ -126,6 +126,21 @@ struct HModel {
 };
 
 constexpr int kRowCap = 1024;
+constexpr int kStageCap = 128;   // staging slot per row of the single-pass H build
+
+// Staged rows (kStageCap apart) -> CSR.
+__global__ void compact_rows_kernel(const int32_t* __restrict__ scol, const double* __restrict__ sval, int64_t n,
+                                    const int64_t* __restrict__ rowptr, int32_t* col, double* val) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / kStageCap;
+    const int k = (int)(t % kStageCap);
+    if (i >= n) return;
+    const int64_t b = rowptr[i];
+    if (k < rowptr[i + 1] - b) {
+        col[b + k] = scol[i * kStageCap + k];
+        val[b + k] = sval[i * kStageCap + k];
+    }
+}
 
 // One warp per row.  pass 0: count neighbours; pass 1: write sorted (col, val).
 __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ pos, const float4* __restrict__ pos4,
@@ -181,6 +196,15 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
         if (lane == 0) cnt[i] = m;
         return;
     }
+    if (pass == 2) {
+        // single-pass build: the sorted row goes to a staging slot of kStageCap entries (a
+        // longer row sets the staging flag, overflow[1], and the host runs the fill pass instead)
+        if (lane == 0) cnt[i] = m;
+        if (m > kStageCap) {
+            if (lane == 0) atomicExch(overflow + 1, 1);
+            return;
+        }
+    }
     // sort the row's columns (odd-even transposition within the warp)
     for (int phase = 0; phase < m; ++phase) {
         for (int t = 2 * lane + (phase & 1); t + 1 < m; t += 64) {
@@ -189,7 +213,7 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
         }
         __syncwarp();
     }
-    const int64_t base = rowptr[i];
+    const int64_t base = pass == 2 ? i * kStageCap : rowptr[i];
     for (int t = lane; t < m; t += 32) {
         const int j = buf[w][t];
         double v;
@@ -491,10 +515,10 @@ extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gb
     GBE_TRY(gbe_alloc(&cur.p, ncells * 4));
     GBE_TRY(gbe_alloc(&mem.p, n * 4));
     GBE_TRY(gbe_alloc(&cnt.p, n * 4));
-    GBE_TRY(gbe_alloc(&flag.p, 4));
+    GBE_TRY(gbe_alloc(&flag.p, 8));   // [0] a row above kRowCap, [1] a row above kStageCap
     GBE_CUDA_TRY(cudaMemsetAsync(ccnt.p, 0, ncells * 4, s));
     GBE_CUDA_TRY(cudaMemsetAsync(cur.p, 0, ncells * 4, s));
-    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 4, s));
+    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 8, s));
     const unsigned nb = (unsigned)((n + 255) / 256);
     cell_count_kernel<<<nb, 256, 0, s>>>(pos, n, g, cell.as<int32_t>(), ccnt.as<int32_t>());
     GBE_TRY(scan_exclusive(ctx, ccnt.as<int32_t>(), cstart.as<int64_t>(), ncells, nullptr));
@@ -505,25 +529,40 @@ extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gb
     pos_f32_kernel<<<nb, 256, 0, s>>>(pos, n, p4.as<float4>());
     const float lim2 = filter_lim2(model->rcut, st->box);
     const unsigned rb = (unsigned)((n + 7) / 8);
-    hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 0,
+    // one neighbour search: sorted rows into staging slots, then a compaction; a row longer
+    // than a slot falls back to a second search that writes the CSR directly
+    DevBuf scol, sval;
+    GBE_TRY(gbe_alloc(&scol.p, n * kStageCap * 4));
+    GBE_TRY(gbe_alloc(&sval.p, n * kStageCap * 8));
+    hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 2,
                                      cnt.as<int32_t>(),
-                                     nullptr, nullptr, nullptr, flag.as<int>());
+                                     nullptr, scol.as<int32_t>(), sval.as<double>(), flag.as<int>());
     GBE_CUDA_TRY(cudaGetLastError());
     gbe_hamiltonian* H = new gbe_hamiltonian();
     H->n = n;
     int r = gbe_alloc((void**)&H->rowptr, (n + 1) * 8);
     int64_t nnz = 0;
     if (r == GBE_OK) r = scan_exclusive(ctx, cnt.as<int32_t>(), H->rowptr, n, &nnz);
-    int ovf = 0;
-    if (r == GBE_OK) r = read_flag(ctx, flag.as<int>(), &ovf);
-    if (r == GBE_OK && ovf) { gbe_set_error("a row of H has more than %d neighbours", kRowCap); r = GBE_ECAPACITY; }
+    int ovf[2] = {0, 0};
+    if (r == GBE_OK) {
+        cudaError_t fe = cudaMemcpyAsync(ovf, flag.p, 8, cudaMemcpyDeviceToHost, s);
+        if (fe == cudaSuccess) fe = cudaStreamSynchronize(s);
+        if (fe != cudaSuccess) {
+            gbe_set_error("hbuild: reading the overflow flags: %s", cudaGetErrorString(fe));
+            r = GBE_ECUDA;
+        }
+    }
+    if (r == GBE_OK && ovf[0]) { gbe_set_error("a row of H has more than %d neighbours", kRowCap); r = GBE_ECAPACITY; }
     if (r == GBE_OK) r = gbe_alloc((void**)&H->col, nnz * 4);
     if (r == GBE_OK) r = gbe_alloc((void**)&H->val, nnz * 8);
     if (r != GBE_OK) { gbe_free_hamiltonian(H); return r; }
     H->nnz = nnz;
-    hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 1,
-                                     cnt.as<int32_t>(),
-                                     H->rowptr, H->col, H->val, flag.as<int>());
+    if (!ovf[1])
+        compact_rows_kernel<<<(unsigned)((n * kStageCap + 255) / 256), 256, 0, s>>>(
+            scol.as<int32_t>(), sval.as<double>(), n, H->rowptr, H->col, H->val);
+    else
+        hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cstart.as<int64_t>(), mem.as<int32_t>(), mdl,
+                                         1, cnt.as<int32_t>(), H->rowptr, H->col, H->val, flag.as<int>());
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

@@ -702,6 +702,16 @@ extern "C" int gbe_free_subs(gbe_subs* X) {
     return GBE_OK;
 }
 
+// FP64 iterates of both ping-pong sides, allocated (and cleared) on first use.
+static int ensure_f64(gbe_subs* X, cudaStream_t st) {
+    for (int i = 0; i < 2; ++i)
+        if (!X->f64[i]) {
+            GBE_TRY(gbe_alloc((void**)&X->f64[i], X->total_elems * 8));
+            GBE_CUDA_TRY(cudaMemsetAsync(X->f64[i], 0, X->total_elems * 8, st));
+        }
+    return GBE_OK;
+}
+
 static void make_items(const std::vector<int32_t>& dim, const std::vector<int32_t>& cost, int tile,
                        std::vector<TileItem>& items, bool full = false) {
     items.clear();
@@ -766,7 +776,8 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     X->n_items_64_full = (int)ft_64.size();
     X->max_units = (int)std::max<int64_t>(X->P, std::max(X->n_items_tc_full, X->n_items_64_full));
     int r = GBE_OK;
-#define ALLOC(ptr, bytes) if (r == GBE_OK) r = gbe_alloc((void**)&(ptr), (bytes))
+#define ALLOC(ptr, bytes) \
+    do { if (r == GBE_OK) r = gbe_alloc((void**)&(ptr), (bytes)); } while (0)
     ALLOC(X->d_off, X->P * 8);
     ALLOC(X->d_mpad, X->P * 4);
     ALLOC(X->d_m, X->P * 4);
@@ -777,10 +788,16 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     ALLOC(X->d_items_64_full, std::max<int64_t>(1, X->n_items_64_full) * sizeof(TileItem));
     ALLOC(X->d_partials, 2 * (int64_t)X->max_units * 8);
     ALLOC(X->d_ctrl, sizeof(Sp2Ctrl));
+    // FP64 iterates exist from the start only in FP64 states; mixed states allocate them when
+    // a run first needs FP64 steps (ensure_f64)
     for (int i = 0; i < 2; ++i) {
-        ALLOC(X->f64[i], total * 8);
-        if (prec != GBE_PREC_FP64) ALLOC(X->planes[i], 4 * total * 2);
+        if (prec == GBE_PREC_FP64) {
+            ALLOC(X->f64[i], total * 8);
+        } else {
+            ALLOC(X->planes[i], 4 * total * 2);
+        }
     }
+    if (r == GBE_OK && prec != GBE_PREC_FP64 && !(X->planes[0] && X->planes[1])) r = GBE_ENOMEM;
 #undef ALLOC
     if (r != GBE_OK) { gbe_free_subs(X); return r; }
     if (cudaMallocHost((void**)&X->h_ctrl, sizeof(Sp2Ctrl)) != cudaSuccess) {
@@ -800,10 +817,11 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
         cudaMemcpyAsync(X->d_items_tc_full, ft_tc.data(), ft_tc.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
     if (X->n_items_64_full)
         cudaMemcpyAsync(X->d_items_64_full, ft_64.data(), ft_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
-    for (int i = 0; i < 2; ++i) {
-        cudaMemsetAsync(X->f64[i], 0, total * 8, st);
-        if (X->planes[i]) cudaMemsetAsync(X->planes[i], 0, 4 * total * 2, st);
-    }
+    // The split planes need no clearing: the gather writes every stored (upper) block of side 0,
+    // padding included, and each squaring writes every stored block of the side it produces
+    // before any launch reads it.
+    for (int i = 0; i < 2; ++i)
+        if (X->f64[i]) cudaMemsetAsync(X->f64[i], 0, total * 8, st);
     GBE_CUDA_TRY(cudaStreamSynchronize(st));
     if (prec != GBE_PREC_FP64) {
         r = gbe_tc_make_tmaps(X);
@@ -1073,6 +1091,7 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     if (in.prec != GBE_PREC_FP64 && in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len <= in.fp64_tail) in.mode = 1;
     const bool fp64_steps = X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0;
     GBE_TRY(check_gather_fits(ctx, X));
+    if (fp64_steps) GBE_TRY(ensure_f64(X, st));
     // kernel attributes are set outside any capture
     {
         const GatherLayout L = gather_layout(X);
@@ -1344,6 +1363,7 @@ extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const bool fp64 = X->prec == GBE_PREC_FP64;
+    if (fp64) GBE_TRY(ensure_f64(X, st));
     // the fixed x lives on side 2
     if (fp64 && !X->f64[2]) GBE_TRY(gbe_alloc((void**)&X->f64[2], X->total_elems * 8));
     if (!fp64 && !X->planes[2]) {

@@ -46,13 +46,22 @@ def compare_h(Hg, Ho, pos, box, rcut=2.5):
     np.testing.assert_allclose(dg[both], do[both], rtol=1e-14, atol=0)
 
 
-@pytest.mark.parametrize("kind", ["lattice", "disordered"])
+@pytest.mark.parametrize("kind", ["lattice", "disordered", "dense"])
 def test_hamiltonian_parity(ctx, kind):
-    w = synth.lattice(8, seed=2) if kind == "lattice" else synth.disordered(1500, seed=7)
+    """"dense": density 3/a^3, ~196 neighbours per row, longer than the single-pass build's
+    128-entry staging rows, so the build takes its second neighbour search."""
+    if kind == "lattice":
+        w = synth.lattice(8, seed=2)
+    elif kind == "disordered":
+        w = synth.disordered(1500, seed=7)
+    else:
+        w = synth.disordered(2000, density=3.0, seed=8)
     st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
     Hg = h_to_scipy(gbe.build_hamiltonian(ctx, st))
     Ho = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
     compare_h(Hg, Ho, w["pos"], w["box"])
+    rowlen = np.diff(Hg.indptr)
+    assert (rowlen.max() > 128) == (kind == "dense"), rowlen.max()
     # rows sorted, diagonal present
     assert all(np.all(np.diff(Hg.indices[Hg.indptr[i]:Hg.indptr[i + 1]]) > 0) for i in range(0, Hg.shape[0], 97))
     np.testing.assert_array_equal(Hg.diagonal(), w["onsite"])
