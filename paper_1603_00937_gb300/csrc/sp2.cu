@@ -542,16 +542,17 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
                                                        const uint16_t* planes0, const uint16_t* planes1,
                                                        int64_t plane_stride, const double* f0, const double* f1,
                                                        int64_t width, int32_t* ell_col, double* ell_val,
-                                                       double drop_tol) {
-    const int s = blockIdx.x;
+                                                       double drop_tol, int jblocks) {
+    // jblocks CTAs per subgraph, one core column (ELL row) per warp
+    const int s = blockIdx.x / jblocks, j = (blockIdx.x % jblocks) * 8 + (threadIdx.x >> 5);
     const int m = g.m[s], c = g.c[s], mpad = g.mpad[s];
     const int64_t off = g.off[s], base = sub_ptr[s];
     const int cur = ctrl->cur, fmt = ctrl->fmt, prec = ctrl->prec;
     const double scale = ctrl->out_scale;
     const uint16_t* pl = cur ? planes1 : planes0;
     const double* f = cur ? f1 : f0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = warp; j < c; j += 8) {
+    const int lane = threadIdx.x & 31;
+    if (j < c) {
         const int64_t row = sub_idx[base + j];
         int32_t* oc = ell_col + row * width;
         double* ov = ell_val + row * width;
@@ -1267,9 +1268,12 @@ extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* 
     }
     // rows outside every core keep the empty entry (the assembly pads the rows it writes)
     if (!parts->cores_cover) fill_ell_kernel<<<ctx->sm_count * 4, 256, 0, st>>>(total, col, val);
-    assemble_kernel<<<(unsigned)X->P, 256, 0, st>>>(X->d_ctrl, parts->d_sub_ptr, parts->d_sub_idx, geom_of(X),
-                                                      X->planes[0], X->planes[1], X->total_elems, X->f64[0],
-                                                      X->f64[1], D->width, col, val, drop_tol);
+    int max_c = 1;
+    for (int64_t q = 0; q < X->P; ++q) max_c = std::max(max_c, X->h_c[q]);
+    const int jblocks = (max_c + 7) / 8;
+    assemble_kernel<<<(unsigned)(X->P * jblocks), 256, 0, st>>>(X->d_ctrl, parts->d_sub_ptr, parts->d_sub_idx, geom_of(X),
+                                                                 X->planes[0], X->planes[1], X->total_elems, X->f64[0],
+                                                                 X->f64[1], D->width, col, val, drop_tol, jblocks);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && staged) {
         e = cudaMemcpyAsync(D->col, col, total * 4, cudaMemcpyDeviceToHost, st);
