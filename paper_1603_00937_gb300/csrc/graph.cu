@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(256) rowset_kernel(int mode, int64_t n, const 
                                                      const int32_t* __restrict__ s1ci, const int64_t* __restrict__ s2rp,
                                                      const int32_t* __restrict__ s2ci, const int64_t* __restrict__ s3rp,
                                                      const int32_t* __restrict__ s3ci, int hops, int pass, int32_t* cnt,
-                                                     const int64_t* __restrict__ outrp, int32_t* outci, int* overflow) {
+                                                     const int64_t* __restrict__ outrp, int32_t* outci, int* overflow,
+                                                     int stage_cap) {
     extern __shared__ unsigned char smraw[];
     RowSetSmem& S = *reinterpret_cast<RowSetSmem*>(smraw);
     for (int64_t row = blockIdx.x; row < n; row += gridDim.x) {
@@ -316,12 +317,32 @@ __global__ void __launch_bounds__(256) rowset_kernel(int mode, int64_t n, const 
         }
         if (pass == 0) {
             if (threadIdx.x == 0) cnt[i] = m;
+        } else if (pass == 2) {
+            // single-pass build: the sorted row goes to a staging slot of stage_cap entries (a
+            // longer row sets overflow[1], and the host runs the fill pass instead)
+            if (threadIdx.x == 0) {
+                cnt[i] = m;
+                if (m > stage_cap) atomicExch(overflow + 1, 1);
+            }
+            if (m <= stage_cap) {
+                const int64_t base = (int64_t)i * stage_cap;
+                for (int t = threadIdx.x; t < m; t += blockDim.x) outci[base + t] = S.list[t];
+            }
         } else {
             const int64_t base = outrp[i];
             for (int t = threadIdx.x; t < m; t += blockDim.x) outci[base + t] = S.list[t];
         }
         __syncthreads();
     }
+}
+
+// Staged rows (stage_cap apart) -> CSR column indices, one warp per row.
+__global__ void compact_set_rows_kernel(const int32_t* __restrict__ stage, int64_t n, int stage_cap,
+                                        const int64_t* __restrict__ rp, int32_t* ci) {
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int64_t b = rp[i], m = rp[i + 1] - b;
+    for (int64_t t = threadIdx.x & 31; t < m; t += 32) ci[b + t] = stage[i * stage_cap + t];
 }
 
 // ELL D -> pattern of kept entries (|D_ki| >= tau) as CSR by ELL row (row i lists k),
@@ -445,10 +466,14 @@ size_t rowset_smem() { return sizeof(RowSetSmem); }
 int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thresh, const int64_t* s1rp,
                const int32_t* s1ci, const int64_t* s2rp, const int32_t* s2ci, const int64_t* s3rp, const int32_t* s3ci,
                int hops, int64_t** rp_out, int32_t** ci_out, int64_t* nnz_out) {
-    DevBuf cnt, flag;
+    DevBuf cnt, flag, stage;
     GBE_TRY(gbe_alloc(&cnt.p, n * 4));
-    GBE_TRY(gbe_alloc(&flag.p, 4));
-    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 4, ctx->stream));
+    GBE_TRY(gbe_alloc(&flag.p, 8));   // [0] a row above kSetMax, [1] a row above the staging slot
+    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 8, ctx->stream));
+    // one set construction per row into staging slots (at most 64 Mi entries in all), then a
+    // compaction; a row longer than its slot falls back to a second construction pass
+    const int stage_cap = (int)std::min<int64_t>(kSetMax, std::max<int64_t>(128, ((int64_t)64 << 20) / n));
+    GBE_TRY(gbe_alloc(&stage.p, n * stage_cap * 4));
     const size_t sm = rowset_smem();
     cudaFuncSetAttribute(rowset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     const int grid = (int)std::min<int64_t>(n, (int64_t)ctx->sm_count * 3);
@@ -456,23 +481,35 @@ int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thres
     const int32_t* hci = H ? H->col : nullptr;
     const double* hva = H ? H->val : nullptr;
     rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp, s3ci,
-                                                  hops, 0, cnt.as<int32_t>(), nullptr, nullptr, flag.as<int>());
+                                                  hops, 2, cnt.as<int32_t>(), nullptr, stage.as<int32_t>(), flag.as<int>(),
+                                                  stage_cap);
     GBE_CUDA_TRY(cudaGetLastError());
     int64_t* rp = nullptr;
     GBE_TRY(gbe_alloc((void**)&rp, (n + 1) * 8));
     int64_t nnz = 0;
     int r = scan_exclusive(ctx, cnt.as<int32_t>(), rp, n, &nnz);
-    int ovf = 0;
-    if (r == GBE_OK) r = read_flag(ctx, flag.as<int>(), &ovf);
-    if (r == GBE_OK && ovf) {
+    int ovf[2] = {0, 0};
+    if (r == GBE_OK) {
+        cudaError_t fe = cudaMemcpyAsync(ovf, flag.p, 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (fe == cudaSuccess) fe = cudaStreamSynchronize(ctx->stream);
+        if (fe != cudaSuccess) {
+            gbe_set_error("rowset: reading the overflow flags: %s", cudaGetErrorString(fe));
+            r = GBE_ECUDA;
+        }
+    }
+    if (r == GBE_OK && ovf[0]) {
         gbe_set_error("graph row exceeds %d entries", kSetMax);
         r = GBE_ECAPACITY;
     }
     int32_t* ci = nullptr;
     if (r == GBE_OK) r = gbe_alloc((void**)&ci, std::max<int64_t>(nnz, 1) * 4);
     if (r != GBE_OK) { gbe_free(rp); return r; }
-    rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp, s3ci,
-                                                  hops, 1, cnt.as<int32_t>(), rp, ci, flag.as<int>());
+    if (!ovf[1])
+        compact_set_rows_kernel<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(stage.as<int32_t>(), n, stage_cap, rp,
+                                                                                ci);
+    else
+        rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp,
+                                                      s3ci, hops, 1, cnt.as<int32_t>(), rp, ci, flag.as<int>(), stage_cap);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
