@@ -108,15 +108,80 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
             if (v == j) { hij = hva[mid]; break; }
             if (v < j) a = mid + 1; else b = mid - 1;
         }
-        const double h2 = row_dot(hrp, hci, hva, (int)i, j);
         const double ej = onsite[j];
         float* f = feat + (base + t) * kNF;
         f[0] = -log10f(fmaxf((float)fabs(hij), 1e-12f)) / 12.0f;
-        f[1] = -log10f(fmaxf((float)fabs(h2), 1e-12f)) / 12.0f;
+        // f[1], the (H^2)_ij feature, is written by h2_feature_kernel
         f[2] = (float)(r / rcand);
         f[3] = (float)fmin(ei, ej);
         f[4] = (float)fmax(ei, ej);
         pj[base + t] = j;
+    }
+}
+
+// Row i of H^2 for every site i, then the (H^2)_ij feature of its candidate pairs.  One warp
+// per site accumulates (H^2)_il = sum_k H_ik H_kl in a shared-memory hash table keyed by l,
+// taking k in ascending order (one row k at a time, its entries across the lanes): every
+// (H^2)_ij is then the same sequence of products and additions as the ordered merge of rows
+// i and j (H is symmetric to the last bit), so the feature is symmetric in (i, j) bit for
+// bit.  A row of H^2 with more entries than the table holds is computed by that merge.
+constexpr int kH2Slots = 1024;   // hash slots per warp (a row of H^2 within 5a has ~520 entries)
+constexpr int kH2Warps = 4;
+constexpr size_t kH2Smem = (size_t)kH2Warps * kH2Slots * (4 + 8);
+
+__device__ __forceinline__ unsigned h2_hash(int l) { return ((unsigned)l * 2654435761u) >> 22; }   // 10 bits
+
+__global__ void __launch_bounds__(32 * kH2Warps) h2_feature_kernel(int64_t n, const int64_t* __restrict__ hrp,
+                                                                    const int32_t* __restrict__ hci,
+                                                                    const double* __restrict__ hva,
+                                                                    const int64_t* __restrict__ prp,
+                                                                    const int32_t* __restrict__ pj, float* feat) {
+    extern __shared__ unsigned char h2sm[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * kH2Warps + w;
+    if (i >= n) return;
+    int* keys = reinterpret_cast<int*>(h2sm) + w * kH2Slots;
+    double* vals = reinterpret_cast<double*>(h2sm + (size_t)kH2Warps * kH2Slots * 4) + w * kH2Slots;
+    for (int t = lane; t < kH2Slots; t += 32) {
+        keys[t] = -1;
+        vals[t] = 0.0;
+    }
+    __syncwarp();
+    bool ok = true;
+    for (int64_t p = hrp[i]; p < hrp[i + 1]; ++p) {
+        const int k = hci[p];
+        const double hik = hva[p];
+        for (int64_t q = hrp[k] + lane; q < hrp[k + 1]; q += 32) {
+            const int l = hci[q];
+            unsigned h = h2_hash(l);
+            int probes = 0;
+            while (true) {
+                const int old = atomicCAS(&keys[h], -1, l);
+                if (old == -1 || old == l) break;
+                if (++probes == kH2Slots) break;
+                h = (h + 1) & (kH2Slots - 1);
+            }
+            if (probes < kH2Slots) vals[h] = __dadd_rn(vals[h], __dmul_rn(hik, hva[q]));   // one lane per key
+            else ok = false;
+        }
+        __syncwarp();
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    for (int64_t t = prp[i] + lane; t < prp[i + 1]; t += 32) {
+        const int j = pj[t];
+        double h2 = 0.0;
+        if (ok) {
+            unsigned h = h2_hash(j);
+            for (int probes = 0; probes < kH2Slots; ++probes) {
+                const int key = keys[h];
+                if (key == j) { h2 = vals[h]; break; }
+                if (key == -1) break;
+                h = (h + 1) & (kH2Slots - 1);
+            }
+        } else {
+            h2 = row_dot(hrp, hci, hva, (int)i, j);
+        }
+        feat[t * kNF + 1] = -log10f(fmaxf((float)fabs(h2), 1e-12f)) / 12.0f;
     }
 }
 
@@ -447,6 +512,13 @@ extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr*
                                     cnt.as<int32_t>(),
                                     P->rowptr, P->j, P->feat, rp, ci, va, flag.as<int>());
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(h2_feature_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kH2Smem);
+    if (e == cudaSuccess) {
+        h2_feature_kernel<<<(unsigned)((n + kH2Warps - 1) / kH2Warps), 32 * kH2Warps, kH2Smem, s>>>(n, rp, ci, va, P->rowptr,
+                                                                                                   P->j, P->feat);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         gbe_free_pairs(P);

@@ -70,12 +70,14 @@ def dis(ctx):
     return dict(w=w, H=H, st=st, Hg=Hg, P=P, I=I, J=J, R=R, F=F)
 
 
-@pytest.mark.parametrize("kind", ["lattice", "disordered"])
+@pytest.mark.parametrize("kind", ["lattice", "disordered", "dense"])
 def test_pairs_and_features(ctx, kind, dis):
+    """"dense": density 3/a^3, whose rows of H^2 (~1600 sites within 5a) overflow the
+    per-warp hash table of the (H^2)_ij feature, so those sites take the ordered row merge."""
     if kind == "disordered":
         w, H, P, I, J, F = dis["w"], dis["H"], dis["P"], dis["I"], dis["J"], dis["F"]
     else:
-        w = synth.lattice(10, seed=5)
+        w = synth.lattice(10, seed=5) if kind == "lattice" else synth.disordered(2000, density=3.0, seed=8)
         H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
         st, Hg = gpu_system(ctx, w)
         P = gbe.pairs_build(ctx, st, Hg.csr(), RCAND)
@@ -88,6 +90,10 @@ def test_pairs_and_features(ctx, kind, dis):
     np.testing.assert_allclose(fg[:, 0], F[:, 0], rtol=0, atol=2e-7)
     np.testing.assert_allclose(fg[:, 1], F[:, 1], rtol=0, atol=2e-7)
     np.testing.assert_allclose(fg[:, 2:], F[:, 2:], rtol=1.2e-7, atol=0)
+    # every feature is symmetric in (i, j) bit for bit
+    key = I.astype(np.int64) * N + J
+    back = np.searchsorted(key, J.astype(np.int64) * N + I)
+    np.testing.assert_array_equal(fg, fg[back])
 
 
 def test_forward_matches_oracle(ctx, dis):
