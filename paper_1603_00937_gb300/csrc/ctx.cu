@@ -38,7 +38,18 @@ namespace {
 thread_local cudaStream_t t_stream = nullptr;
 thread_local cudaMemPool_t t_pool = nullptr;
 std::mutex g_alloc_mu;
-std::unordered_map<void*, cudaStream_t> g_pooled;   // pool allocation -> stream it was made on
+struct PooledBlock {
+    cudaStream_t stream;   // stream the block was allocated on (and is freed on)
+    cudaMemPool_t pool;
+};
+std::unordered_map<void*, PooledBlock> g_pooled;
+// Live blocks per pool, and whether the pool's context was destroyed: a pool outlives its
+// context until its last block is freed (objects may be released after their context).
+struct PoolState {
+    int64_t live = 0;
+    bool closed = false;
+};
+std::unordered_map<cudaMemPool_t, PoolState> g_pools;
 }  // namespace
 
 AllocScope::AllocScope(const gbe_ctx* ctx) : prev_stream(t_stream), prev_pool(t_pool) {
@@ -66,26 +77,57 @@ int gbe_alloc(void** p, size_t bytes) {
     }
     if (pooled) {
         std::lock_guard<std::mutex> lock(g_alloc_mu);
-        g_pooled[*p] = t_stream;
+        g_pooled[*p] = PooledBlock{t_stream, t_pool};
+        g_pools[t_pool].live += 1;
     }
     return GBE_OK;
 }
 
 void gbe_free(void* p) {
     if (!p) return;
-    bool pooled = false;
-    cudaStream_t s = nullptr;
+    bool pooled = false, destroy = false;
+    PooledBlock b{nullptr, nullptr};
     {
         std::lock_guard<std::mutex> lock(g_alloc_mu);
         auto it = g_pooled.find(p);
         if (it != g_pooled.end()) {
             pooled = true;
-            s = it->second;
+            b = it->second;
             g_pooled.erase(it);
+            PoolState& ps = g_pools[b.pool];
+            ps.live -= 1;
+            if (ps.live == 0 && ps.closed) {
+                destroy = true;
+                g_pools.erase(b.pool);
+            }
         }
     }
-    if (pooled) cudaFreeAsync(p, s);
-    else cudaFree(p);
+    if (!pooled) {
+        cudaFree(p);
+        return;
+    }
+    cudaFreeAsync(p, b.stream);
+    if (destroy) {   // the last block of a destroyed context's pool
+        cudaStreamSynchronize(b.stream);
+        cudaMemPoolDestroy(b.pool);
+    }
+}
+
+// Destroy a context's pool now, or, while blocks of it are still held by live objects,
+// when the last of them is freed.
+static void release_pool(cudaMemPool_t pool) {
+    bool now = false;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        auto it = g_pools.find(pool);
+        if (it == g_pools.end() || it->second.live == 0) {
+            now = true;
+            if (it != g_pools.end()) g_pools.erase(it);
+        } else {
+            it->second.closed = true;
+        }
+    }
+    if (now) cudaMemPoolDestroy(pool);
 }
 
 int gbe_sync(gbe_ctx* ctx) {
@@ -129,11 +171,11 @@ extern "C" int gbe_create(gbe_ctx** out, int device, void* cuda_stream) {
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
     AllocScope scope(c);
     int r = gbe_alloc(&c->d_scratch, 4096);
-    if (r != GBE_OK) { cudaMemPoolDestroy(c->pool); delete c; return r; }
+    if (r != GBE_OK) { release_pool(c->pool); delete c; return r; }
     if (cudaMallocHost(&c->h_scratch, 4096) != cudaSuccess) {
         gbe_free(c->d_scratch);
         cudaStreamSynchronize(c->stream);
-        cudaMemPoolDestroy(c->pool);
+        release_pool(c->pool);
         delete c;
         gbe_set_error("cudaMallocHost failed");
         return GBE_ENOMEM;
@@ -143,7 +185,7 @@ extern "C" int gbe_create(gbe_ctx** out, int device, void* cuda_stream) {
         gbe_free(c->d_scratch);
         cudaStreamSynchronize(c->stream);
         cudaFreeHost(c->h_scratch);
-        cudaMemPoolDestroy(c->pool);
+        release_pool(c->pool);
         delete c;
         return r;
     }
@@ -158,7 +200,7 @@ extern "C" int gbe_destroy(gbe_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     cudaFreeHost(ctx->h_scratch);
     // blocks still held by live objects keep the pool alive until they are freed
-    cudaMemPoolDestroy(ctx->pool);
+    release_pool(ctx->pool);
     delete ctx;
     return GBE_OK;
 }

@@ -73,3 +73,25 @@ def test_oversized_subgraph_rejected(ctx):
     parts2 = import_parts(ctx, N, ok, nc2)
     X, rep = gbe.sp2_submatrices(ctx, Hd, parts2, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=[1, 0]))
     assert rep["iters"] == 2 and rep["status"] == 0
+
+
+def test_objects_outliving_their_context():
+    """A context destroyed while its objects still hold device memory (as when Python's
+    cycle collector finalises them in any order): the objects are freed afterwards without
+    error, and a new context works."""
+    w, H, _, subs, nc = lattice_case(6, seed=1, thr=1e-3, ncell=(3, 3, 3))
+    N = H.shape[0]
+    c1 = gbe.Context(0)
+    parts = import_parts(c1, N, subs, nc)
+    X, rep = gbe.sp2_submatrices(c1, device_csr(H), parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=[1, 0, 1]))
+    assert rep["iters"] == 3
+    c1.close()
+    X.close()
+    parts.close()
+    c2 = gbe.Context(0)
+    parts2 = import_parts(c2, N, subs, nc)
+    X2, rep2 = gbe.sp2_submatrices(c2, device_csr(H), parts2, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=[1, 0, 1]))
+    assert rep2["iters"] == 3 and rep2["t1"] == rep["t1"]
+    X2.close()
+    parts2.close()
+    c2.close()
