@@ -254,7 +254,10 @@ typedef struct {
 int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, gbe_subs** X);
 int gbe_free_subs(gbe_subs* X);
 
-/* Enqueue one density-matrix build on the stream without synchronising:
+/* Enqueue one density-matrix build on the stream without synchronising.  With graph launch
+ * on (gbe_set_graph_launch, the default) a state's second run with the same inputs and
+ * parameters captures the run as two CUDA graphs and later such runs relaunch them; a first
+ * run, or a run after a change, is launched kernel by kernel.  The build:
  * Gershgorin bounds of H (FP64, a4), gather + scale of every x[s] (a4), and the SP2
  * loop (a5 squarings, a6 global FP64 trace + branch, a7 branch apply in the squaring
  * epilogue), with convergence decided on the device.  `H` must be device CSR.
@@ -315,9 +318,9 @@ int gbe_subs_set_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config* cfg);
 /* Autotuner (spec batching requirement, not in the paper): time every built
  * configuration of X's precision on the caller's own problem and install the fastest.
  * One SP2 run with `params` (its branch decisions as given) fixes the branch sequence;
- * every candidate then replays that sequence without FP64 tail steps, once untimed and
- * `reps` times timed with CUDA events on the context stream, so all candidates do the
- * same work.  The choice is cached in the context under the state's shape (precision,
+ * every candidate then replays that sequence without FP64 tail steps, twice untimed (the
+ * second run captures its CUDA graphs) and `reps` times timed with CUDA events on the
+ * context stream, so all candidates do the same work.  The choice is cached in the context under the state's shape (precision,
  * SM count, subgraph sizes): states created later with the same shape start with it, and
  * a later autotune of such a state returns the cached choice without timing (rep->cached).
  * Afterwards X holds the last candidate's iterates: run gbe_sp2_run again for a result.

@@ -1110,18 +1110,26 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
                                  H->n, H->nnz};
         memcpy(k + sizeof(in), ptrs, sizeof(ptrs));
         k[sizeof(in) + sizeof(ptrs)] = fp64_steps ? 1 : 0;
-        if (!X->gexec[0] || key != X->gkey) {
-            GBE_TRY(build_graphs(ctx, H, in, X, fp64_steps));
-            X->gkey = key;
+        // The graphs are captured on the second run with the same inputs and parameters, and
+        // relaunched while they stay the same: a run made once (such as a new state per MD
+        // step) is launched step by step instead of paying for a capture.
+        const bool have = X->gexec[0] && key == X->gkey;
+        if (have || (!X->gexec[0] && key == X->gkey)) {
+            if (!have) {
+                GBE_TRY(build_graphs(ctx, H, in, X, fp64_steps));
+                X->gkey = key;
+            }
+            cudaEventRecord(X->ev[0], st);
+            GBE_CUDA_TRY(cudaGraphLaunch(X->gexec[0], st));
+            cudaEventRecord(X->ev[1], st);
+            GBE_CUDA_TRY(cudaGraphLaunch(X->gexec[1], st));
+            cudaEventRecord(X->ev[2], st);
+            X->last_slots = 0;
+            X->last_prof = false;
+            return GBE_OK;
         }
-        cudaEventRecord(X->ev[0], st);
-        GBE_CUDA_TRY(cudaGraphLaunch(X->gexec[0], st));
-        cudaEventRecord(X->ev[1], st);
-        GBE_CUDA_TRY(cudaGraphLaunch(X->gexec[1], st));
-        cudaEventRecord(X->ev[2], st);
-        X->last_slots = 0;
-        X->last_prof = false;
-        return GBE_OK;
+        drop_graphs(X);
+        X->gkey = key;
     }
     cudaEventRecord(X->ev[0], st);
     GBE_TRY(enqueue_prologue(ctx, H, in, X));
@@ -1135,8 +1143,11 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
             X->ev_64.push_back(b);
         }
     }
-    X->last_slots = prm->n_max;
-    for (int slot = 0; slot < prm->n_max; ++slot) GBE_TRY(enqueue_step(ctx, X, fp64_steps, slot, 0, false));
+    // a replayed sequence takes exactly seq_len steps; otherwise n_max slots (the slots after
+    // the device's stop decision exit at once)
+    const int slots = in.branch_mode == GBE_BRANCH_REPLAY ? std::min(prm->n_max, in.seq_len) : prm->n_max;
+    X->last_slots = slots;
+    for (int slot = 0; slot < slots; ++slot) GBE_TRY(enqueue_step(ctx, X, fp64_steps, slot, 0, false));
     X->last_prof = prof;
     GBE_CUDA_TRY(cudaGetLastError());
     cudaEventRecord(X->ev[2], st);

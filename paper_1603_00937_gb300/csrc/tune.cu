@@ -4,7 +4,7 @@
 //
 // All candidates replay one branch sequence (fixed by a first run with the caller's
 // parameters), so each does the same squarings; times are CUDA-event means over `reps`
-// runs after one untimed run (which also captures the run's CUDA graphs).
+// runs after two untimed runs (the second captures the run's CUDA graphs).
 #include <algorithm>
 #include <cstring>
 
@@ -14,7 +14,8 @@ namespace {
 
 int timed_runs(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* prm, gbe_subs* X,
                int reps, float* ms) {
-    GBE_TRY(gbe_sp2_run(ctx, H, parts, prm, X));   // untimed: graph capture, warm caches
+    // untimed: the first run of new inputs goes step by step, the second captures the graphs
+    for (int i = 0; i < 2; ++i) GBE_TRY(gbe_sp2_run(ctx, H, parts, prm, X));
     GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     GBE_CUDA_TRY(cudaEventCreate(&e0));

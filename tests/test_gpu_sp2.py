@@ -184,8 +184,9 @@ def test_drop_tolerance_and_width_query(ctx, c1):
 @pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6])
 def test_graph_launch_matches_step_launch(prec):
     """The CUDA-graph path (device-driven loop) and the step-by-step launch path run the same
-    kernels: identical decisions and bit-identical D; the captured graphs are reused while
-    inputs and parameters are unchanged and recaptured when they change."""
+    kernels: identical decisions and bit-identical D.  A state's first run with given inputs
+    and parameters is launched step by step, the second captures the graphs, later ones
+    relaunch them; a change of parameters goes back to a step-by-step run."""
     case = ragged_case()
     H = case["H"]
     N = H.shape[0]
@@ -198,12 +199,16 @@ def test_graph_launch_matches_step_launch(prec):
         Hd = device_csr(H)
         p = gbe.sp2_params(N // 2, prec=prec, n_max=60)
         X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p)
+        if mode != "steps":
+            X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p, X)          # captured (graph modes)
         if mode == "graph-again":
-            # relaunch (reuse), then a changed parameter set (replay) forces a recapture
-            X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p, X)
-            X2, rep2 = gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=prec, seq=rep["seq"][:5]), X)
-            assert rep2["iters"] == 5
-            X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p, X)
+            X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p, X)          # relaunched
+            short = gbe.sp2_params(N // 2, prec=prec, seq=rep["seq"][:5])
+            for _ in range(2):                                           # new parameters: steps, capture
+                X2, rep2 = gbe.sp2_submatrices(ctx, Hd, parts, short, X)
+                assert rep2["iters"] == 5
+            for _ in range(2):                                           # back: steps, capture
+                X, rep = gbe.sp2_submatrices(ctx, Hd, parts, p, X)
         D, _, _ = assembled_dense(ctx, X, parts, N)
         outs.append((rep["seq"], rep["stop"], D))
     for seq, stop, D in outs[1:]:
