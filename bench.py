@@ -531,7 +531,7 @@ def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbe", choices=["gbe", "reference"])
     ap.add_argument("--workload", default="lattice32", choices=sorted(WORKLOADS))
