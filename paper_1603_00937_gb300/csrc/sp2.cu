@@ -358,6 +358,30 @@ __device__ void decide_body(Sp2Ctrl* ctrl, const double* __restrict__ partials, 
 // ----------------------------------------------------------------------------- FP64 squaring
 // 64 x 64 output tiles (I <= J) of X_{n+1} = f(X_n) per subgraph, DFMA with register
 // blocking; the branch is applied in the epilogue and the tile is mirrored to (J, I).
+// FP32 -> FP64 widening with integer operations only (exact for zero and normal floats,
+// which every split plane value and the partial sums below are).
+__device__ __forceinline__ double f32_to_f64_int(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0) return 0.0;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// The values of oz_value / bf_value with one FP64 addition each (the narrow FP64 pipe is
+// what bounds an element-wise pass over the planes): s1 + s2 is exact in FP32 (s2 is the
+// fp16 rounding residual of s1, the two significands span at most 22 bits), and both sums
+// are exact in FP64.
+__device__ __forceinline__ double oz_value_fast(uint16_t s0, uint16_t s1, uint16_t s2) {
+    const float r = (h_val(s1) + h_val(s2)) * (1.0f / 2048.0f);
+    return f32_to_f64_int(h_val(s0)) + f32_to_f64_int(r);
+}
+
+__device__ __forceinline__ double bf_value_fast(uint16_t hi, uint16_t lo) {
+    return f32_to_f64_int(b_val(hi)) + f32_to_f64_int(b_val(lo));
+}
+
 __device__ __forceinline__ double load_x(int fmt, int prec, const uint16_t* pl, int64_t ps, const double* f,
                                          int64_t off, int mpad, int r, int c) {
     if (fmt == 1) return f[blk_index(off, mpad, r, c)];
@@ -552,7 +576,62 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
     const uint16_t* pl = cur ? planes1 : planes0;
     const double* f = cur ? f1 : f0;
     const int lane = threadIdx.x & 31;
-    if (j < c) {
+    if (j < c && drop_tol <= 0.0) {
+        // every entry kept, in local order: lane takes 8 consecutive k; in an upper block
+        // they are one 16-byte run per plane (64 bytes of FP64)
+        const int64_t row = sub_idx[base + j];
+        int32_t* oc = ell_col + row * width;
+        double* ov = ell_val + row * width;
+        const int jb = j >> 7;
+        for (int k0 = 8 * lane; k0 < m; k0 += 256) {
+            double v[8];
+            if ((k0 >> 7) >= jb) {
+                const int64_t e = blk_index(off, mpad, j, k0);
+                if (fmt == 1) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const double2 d2 = reinterpret_cast<const double2*>(f + e)[t];
+                        v[2 * t] = d2.x;
+                        v[2 * t + 1] = d2.y;
+                    }
+                } else if (prec == GBE_PREC_FP16X6) {
+                    const uint4 a = *reinterpret_cast<const uint4*>(pl + e);
+                    const uint4 b = *reinterpret_cast<const uint4*>(pl + plane_stride + e);
+                    const uint4 cc = *reinterpret_cast<const uint4*>(pl + 2 * plane_stride + e);
+                    const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w},
+                                   cw[4] = {cc.x, cc.y, cc.z, cc.w};
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int sh = 16 * (t & 1);
+                        v[t] = oz_value_fast((uint16_t)(aw[t >> 1] >> sh), (uint16_t)(bw[t >> 1] >> sh),
+                                             (uint16_t)(cw[t >> 1] >> sh));
+                    }
+                } else {
+                    const uint4 a = *reinterpret_cast<const uint4*>(pl + e);
+                    const uint4 b = *reinterpret_cast<const uint4*>(pl + plane_stride + e);
+                    const uint32_t aw[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int sh = 16 * (t & 1);
+                        v[t] = bf_value_fast((uint16_t)(aw[t >> 1] >> sh), (uint16_t)(bw[t >> 1] >> sh));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < 8; ++t) v[t] = load_x(fmt, prec, pl, plane_stride, f, off, mpad, j, k0 + t);
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+                if (k0 + t < m) {
+                    oc[k0 + t] = sub_idx[base + k0 + t];
+                    ov[k0 + t] = scale == 1.0 ? v[t] : v[t] * scale;
+                }
+        }
+        for (int p = m + lane; p < width; p += 32) {
+            oc[p] = -1;
+            ov[p] = 0.0;
+        }
+    } else if (j < c) {
         const int64_t row = sub_idx[base + j];
         int32_t* oc = ell_col + row * width;
         double* ov = ell_val + row * width;
