@@ -205,14 +205,20 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
             return;
         }
     }
-    // sort the row's columns (odd-even transposition within the warp)
-    for (int phase = 0; phase < m; ++phase) {
-        for (int t = 2 * lane + (phase & 1); t + 1 < m; t += 64) {
-            const int x = buf[w][t], y = buf[w][t + 1];
-            if (x > y) { buf[w][t] = y; buf[w][t + 1] = x; }
+    // sort the row's columns: bitonic within the warp, padded to a power of two with INT_MAX
+    int np2 = 1;
+    while (np2 < m) np2 <<= 1;
+    for (int t = m + lane; t < np2; t += 32) buf[w][t] = 0x7FFFFFFF;
+    __syncwarp();
+    for (int k = 2; k <= np2; k <<= 1)
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int t2 = lane; t2 < (np2 >> 1); t2 += 32) {
+                const int lo = (t2 / jj) * 2 * jj + (t2 % jj), hi = lo + jj;
+                const int x = buf[w][lo], y = buf[w][hi];
+                if ((x > y) == ((lo & k) == 0)) { buf[w][lo] = y; buf[w][hi] = x; }
+            }
+            __syncwarp();
         }
-        __syncwarp();
-    }
     const int64_t base = pass == 2 ? i * kStageCap : rowptr[i];
     for (int t = lane; t < m; t += 32) {
         const int j = buf[w][t];
