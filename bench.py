@@ -89,7 +89,7 @@ TRAFFIC_SOURCES = {
     "sp2_square_tc_fp16x6": ["paper_1603_00937_gb300/csrc/sp2_tc.cu", "paper_1603_00937_gb300/csrc/split.cuh",
                              "paper_1603_00937_gb300/csrc/gbe_internal.h"],
 }
-TRAFFIC_KERNEL_RE = {"sp2_square_tc_fp16x6": r"sp2_square_tc_kernel<1, (0|false)(, \d+)?>"}   # <PREC = FP16X6, FOE = false, ring depth>
+TRAFFIC_KERNEL_RE = {"sp2_square_tc_fp16x6": r"sp2_square_tc_kernel<1, (0|false)(, \d+)*>"}   # <FP16X6, FOE = false, ring depth, K-chunk>
 
 
 def record_traffic(report, kernel, workload, capture_md):
@@ -264,8 +264,8 @@ def configure(args, gbe, ctx, H, parts, prm, X):
     if prm.prec == gbe.PREC_FP64:
         return None
     if args.config:
-        stages, sched = (int(v) for v in args.config.split(","))
-        gbe.subs_set_config(ctx, X, stages, sched)
+        v = [int(x) for x in args.config.split(",")]
+        gbe.subs_set_config(ctx, X, v[0], v[1], v[2] if len(v) > 2 else 0)
         return {"forced": gbe.subs_get_config(X)}
     if args.no_autotune:
         return {"default": gbe.subs_get_config(X)}
@@ -545,9 +545,10 @@ def main():
                          "kernels inside conditional graph nodes)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="skip the squaring kernel's autotuner (default launch configuration)")
-    ap.add_argument("--config", metavar="STAGES,SCHEDULE",
+    ap.add_argument("--config", metavar="STAGES,SCHEDULE[,KCHUNK]",
                     help="force the squaring kernel's launch configuration instead of autotuning, e.g. 4,0 "
-                         "(schedule 0 round-robin, 1 balanced ranges); used to profile the tuned choice")
+                         "(schedule 0 round-robin, 1 balanced ranges; K-chunk 32 or 16); used to profile the "
+                         "tuned choice")
     ap.add_argument("--record-traffic", metavar="REPORT",
                     help="write the DRAM traffic record of the FP16X6 squaring kernel for --workload "
                          "from this ncu report (no GPU needed), then exit")

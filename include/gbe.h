@@ -280,15 +280,19 @@ int gbe_sp2_submatrices(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts,
 
 /* Launch configuration of the tensor-core squaring that runs every submatrix of an SP2
  * step in one persistent launch (one CTA per SM):
- *   stages    depth of the TMA operand ring in 32-column K-chunks (0: the precision's
- *             default; FP16X6 is built with 3 and 4, BF16X3 with 4, 6 and 7)
+ *   kchunk    columns of K one ring stage holds: 32 (or 0) or 16.  Half-width stages
+ *             release their shared memory to the next copy twice as often, so the same
+ *             bytes in flight cover more of the copy latency, at twice the barrier traffic
+ *   stages    depth of the TMA operand ring (0: the default, 4 / 8 stages of 32 / 16
+ *             columns for FP16X6 and 6 / 12 for BF16X3; FP16X6 is also built with 3 / 6,
+ *             BF16X3 with 4, 7 / 14)
  *   schedule  how the upper-triangular 128 x 128 output tiles of all subgraphs (ordered
  *             subgraph by subgraph, largest first) are dealt to the CTAs:
  *             GBE_SCHED_ROUND_ROBIN    CTA b takes tiles b, b + grid, ... (the tiles of one
  *                                      subgraph run side by side on neighbouring CTAs)
  *             GBE_SCHED_BALANCED_RANGES CTA b takes one contiguous run of tiles, the runs
- *                                      cut so that every CTA gets the same number of
- *                                      K-chunks (sum over its tiles of ceil(m_s / 32))
+ *                                      cut so that every CTA gets about the same depth of
+ *                                      K (sum over its tiles of ceil(m_s / 16))
  * The configuration changes no result: every tile is computed by the same instructions
  * in the same order whichever CTA runs it, and the trace partials are summed in tile
  * order.  It applies to GBE_PREC_FP16X6 / GBE_PREC_BF16X3 states (FP64 states ignore it).
@@ -297,6 +301,7 @@ enum { GBE_SCHED_ROUND_ROBIN = 0, GBE_SCHED_BALANCED_RANGES = 1 };
 typedef struct {
     int stages;
     int schedule;
+    int kchunk;
 } gbe_tc_config;
 
 #define GBE_TUNE_MAX 16

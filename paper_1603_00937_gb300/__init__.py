@@ -111,7 +111,7 @@ class Sp2Report(ctypes.Structure):
 
 
 class TcConfig(ctypes.Structure):
-    _fields_ = [("stages", ctypes.c_int), ("schedule", ctypes.c_int)]
+    _fields_ = [("stages", ctypes.c_int), ("schedule", ctypes.c_int), ("kchunk", ctypes.c_int)]
 
 
 class TuneReport(ctypes.Structure):
@@ -119,8 +119,9 @@ class TuneReport(ctypes.Structure):
                 ("best", ctypes.c_int), ("iters", ctypes.c_int), ("cached", ctypes.c_int)]
 
     def as_dict(self):
-        cands = [dict(stages=self.cand[i].stages, schedule=SCHED_NAMES.get(self.cand[i].schedule, "?"),
-                      ms_per_run=self.ms[i]) for i in range(self.n)]
+        cands = [dict(kchunk=self.cand[i].kchunk or 32, stages=self.cand[i].stages,
+                      schedule=SCHED_NAMES.get(self.cand[i].schedule, "?"), ms_per_run=self.ms[i])
+                 for i in range(self.n)]
         return dict(candidates=cands, best=cands[self.best] if self.n else None, iters=self.iters,
                     cached=bool(self.cached))
 
@@ -411,11 +412,11 @@ def sp2_report_get(ctx, X):
 def subs_get_config(X):
     c = TcConfig()
     check(load_library().gbe_subs_get_config(X.handle, ctypes.byref(c)), "gbe_subs_get_config")
-    return dict(stages=c.stages, schedule=c.schedule)
+    return dict(stages=c.stages, schedule=c.schedule, kchunk=c.kchunk)
 
 
-def subs_set_config(ctx, X, stages=0, schedule=SCHED_ROUND_ROBIN):
-    c = TcConfig(stages, schedule)
+def subs_set_config(ctx, X, stages=0, schedule=SCHED_ROUND_ROBIN, kchunk=0):
+    c = TcConfig(stages, schedule, kchunk)
     check(load_library().gbe_subs_set_config(ctx.handle, X.handle, ctypes.byref(c)), "gbe_subs_set_config")
 
 

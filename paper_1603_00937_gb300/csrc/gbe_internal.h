@@ -151,7 +151,8 @@ struct gbe_subs {
     Sp2Ctrl* h_ctrl = nullptr;       // pinned
     // tensor maps for the split planes (opaque 128-byte CUtensorMap blobs)
     // TMA descriptors [side][view: K-chunk, transposed][box: A planes, B planes, diagonal B]
-    alignas(64) unsigned char tmap[3][2][3][128];
+    alignas(64) unsigned char tmap[3][2][3][128];     // ring stages of 32 columns of K
+    alignas(64) unsigned char tmap16[3][2][3][128];   // ring stages of 16 columns
     bool tmap_ok = false;
     // phase timing
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -171,7 +172,7 @@ struct gbe_subs {
     double mma_flops_full = 0.0, fp64_flops_full = 0.0;   // per product over all tiles
     // launch configuration of the tensor-core squaring (ring depth, work schedule); with the
     // balanced-range schedule CTA b takes items [d_cta_ptr[b], d_cta_ptr[b + 1])
-    gbe_tc_config tc_cfg{0, GBE_SCHED_ROUND_ROBIN};
+    gbe_tc_config tc_cfg{0, GBE_SCHED_ROUND_ROBIN, 0};
     int32_t* d_cta_ptr = nullptr;
     int cta_grid = 0;
 };
@@ -200,8 +201,9 @@ int gbe_tc_make_tmaps(gbe_subs* X);
 int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot);
 int gbe_tc_launch_foe(gbe_ctx* ctx, gbe_subs* X, int a_side, int b_side, int c_side, float alpha, double gamma);
 int gbe_tc_prepare(gbe_ctx* ctx);
-// ring depths the SP2 squaring kernel of a precision is built with (returns their count)
-int gbe_tc_stage_options(int prec, int* stages, int cap);
+// ring depths the SP2 squaring kernel of a precision and K-chunk width (0 = 32) is built
+// with (returns their count)
+int gbe_tc_stage_options(int prec, int kc, int* stages, int cap);
 // install a launch configuration on a state (work schedule rebuilt, SP2 graphs dropped)
 int gbe_subs_apply_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config& cfg);
 // shape key of a state for the context's tuning cache

@@ -936,9 +936,10 @@ std::vector<int64_t> gbe_subs_shape_key(const gbe_ctx* ctx, const gbe_subs* X) {
 
 int gbe_subs_apply_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config& cfg) {
     GBE_CHECK_ARG(cfg.schedule == GBE_SCHED_ROUND_ROBIN || cfg.schedule == GBE_SCHED_BALANCED_RANGES, "schedule");
+    GBE_CHECK_ARG(cfg.kchunk == 0 || cfg.kchunk == 16 || cfg.kchunk == 32, "kchunk must be 0, 16 or 32");
     if (X->prec != GBE_PREC_FP64 && cfg.stages != 0) {
         int opt[8];
-        const int n = gbe_tc_stage_options(X->prec, opt, 8);
+        const int n = gbe_tc_stage_options(X->prec, cfg.kchunk, opt, 8);
         bool found = false;
         for (int i = 0; i < n; ++i) found = found || opt[i] == cfg.stages;
         GBE_CHECK_ARG(found, "the squaring kernel of this precision is not built with that many stages");
@@ -956,7 +957,7 @@ int gbe_subs_apply_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config& cfg) {
         std::vector<double> cost(n);
         double total = 0.0;
         for (int i = 0; i < n; ++i) {
-            cost[i] = (double)((X->h_m[items[i].s] + 31) / 32);
+            cost[i] = (double)((X->h_m[items[i].s] + 15) / 16);
             total += cost[i];
         }
         // contiguous runs of nearly equal cost, at least one item each

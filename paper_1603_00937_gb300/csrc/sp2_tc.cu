@@ -32,7 +32,10 @@ namespace {
 
 constexpr int kEpiWarps = 8;                       // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;      // producer, MMA issuer, epilogue
-constexpr int kTileBytes = 128 * 32 * 2;   // 128 rows x 32 halfs: 4 column groups of 128 x 16 bytes
+// One operand slot holds a K-chunk of KC columns (32 or 16) of a 128-row block: KC/8 column
+// groups of 128 rows x 16 bytes, contiguous in the blocked layout.
+template <int KC>
+constexpr int tile_bytes() { return 128 * KC * 2; }
 constexpr int kTmemCols = 512;
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -146,13 +149,14 @@ __device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
     d |= (uint64_t)1 << 46;
     return d;
 }
-// Same for an MN-major (transposed) operand tile [16 groups of 8 rows][32 k][8]: core
-// matrices 128 bytes apart along K (leading byte offset), 512 bytes apart along M/N.
+// Same for an MN-major (transposed) operand tile [16 groups of 8 rows][KC k][8]: core
+// matrices 128 bytes apart along K (leading byte offset), 16 KC bytes apart along M/N.
+template <int KC>
 __device__ __forceinline__ uint64_t sdesc_mnmajor(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)(128 >> 4) << 16;
-    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)((16 * KC) >> 4) << 32;
     d |= (uint64_t)1 << 46;
     return d;
 }
@@ -195,12 +199,17 @@ __host__ __device__ constexpr int nib(uint32_t v, int i) { return (int)((v >> (4
 template <class R> __device__ __forceinline__ int slot_plane(int s) { return nib(R::kPlane, s); }
 template <class R> __device__ __forceinline__ int slot_alias(int s) { return nib(R::kAlias1, s) - 1; }
 
-// Shared memory of a CTA with an NS-deep operand ring (NS = 0: the recipe's default depth).
-template <int PREC, int NS = 0>
+// Default ring depth: the recipe's for 32-column chunks, twice that for 16-column ones (the
+// same bytes in flight).
+template <int PREC, int KC>
+constexpr int default_stages() { return Recipe<PREC>::kStages * (32 / KC); }
+
+// Shared memory of a CTA with an NS-deep ring of KC-column chunks (NS = 0: the default).
+template <int PREC, int NS = 0, int KC = 32>
 constexpr size_t smem_bytes() {
     using R = Recipe<PREC>;
-    constexpr int ns = NS ? NS : R::kStages;
-    return 1024 /*align slack*/ + (size_t)ns * R::kSlots * kTileBytes + 512 /*barriers, flags, reduction*/;
+    constexpr int ns = NS ? NS : default_stages<PREC, KC>();
+    return 1024 /*align slack*/ + (size_t)ns * R::kSlots * tile_bytes<KC>() + 512 /*barriers, flags, reduction*/;
 }
 
 // Optional wait-time counters (build with -DGBE_TC_STATS): cycles each role spends in
@@ -248,15 +257,18 @@ struct TcArgs {
 
 // FOE = false: one SP2 squaring X_{n+1} = X_n^2 or 2 X_n - X_n^2 (branch from the device).
 // FOE = true: one step of a Chebyshev expansion, out = alpha x b - c + gamma I (arguments).
-// NS_: depth of the operand ring in K-chunks (0: the recipe's default).
-template <int PREC, bool FOE, int NS_>
+// NS_: depth of the operand ring (0: the default for KC); KC: columns of K per ring stage
+// (32, or 16 for twice as many stages in the same shared memory).
+template <int PREC, bool FOE, int NS_, int KC>
 __global__ void __launch_bounds__(kThreads, 1)
     sp2_square_tc_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     using R = Recipe<PREC>;
-    constexpr int NS = NS_ ? NS_ : R::kStages;
+    constexpr int NS = NS_ ? NS_ : default_stages<PREC, KC>();
+    constexpr int kTileBytes = tile_bytes<KC>();
+    constexpr int kCPB = 128 / KC;            // K-chunks per 128-column block
     extern __shared__ unsigned char smem_raw[];
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* tiles = smem;                                          // NS * kSlots * 8 KB
+    unsigned char* tiles = smem;                                          // NS * kSlots * KC/4 KB
     uint64_t* bars = (uint64_t*)(tiles + (size_t)NS * R::kSlots * kTileBytes);
     uint64_t* full = bars;             // [NS]
     uint64_t* empty = bars + NS;       // [NS]
@@ -331,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const TileItem w = args.items[it];
                 const int mpad = args.g.mpad[w.s], m = args.g.m[w.s];
                 const int64_t off = args.g.off[w.s];
-                const int nk = (m + 31) >> 5;
+                const int nk = (m + KC - 1) / KC;
                 // a diagonal tile of a squaring takes B's planes s0..s2 from A's slots
                 const bool diag = (w.I == w.J) && !FOE;
                 const int nload = R::kA + (diag ? R::kDiag : R::kSlots - R::kA);
@@ -347,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     issued_mask |= 1u << stage;
                     issued_par = (issued_par & ~(1u << stage)) | (phase << stage);
                     unsigned char* st = tiles + (size_t)stage * R::kSlots * kTileBytes;
-                    const int kb = kc >> 2;
+                    const int kb = kc / kCPB;
                     const int64_t g0 = off >> 10;
                     // side A (row block I), then side B (column block J): one box per side
 #pragma unroll
@@ -362,14 +374,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // a Chebyshev step's b is not symmetric to the last bit: its block (kb, J)
                         // itself, as an MN-major tile, whatever kb and J are
                         if (Rt <= kb && !(FOE && side == 1)) {
-                            // stored block (Rt, kb): 4 column groups of 1024 elements = 16 view rows of 256
-                            const int64_t y = (g0 + (int64_t)Rt * (mpad >> 3) + 4 * kc) << 2;
+                            // stored block (Rt, kb): KC/8 column groups of 1024 elements = KC/2
+                            // view rows of 256
+                            const int64_t y = (g0 + (int64_t)Rt * (mpad >> 3) + (KC / 8) * kc) << 2;
                             tma_load_3d(dst, &tm[0][bx], &full[stage], 0, (int)y, z);
                         } else {
-                            // lower block: rows 32 (kc & 3).. of stored block (kb, Rt), its 16 column
-                            // groups -> [16 groups][32 rows][8], an MN-major operand tile
+                            // lower block: rows KC (kc mod kCPB).. of stored block (kb, Rt), its 16
+                            // column groups -> [16 groups][KC rows][8], an MN-major operand tile
                             const int64_t y = g0 + (int64_t)kb * (mpad >> 3) + 16 * Rt;
-                            tma_load_3d(dst, &tm[1][bx], &full[stage], 256 * (kc & 3), (int)y, z);
+                            tma_load_3d(dst, &tm[1][bx], &full[stage], 8 * KC * (kc % kCPB), (int)y, z);
                         }
                     }
                     if (++stage == NS) { stage = 0; phase ^= 1; }
@@ -409,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #endif
             const TileItem w = args.items[it];
             const int m = args.g.m[w.s];
-            const int nk = (m + 31) >> 5;
+            const int nk = (m + KC - 1) / KC;
             const bool diag = (w.I == w.J) && !FOE;
 #ifdef GBE_TC_STATS
             st_acc[6] += (unsigned long long)(clock64() - ts0);
@@ -435,19 +448,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #endif
                 tc_fence_after();
                 const uint32_t sbase = tiles_addr + (uint32_t)(stage * R::kSlots * kTileBytes);
-                const int kb = kc >> 2;
+                const int kb = kc / kCPB;
                 const bool tA = w.I > kb, tB = FOE || w.J > kb;   // operand loaded transposed (MN-major)
                 const uint32_t idesc_t = idesc | ((uint32_t)tA << 15) | ((uint32_t)tB << 16);
 #pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
+                for (int ks = 0; ks < KC / 16; ++ks) {
 #pragma unroll
                     for (int p = 0; p < R::kProducts; ++p) {
                         const int a = nib(R::kPa, p), acc = nib(R::kPacc, p);
                         int b = nib(R::kPb, p);
                         if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);   // never for FOE
                         const uint32_t aa = sbase + a * kTileBytes, ba = sbase + b * kTileBytes;
-                        const uint64_t da = tA ? sdesc_mnmajor(aa + ks * 256) : sdesc_kmajor(aa + ks * 4096);
-                        const uint64_t db = tB ? sdesc_mnmajor(ba + ks * 256) : sdesc_kmajor(ba + ks * 4096);
+                        const uint64_t da = tA ? sdesc_mnmajor<KC>(aa + ks * 256) : sdesc_kmajor(aa + ks * 4096);
+                        const uint64_t db = tB ? sdesc_mnmajor<KC>(ba + ks * 256) : sdesc_kmajor(ba + ks * 4096);
                         // the first product into each accumulator overwrites it
                         bool first = (kc == 0 && ks == 0);
                         if (first) {
@@ -680,25 +693,33 @@ extern "C" int gbe_tc_stats(unsigned long long* out, int reset) {
 struct TcVariant {
     int prec;
     bool foe;
+    int kc;       // K-chunk width of a ring stage
     int stages;
     const void* fn;
     size_t smem;
 };
-#define GBE_TC_VARIANT(P, F, N) \
-    TcVariant { P, F, N ? N : Recipe<P>::kStages, (const void*)sp2_square_tc_kernel<P, F, N>, smem_bytes<P, N>() }
+#define GBE_TC_VARIANT(P, F, N, K)                                                                          \
+    TcVariant {                                                                                              \
+        P, F, K, N ? N : default_stages<P, K>(), (const void*)sp2_square_tc_kernel<P, F, N, K>, smem_bytes<P, N, K>() \
+    }
 static const TcVariant kVariants[] = {
-    GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 0), GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 3),
-    GBE_TC_VARIANT(GBE_PREC_FP16X6, true, 0),  GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 0),
-    GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 4), GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 7),
+    GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 0, 32), GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 3, 32),
+    GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 0, 16), GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 6, 16),
+    GBE_TC_VARIANT(GBE_PREC_FP16X6, true, 0, 32),  GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 0, 32),
+    GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 4, 32), GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 7, 32),
+    GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 0, 16), GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 14, 16),
 };
 #undef GBE_TC_VARIANT
 
-// stages = 0: the recipe's default depth
-static const TcVariant* find_variant(int prec, bool foe, int stages) {
-    if (stages == 0)
-        stages = prec == GBE_PREC_FP16X6 ? Recipe<GBE_PREC_FP16X6>::kStages : Recipe<GBE_PREC_BF16X3>::kStages;
+// stages = 0: the default depth for the chunk width; kc = 0: 32 columns
+static const TcVariant* find_variant(int prec, bool foe, int stages, int kc) {
+    if (kc == 0) kc = 32;
+    if (stages == 0) {
+        const int base = prec == GBE_PREC_FP16X6 ? Recipe<GBE_PREC_FP16X6>::kStages : Recipe<GBE_PREC_BF16X3>::kStages;
+        stages = base * (32 / kc);
+    }
     for (const TcVariant& v : kVariants)
-        if (v.prec == prec && v.foe == foe && v.stages == stages) return &v;
+        if (v.prec == prec && v.foe == foe && v.kc == kc && v.stages == stages) return &v;
     return nullptr;
 }
 
@@ -727,10 +748,11 @@ int gbe_tc_prepare(gbe_ctx* ctx) {
     return GBE_OK;
 }
 
-int gbe_tc_stage_options(int prec, int* stages, int cap) {
+int gbe_tc_stage_options(int prec, int kc, int* stages, int cap) {
+    if (kc == 0) kc = 32;
     int n = 0;
     for (const TcVariant& v : kVariants)
-        if (v.prec == prec && !v.foe && n < cap) stages[n++] = v.stages;
+        if (v.prec == prec && !v.foe && v.kc == kc && n < cap) stages[n++] = v.stages;
     return n;
 }
 
@@ -742,22 +764,25 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
     const int nplanes = 4;   // plane buffers hold 4 planes of total_elems for every split format
     const bool fp16 = X->prec != GBE_PREC_BF16X3;
     const int depth[3] = {fp16 ? 3 : 2, fp16 ? 4 : 2, fp16 ? 1 : 1};
+    for (int w = 0; w < 2; ++w)   // ring stages of 32 (w = 0) or 16 (w = 1) columns of K
     for (int side = 0; side < 3; ++side)
         for (int view = 0; view < 2; ++view)
             for (int bx = 0; bx < 3; ++bx) {
+                unsigned char* slot = w == 0 ? X->tmap[side][view][bx] : X->tmap16[side][view][bx];
+                const cuuint32_t kc = w == 0 ? 32 : 16;
                 CUtensorMap m;
                 memset(&m, 0, sizeof(m));
-                // view 0: rows of 256 elements (512 B); a 32-column K-chunk of a row block is one
-                // contiguous 8 KB run = a 256 x 16 box per plane, copied unchanged.
-                // view 1 (transposed): one 2 KB column group per row; a 256 x 16 box takes 32 rows
+                // view 0: rows of 256 elements (512 B); a KC-column K-chunk of a row block is one
+                // contiguous run of KC/8 column groups = a 256 x KC/2 box per plane, copied unchanged.
+                // view 1 (transposed): one 2 KB column group per row; an 8 KC x 16 box takes KC rows
                 // of 16 consecutive column groups.  Planes are the third dimension.
                 const cuuint64_t inner = view == 0 ? 256 : 1024;
                 cuuint64_t dims[3] = {inner, (cuuint64_t)(X->total_elems / inner), (cuuint64_t)nplanes};
                 cuuint64_t strides[2] = {inner * 2, (cuuint64_t)X->total_elems * 2};
-                cuuint32_t box[3] = {256, 16, (cuuint32_t)depth[bx]};
+                cuuint32_t box[3] = {view == 0 ? 256u : 8u * kc, view == 0 ? kc / 2u : 16u, (cuuint32_t)depth[bx]};
                 cuuint32_t estr[3] = {1, 1, 1};
                 if (!X->planes[side]) {   // side 2 exists only once a Chebyshev expansion ran
-                    memset(X->tmap[side][view][bx], 0, 128);
+                    memset(slot, 0, 128);
                     continue;
                 }
                 CUresult r = g_encode_tiled(&m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
@@ -769,7 +794,7 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
                     return GBE_ECUDA;
                 }
                 static_assert(sizeof(CUtensorMap) == 128, "CUtensorMap size");
-                memcpy(X->tmap[side][view][bx], &m, sizeof(m));
+                memcpy(slot, &m, sizeof(m));
             }
     X->tmap_ok = true;
     return GBE_OK;
@@ -795,9 +820,10 @@ int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot) {
         gbe_set_error("tensor maps missing");
         return GBE_ECUDA;
     }
-    const TcVariant* v = find_variant(X->prec, false, X->tc_cfg.stages);
+    const TcVariant* v = find_variant(X->prec, false, X->tc_cfg.stages, X->tc_cfg.kchunk);
     if (!v) {
-        gbe_set_error("no tensor-core kernel with %d stages for precision %d", X->tc_cfg.stages, X->prec);
+        gbe_set_error("no tensor-core kernel with %d stages of %d columns for precision %d", X->tc_cfg.stages,
+                      X->tc_cfg.kchunk, X->prec);
         return GBE_EINVAL;
     }
     TcArgs a = tc_args(X, slot);
@@ -807,8 +833,8 @@ int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot) {
         grid = X->cta_grid;
     }
     TcMaps maps;
-    static_assert(sizeof(maps) == sizeof(X->tmap), "tensor map set size");
-    memcpy(&maps, X->tmap, sizeof(maps));
+    static_assert(sizeof(maps) == sizeof(X->tmap) && sizeof(maps) == sizeof(X->tmap16), "tensor map set size");
+    memcpy(&maps, v->kc == 16 ? X->tmap16 : X->tmap, sizeof(maps));
     void* kargs[2] = {&maps, &a};
     GBE_CUDA_TRY(cudaLaunchKernel(v->fn, dim3(grid), dim3(kThreads), kargs, v->smem, ctx->stream));
     return GBE_OK;
@@ -832,7 +858,8 @@ int gbe_tc_launch_foe(gbe_ctx* ctx, gbe_subs* X, int a_side, int b_side, int c_s
     TcMaps maps;
     memcpy(&maps, X->tmap, sizeof(maps));
     const int gridf = std::max(1, std::min(X->n_items_tc_full, ctx->sm_count));
-    sp2_square_tc_kernel<GBE_PREC_FP16X6, true, 0><<<gridf, kThreads, smem_bytes<GBE_PREC_FP16X6>(), ctx->stream>>>(maps, a);
+    sp2_square_tc_kernel<GBE_PREC_FP16X6, true, 0, 32>
+        <<<gridf, kThreads, smem_bytes<GBE_PREC_FP16X6, 0, 32>(), ctx->stream>>>(maps, a);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }

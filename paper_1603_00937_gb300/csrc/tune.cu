@@ -1,5 +1,5 @@
 // Autotuner of the batched tensor-core squaring: every built launch configuration of a
-// state's precision (operand-ring depth x tile schedule) is timed on the caller's own
+// state's precision (K-chunk width x operand-ring depth x tile schedule) is timed on the caller's own
 // problem, and the fastest is installed and cached in the context by state shape.
 //
 // All candidates replay one branch sequence (fixed by a first run with the caller's
@@ -73,11 +73,13 @@ extern "C" int gbe_sp2_autotune(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts*
                 rep->cached = 1;
                 return GBE_OK;
             }
-        int st[8];
-        const int ns = gbe_tc_stage_options(X->prec, st, 8);
-        for (int i = 0; i < ns; ++i)
-            for (int sched : {GBE_SCHED_ROUND_ROBIN, GBE_SCHED_BALANCED_RANGES})
-                if ((int)cand.size() < GBE_TUNE_MAX) cand.push_back(gbe_tc_config{st[i], sched});
+        for (int kc : {32, 16}) {
+            int st[8];
+            const int ns = gbe_tc_stage_options(X->prec, kc, st, 8);
+            for (int i = 0; i < ns; ++i)
+                for (int sched : {GBE_SCHED_ROUND_ROBIN, GBE_SCHED_BALANCED_RANGES})
+                    if ((int)cand.size() < GBE_TUNE_MAX) cand.push_back(gbe_tc_config{st[i], sched, kc});
+        }
     }
 
     // the branch sequence every candidate replays

@@ -5,7 +5,7 @@ cores, |H^2| >= 0.1): 64 subgraphs of uneven size spread over several 128-wide b
 so one launch holds ~1000 upper tiles of different K depths, several per CTA, with
 ragged edges.  The oracle's free-running branch sequence is replayed on the GPU.
 
-(a) Every built configuration (operand-ring depth x tile schedule) gives bit-identical
+(a) Every built configuration (K-chunk width x ring depth x tile schedule) gives bit-identical
     D and traces: a tile is computed by the same instructions in the same order
     whichever CTA runs it, and the per-tile trace partials are summed in tile order.
 (b) The autotuner times every configuration, installs the fastest, and caches it by
@@ -24,7 +24,8 @@ pytestmark = pytest.mark.gpu
 
 from tests.gpu_helpers import assembled_dense, device_csr, gbe, import_parts, torch  # noqa: E402,F401
 
-STAGES = {gbe.PREC_FP16X6: [3, 4], gbe.PREC_BF16X3: [4, 6, 7]}
+# ring depths each precision is built with, per K-chunk width
+STAGES = {gbe.PREC_FP16X6: {32: [3, 4], 16: [6, 8]}, gbe.PREC_BF16X3: {32: [4, 6, 7], 16: [12, 14]}}
 N = 4096
 
 
@@ -59,15 +60,16 @@ def test_every_config_gives_identical_D(ctx, case, prec):
     X = gbe.subs_create(ctx, parts, prec)
     ms = np.array([len(s) for s in case["subs"]])
     assert len(np.unique((ms + 127) // 128)) >= 2
-    assert gbe.subs_get_config(X) == dict(stages=0, schedule=gbe.SCHED_ROUND_ROBIN)
+    assert gbe.subs_get_config(X) == dict(stages=0, schedule=gbe.SCHED_ROUND_ROBIN, kchunk=0)
     D0, rep0 = run(ctx, Hd, parts, params, X)
-    for stages in STAGES[prec]:
-        for sched in (gbe.SCHED_ROUND_ROBIN, gbe.SCHED_BALANCED_RANGES):
-            gbe.subs_set_config(ctx, X, stages, sched)
-            assert gbe.subs_get_config(X) == dict(stages=stages, schedule=sched)
-            D, rep = run(ctx, Hd, parts, params, X)
-            assert np.array_equal(D, D0), (stages, sched, np.abs(D - D0).max())
-            assert rep["t1"] == rep0["t1"] and rep["t2"] == rep0["t2"], (stages, sched)
+    for kc, depths in STAGES[prec].items():
+        for stages in depths:
+            for sched in (gbe.SCHED_ROUND_ROBIN, gbe.SCHED_BALANCED_RANGES):
+                gbe.subs_set_config(ctx, X, stages, sched, kc)
+                assert gbe.subs_get_config(X) == dict(stages=stages, schedule=sched, kchunk=kc)
+                D, rep = run(ctx, Hd, parts, params, X)
+                assert np.array_equal(D, D0), (kc, stages, sched, np.abs(D - D0).max())
+                assert rep["t1"] == rep0["t1"] and rep["t2"] == rep0["t2"], (kc, stages, sched)
     if prec == gbe.PREC_FP16X6:
         err = np.abs(D0 - case["D"]).max()
         assert err <= 1e-5, err
@@ -84,14 +86,16 @@ def test_autotune_installs_fastest_and_caches(case):
     print("autotune:", rep)
     cands = rep["candidates"]
     assert not rep["cached"] and rep["iters"] == len(case["seq"])
-    assert len(cands) == 2 * len(STAGES[gbe.PREC_FP16X6])
-    assert {(c["stages"], c["schedule"]) for c in cands} == \
-        {(s, n) for s in STAGES[gbe.PREC_FP16X6] for n in ("round_robin", "balanced_ranges")}
+    want = {(kc, s, n) for kc, depths in STAGES[gbe.PREC_FP16X6].items() for s in depths
+            for n in ("round_robin", "balanced_ranges")}
+    assert len(cands) == len(want)
+    assert {(c["kchunk"], c["stages"], c["schedule"]) for c in cands} == want
     assert all(c["ms_per_run"] > 0 for c in cands)
     best = rep["best"]
     assert best["ms_per_run"] == min(c["ms_per_run"] for c in cands)
     cfg = gbe.subs_get_config(X)
     assert cfg["stages"] == best["stages"] and gbe.SCHED_NAMES[cfg["schedule"]] == best["schedule"]
+    assert (cfg["kchunk"] or 32) == best["kchunk"]
     D, _ = run(ctx, Hd, parts, params, X)
     assert np.array_equal(D, D0)
     assert np.abs(D - case["D"]).max() <= 1e-5
@@ -104,7 +108,7 @@ def test_autotune_installs_fastest_and_caches(case):
     assert np.array_equal(D2, D0)
     # a state of another precision has its own entry
     X3 = gbe.subs_create(ctx, parts, gbe.PREC_BF16X3)
-    assert gbe.subs_get_config(X3) == dict(stages=0, schedule=gbe.SCHED_ROUND_ROBIN)
+    assert gbe.subs_get_config(X3) == dict(stages=0, schedule=gbe.SCHED_ROUND_ROBIN, kchunk=0)
     for h in (X3, X2, X, parts):
         h.close()
     ctx.close()
@@ -113,8 +117,8 @@ def test_autotune_installs_fastest_and_caches(case):
 def test_invalid_config_rejected(ctx, case):
     parts = import_parts(ctx, N, case["subs"], case["nc"])
     X = gbe.subs_create(ctx, parts, gbe.PREC_FP16X6)
-    for stages, sched in ((5, 0), (6, 0), (4, 7), (-1, 0)):
+    for stages, sched, kc in ((5, 0, 0), (6, 0, 32), (4, 0, 16), (4, 7, 0), (-1, 0, 0), (4, 0, 8)):
         with pytest.raises(gbe.GbeError) as e:
-            gbe.subs_set_config(ctx, X, stages, sched)
+            gbe.subs_set_config(ctx, X, stages, sched, kc)
         assert e.value.code == gbe.GBE_EINVAL
-    assert gbe.subs_get_config(X) == dict(stages=0, schedule=gbe.SCHED_ROUND_ROBIN)
+    assert gbe.subs_get_config(X) == dict(stages=0, schedule=gbe.SCHED_ROUND_ROBIN, kchunk=0)
