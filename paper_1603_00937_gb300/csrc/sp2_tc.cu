@@ -304,6 +304,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     const int cur = hdr[1], branch = hdr[2];
     const long long budget = ctrl->timeout_cycles;
+    // the drains after an abort wait for work already issued (copies, MMAs), which finishes
+    // in microseconds: at least ~1 s of clock whatever the caller's budget, so that no copy
+    // lands and no MMA writes TMEM after the CTA has released them
+    const long long drain_budget = budget > 2000000000LL ? budget : 2000000000LL;
     // [view][box] maps of the A and B operand sides; planes the epilogue reads and writes
     const CUtensorMap(*tmA)[3] = maps.m[FOE ? args.a_side : cur];
     const CUtensorMap(*tmB)[3] = maps.m[FOE ? args.b_side : cur];
@@ -395,7 +399,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int i = 0; i < NS; ++i)
                     if (issued_mask & (1u << i)) {
                         const long long t0 = clock64();
-                        while (!mbar_try_wait(&full[i], (issued_par >> i) & 1u) && clock64() - t0 < budget) {
+                        while (!mbar_try_wait(&full[i], (issued_par >> i) & 1u) && clock64() - t0 < drain_budget) {
                         }
                     }
             }
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         umma_commit(drain);
         if (lane == 0) {
             const long long t0 = clock64();
-            while (!mbar_try_wait(drain, 0) && clock64() - t0 < budget) {
+            while (!mbar_try_wait(drain, 0) && clock64() - t0 < drain_budget) {
             }
         }
         __syncwarp();

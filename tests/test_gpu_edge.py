@@ -95,3 +95,25 @@ def test_objects_outliving_their_context():
     X2.close()
     parts2.close()
     c2.close()
+
+
+def test_device_wait_timeout_is_reported(ctx):
+    """The tensor-core kernel's device-side waits are bounded.  With a wait budget far below
+    the latency of an operand copy every CTA gives up, records GBE_ETIMEOUT, waits (about a
+    second at most) for the copies and MMAs it already issued, frees its TMEM and returns;
+    the run reports the error, the context stays usable, and a run with the default budget
+    then gives the same D as before."""
+    w, H, _, subs, nc = lattice_case(6, seed=1, thr=1e-3, ncell=(3, 3, 3))
+    N = H.shape[0]
+    parts = import_parts(ctx, N, subs, nc)
+    Hd = device_csr(H)
+    seq = [1, 0, 1]
+    X, rep = gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=seq))
+    D0, _, _ = assembled_dense(ctx, X, parts, N)
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=seq, timeout_ms=1e-5), X)
+    assert e.value.code == gbe.GBE_ETIMEOUT
+    X, rep = gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=seq), X)
+    assert rep["status"] == 0 and rep["iters"] == len(seq)
+    D1, _, _ = assembled_dense(ctx, X, parts, N)
+    assert np.array_equal(D0, D1)
