@@ -178,6 +178,22 @@ typedef struct {
  * sizes size every later buffer).  GBE_ECAPACITY when a subgraph exceeds max_sub. */
 int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* params,
                   gbe_parts** parts);
+/* Cost-driven choice of the partition size (Sec. II.B: the error hardly depends on the number
+ * of communities while the cost varies strongly with it, and an optimised partitioning
+ * brings it down; Sec. III: adjust the partitioning to the computational platform).  Each
+ * candidate replaces params->ncell (GBE_PART_SPATIAL_CELLS: candidates[3 i .. 3 i + 2]) or
+ * params->core_size (GBE_PART_INDEX_BLOCKS: candidates[3 i]) and is partitioned with
+ * gbe_partition; its cost is the squaring work of one SP2 step on this library's kernels
+ * for precision `prec`: GBE_PREC_FP16X6 / BF16X3 sum over subgraphs of
+ * products x 2 x 128^2 x 32 ceil(m_s / 32) x T_s (T_s + 1) / 2 with T_s = ceil(m_s / 128)
+ * (6 / 3 products), GBE_PREC_FP64 the same over 64 x 64 tiles and K in steps of 16
+ * (flops; upper tiles only).  A candidate whose partition fails (a subgraph above max_sub or
+ * above the 2432 vertices the gather holds) costs +inf.  cost[ncand] receives the costs,
+ * *best the index of the cheapest and *parts its partition (library-owned; NULL and
+ * GBE_ECAPACITY when every candidate failed).  Not in the paper as an algorithm: the paper
+ * uses METIS with a chosen number of communities. */
+int gbe_partition_autotune(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* params, int prec,
+                           const int32_t* candidates, int ncand, double* cost, int* best, gbe_parts** parts);
 /* Sizes: number of subgraphs P, total local indices, max subgraph size. */
 int gbe_parts_info(const gbe_parts* parts, int64_t* P, int64_t* total, int64_t* max_m);
 /* Copy to host: core_count[P] int32, sub_ptr[P+1] int64, sub_idx[total] int32. */

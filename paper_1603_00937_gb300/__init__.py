@@ -40,7 +40,7 @@ EXPORTS = [
     "gbe_free_pairs", "gbe_mlp_create", "gbe_mlp_param_count", "gbe_mlp_set_params", "gbe_mlp_get_params",
     "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_free_mlp",
     "gbe_sp2_gap_estimate", "gbe_sp2_sequence", "gbe_fermi_coefficients", "gbe_foe_run", "gbe_foe_report_get",
-    "gbe_subs_get_config", "gbe_subs_set_config", "gbe_sp2_autotune",
+    "gbe_subs_get_config", "gbe_subs_set_config", "gbe_sp2_autotune", "gbe_partition_autotune",
 ]
 
 
@@ -165,6 +165,7 @@ def load_library(path=LIB_PATH):
         "gbe_foe_report_get": (I32, [P, P, P]),
         "gbe_subs_get_config": (I32, [P, P]), "gbe_subs_set_config": (I32, [P, P, P]),
         "gbe_sp2_autotune": (I32, [P, P, P, P, P, I32, P]),
+        "gbe_partition_autotune": (I32, [P, P, P, I32, P, I32, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -364,6 +365,23 @@ def partition(ctx, S, mode=PART_SPATIAL_CELLS, ncell=(1, 1, 1), site_struct=None
     h = ctypes.c_void_p()
     check(load_library().gbe_partition(ctx.handle, S.handle, ctypes.byref(p), ctypes.byref(h)), "gbe_partition")
     return Parts(ctx, h)
+
+
+def partition_autotune(ctx, S, candidates, prec=PREC_FP16X6, mode=PART_SPATIAL_CELLS, site_struct=None, max_sub=0):
+    """Cost-driven partition size: candidates are ncell triples (spatial cells) or core sizes
+    (index blocks).  Returns (Parts of the cheapest, index of it, per-candidate costs)."""
+    cand = np.zeros((len(candidates), 3), dtype=np.int32)
+    for i, c in enumerate(candidates):
+        cand[i, :len(np.atleast_1d(c))] = np.atleast_1d(c)
+    pp = PartitionParams(mode, (ctypes.c_int * 3)(1, 1, 1),
+                         ctypes.cast(ctypes.pointer(site_struct), ctypes.c_void_p) if site_struct is not None else None,
+                         0, max_sub)
+    cost = np.zeros(len(candidates), dtype=np.float64)
+    best = ctypes.c_int()
+    h = ctypes.c_void_p()
+    check(load_library().gbe_partition_autotune(ctx.handle, S.handle, ctypes.byref(pp), prec, _ptr(cand), len(cand),
+                                                _ptr(cost), ctypes.byref(best), ctypes.byref(h)), "gbe_partition_autotune")
+    return Parts(ctx, h), best.value, cost
 
 
 def parts_import(ctx, n, core_count, sub_ptr, sub_idx):

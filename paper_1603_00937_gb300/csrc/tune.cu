@@ -6,7 +6,9 @@
 // parameters), so each does the same squarings; times are CUDA-event means over `reps`
 // runs after two untimed runs (the second captures the run's CUDA graphs).
 #include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <limits>
 
 #include "gbe_internal.h"
 
@@ -117,5 +119,72 @@ extern "C" int gbe_sp2_autotune(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts*
             if (kv.first == key) { kv.second = cand[best]; stored = true; }
         if (!stored) ctx->tune_cache.emplace_back(key, cand[best]);
     }
+    return GBE_OK;
+}
+
+// ----------------------------------------------------------------------------- partition size
+namespace {
+
+// Executed squaring flops of one SP2 step for the subgraph sizes of a partition.
+double step_flops(int prec, const std::vector<int64_t>& sub_ptr) {
+    double f = 0.0;
+    for (size_t s = 0; s + 1 < sub_ptr.size(); ++s) {
+        const double m = (double)(sub_ptr[s + 1] - sub_ptr[s]);
+        if (prec == GBE_PREC_FP64) {
+            const double T = std::ceil(m / 64.0), k = 16.0 * std::ceil(m / 16.0);
+            f += 2.0 * 64.0 * 64.0 * k * T * (T + 1.0) / 2.0;
+        } else {
+            const double T = std::ceil(m / 128.0), k = 32.0 * std::ceil(m / 32.0);
+            const double nprod = prec == GBE_PREC_FP16X6 ? 6.0 : 3.0;
+            f += nprod * 2.0 * 128.0 * 128.0 * k * T * (T + 1.0) / 2.0;
+        }
+    }
+    return f;
+}
+
+}  // namespace
+
+extern "C" int gbe_partition_autotune(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* params, int prec,
+                                      const int32_t* candidates, int ncand, double* cost, int* best, gbe_parts** parts) {
+    AllocScope alloc_scope_(ctx);
+    GBE_CHECK_ARG(ctx && S && params && candidates && cost && best && parts, "NULL argument");
+    GBE_CHECK_ARG(ncand >= 1, "no candidates");
+    GBE_CHECK_ARG(prec == GBE_PREC_FP64 || prec == GBE_PREC_FP16X6 || prec == GBE_PREC_BF16X3, "unknown prec");
+    GBE_CHECK_ARG(params->mode == GBE_PART_SPATIAL_CELLS || params->mode == GBE_PART_INDEX_BLOCKS, "partition mode");
+    *parts = nullptr;
+    *best = -1;
+    gbe_parts* keep = nullptr;
+    for (int i = 0; i < ncand; ++i) {
+        gbe_partition_params p = *params;
+        if (p.mode == GBE_PART_SPATIAL_CELLS)
+            for (int d = 0; d < 3; ++d) p.ncell[d] = candidates[3 * i + d];
+        else
+            p.core_size = candidates[3 * i];
+        gbe_parts* P = nullptr;
+        const int r = gbe_partition(ctx, S, &p, &P);
+        cost[i] = std::numeric_limits<double>::infinity();
+        if (r == GBE_ECAPACITY || r == GBE_EINVAL) continue;   // infeasible (or meaningless) candidate
+        if (r != GBE_OK) {
+            gbe_free_parts(keep);
+            return r;
+        }
+        if (P->max_m > 2432) {   // beyond what the gather's shared memory holds
+            gbe_free_parts(P);
+            continue;
+        }
+        cost[i] = step_flops(prec, P->h_sub_ptr);
+        if (*best < 0 || cost[i] < cost[*best]) {
+            gbe_free_parts(keep);
+            keep = P;
+            *best = i;
+        } else {
+            gbe_free_parts(P);
+        }
+    }
+    if (!keep) {
+        gbe_set_error("no candidate partition fits");
+        return GBE_ECAPACITY;
+    }
+    *parts = keep;
     return GBE_OK;
 }

@@ -186,6 +186,36 @@ def test_partition_capacity_error(ctx, lat):
     assert e.value.code == gbe.GBE_ECAPACITY
 
 
+@pytest.mark.parametrize("prec", [gbe.PREC_FP16X6, gbe.PREC_FP64])
+def test_partition_autotune_picks_cheapest(ctx, prec):
+    """Cost-driven partition size on the 16^3 lattice (|H^2| >= 0.15 graph): every candidate
+    cell grid is partitioned and costed by the squaring work of one SP2 step (checked here
+    against the formula on the exported subgraph sizes); a grid whose subgraphs exceed what
+    the gather holds (one cell: 4096 sites) is infeasible; the cheapest one is returned."""
+    w = synth.lattice(16, seed=3)
+    st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
+    Hg = gbe.build_hamiltonian(ctx, st)
+    G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_H2_THRESH, thresh=0.15)
+    cands = [(1, 1, 1), (2, 2, 2), (4, 4, 4), (8, 8, 8), (16, 16, 16)]
+    parts, best, cost = gbe.partition_autotune(ctx, G, cands, prec=prec, site_struct=st)
+    assert np.isinf(cost[0]) and np.all(np.isfinite(cost[1:]))
+    for i, c in enumerate(cands[1:], start=1):
+        _, sp, _ = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=c, site_struct=st).export()
+        m = np.diff(sp).astype(np.float64)
+        if prec == gbe.PREC_FP64:
+            T, k = np.ceil(m / 64), 16 * np.ceil(m / 16)
+            want = np.sum(2 * 64 * 64 * k * T * (T + 1) / 2)
+        else:
+            T, k = np.ceil(m / 128), 32 * np.ceil(m / 32)
+            want = np.sum(6 * 2 * 128 * 128 * k * T * (T + 1) / 2)
+        np.testing.assert_allclose(cost[i], want, rtol=1e-12)
+    assert best == int(np.argmin(cost))
+    cc, sp, si = parts.export()
+    cc2, sp2_, si2 = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=cands[best], site_struct=st).export()
+    assert np.array_equal(cc, cc2) and np.array_equal(sp, sp2_) and np.array_equal(si, si2)
+    print("partition costs:", dict(zip(cands, cost)), "best", cands[best])
+
+
 @pytest.mark.parametrize("prec,tol", [(gbe.PREC_FP64, 1e-10), (gbe.PREC_FP16X6, 1e-6)])
 def test_end_to_end_gpu_chain(ctx, prec, tol):
     """GPU H -> graph -> partition -> SP2 -> assembly against the oracle's own chain."""
