@@ -35,6 +35,10 @@ UNIT = "orbitals/s"
 WORKLOADS = {
     # the configuration the metric is quoted on: 32^3 lattice, cores of 64, m_s ~ 460-480
     "lattice32": dict(kind="lattice", L=32, seed=0, thresh=0.15, ncell=(8, 8, 8)),
+    # the same lattice with the partition size chosen by gbe_partition_autotune among cell
+    # grids of 4^3 .. 32^3 (cores of 512 .. 1 sites) by the modelled squaring time per SP2 step
+    "lattice32tuned": dict(kind="lattice", L=32, seed=0, thresh=0.15, ncell=(8, 8, 8),
+                           ncell_candidates=[(4, 4, 4), (8, 8, 8), (16, 16, 16), (32, 32, 32)]),
     # small case (8^3, |H^2| >= 1e-5 graph, cores of 8, m_s ~ 470-510)
     "lattice8": dict(kind="lattice", L=8, seed=0, thresh=1e-5, ncell=(4, 4, 4)),
     # 16^3 slice of the 32^3 workload (same m_s distribution, 64 subgraphs): profiling case
@@ -594,7 +598,15 @@ def main():
     Hh = gbe.build_hamiltonian(ctx, st)
     Hv = Hh.csr()
     G = gbe.build_graph(ctx, Hv, gbe.GRAPH_H2_THRESH, thresh=wl["thresh"])
-    parts = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=wl["ncell"], site_struct=st)
+    part_tune = None
+    if wl.get("ncell_candidates"):
+        prec0 = getattr(gbe, "PREC_" + PRECS[args.prec][0])
+        parts, bi, pcost = gbe.partition_autotune(ctx, G, wl["ncell_candidates"], prec=prec0, site_struct=st)
+        part_tune = {"candidates": [list(c) for c in wl["ncell_candidates"]],
+                     "modelled_squaring_us_per_step": [None if not np.isfinite(c) else float(c) for c in pcost],
+                     "chosen": list(wl["ncell_candidates"][bi])}
+    else:
+        parts = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=wl["ncell"], site_struct=st)
     P, total, max_m = parts.info()
     cc, sptr, _ = parts.export()
     ms = np.diff(sptr)
@@ -742,6 +754,8 @@ def main():
         "clocks": clk,
         "autotune": tune,
     }
+    if part_tune:
+        line["partition_autotune"] = part_tune
     line.update(out)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if wl["kind"] == "lattice":

@@ -183,11 +183,12 @@ int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* 
  * brings it down; Sec. III: adjust the partitioning to the computational platform).  Each
  * candidate replaces params->ncell (GBE_PART_SPATIAL_CELLS: candidates[3 i .. 3 i + 2]) or
  * params->core_size (GBE_PART_INDEX_BLOCKS: candidates[3 i]) and is partitioned with
- * gbe_partition; its cost is the squaring work of one SP2 step on this library's kernels
- * for precision `prec`: GBE_PREC_FP16X6 / BF16X3 sum over subgraphs of
- * products x 2 x 128^2 x 32 ceil(m_s / 32) x T_s (T_s + 1) / 2 with T_s = ceil(m_s / 128)
- * (6 / 3 products), GBE_PREC_FP64 the same over 64 x 64 tiles and K in steps of 16
- * (flops; upper tiles only).  A candidate whose partition fails (a subgraph above max_sub or
+ * gbe_partition; its cost is a model of the squaring time of one SP2 step on this
+ * library's kernels for precision `prec`, in microseconds: GBE_PREC_FP16X6 / BF16X3 sum
+ * over subgraphs of T_s (T_s + 1) / 2 upper tiles (T_s = ceil(m_s / 128)) times
+ * max(7.5, c ceil(m_s / 32)) / (number of SMs), c = 0.6 (FP16X6) or 0.3 (BF16X3): a tile's
+ * epilogue against its MMAs, fitted to GB300 runs; GBE_PREC_FP64 the FP64 flops
+ * 2 x 64^2 x 16 ceil(m_s / 16) per upper 64 x 64 tile at 1.2 TFLOP/s.  A candidate whose partition fails (a subgraph above max_sub or
  * above the 2432 vertices the gather holds) costs +inf.  cost[ncand] receives the costs,
  * *best the index of the cheapest and *parts its partition (library-owned; NULL and
  * GBE_ECAPACITY when every candidate failed).  Not in the paper as an algorithm: the paper

@@ -125,21 +125,30 @@ extern "C" int gbe_sp2_autotune(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts*
 // ----------------------------------------------------------------------------- partition size
 namespace {
 
-// Executed squaring flops of one SP2 step for the subgraph sizes of a partition.
-double step_flops(int prec, const std::vector<int64_t>& sub_ptr) {
-    double f = 0.0;
+// Modelled squaring time of one SP2 step (microseconds on the whole GPU) for the subgraph
+// sizes of a partition.
+//  Tensor-core paths: every upper 128 x 128 tile costs max(E, C ceil(m_s / 32)) on one SM,
+//  the epilogue (E: TMEM read-out, split and stores of the tile) overlapping the MMAs of
+//  the next tile (C per 32-column K-chunk).  E = 7.5 us and C = 0.6 us (FP16X6; C halves with
+//  BF16X3's 3 products) are fitted to GB300 launches of the 32^3 lattice with cores of 64
+//  sites (5120 tiles of 15 chunks: 0.345 ms) and of 8 sites (12288 tiles of 6 chunks:
+//  0.696 ms), both 152 SMs.
+//  FP64 path: the FP64 pipe's flops, 2 * 64^2 * K per upper 64 x 64 tile with K in steps of
+//  16, at 1.2 TFLOP/s.
+double step_time_us(int prec, int sm_count, const std::vector<int64_t>& sub_ptr) {
+    double t = 0.0;
     for (size_t s = 0; s + 1 < sub_ptr.size(); ++s) {
         const double m = (double)(sub_ptr[s + 1] - sub_ptr[s]);
         if (prec == GBE_PREC_FP64) {
             const double T = std::ceil(m / 64.0), k = 16.0 * std::ceil(m / 16.0);
-            f += 2.0 * 64.0 * 64.0 * k * T * (T + 1.0) / 2.0;
+            t += 2.0 * 64.0 * 64.0 * k * T * (T + 1.0) / 2.0 / 1.2e6;   // flops / (1.2e12 / 1e6)
         } else {
-            const double T = std::ceil(m / 128.0), k = 32.0 * std::ceil(m / 32.0);
-            const double nprod = prec == GBE_PREC_FP16X6 ? 6.0 : 3.0;
-            f += nprod * 2.0 * 128.0 * 128.0 * k * T * (T + 1.0) / 2.0;
+            const double T = std::ceil(m / 128.0), nk = std::ceil(m / 32.0);
+            const double c = prec == GBE_PREC_FP16X6 ? 0.6 : 0.3;
+            t += T * (T + 1.0) / 2.0 * std::max(7.5, c * nk) / (double)sm_count;
         }
     }
-    return f;
+    return t;
 }
 
 }  // namespace
@@ -172,7 +181,7 @@ extern "C" int gbe_partition_autotune(gbe_ctx* ctx, const gbe_graph* S, const gb
             gbe_free_parts(P);
             continue;
         }
-        cost[i] = step_flops(prec, P->h_sub_ptr);
+        cost[i] = step_time_us(prec, ctx->sm_count, P->h_sub_ptr);
         if (*best < 0 || cost[i] < cost[*best]) {
             gbe_free_parts(keep);
             keep = P;

@@ -189,9 +189,10 @@ def test_partition_capacity_error(ctx, lat):
 @pytest.mark.parametrize("prec", [gbe.PREC_FP16X6, gbe.PREC_FP64])
 def test_partition_autotune_picks_cheapest(ctx, prec):
     """Cost-driven partition size on the 16^3 lattice (|H^2| >= 0.15 graph): every candidate
-    cell grid is partitioned and costed by the squaring work of one SP2 step (checked here
-    against the formula on the exported subgraph sizes); a grid whose subgraphs exceed what
-    the gather holds (one cell: 4096 sites) is infeasible; the cheapest one is returned."""
+    cell grid is partitioned and costed by the modelled squaring time of one SP2 step
+    (checked here against the formula on the exported subgraph sizes); a grid whose
+    subgraphs exceed what the gather holds (one cell: 4096 sites) is infeasible; the cheapest
+    one is returned."""
     w = synth.lattice(16, seed=3)
     st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
     Hg = gbe.build_hamiltonian(ctx, st)
@@ -204,10 +205,10 @@ def test_partition_autotune_picks_cheapest(ctx, prec):
         m = np.diff(sp).astype(np.float64)
         if prec == gbe.PREC_FP64:
             T, k = np.ceil(m / 64), 16 * np.ceil(m / 16)
-            want = np.sum(2 * 64 * 64 * k * T * (T + 1) / 2)
+            want = np.sum(2 * 64 * 64 * k * T * (T + 1) / 2 / 1.2e6)
         else:
-            T, k = np.ceil(m / 128), 32 * np.ceil(m / 32)
-            want = np.sum(6 * 2 * 128 * 128 * k * T * (T + 1) / 2)
+            T, nk = np.ceil(m / 128), np.ceil(m / 32)
+            want = np.sum(T * (T + 1) / 2 * np.maximum(7.5, 0.6 * nk)) / ctx.sm_count
         np.testing.assert_allclose(cost[i], want, rtol=1e-12)
     assert best == int(np.argmin(cost))
     cc, sp, si = parts.export()
