@@ -337,7 +337,7 @@ typedef struct {
 int gbe_subs_get_config(const gbe_subs* X, gbe_tc_config* cfg);
 int gbe_subs_set_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config* cfg);
 
-/* Autotuner (spec batching requirement, not in the paper): time every built
+/* Autotuner (not in the paper; the paper runs one dense GEMM per submatrix): time every built
  * configuration of X's precision on the caller's own problem and install the fastest.
  * One SP2 run with `params` (its branch decisions as given) fixes the branch sequence;
  * every candidate then replays that sequence without FP64 tail steps, twice untimed (the
