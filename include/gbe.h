@@ -342,8 +342,9 @@ int gbe_subs_set_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config* cfg);
  * One SP2 run with `params` (its branch decisions as given) fixes the branch sequence;
  * every candidate then replays that sequence without FP64 tail steps, twice untimed (the
  * second run captures its CUDA graphs) and `reps` times timed with CUDA events on the
- * context stream, so all candidates do the same work.  The choice is cached in the context under the state's shape (precision,
- * SM count, subgraph sizes): states created later with the same shape start with it, and
+ * context stream, so all candidates do the same work.  The choice is cached in the
+ * context under the state's shape (precision, SM count, subgraph sizes): states created
+ * later with the same shape start with it, and
  * a later autotune of such a state returns the cached choice without timing (rep->cached).
  * Afterwards X holds the last candidate's iterates: run gbe_sp2_run again for a result.
  * H must be device CSR.  Synchronises.  FP64 states: nothing to tune (one candidate). */
