@@ -188,8 +188,9 @@ int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* 
  * over subgraphs of T_s (T_s + 1) / 2 upper tiles (T_s = ceil(m_s / 128)) times
  * max(7.5, c ceil(m_s / 32)) / (number of SMs), c = 0.6 (FP16X6) or 0.3 (BF16X3): a tile's
  * epilogue against its MMAs, fitted to GB300 runs; GBE_PREC_FP64 the FP64 flops
- * 2 x 64^2 x 16 ceil(m_s / 16) per upper 64 x 64 tile at 1.2 TFLOP/s.  A candidate whose partition fails (a subgraph above max_sub or
- * above the 2432 vertices the gather holds) costs +inf.  cost[ncand] receives the costs,
+ * 2 x 64^2 x 16 ceil(m_s / 16) per upper 64 x 64 tile at 1.2 TFLOP/s.  A candidate whose
+ * partition fails (a subgraph above max_sub or above the 2432 vertices the gather holds)
+ * costs +inf.  cost[ncand] receives the costs,
  * *best the index of the cheapest and *parts its partition (library-owned; NULL and
  * GBE_ECAPACITY when every candidate failed).  Not in the paper as an algorithm: the paper
  * uses METIS with a chosen number of communities. */
