@@ -576,6 +576,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
     const uint16_t* pl = cur ? planes1 : planes0;
     const double* f = cur ? f1 : f0;
     const int lane = threadIdx.x & 31;
+    __shared__ double abuf[8][32 * 9];
     if (j < c && drop_tol <= 0.0) {
         // every entry kept, in local order: lane takes 8 consecutive k; in an upper block
         // they are one 16-byte run per plane (64 bytes of FP64)
@@ -583,9 +584,12 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
         int32_t* oc = ell_col + row * width;
         double* ov = ell_val + row * width;
         const int jb = j >> 7;
-        for (int k0 = 8 * lane; k0 < m; k0 += 256) {
-            double v[8];
-            if ((k0 >> 7) >= jb) {
+        for (int kb0 = 0; kb0 < m; kb0 += 256) {   // warp-uniform trip count
+            const int k0 = kb0 + 8 * lane;
+            double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            if (k0 >= m) {
+                // past the row's end: nothing to load (k0 + 7 < mpad holds for k0 < m only)
+            } else if ((k0 >> 7) >= jb) {
                 const int64_t e = blk_index(off, mpad, j, k0);
                 if (fmt == 1) {
 #pragma unroll
@@ -620,12 +624,22 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
 #pragma unroll
                 for (int t = 0; t < 8; ++t) v[t] = load_x(fmt, prec, pl, plane_stride, f, off, mpad, j, k0 + t);
             }
+            // through shared memory (rows of 9 doubles: at most 2-way bank conflicts) so that
+            // each store instruction writes 32 consecutive entries of the ELL row
+            double* tb = abuf[threadIdx.x >> 5];
+            __syncwarp();
 #pragma unroll
-            for (int t = 0; t < 8; ++t)
-                if (k0 + t < m) {
-                    oc[k0 + t] = sub_idx[base + k0 + t];
-                    ov[k0 + t] = scale == 1.0 ? v[t] : v[t] * scale;
+            for (int t = 0; t < 8; ++t) tb[9 * lane + t] = v[t];
+            __syncwarp();
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int pidx = lane + 32 * q, k = kb0 + pidx;
+                if (k < m) {
+                    const double x = tb[9 * (pidx >> 3) + (pidx & 7)];
+                    oc[k] = sub_idx[base + k];
+                    ov[k] = scale == 1.0 ? x : x * scale;
                 }
+            }
         }
         for (int p = m + lane; p < width; p += 32) {
             oc[p] = -1;
