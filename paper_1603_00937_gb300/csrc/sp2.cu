@@ -369,13 +369,23 @@ __device__ __forceinline__ double f32_to_f64_int(float x) {
     return __longlong_as_double((long long)b);
 }
 
-// The values of oz_value / bf_value with one FP64 addition each (the narrow FP64 pipe is
+// The values of oz_value / bf_value with at most one FP64 addition (the narrow FP64 pipe is
 // what bounds an element-wise pass over the planes): s1 + s2 is exact in FP32 (s2 is the
-// fp16 rounding residual of s1, the two significands span at most 22 bits), and both sums
+// fp16 rounding residual of s1, the two significands span at most 22 bits), and the sums
 // are exact in FP64.
+// FP16X6 without any FP64 instruction: s0 = k0 2^-10 and s1 + s2 = R 2^-24 exactly (fp16
+// values on the split's grids), so x = (k0 2^25 + R) 2^-35 with an integer below 2^36 that
+// is normalised into the FP64 bit pattern directly.
 __device__ __forceinline__ double oz_value_fast(uint16_t s0, uint16_t s1, uint16_t s2) {
-    const float r = (h_val(s1) + h_val(s2)) * (1.0f / 2048.0f);
-    return f32_to_f64_int(h_val(s0)) + f32_to_f64_int(r);
+    const long long k0 = (long long)__float2int_rn(h_val(s0) * 1024.0f);
+    const long long R = (long long)__float2int_rn((h_val(s1) + h_val(s2)) * 16777216.0f);
+    const long long total = (k0 << 25) + R;
+    if (total == 0) return 0.0;
+    const unsigned long long sign = total < 0 ? 1ull : 0ull;
+    const unsigned long long mag = (unsigned long long)(total < 0 ? -total : total);
+    const int e = 63 - __clzll((long long)mag);   // top bit, below 36
+    const unsigned long long mant = (mag << (52 - e)) & 0xFFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)((sign << 63) | ((unsigned long long)(e - 35 + 1023) << 52) | mant));
 }
 
 __device__ __forceinline__ double bf_value_fast(uint16_t hi, uint16_t lo) {
@@ -584,6 +594,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
         int32_t* oc = ell_col + row * width;
         double* ov = ell_val + row * width;
         const int jb = j >> 7;
+        const bool unit_scale = (scale == 1.0);
         for (int kb0 = 0; kb0 < m; kb0 += 256) {   // warp-uniform trip count
             const int k0 = kb0 + 8 * lane;
             double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -637,7 +648,7 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
                 if (k < m) {
                     const double x = tb[9 * (pidx >> 3) + (pidx & 7)];
                     oc[k] = sub_idx[base + k];
-                    ov[k] = scale == 1.0 ? x : x * scale;
+                    ov[k] = unit_scale ? x : x * scale;
                 }
             }
         }
