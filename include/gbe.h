@@ -190,10 +190,10 @@ int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* 
  * epilogue against its MMAs, fitted to GB300 runs; GBE_PREC_FP64 the FP64 flops
  * 2 x 64^2 x 16 ceil(m_s / 16) per upper 64 x 64 tile at 1.2 TFLOP/s.  A candidate whose
  * partition fails (a subgraph above max_sub or above the 2432 vertices the gather holds)
- * costs +inf.  cost[ncand] receives the costs,
- * *best the index of the cheapest and *parts its partition (library-owned; NULL and
- * GBE_ECAPACITY when every candidate failed).  Not in the paper as an algorithm: the paper
- * uses METIS with a chosen number of communities. */
+ * costs +inf; any other error of gbe_partition (an invalid candidate) is returned.
+ * cost[ncand] receives the costs, *best the index of the cheapest and *parts its partition
+ * (library-owned; NULL and GBE_ECAPACITY when every candidate failed).  Not in the paper as
+ * an algorithm: the paper uses METIS with a chosen number of communities. */
 int gbe_partition_autotune(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* params, int prec,
                            const int32_t* candidates, int ncand, double* cost, int* best, gbe_parts** parts);
 /* Sizes: number of subgraphs P, total local indices, max subgraph size. */

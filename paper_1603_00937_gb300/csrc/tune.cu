@@ -172,7 +172,7 @@ extern "C" int gbe_partition_autotune(gbe_ctx* ctx, const gbe_graph* S, const gb
         gbe_parts* P = nullptr;
         const int r = gbe_partition(ctx, S, &p, &P);
         cost[i] = std::numeric_limits<double>::infinity();
-        if (r == GBE_ECAPACITY || r == GBE_EINVAL) continue;   // infeasible (or meaningless) candidate
+        if (r == GBE_ECAPACITY) continue;   // infeasible candidate (a subgraph above max_sub)
         if (r != GBE_OK) {
             gbe_free_parts(keep);
             return r;
