@@ -162,44 +162,59 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
         __syncwarp();
         if (a < m) {
             const int64_t gi = sidx[a];
-            for (int64_t p = rowptr[gi] + lane; p < rowptr[gi + 1]; p += 32) {
-                const int b = hash_local(htab, hbits, col[p]);
-                if (b < 0) continue;
-                const double h = val[p];
-                uint2 packed;
-                if constexpr (prec == GBE_PREC_FP64) {
-                    // the exact quotients, as the FP64 oracle computes them
-                    const double x = foe ? (h - (a == b ? centre : 0.0)) / half : ((a == b ? emax : 0.0) - h) / range;
-                    if (a < c) {
-                        t2 += x * x;
-                        if (a == b) t1 += x;
-                    }
-                    packed = make_uint2((uint32_t)__double2loint(x), (uint32_t)__double2hiint(x));
-                } else {
-                    // split paths need x to ~2^-35: off-diagonal x = -h / range as an FP32 pair
-                    // product (no FP64 arithmetic: this part's FP64 pipe is narrow); the diagonal
-                    // (one entry per row) in FP64
-                    float xh, xl;
-                    if (a == b) {
-                        const double x = (shift - h) * gsc;
-                        f64_to_f32_pair(x, xh, xl);
-                        if (a < c) t1 += x;
-                    } else {
-                        float hh, hl;
-                        f64_to_f32_pair(h, hh, hl);
-                        neg_mul_pair(hh, hl, ih, il, xh, xl);
-                    }
-                    if (a < c) df_add_sq(t2h, t2l, xh, xl, 1.0f);
-                    if constexpr (prec == GBE_PREC_FP16X6) {
-                        const OzSplit o = oz_split_pq(xh, xl);
-                        packed = make_uint2((uint32_t)o.s0 | ((uint32_t)o.s1 << 16), (uint32_t)o.s2 | ((uint32_t)o.s1s << 16));
-                    } else {
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(xh);
-                        const uint16_t lo = b_bits(__float2bfloat16_rn((xh - __bfloat162float(hi)) + xl));
-                        packed = make_uint2((uint32_t)b_bits(hi) | ((uint32_t)lo << 16), 0u);
-                    }
+            const int64_t r0 = rowptr[gi], r1 = rowptr[gi + 1];
+            for (int64_t p0 = r0 + lane; p0 < r1; p0 += 96) {
+                // this lane's entries p0, p0 + 32, p0 + 64: their loads are issued together,
+                // then the entries are taken in that order (the order the traces add them)
+                int cj[3];
+                double hv[3];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int64_t p = p0 + 32 * u;
+                    cj[u] = p < r1 ? col[p] : -1;
+                    hv[u] = p < r1 ? val[p] : 0.0;
                 }
-                rowbuf[b] = packed;
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    if (cj[u] < 0) continue;
+                    const int b = hash_local(htab, hbits, cj[u]);
+                    if (b < 0) continue;
+                    const double h = hv[u];
+                    uint2 packed;
+                    if constexpr (prec == GBE_PREC_FP64) {
+                        // the exact quotients, as the FP64 oracle computes them
+                        const double x = foe ? (h - (a == b ? centre : 0.0)) / half : ((a == b ? emax : 0.0) - h) / range;
+                        if (a < c) {
+                            t2 += x * x;
+                            if (a == b) t1 += x;
+                        }
+                        packed = make_uint2((uint32_t)__double2loint(x), (uint32_t)__double2hiint(x));
+                    } else {
+                        // split paths need x to ~2^-35: off-diagonal x = -h / range as an FP32 pair
+                        // product (no FP64 arithmetic: this part's FP64 pipe is narrow); the diagonal
+                        // (one entry per row) in FP64
+                        float xh, xl;
+                        if (a == b) {
+                            const double x = (shift - h) * gsc;
+                            f64_to_f32_pair(x, xh, xl);
+                            if (a < c) t1 += x;
+                        } else {
+                            float hh, hl;
+                            f64_to_f32_pair(h, hh, hl);
+                            neg_mul_pair(hh, hl, ih, il, xh, xl);
+                        }
+                        if (a < c) df_add_sq(t2h, t2l, xh, xl, 1.0f);
+                        if constexpr (prec == GBE_PREC_FP16X6) {
+                            const OzSplit o = oz_split_pq(xh, xl);
+                            packed = make_uint2((uint32_t)o.s0 | ((uint32_t)o.s1 << 16), (uint32_t)o.s2 | ((uint32_t)o.s1s << 16));
+                        } else {
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(xh);
+                            const uint16_t lo = b_bits(__float2bfloat16_rn((xh - __bfloat162float(hi)) + xl));
+                            packed = make_uint2((uint32_t)b_bits(hi) | ((uint32_t)lo << 16), 0u);
+                        }
+                    }
+                    rowbuf[b] = packed;
+                }
             }
         }
         if constexpr (prec == GBE_PREC_FP64) {
