@@ -268,7 +268,10 @@ typedef struct {
 } gbe_sp2_report;
 
 /* Allocate the SP2 state for a partition and precision (dense padded tiles in HBM,
- * ping-pong buffers, trace partials, device control block).  Reusable across calls. */
+ * ping-pong buffers, trace partials, device control block).  Reusable across calls.  A
+ * mixed-precision state allocates its FP64 iterates only when a run first needs FP64 steps
+ * (fp64_tail > 0); a state starts with the launch configuration the context's autotuner
+ * cache holds for its shape, if any (gbe_sp2_autotune). */
 int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, gbe_subs** X);
 int gbe_free_subs(gbe_subs* X);
 
