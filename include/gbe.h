@@ -26,6 +26,12 @@
  *     GBE_ENODEV and every other call GBE_EINVAL on a NULL context.
  *   - Device-side waits are bounded; a wait that runs out reports GBE_ETIMEOUT and the
  *     context remains usable.
+ *
+ * Two tuners sit beside the method (neither is in the paper): gbe_sp2_autotune picks the
+ * launch configuration of the batched squaring on the caller's problem (results are bit
+ * for bit the same under every configuration), and gbe_partition_autotune picks the
+ * partition size by a cost model of these kernels (a different partition: the truncation
+ * of the graph-based expansion changes with it, as the paper's Sec. II.B describes).
  */
 #ifndef GBE_H
 #define GBE_H
