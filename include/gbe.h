@@ -30,8 +30,9 @@
  * Two tuners sit beside the method (neither is in the paper): gbe_sp2_autotune picks the
  * launch configuration of the batched squaring on the caller's problem (results are bit
  * for bit the same under every configuration), and gbe_partition_autotune picks the
- * partition size by a cost model of these kernels (a different partition: the truncation
- * of the graph-based expansion changes with it, as the paper's Sec. II.B describes).
+ * partition size by a cost model of these kernels (a different partition changes D within
+ * the truncation error of the graph, which Sec. II.B finds fairly insensitive to the
+ * number of communities).
  */
 #ifndef GBE_H
 #define GBE_H
