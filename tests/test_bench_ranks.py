@@ -64,3 +64,25 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["unit"] == "orbitals/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_traffic_record_voided_by_source_change(tmp_path, monkeypatch):
+    """The roofline's DRAM-traffic figure comes from a committed ncu record only while the
+    squaring kernel's sources hash to the value stored with it; any change voids it (null)."""
+    import shutil
+    sys.path.insert(0, ROOT)
+    import bench
+    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic_sp2_square_tc_fp16x6_lattice32.json")))
+    root = tmp_path / "repo"
+    (root / "profiles").mkdir(parents=True)
+    shutil.copy(os.path.join(ROOT, "profiles", "traffic_sp2_square_tc_fp16x6_lattice32.json"), root / "profiles")
+    for src in rec["sources"]:
+        (root / src).parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(ROOT, src), root / src)
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    t = bench.captured_traffic("sp2_square_tc_fp16x6", "lattice32")
+    assert t == sum(rec["dram_bytes_per_launch"]) / len(rec["dram_bytes_per_launch"])
+    with open(root / rec["sources"][0], "a") as f:
+        f.write("\n// changed\n")
+    assert bench.captured_traffic("sp2_square_tc_fp16x6", "lattice32") is None
+    assert bench.captured_traffic("sp2_square_tc_fp16x6", "no_such_workload") is None
