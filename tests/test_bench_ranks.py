@@ -1,10 +1,13 @@
-"""Host logic of bench.py's multi-process mode on CPU (gloo, world size 2): the whole-job
-time is the maximum over ranks, and the reference arm prints from rank 0 only."""
+"""Host logic of bench.py on CPU: in multi-process mode (gloo, world size 2) the whole-job
+time is the maximum over ranks, the reference arm prints from rank 0 only, and a clock
+record that voids a timing on any rank makes every rank measure again; the nvidia-smi
+clock summary and its verdict; the traffic record's tie to the kernel sources."""
 import json
 import os
 import socket
 import subprocess
 import sys
+import time
 
 import pytest
 
@@ -86,3 +89,78 @@ def test_traffic_record_voided_by_source_change(tmp_path, monkeypatch):
         f.write("\n// changed\n")
     assert bench.captured_traffic("sp2_square_tc_fp16x6", "lattice32") is None
     assert bench.captured_traffic("sp2_square_tc_fp16x6", "no_such_workload") is None
+
+
+def _smi(sm, smax, hw="Not Active", hwt="Not Active", swt="Not Active", pcap="Not Active"):
+    """One line of nvidia-smi's CSV for the sampler's query (noheader, nounits)."""
+    return "0, %s, %s, 1100.5, 0x0, %s, %s, %s, %s" % (sm, smax, hw, hwt, swt, pcap)
+
+
+def test_clock_summary_and_verdict():
+    sys.path.insert(0, ROOT)
+    import bench
+    lines = [_smi(2070, 2070), _smi(1980, 2070, pcap="Active"), _smi(2055, 2070), "garbage", "",
+             _smi("[N/A]", 2070), "0, 2070, 2070"]
+    clk = bench.summarize_clock_lines(lines)
+    assert clk == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.clock_verdict(clk) is None                      # the power cap is kept, not rejected
+    for field in ("hw", "hwt", "swt"):
+        c = bench.summarize_clock_lines([_smi(2070, 2070), _smi(1900, 2070, **{field: "Active"})])
+        assert bench.clock_verdict(c).startswith("throttled: ")
+    stuck = bench.summarize_clock_lines([_smi(1200, 2070)] * 5)
+    assert stuck["reasons"] == [] and "1200 of 2070" in bench.clock_verdict(stuck)
+    # a low clock with a reason reported is the power cap's doing, not a lock
+    assert bench.clock_verdict(bench.summarize_clock_lines([_smi(1500, 2070, pcap="Active")] * 5)) is None
+    assert bench.summarize_clock_lines([]) == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    assert bench.clock_verdict({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}) is None
+
+
+def _verdict_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # only rank 1 saw a slowdown: both ranks must take the re-measure branch together
+        clk = bench.summarize_clock_lines([_smi(2070, 2070, hwt="Active" if rank == 1 else "Not Active")])
+        why = bench.clock_verdict(clk)
+        out[rank] = bench.max_over_ranks(1.0 if why else 0.0, world) > 0
+    finally:
+        dist.destroy_process_group()
+
+
+def test_remeasure_decision_is_collective():
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_verdict_worker, args=(2, free_port(), out), nprocs=2, start_method="spawn")
+        assert dict(out) == {0: True, 1: True}
+
+
+def test_clock_sampler_with_fake_smi(tmp_path, monkeypatch):
+    """The sampler against a stand-in nvidia-smi on PATH: it waits for the first sample,
+    drops what was read before the region, and summarises what came during it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    # the first line (read before the region opens) reports a slowdown that must not count
+    fake.write_text("#!/bin/sh\n"
+                    "echo '%s'\n"
+                    "while true; do echo '%s'; sleep 0.05; done\n"
+                    % (_smi(900, 2070, hwt="Active"), _smi(2070, 2070, pcap="Active")))
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", str(tmp_path) + os.pathsep + os.environ["PATH"])
+    s = bench.ClockSampler(0)
+    s.start()
+    assert s.first.is_set()
+    time.sleep(0.5)
+    clk = s.stop()
+    assert clk["samples"] >= 3 and clk["sm_mhz"] == 2070.0 and clk["reasons"] == ["sw_power_cap"]
+    assert bench.clock_verdict(clk) is None
+    assert s.proc.poll() is not None
+    # no nvidia-smi at all: the record says so and voids nothing
+    monkeypatch.setenv("PATH", str(tmp_path / "empty"))
+    s = bench.ClockSampler(0)
+    s.start()
+    clk = s.stop()
+    assert clk["reasons"] == ["nvidia-smi unavailable"] and bench.clock_verdict(clk) is None
