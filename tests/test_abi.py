@@ -41,6 +41,18 @@ def test_strerror_names_codes(lib):
     import paper_1603_00937_gb300 as gbe
     assert lib.gbe_strerror(gbe.GBE_ETIMEOUT).decode() == "device wait timed out"
     assert lib.gbe_strerror(0).decode() == "ok"
+    # every code the header defines has its own name, and the binding's constants agree
+    with open(os.path.join(ROOT, "include", "gbe.h")) as f:
+        codes = dict(re.findall(r"#define\s+(GBE_(?:OK|E[A-Z]+))\s+(-?\d+)", f.read()))
+    assert len(codes) >= 9
+    names = set()
+    for name, val in codes.items():
+        assert getattr(gbe, name) == int(val), name
+        msg = lib.gbe_strerror(int(val)).decode()
+        assert msg != "unknown error", name
+        names.add(msg)
+    assert len(names) == len(codes)
+    assert lib.gbe_strerror(-99).decode() == "unknown error"
 
 
 def test_create_without_gpu_fails_loudly(lib):
