@@ -16,13 +16,17 @@ def dense_pattern(G):
 
 
 def test_h2_threshold_brute_force():
-    _, H = small_h()
-    Hd = H.toarray()
-    H2 = Hd @ Hd
-    for thr in (1e-5, 1e-2, 0.3):
-        ref = (np.abs(H2) >= thr) | np.eye(len(Hd), dtype=bool)
-        ref = ref | ref.T
-        np.testing.assert_array_equal(dense_pattern(graph.h2_threshold(H, thr)), ref)
+    w = synth.disordered(150, seed=3)
+    for H in (small_h()[1], hamiltonian.build_h(w["pos"], w["box"], w["onsite"])):
+        Hd = H.toarray()
+        H2 = Hd @ Hd
+        for thr in (1e-5, 1e-2, 0.3):
+            ref = (np.abs(H2) >= thr) | np.eye(len(Hd), dtype=bool)
+            ref = ref | ref.T
+            np.testing.assert_array_equal(dense_pattern(graph.h2_threshold(H, thr)), ref)
+    # the disordered case has (H^2)_ij <= -thr entries, so a threshold on the signed value
+    # rather than the magnitude (Eq. 2 reading) fails above
+    assert (H2 <= -0.3).any()
 
 
 def test_d_threshold_symmetrises():
@@ -61,11 +65,14 @@ def test_lattice_cores_are_2x2x2_blocks():
 
 
 def test_halo_brute_force():
-    _, H = small_h(L=4, seed=2)
-    S = graph.h2_threshold(H, 1e-2)
+    _, H = small_h(L=6, seed=2)
+    S = graph.h2_threshold(H, 1.0)
     Sd = dense_pattern(S)
     cores = partition.block_cores(H.shape[0], 7)
     subs, nc = partition.subgraphs(S, cores)
+    # a sparse graph (about 34 of 216 neighbours per vertex): core members' neighbourhoods
+    # differ, so a halo of one member alone, or of the wrong members, fails below
+    assert max(len(idx) for idx in subs) < H.shape[0] // 2
     for C, idx, c in zip(cores, subs, nc):
         assert c == len(C)
         np.testing.assert_array_equal(idx[:c], C)

@@ -54,6 +54,23 @@ def test_fp16_rounding_of_weights():
     assert r[0] == 1.0 and r[2] == 65504.0 and abs(r[1] - 0.1) < 1e-4
 
 
+def test_rounded_network_uses_fp16_weights():
+    """The default (rounded) forward pass and gradient are those of the network whose
+    weights are the parameters rounded to IEEE half precision (numpy's float16 cast)."""
+    h = 8
+    rng = np.random.default_rng(6)
+    p = rng.normal(0, 0.5, mlp.n_params(h))
+    ph = p.astype(np.float16).astype(np.float64)
+    assert np.any(ph != p)
+    F, y = small_batch()
+    np.testing.assert_array_equal(mlp.forward(p, F, h), mlp.forward(ph, F, h, rounded=False))
+    assert np.abs(mlp.forward(p, F, h) - mlp.forward(p, F, h, rounded=False)).max() > 1e-6
+    l1, g1 = mlp.loss_and_grad(p, F, y, h=h)
+    l2, g2 = mlp.loss_and_grad(ph, F, y, h=h, rounded=False)
+    assert l1 == l2
+    np.testing.assert_array_equal(g1, g2)
+
+
 def test_pairs_and_features_symmetric():
     w = synth.disordered(300, seed=4)
     H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])

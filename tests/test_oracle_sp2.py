@@ -189,6 +189,24 @@ def test_graph_assembly_support_and_trace(c1):
     assert log.e[-1] < 1e-10
 
 
+def test_graph_traces_are_core_traces(c1):
+    """The cores partition the vertices, so the global traces of graph SP2 sum each
+    subgraph's diagonal over its core positions only: at step 0 they are Tr X_0 and
+    Tr X_0^2 of the whole matrix (each core's halo holds all its neighbours in H, so
+    (x_s^2)_jj is the full row-times-column product)."""
+    w, H = c1
+    N = H.shape[0]
+    S = graph.h2_threshold(H, 1e-5)
+    cores = partition.spatial_cores(w["pos"], w["box"], (4, 4, 4))
+    subs, nc = partition.subgraphs(S, cores)
+    assert sum(nc) == N and max(len(s) for s in subs) < N
+    lo, hi = sp2.gershgorin(H)
+    X0 = (hi * np.eye(N) - H.toarray()) / (hi - lo)
+    _, log = sp2.sp2_graph(H, subs, nc, N // 2, seq=[1])
+    assert abs(log.t1[0] - np.trace(X0)) < 1e-11
+    assert abs(log.t2[0] - np.sum(X0 * X0)) < 1e-11      # Tr X0^2 of a symmetric X0
+
+
 def test_free_mode_stall_rule():
     log = sp2.Log()
     # e values fall then rise: stall must fire at the first n >= n_min with e_n >= e_{n-2}
