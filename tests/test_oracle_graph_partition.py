@@ -47,6 +47,12 @@ def test_eq8_and_hk_brute_force():
     P = ((Hd != 0) | np.eye(len(Hd), dtype=bool)).astype(int)
     ref3 = (P @ P @ P) > 0
     np.testing.assert_array_equal(dense_pattern(graph.hk_pattern(H, 3)), ref3)
+    # a 1-D chain, where the pattern of H^k is the band |i - j| <= k (closed form)
+    n = 16
+    T = sp.diags([np.ones(n - 1), np.ones(n), np.ones(n - 1)], [-1, 0, 1]).tocsr()
+    band = np.abs(np.subtract.outer(np.arange(n), np.arange(n)))
+    for k in (1, 2, 3, 5):
+        np.testing.assert_array_equal(dense_pattern(graph.hk_pattern(T, k)), band <= k)
 
 
 def test_cell_ids_closed_form():

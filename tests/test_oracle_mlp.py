@@ -71,6 +71,14 @@ def test_rounded_network_uses_fp16_weights():
     np.testing.assert_array_equal(g1, g2)
 
 
+def test_labels_threshold_the_magnitude():
+    D = np.array([[0.5, -0.02, 1e-3], [0.01, 0.5, -1e-5], [0.0, 0.3, -0.5]])
+    I = np.array([0, 0, 1, 1, 2, 2, 0])
+    J = np.array([1, 2, 0, 2, 0, 1, 0])
+    np.testing.assert_array_equal(mlp.labels(D, I, J, 1e-2), [1, 0, 1, 0, 0, 1, 1])
+    np.testing.assert_array_equal(mlp.labels(sp.csr_matrix(D), I, J, 1e-5), [1, 1, 1, 1, 0, 1, 1])
+
+
 def test_pairs_and_features_symmetric():
     w = synth.disordered(300, seed=4)
     H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])

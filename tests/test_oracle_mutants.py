@@ -55,15 +55,17 @@ def c1(pins):
 
 
 def run_pins(specs):
-    """Run pin functions; return the names of those that failed an assertion."""
+    """Run pin functions; return (name, exception type) of those that failed.  A pin that
+    fails by an exception other than an assertion (the planted mistake made the oracle
+    raise, e.g. a sequence that never converges) also counts: the suite goes red."""
     failed = []
     for modname, fname, *args in specs:
         m = sys.modules[modname]
         call = [c1(m) if a == "c1" else a for a in args]
         try:
             getattr(m, fname)(*call)
-        except AssertionError:
-            failed.append(fname)
+        except Exception as e:   # noqa: BLE001
+            failed.append((fname, type(e).__name__))
     return failed
 
 
@@ -150,6 +152,60 @@ CASES = [
     ("exact-occupies-top-levels", "oracle.exact",
      [("Vo = V[:, :n_occ]", "Vo = V[:, -n_occ:]")],
      [(SP2, "test_dense_sp2_matches_eigh_and_projector_invariants", "c1")]),
+    ("thresholded-squares-not-thresholded", "oracle.sp2",
+     [("Sq = threshold_to(X @ X, S)", "Sq = (X @ X).tocsr()")],
+     [(SP2, "test_thresholded_sp2_one_step_equals_graph_sp2", "c1", 1)]),
+    ("thresholded-branch-applied-as-square", "oracle.sp2",
+     [("X = Sq if b else (2.0 * X - Sq).tocsr()", "X = Sq")],
+     [(SP2, "test_thresholded_sp2_one_step_equals_graph_sp2", "c1", 0)]),
+    ("gap-sequence-stops-on-one-level", "oracle.sp2",
+     [("while not (1.0 - xh <= tol and xl <= tol):", "while not (1.0 - xh <= tol or xl <= tol):")],
+     [(SEQ, "test_gap_sequence_gives_step_function"), (SEQ, "test_gap_sequence_on_lattice_matches_eigh")]),
+    ("gap-sequence-two-occupied-levels", "oracle.sp2",
+     [("b = choose_square(xh + xl, xh * xh + xl * xl, 1.0)", "b = choose_square(xh + xl, xh * xh + xl * xl, 2.0)")],
+     [(SEQ, "test_gap_sequence_gives_step_function")]),
+    ("fermi-sign", "oracle.sp2",
+     [("return 0.5 * (1.0 - np.tanh(0.5 * z))", "return 0.5 * (1.0 + np.tanh(0.5 * z))")],
+     [(FOE, "test_fermi_function_closed_form")]),
+    ("foe-half-width-doubled", "oracle.sp2",
+     [("xs.append(clenshaw_dense((h - a * np.eye(len(idx))) / b, coeffs))",
+       "xs.append(clenshaw_dense((h - a * np.eye(len(idx))) / (2.0 * b), coeffs))")],
+     [(FOE, "test_foe_complete_graph_equals_fermi_of_eigenvalues")]),
+    ("tree-build-one-sided", "oracle.hamiltonian",
+     [("rows = np.concatenate([i, j, np.arange(N)])", "rows = np.concatenate([i, i, np.arange(N)])")],
+     [(HAM, "test_tree_build_equals_brute_force", "lattice")]),
+    ("eq8-paths-of-length-one", "oracle.graph",
+     [("A2 = (A @ A).tocsr()", "A2 = A.tocsr()")],
+     [(GP, "test_eq8_and_hk_brute_force")]),
+    ("eq8-without-h-pattern", "oracle.graph",
+     [("A = (d_threshold(D, tau).astype(np.int64) + pattern(H).astype(np.int64)).tocsr()",
+       "A = d_threshold(D, tau).astype(np.int64).tocsr()")],
+     [(GP, "test_eq8_and_hk_brute_force")]),
+    ("hk-one-power-short", "oracle.graph",
+     [("for _ in range(k - 1):", "for _ in range(k - 2):")],
+     [(GP, "test_eq8_and_hk_brute_force")]),
+    ("h2-rows-without-abs", "oracle.graph",
+     [("R = sp.csr_matrix((np.abs(R.data) >= thresh, R.indices, R.indptr), shape=R.shape)",
+       "R = sp.csr_matrix((R.data >= thresh, R.indices, R.indptr), shape=R.shape)")],
+     [(GP, "test_h2_threshold_rows_equals_full")]),
+    ("candidates-without-minimum-image", "oracle.mlp",
+     [("        d = d - box * np.round(d / box)\n        r = np.sqrt", "        r = np.sqrt")],
+     [(MLP, "test_candidate_pairs_simple_cubic_shells", 1.5, 18)]),
+    ("h2-feature-is-h", "oracle.mlp",
+     [("h2ij = np.asarray(H[I].multiply(H[J]).sum(axis=1)).ravel()", "h2ij = hij")],
+     [(MLP, "test_h2_feature_equals_matrix_square")]),
+    ("onsite-feature-not-symmetrised", "oracle.mlp",
+     [("f[:, 3] = np.minimum(onsite[I], onsite[J])", "f[:, 3] = onsite[I]")],
+     [(MLP, "test_pairs_and_features_symmetric")]),
+    ("hopping-feature-scale", "oracle.mlp",
+     [("f[:, 0] = -np.log10(np.maximum(np.abs(hij), 1e-12)) / 12.0", "f[:, 0] = -np.log10(np.maximum(np.abs(hij), 1e-12)) / 10.0")],
+     [(MLP, "test_pairs_and_features_symmetric")]),
+    ("labels-of-signed-d", "oracle.mlp",
+     [("return (np.abs(np.asarray(D[I, J]).ravel()) >= tau)", "return (np.asarray(D[I, J]).ravel() >= tau)")],
+     [(MLP, "test_labels_threshold_the_magnitude")]),
+    ("graph-from-logits-drops-h", "oracle.mlp",
+     [("return graph._finish(E + graph.pattern(H))", "return graph._finish(E)")],
+     [(MLP, "test_graph_from_logits_limits_and_example")]),
 ]
 
 
@@ -159,3 +215,12 @@ def test_planted_mistake_is_caught(monkeypatch, modname, edits, pins):
     install(monkeypatch, orig, mod)
     failed = run_pins(pins)
     assert failed, "no pin caught the planted mistake"
+
+
+def test_unplanted_oracle_passes_the_same_pins():
+    """Control: every pin call above passes on the real oracle, so a failure under a
+    planted mistake is the mistake's doing (not a mis-specified call)."""
+    for name in PIN_MODULES:
+        importlib.import_module(name)
+    specs = sorted({tuple(p) for c in CASES for p in c[3]}, key=repr)
+    assert run_pins(specs) == []

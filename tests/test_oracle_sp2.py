@@ -136,6 +136,25 @@ def test_one_sp2_step_column_identity(c1):
         np.testing.assert_allclose(col, ref[:, i], rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("bit", [1, 0])
+def test_thresholded_sp2_one_step_equals_graph_sp2(c1, bit):
+    """O3 against O4 where Eq. 6 is exact: after one SP2 step (X^2 or 2X - X^2) the
+    thresholded sparse iterate equals the assembly of single-vertex subgraph iterates, and
+    the threshold bites (the unthresholded step has entries outside S)."""
+    _, H = c1
+    N = H.shape[0]
+    S = graph.h2_threshold(H, 1e-3)
+    subs, nc = partition.subgraphs(S, partition.single_vertex_cores(N))
+    Xt, lt = sp2.sp2_thresholded(H, S, N // 2, seq=[bit])
+    Dg, lg = sp2.sp2_graph(H, subs, nc, N // 2, seq=[bit])
+    assert lt.seq == lg.seq == [bit]
+    assert np.abs(Xt.toarray() - Dg.toarray()).max() < 1e-15
+    X0 = sp2.initial_x(H, sp2.gershgorin(H)).toarray()
+    full = X0 @ X0 if bit else 2 * X0 - X0 @ X0
+    outside = ~S.toarray()
+    assert np.abs(full[outside]).max() > 1e-6 and np.all(Xt.toarray()[outside] == 0.0)
+
+
 def test_chebyshev_graph_identity(c1):
     """Eq. (6) is exact for serial expansions (Eqs. 1, 4, 5): thresholded sparse
     Chebyshev P_tau(X) equals the column assembly of per-vertex dense expansions."""
