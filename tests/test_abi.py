@@ -146,3 +146,30 @@ def test_binding_structs_match_header(tmp_path):
         assert int(got["%s size" % py]) == ctypes.sizeof(S), py
         for f in S._fields_:
             assert int(got["%s.%s" % (py, f[0])]) == getattr(S, f[0]).offset, (py, f[0])
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    import paper_1603_00937_gb300 as gbe
+    monkeypatch.setattr(gbe, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        gbe.load_library(str(tmp_path / "libgbe.so"))
+
+
+def test_product_path_never_touches_the_oracle():
+    """The package neither imports nor names the CPU oracle: importing it loads no oracle
+    module, and no source file of the package or the C headers refers to it."""
+    import sys
+    code = ("import sys; import paper_1603_00937_gb300 as g; g.load_library(); "
+            "bad = [m for m in sys.modules if m == 'oracle' or m.startswith('oracle.')]; "
+            "assert not bad, bad")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    pkg = os.path.join(ROOT, "paper_1603_00937_gb300")
+    files = [os.path.join(d, f) for d, _, fs in os.walk(pkg) if "_build" not in d and "__pycache__" not in d
+             for f in fs if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp"))]
+    files += [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))]
+    assert len(files) >= 10
+    for fn in files:
+        text = open(fn).read()
+        assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), fn
+        assert "oracle/" not in text and '"oracle"' not in text, fn
