@@ -173,3 +173,17 @@ def test_product_path_never_touches_the_oracle():
         text = open(fn).read()
         assert not re.search(r"^\s*(from|import)\s+oracle\b", text, re.M), fn
         assert "oracle/" not in text and '"oracle"' not in text, fn
+
+
+def test_oracle_and_inputs_never_touch_the_package():
+    """The converse: the oracle and the shared seeded-input module import neither the
+    package nor its library, and the input module imports nothing of the oracle."""
+    for sub in ("oracle", "synth"):
+        d = os.path.join(ROOT, sub)
+        for fn in os.listdir(d):
+            if not fn.endswith(".py"):
+                continue
+            text = open(os.path.join(d, fn)).read()
+            assert "paper_1603_00937_gb300" not in text and "libgbe" not in text and "ctypes" not in text, fn
+            if sub == "synth":
+                assert not re.search(r"^\s*(from|import)\s+(oracle|\.)", text, re.M), fn
