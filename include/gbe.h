@@ -102,7 +102,9 @@ typedef struct {
  * when the device is absent or is not compute capability 10.3. */
 int gbe_create(gbe_ctx** ctx, int device, void* cuda_stream);
 int gbe_destroy(gbe_ctx* ctx);
-/* Change the stream later calls are ordered on. */
+/* Change the stream later calls are ordered on.  Device memory of objects created
+ * before the change stays ordered on the stream it was allocated on, and is released on
+ * that stream when the object is freed: keep that stream alive until then. */
 int gbe_set_stream(gbe_ctx* ctx, void* cuda_stream);
 /* Profiling switch: when on, gbe_sp2_run records a CUDA event pair around every
  * squaring launch on the context stream and gbe_sp2_report_get sums the durations of
