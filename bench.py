@@ -566,7 +566,7 @@ def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU leg
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)
@@ -590,7 +590,11 @@ def main():
     ap.add_argument("--record-traffic", metavar="REPORT",
                     help="write the DRAM traffic record of the FP16X6 squaring kernel for --workload "
                          "from this ncu report (no GPU needed), then exit")
-    args = ap.parse_args()
+    return ap.parse_args(argv)
+
+
+def main():
+    args = parse_args()
     if args.record_traffic:
         record_traffic(args.record_traffic, "sp2_square_tc_fp16x6", args.workload,
                        "profiles/sp2_square_tc_%s_%s.md" % (args.prec, args.workload))
