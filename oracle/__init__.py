@@ -19,4 +19,6 @@ Modules
 
 Pins (tests/test_oracle_*.py) tie each function to closed forms, textbook routines,
 brute force and the paper's exact Eq. (6) identity; see the module docstrings.
+tests/test_oracle_mutants.py plants plausible mistakes in these modules' source, one at
+a time, and checks that a pin catches each.
 """
