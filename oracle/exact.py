@@ -8,6 +8,8 @@ import numpy as np
 
 
 def density_matrix(H, n_occ):
+    """Zero-temperature D = theta(mu I - H) (Sec. II.A, the zero-temperature limit of Eq. 7):
+    the projector on the n_occ lowest eigenvectors, by LAPACK eigh.  Returns (D, eigenvalues)."""
     Hd = H.toarray() if hasattr(H, "toarray") else np.asarray(H)
     w, V = np.linalg.eigh(Hd)
     Vo = V[:, :n_occ]
@@ -15,5 +17,7 @@ def density_matrix(H, n_occ):
 
 
 def homo_lumo(H, n_occ):
+    """Highest occupied and lowest unoccupied eigenvalues (the gap that fixes the SP2
+    sequence of the MD run, Sec. II.C)."""
     _, w = density_matrix(H, n_occ)
     return w[n_occ - 1], w[n_occ]

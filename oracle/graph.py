@@ -15,7 +15,9 @@ import scipy.sparse as sp
 
 
 def _finish(A):
-    """Symmetrise, add the diagonal, drop explicit zeros; boolean CSR with sorted indices."""
+    """Symmetrise, add the diagonal, drop explicit zeros; boolean CSR with sorted indices
+    (a graph S_tau has a vertex per row, Sec. II.A; the symmetrised pattern and the
+    diagonal are readings of Eq. 2)."""
     A = sp.csr_matrix(A, dtype=bool)
     A = (A + A.T + sp.identity(A.shape[0], dtype=bool, format="csr")).tocsr()
     A.eliminate_zeros()
@@ -24,7 +26,8 @@ def _finish(A):
 
 
 def pattern(M):
-    """Boolean pattern of the stored entries of a sparse matrix (zeros included)."""
+    """Boolean pattern of the stored entries of a sparse matrix (zeros included; helper of the
+    Eq. 2 / Eq. 8 graphs)."""
     M = sp.csr_matrix(M)
     P = sp.csr_matrix((np.ones(M.nnz, dtype=bool), M.indices.copy(), M.indptr.copy()), shape=M.shape)
     return P
@@ -40,7 +43,8 @@ def h2_threshold(H, thresh):
 
 
 def d_threshold(D, tau):
-    """Pattern of the thresholded density matrix floor(D)_tau: edge if |D_ij| >= tau."""
+    """Pattern of the thresholded density matrix floor(D)_tau: edge if |D_ij| >= tau (Eq. 2 on
+    a prior D, as Sec. II.A estimates S_tau from an approximate prior density matrix)."""
     D = sp.csr_matrix(D, dtype=np.float64)
     keep = np.abs(D.data) >= tau
     A = sp.csr_matrix((keep, D.indices, D.indptr), shape=D.shape)
@@ -61,7 +65,8 @@ def eq8_symbolic(D, H, tau):
 
 
 def hk_pattern(H, k):
-    """Pattern of H^k: vertices joined by a path of length <= k in the pattern of H."""
+    """Pattern of H^k: vertices joined by a path of length <= k in the pattern of H (a graph
+    with extra edges, which obs. iii and viii allow without loss of accuracy)."""
     P = _finish(pattern(H)).astype(np.int64)
     R = P.copy()
     for _ in range(k - 1):
@@ -85,7 +90,7 @@ def complete_blocks(labels):
 
 
 def h2_threshold_rows(H, thresh, rows):
-    """Rows `rows` of h2_threshold(H, thresh), computed from those rows of H^2 alone
+    """Rows `rows` of h2_threshold(H, thresh) (Eq. 2 on H^2), computed from those rows of H^2 alone
     (H^2 is symmetric, so the symmetrisation adds nothing beyond rounding ties); returns
     an N x N boolean CSR whose other rows are empty."""
     H = sp.csr_matrix(H, dtype=np.float64)

@@ -15,19 +15,21 @@ DECAY = 0.3     # in units of a
 
 
 def pair_geometry(pos_i, pos_all, box):
-    """Minimum-image separation vectors and distances from rows pos_i to all sites."""
+    """Minimum-image distances from rows pos_i to all sites (workload model; the paper's
+    SCC-DFTB H of Sec. II.B is not reproduced)."""
     d = pos_i[:, None, :] - pos_all[None, :, :]
     d = d - box * np.round(d / box)
     return np.sqrt(np.einsum("ijk,ijk->ij", d, d))
 
 
 def hopping(r, a=1.0):
-    """Hopping element for separation r (no cutoff applied)."""
+    """Hopping element for separation r (no cutoff applied; workload model, module docstring)."""
     return -1.0 * np.exp(-(r - a) / (DECAY * a))
 
 
 def build_h(pos, box, onsite, a=1.0, rcut=RCUT, rows=None, chunk=1024):
-    """Sparse CSR H (float64, sorted column indices, diagonal stored).
+    """Sparse CSR H of the workload model (module docstring; stands in for Sec. II.B's H),
+    float64, sorted column indices, diagonal stored.
 
     rows: optional subset of row indices; then an [len(rows), N] CSR of those rows.
     """
@@ -55,7 +57,8 @@ def build_h(pos, box, onsite, a=1.0, rcut=RCUT, rows=None, chunk=1024):
 
 
 def build_h_tree(pos, box, onsite, a=1.0, rcut=RCUT):
-    """The same H as build_h for systems too large for its O(N^2) scan.
+    """The same H as build_h (workload model, module docstring) for systems too large for its
+    O(N^2) scan.
 
     Candidate neighbours come from scipy's periodic k-d tree (a library search, queried
     with a radius slightly above the cutoff); every candidate's distance and hopping are

@@ -31,10 +31,12 @@ HIDDEN = 64
 
 
 def n_params(h=HIDDEN):
+    """Length of the flat parameter vector (layout in the module docstring; not in the paper)."""
     return h * NF + h + h * h + h + h + 1
 
 
 def unpack(p, h=HIDDEN):
+    """Views (W1, b1, W2, b2, w3, b3) of the flat parameter vector (layout in the module docstring)."""
     p = np.asarray(p, dtype=np.float64)
     o = 0
     W1 = p[o:o + h * NF].reshape(h, NF); o += h * NF
@@ -47,7 +49,7 @@ def unpack(p, h=HIDDEN):
 
 
 def init_params(seed, h=HIDDEN):
-    """Seeded He-style initialisation (fp32 values)."""
+    """Seeded He-style initialisation (fp32 values; the learned proposal is not in the paper)."""
     rng = np.random.default_rng(seed)
     W1 = rng.normal(0, np.sqrt(2.0 / NF), (h, NF))
     W2 = rng.normal(0, np.sqrt(2.0 / h), (h, h))
@@ -57,11 +59,13 @@ def init_params(seed, h=HIDDEN):
 
 
 def fp16_round(p):
+    """Parameters rounded to IEEE half precision (the weights the forward pass uses; module docstring)."""
     return np.asarray(p, dtype=np.float32).astype(np.float16).astype(np.float64)
 
 
 def candidate_pairs(pos, box, rcand, rows=None):
-    """All ordered pairs (i, j), i != j, with minimum-image distance < rcand; sorted by (i, j).
+    """Candidate edges of the learned graph (module docstring; not in the paper): all ordered
+    pairs (i, j), i != j, with minimum-image distance < rcand; sorted by (i, j).
 
     rows: optional ascending subset of i (all rows by default)."""
     N = len(pos)
@@ -76,7 +80,7 @@ def candidate_pairs(pos, box, rcand, rows=None):
 
 
 def features(H, onsite, I, J, R, rcand):
-    """Feature matrix [npairs, 5] (FP64).
+    """Feature matrix [npairs, 5] (FP64) of the module docstring.
 
     (H^2)_ij = sum_k H_ik H_kj is taken as the dot product of rows i and j (H is
     symmetric), so H may hold only the rows of the sites the pairs touch."""
@@ -93,6 +97,7 @@ def features(H, onsite, I, J, R, rcand):
 
 
 def forward(p, F, h=HIDDEN, cache=False, rounded=True):
+    """Logits z of the width-h network for the feature rows F (module docstring)."""
     W1, b1, W2, b2, w3, b3 = unpack(fp16_round(p) if rounded else p, h)
     a1 = F @ W1.T + b1
     h1 = np.maximum(a1, 0.0)
@@ -103,12 +108,13 @@ def forward(p, F, h=HIDDEN, cache=False, rounded=True):
 
 
 def bce_loss(z, y):
-    """Mean binary cross-entropy with logits, numerically stable form."""
+    """Mean binary cross-entropy with logits, numerically stable form (module docstring)."""
     return float(np.mean(np.maximum(z, 0.0) - y * z + np.log1p(np.exp(-np.abs(z)))))
 
 
 def loss_and_grad(p, F, y, h=HIDDEN, rounded=True):
-    """Loss and analytic gradient w.r.t. the (fp16-rounded) parameters, FP64."""
+    """Loss and analytic gradient (back-propagation written out) w.r.t. the (fp16-rounded)
+    parameters, FP64; module docstring."""
     W1, b1, W2, b2, w3, b3 = unpack(fp16_round(p) if rounded else p, h)
     z, (h1, h2) = forward(p, F, h, cache=True, rounded=rounded)
     n = len(y)
@@ -126,7 +132,7 @@ def loss_and_grad(p, F, y, h=HIDDEN, rounded=True):
 
 
 def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One bias-corrected Adam update; returns (p, m, v) in FP64."""
+    """One bias-corrected Adam update (Kingma and Ba's published rule); returns (p, m, v) in FP64."""
     m = beta1 * m + (1 - beta1) * g
     v = beta2 * v + (1 - beta2) * g * g
     mh = m / (1 - beta1 ** t)
@@ -135,14 +141,15 @@ def adam_step(p, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def labels(D, I, J, tau):
-    """y = 1 where |D_ij| >= tau (D dense or sparse)."""
+    """y = 1 where |D_ij| >= tau (D dense or sparse): the pattern of floor(D)_tau that Sec. II.A
+    estimates S_tau from, as training labels."""
     D = sp.csr_matrix(D)
     return (np.abs(np.asarray(D[I, J]).ravel()) >= tau).astype(np.float64)
 
 
 def graph_from_logits(H, I, J, z, cut):
-    """Proposed graph: candidate pairs with logit z >= cut, united with the pattern of H,
-    symmetrised, with the diagonal (boolean CSR)."""
+    """Proposed S_tau (Sec. II.A graph, learned; module docstring): candidate pairs with logit
+    z >= cut, united with the pattern of H, symmetrised, with the diagonal (boolean CSR)."""
     N = H.shape[0]
     keep = np.asarray(z) >= cut
     E = sp.csr_matrix((np.ones(int(keep.sum()), dtype=bool), (I[keep], J[keep])), shape=(N, N))

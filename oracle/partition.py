@@ -15,6 +15,8 @@ import scipy.sparse as sp
 
 
 def cell_ids(pos, box, ncell):
+    """Linear spatial-cell id of each site (cores stand in for the graph partitioning of
+    Sec. II.B, obs. vi-vii)."""
     ncell = np.asarray(ncell, dtype=np.int64)
     c = np.floor(pos / box * ncell).astype(np.int64)
     c = np.minimum(np.maximum(c, 0), ncell - 1)
@@ -22,7 +24,8 @@ def cell_ids(pos, box, ncell):
 
 
 def spatial_cores(pos, box, ncell):
-    """List of int64 arrays (ascending sites), one per non-empty cell in cell-id order."""
+    """Cores as spatial cells (communities of obs. vi standing in for the METIS partitioning of
+    Sec. II.B): int64 arrays (ascending sites), one per non-empty cell in cell-id order."""
     cid = cell_ids(pos, box, ncell)
     order = np.argsort(cid, kind="stable")
     cs = cid[order]
@@ -31,12 +34,14 @@ def spatial_cores(pos, box, ncell):
 
 
 def block_cores(N, core_size):
-    """Consecutive index blocks of core_size vertices (last one ragged)."""
+    """Cores as consecutive index blocks of core_size vertices (last one ragged; communities of
+    obs. vi)."""
     return [np.arange(s, min(s + core_size, N)) for s in range(0, N, core_size)]
 
 
 def subgraphs(S, cores):
-    """Core+halo local index lists: (sub_idx list, core counts)."""
+    """Core+halo subgraphs (Sec. II.A, Fig. 1, obs. vi): each core set followed by the sorted
+    vertices adjacent to it in S outside it.  Returns (sub_idx list, core counts)."""
     S = sp.csr_matrix(S)
     subs, ncore = [], []
     for C in cores:
@@ -48,4 +53,5 @@ def subgraphs(S, cores):
 
 
 def single_vertex_cores(N):
+    """One core per vertex: the subgraphs s_tau^i of Eq. 6 in its original form (Sec. II.A)."""
     return [np.array([i]) for i in range(N)]

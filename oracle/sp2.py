@@ -25,6 +25,8 @@ import scipy.sparse as sp
 
 
 def gershgorin(H):
+    """Gershgorin bounds (e_min, e_max) of the spectrum of the whole H: the spectral scaling
+    of the recursive expansion cited in Sec. II.A (every subgraph shares them)."""
     H = sp.csr_matrix(H)
     d = H.diagonal()
     off = np.asarray(abs(H).sum(axis=1)).ravel() - np.abs(d)
@@ -32,11 +34,14 @@ def gershgorin(H):
 
 
 def choose_square(t1, t2, n_occ):
-    """Branch rule: True selects X^2, False selects 2X - X^2."""
+    """Branch rule of the SP2 recursion (Sec. II.A, cited): True selects X^2, False 2X - X^2;
+    the choice that moves the trace toward n_occ (a tie selects 2X - X^2)."""
     return abs(t2 - n_occ) < abs(2.0 * t1 - t2 - n_occ)
 
 
 class Log:
+    """Per-step record of an SP2 run (Sec. II.A recursion): branch bits, traces t1 = Tr X_n,
+    t2 = Tr X_n^2, e_n."""
     def __init__(self):
         self.seq, self.t1, self.t2, self.e = [], [], [], []
         self.stop = None
@@ -47,7 +52,8 @@ class Log:
 
 
 def _decide(log, n, t1, t2, n_occ, idem_tol, n_min, n_max, seq):
-    """Record traces of X_n and return the branch bit, or None to stop."""
+    """Record traces of X_n and return the branch bit, or None to stop (idempotency tolerance,
+    stall rule or n_max in global mode; the given sequence in replay mode, Sec. II.C)."""
     e = abs(t1 - t2)
     log.t1.append(t1); log.t2.append(t2); log.e.append(e)
     if seq is not None:
@@ -68,6 +74,8 @@ def _decide(log, n, t1, t2, n_occ, idem_tol, n_min, n_max, seq):
 
 
 def initial_x(H, eps):
+    """X_0 = (e_max I - H) / (e_max - e_min): H mapped into [0, 1] with the occupied end at 1
+    (the recursive expansion of Sec. II.A starts from this)."""
     e_min, e_max = eps
     H = sp.csr_matrix(H, dtype=np.float64)
     N = H.shape[0]
@@ -75,7 +83,8 @@ def initial_x(H, eps):
 
 
 def sp2_dense(H, n_occ, idem_tol=1e-10, n_min=10, n_max=100, seq=None, eps=None):
-    """Dense FP64 SP2 on the whole matrix.  Returns (D, log)."""
+    """Dense FP64 SP2 on the whole matrix (the recursive expansion of Sec. II.A without any
+    threshold).  Returns (D, log)."""
     eps = gershgorin(H) if eps is None else eps
     X = initial_x(H, eps).toarray()
     log = Log()
@@ -117,7 +126,8 @@ def sp2_thresholded(H, S, n_occ, idem_tol=1e-10, n_min=10, n_max=100, seq=None, 
 
 
 def gather_submatrices(H, subs, eps):
-    """x_s = X_0[idx_s, idx_s] for each subgraph (dense FP64)."""
+    """x_s = X_0[idx_s, idx_s] for each subgraph: the dense principal submatrices x[s] of Eq. 6
+    (dense FP64)."""
     X0 = initial_x(H, eps)
     return [X0[idx][:, idx].toarray() for idx in subs]
 
@@ -177,7 +187,8 @@ def chebyshev_thresholded(X, S, coeffs):
 
 
 def chebyshev_dense(x, coeffs):
-    """Dense P(x) = sum_n c_n T_n(x), T_0 = I, T_1 = x, T_n = 2 x T_{n-1} - T_{n-2}."""
+    """Dense P(x) = sum_n c_n T_n(x) (Eq. 1 with Chebyshev T_n), T_0 = I, T_1 = x,
+    T_n = 2 x T_{n-1} - T_{n-2}."""
     m = x.shape[0]
     T0 = np.eye(m)
     T1 = x.copy()
@@ -211,8 +222,8 @@ def chebyshev_graph(X, subs, coeffs):
 #  * the sequence applies the branch rule above to the two-level matrix diag(x_h, x_l) with
 #    one occupied level, until both are within tol of 1 and 0.
 def gap_estimate(t1, t2, seq, n_occ, eps, e_lo, e_hi):
-    """(homo, lumo) from the traces of a finished run; uses the last step whose idempotency
-    error lies in [e_lo, e_hi]."""
+    """(homo, lumo) from the traces of a finished run (Sec. II.C; reading in the comment
+    above); uses the last step whose idempotency error lies in [e_lo, e_hi]."""
     ks = [k for k in range(min(len(t1), len(t2))) if e_lo <= t1[k] - t2[k] <= e_hi]
     if not ks:
         raise ValueError("no step with idempotency error in range")
@@ -233,6 +244,9 @@ def gap_estimate(t1, t2, seq, n_occ, eps, e_lo, e_hi):
 
 
 def sequence_from_gap(eps, homo, lumo, tol, n_max=256):
+    """Branch sequence fixed beforehand from a HOMO-LUMO estimate (Sec. II.C; reading in the
+    comment above): the branch rule applied to the two-level model until both levels are
+    within tol of 1 and 0."""
     e_min, e_max = eps
     xh = (e_max - homo) / (e_max - e_min)
     xl = (e_max - lumo) / (e_max - e_min)
@@ -256,12 +270,14 @@ def sequence_from_gap(eps, homo, lumo, tol, n_max=256):
 #   P = c_0 I + x b_1 - b_2,
 # which is the same polynomial as the forward sum of c_n T_n (Eqs. 4-5) in another order.
 def fermi(e, beta, mu):
-    """Fermi function [exp(beta (e - mu)) + 1]^-1 without overflow."""
+    """Fermi function [exp(beta (e - mu)) + 1]^-1 of Eq. 7, in a form without overflow."""
     z = beta * (np.asarray(e, dtype=np.float64) - mu)
     return 0.5 * (1.0 - np.tanh(0.5 * z))
 
 
 def fermi_chebyshev_coeffs(beta, mu, eps, order):
+    """Chebyshev coefficients c_n of the Fermi function of Eq. 7 on [e_min, e_max]
+    (interpolant at Chebyshev-Gauss nodes; reading in the comment above)."""
     e_min, e_max = eps
     a, b = 0.5 * (e_max + e_min), 0.5 * (e_max - e_min)
     K = 2 * (order + 1)
@@ -274,6 +290,8 @@ def fermi_chebyshev_coeffs(beta, mu, eps, order):
 
 
 def clenshaw_dense(x, coeffs):
+    """sum_n c_n T_n(x) for a dense x by Clenshaw's recurrence (the same polynomial as the
+    forward sum of Eqs. 1, 4-5, in another order; obs. ix allows any order here)."""
     m = x.shape[0]
     b1 = np.zeros((m, m))
     b2 = np.zeros((m, m))
