@@ -99,25 +99,28 @@ typedef struct {
 
 /* Create a context on CUDA device `device`, ordering work on `cuda_stream`
  * (a cudaStream_t; NULL selects the legacy default stream).  Fails with GBE_ENODEV
- * when the device is absent or is not compute capability 10.3. */
+ * when the device is absent or is not compute capability 10.3.  The context calls and
+ * the error calls below are runtime with no counterpart in the paper. */
 int gbe_create(gbe_ctx** ctx, int device, void* cuda_stream);
 int gbe_destroy(gbe_ctx* ctx);
-/* Change the stream later calls are ordered on.  Device memory of objects created
+/* Change the stream later calls are ordered on (runtime; no counterpart in the paper).  Device memory of objects created
  * before the change stays ordered on the stream it was allocated on, and is released on
  * that stream when the object is freed: keep that stream alive until then. */
 int gbe_set_stream(gbe_ctx* ctx, void* cuda_stream);
-/* Profiling switch: when on, gbe_sp2_run records a CUDA event pair around every
+/* Profiling switch (runtime; no counterpart in the paper): when on, gbe_sp2_run records a CUDA event pair around every
  * squaring launch on the context stream and gbe_sp2_report_get sums the durations of
  * the launches that did work (ms_tc / n_tc, ms_fp64 / n_fp64). */
 int gbe_set_profiling(gbe_ctx* ctx, int on);
-/* Launch each SP2 run as two CUDA graphs (default on): the prologue (control block,
+/* Launch each SP2 run as two CUDA graphs (runtime; not in the paper; default on): the prologue (control block,
  * spectral bounds, gather, first decision) and a loop node whose body is one SP2 step,
  * repeated on the device while the run's own decision says continue, so exactly the steps
  * a run needs are executed and no host round trip is involved.  The graphs are captured on
  * the first run and relaunched while parameters and inputs (pointers, sizes) are unchanged.
  * Profiling (gbe_set_profiling) launches step by step instead, to time every squaring. */
 int gbe_set_graph_launch(gbe_ctx* ctx, int on);
-/* Number of SMs of the context's device (grids are sized from it). */
+/* Number of SMs of the context's device (grids are sized from it; no counterpart in the paper).
+ * gbe_strerror names a return code; gbe_last_error_message gives the calling thread's last
+ * error detail (thread-local). */
 int gbe_device_sm_count(const gbe_ctx* ctx);
 const char* gbe_strerror(int code);
 const char* gbe_last_error_message(void);
@@ -155,14 +158,15 @@ typedef struct {
     double logit_cut;         /* MLP mode: keep edges with logit >= logit_cut           */
 } gbe_graph_params;
 
-/* Build S_tau on the GPU.  The graph is undirected, contains every diagonal entry, and
+/* Build S_tau on the GPU (Sec. II.A: Eq. 2 on H^2 or on a prior D, Eq. 8 in its symbolic
+ * form, the pattern of H^k, or the learned proposal).  The graph is undirected, contains every diagonal entry, and
  * is held either explicitly (CSR) or as "base pattern A with path length k", meaning
  * S = pattern(A^k); partitioning expands core sets by k hops directly.  `H` is a
  * device or host CSR.  Synchronises. */
 int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* H, const gbe_graph_params* params, gbe_graph** S);
-/* Materialise the explicit CSR of S (no-op for k = 1) and report its size. */
+/* Materialise the explicit CSR of S_tau (Eq. 2; no-op for k = 1) and report its size. */
 int gbe_graph_size(gbe_ctx* ctx, gbe_graph* S, int64_t* n, int64_t* nnz);
-/* Copy the explicit CSR of S to host arrays rowptr[n+1] (int64) and col[nnz] (int32). */
+/* Copy the explicit CSR of S_tau (Eq. 2) to host arrays rowptr[n+1] (int64) and col[nnz] (int32). */
 int gbe_graph_export(gbe_ctx* ctx, gbe_graph* S, int64_t* rowptr, int32_t* col);
 int gbe_free_graph(gbe_graph* S);
 
@@ -205,13 +209,14 @@ int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* 
  * an algorithm: the paper uses METIS with a chosen number of communities. */
 int gbe_partition_autotune(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* params, int prec,
                            const int32_t* candidates, int ncand, double* cost, int* best, gbe_parts** parts);
-/* Sizes: number of subgraphs P, total local indices, max subgraph size. */
+/* Sizes of the core+halo subgraphs (Sec. II.A, Fig. 1): number P, total local indices, max size. */
 int gbe_parts_info(const gbe_parts* parts, int64_t* P, int64_t* total, int64_t* max_m);
-/* Copy to host: core_count[P] int32, sub_ptr[P+1] int64, sub_idx[total] int32. */
+/* Copy the subgraphs (Sec. II.A, Fig. 1) to host: core_count[P] int32, sub_ptr[P+1] int64,
+ * sub_idx[total] int32. */
 int gbe_parts_export(gbe_ctx* ctx, const gbe_parts* parts, int32_t* core_count, int64_t* sub_ptr,
                      int32_t* sub_idx);
 /* Build a partition from host arrays with the same meaning (core vertices first in
- * each list).  Validates ranges; does not check that the lists match any graph. */
+ * each list; any communities, obs. vi).  Validates ranges; does not check that the lists match any graph. */
 int gbe_parts_import(gbe_ctx* ctx, int64_t n, int64_t P, const int32_t* core_count,
                      const int64_t* sub_ptr, const int32_t* sub_idx, gbe_parts** parts);
 int gbe_free_parts(gbe_parts* parts);
@@ -276,7 +281,8 @@ typedef struct {
     double fp64_flops;     /* FP64 flops issued by the FP64 squarings                      */
 } gbe_sp2_report;
 
-/* Allocate the SP2 state for a partition and precision (dense padded tiles in HBM,
+/* Allocate the SP2 state for a partition and precision: the dense principal submatrices
+ * x[s] of Eq. 6 (dense padded tiles in HBM,
  * ping-pong buffers, trace partials, device control block).  Reusable across calls.  A
  * mixed-precision state allocates its FP64 iterates only when a run first needs FP64 steps
  * (fp64_tail > 0); a state starts with the launch configuration the context's autotuner
@@ -284,7 +290,8 @@ typedef struct {
 int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, gbe_subs** X);
 int gbe_free_subs(gbe_subs* X);
 
-/* Enqueue one density-matrix build on the stream without synchronising.  With graph launch
+/* Enqueue one density-matrix build on the stream without synchronising: the recursive
+ * expansion of Sec. II.A (SP2, X^2 or 2X - X^2) on every x[s] of Eq. 6.  With graph launch
  * on (gbe_set_graph_launch, the default) a state's second run with the same inputs and
  * parameters captures the run as two CUDA graphs and later such runs relaunch them; a first
  * run, or a run after a change, is launched kernel by kernel.  The build:
@@ -296,10 +303,11 @@ int gbe_free_subs(gbe_subs* X);
  * memory (the same bound applies to gbe_foe_run). */
 int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* params,
                 gbe_subs* X);
-/* Synchronise and read the report of the last run on X. */
+/* Synchronise and read the report of the last run on X (the traces and branch sequence of
+ * the Sec. II.A recursion, timings, flops). */
 int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_report* rep);
 
-/* gbe_sp2_run + gbe_sp2_report_get.  *X NULL: allocate a new state; otherwise reuse it
+/* gbe_sp2_run + gbe_sp2_report_get (Sec. II.A, Eq. 6).  *X NULL: allocate a new state; otherwise reuse it
  * (it must come from the same partition and precision).  H may be host CSR (copied in).
  * Returns GBE_ENOCONV when the run stopped at n_max, GBE_ENUMERIC / GBE_ETIMEOUT when
  * the device recorded one, GBE_OK otherwise. */
@@ -344,7 +352,7 @@ typedef struct {
     int cached;                       /* 1: taken from the context's cache, nothing timed    */
 } gbe_tune_report;
 
-/* Read / install the configuration of a state.  Installing one rebuilds the tile schedule
+/* Read / install the configuration of a state (not in the paper).  Installing one rebuilds the tile schedule
  * on the device and drops the state's captured SP2 graphs (recaptured on the next run).
  * GBE_EINVAL for a depth the precision is not built with or an unknown schedule. */
 int gbe_subs_get_config(const gbe_subs* X, gbe_tc_config* cfg);
@@ -373,7 +381,8 @@ int gbe_sp2_autotune(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, con
  * D->width < max m_s.  Device D: enqueue only; host D: synchronises and copies out. */
 int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, double drop_tol, gbe_ell* D);
 
-/* Copy the final dense x_s (m_s x m_s, row-major, FP64) of subgraph s to host. */
+/* Copy the final dense x_s (m_s x m_s, row-major, FP64) of subgraph s to host (the P(x[s])
+ * of Eq. 6 before assembly). */
 int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out);
 
 /* ------------------------------------------------ finite temperature (Chebyshev expansion) */
@@ -410,8 +419,9 @@ typedef struct {
     double mma_flops, alg_flops;
 } gbe_foe_report;
 
-/* Chebyshev interpolant of the Fermi function on [eps_min, eps_max] at 2 (order + 1)
- * Chebyshev-Gauss nodes: c_n = (2 - delta_n0) / K sum_j f(a + b cos t_j) cos(n t_j).  Host only. */
+/* Chebyshev interpolant of the Fermi function of Eq. 7 on [eps_min, eps_max] at 2 (order + 1)
+ * Chebyshev-Gauss nodes: c_n = (2 - delta_n0) / K sum_j f(a + b cos t_j) cos(n t_j).  Host only.
+ * gbe_foe_run and gbe_foe_report_get run and report the Eq. 7 expansion described above. */
 int gbe_fermi_coefficients(double beta, double mu, double eps_min, double eps_max, int order, double* coeffs);
 int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_foe_params* params, gbe_subs* X);
 int gbe_foe_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_foe_report* rep);
@@ -432,7 +442,7 @@ int gbe_foe_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_foe_report* rep);
 int gbe_sp2_gap_estimate(const gbe_sp2_report* rep, double n_occ, double e_lo, double e_hi, double* homo,
                          double* lumo);
 
-/* Branch sequence (seq[i] = 1 for X^2, 0 for 2X-X^2; *len entries written) that drives every
+/* Sec. II.C: branch sequence (seq[i] = 1 for X^2, 0 for 2X-X^2; *len entries written) that drives every
  * eigenvalue <= homo within tol of 1 and every eigenvalue >= lumo within tol of 0 in the
  * scaled variable x = (eps_max - e)/(eps_max - eps_min): the branch rule applied to the
  * two-level matrix diag(x_homo, x_lumo) with one occupied level.  seq: caller-owned, n_max
@@ -454,36 +464,41 @@ int gbe_sp2_sequence(double eps_min, double eps_max, double homo, double lumo, d
  * master copy; gradients are reduced in a fixed order (run-to-run identical). */
 typedef struct gbe_pairs gbe_pairs;
 
-/* Candidate pairs and features on the device (rows ordered by i, then j ascending).
+/* Candidate pairs and features on the device (not in the paper; rows ordered by i, then j
+ * ascending).  gbe_pairs_info gives their count.
  * sites and H may be host or device; H must be symmetric with sorted rows ((H^2)_ij is
  * accumulated in row i over k ascending, which equals the row-j sum bit for bit when H is
  * symmetric to the last bit, as gbe_build_hamiltonian's H is).  GBE_ECAPACITY above 1024
  * candidates per site; GBE_EINVAL unless box > 2 rcand.  Synchronises. */
 int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* sites, const gbe_csr* H, double rcand, gbe_pairs** pairs);
 int gbe_pairs_info(const gbe_pairs* pairs, int64_t* n, int64_t* npairs);
-/* Host copies: rowptr[n+1] (int64), j[npairs] (int32), features[npairs*5] (float32); NULL skips. */
+/* Host copies of the pairs (not in the paper): rowptr[n+1] (int64), j[npairs] (int32),
+ * features[npairs*5] (float32); NULL skips. */
 int gbe_pairs_export(gbe_ctx* ctx, const gbe_pairs* pairs, int64_t* rowptr, int32_t* j, float* features);
-/* Library-owned device arrays of the pairs (valid until gbe_free_pairs); NULL skips. */
+/* Library-owned device arrays of the pairs (not in the paper; valid until gbe_free_pairs);
+ * NULL skips. */
 int gbe_pairs_device(const gbe_pairs* pairs, const int64_t** rowptr, const int32_t** j, const float** features);
 int gbe_free_pairs(gbe_pairs* pairs);
 
-/* Network with zero parameters (hidden must be 64); set them with gbe_mlp_set_params. */
+/* Network with zero parameters (not in the paper; hidden must be 64); set them with
+ * gbe_mlp_set_params.  gbe_mlp_param_count gives their number (4609). */
 int gbe_mlp_create(gbe_ctx* ctx, int hidden, gbe_mlp** mlp);
 int gbe_mlp_param_count(const gbe_mlp* mlp);
-/* host_params: gbe_mlp_param_count floats; also resets the Adam moments and step count. */
+/* host_params (not in the paper): gbe_mlp_param_count floats; setting also resets the Adam
+ * moments and step count. */
 int gbe_mlp_set_params(gbe_ctx* ctx, gbe_mlp* mlp, const float* host_params);
 int gbe_mlp_get_params(gbe_ctx* ctx, const gbe_mlp* mlp, float* host_params);
-/* logits: device float[npairs].  Enqueue only. */
+/* Forward pass of the classifier (not in the paper); logits: device float[npairs].  Enqueue only. */
 int gbe_mlp_forward(gbe_ctx* ctx, const gbe_mlp* mlp, const gbe_pairs* pairs, float* logits);
-/* Mean BCE loss and its gradient at the current parameters; labels: device uint8[npairs]
+/* Mean BCE loss and its gradient at the current parameters (not in the paper); labels: device uint8[npairs]
  * (0/1).  loss (host, nullable) and grad_host (host float[param_count], nullable) are
  * written after a synchronisation.  The gradient stays on the device for the next
  * gbe_mlp_adam_step. */
 int gbe_mlp_gradient(gbe_ctx* ctx, gbe_mlp* mlp, const gbe_pairs* pairs, const uint8_t* labels, double* loss,
                      float* grad_host);
-/* One bias-corrected Adam step with the last gradient.  Enqueue only. */
+/* One bias-corrected Adam step with the last gradient (not in the paper).  Enqueue only. */
 int gbe_mlp_adam_step(gbe_ctx* ctx, gbe_mlp* mlp, float lr, float beta1, float beta2, float eps);
-/* epochs x (gradient + Adam(lr, 0.9, 0.999, 1e-8)) on the device; final_loss (host,
+/* Training (not in the paper): epochs x (gradient + Adam(lr, 0.9, 0.999, 1e-8)) on the device; final_loss (host,
  * nullable) is the mean loss of the last epoch before its update.  Synchronises. */
 int gbe_mlp_train(gbe_ctx* ctx, gbe_mlp* mlp, const gbe_pairs* pairs, const uint8_t* labels, int epochs, float lr,
                   double* final_loss);

@@ -24,3 +24,31 @@ def test_every_oracle_function_cites_a_passage():
                     missing.append("%s:%s" % (fn, node.name))
     assert n >= 50
     assert not missing, missing
+
+
+def test_every_header_entry_point_cites_a_passage():
+    """Each gbe_* prototype in include/*.h sits under a comment that names the passage of the
+    paper it follows, or says that it has no counterpart there."""
+    import re
+    keys = KEYS + ("no counterpart", "paper")
+    bad, n = [], 0
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        lines = open(os.path.join(ROOT, "include", fn)).read().split("\n")
+        for i, line in enumerate(lines):
+            m = re.match(r"^\s*(?:const\s+)?\w+\*?\s+\*?(gbe_\w+)\s*\(", line)
+            if not m:
+                continue
+            n += 1
+            j = i - 1          # up to the nearest comment, across the prototypes of its group
+            while j >= 0 and not lines[j].strip().endswith("*/") and lines[j].strip():
+                j -= 1
+            block = []
+            if j >= 0 and lines[j].strip().endswith("*/"):
+                k = j
+                while k >= 0 and "/*" not in lines[k]:
+                    k -= 1
+                block = lines[k:j + 1]
+            if not any(key in " ".join(block) for key in keys):
+                bad.append(m.group(1))
+    assert n >= 40
+    assert not bad, bad
