@@ -52,3 +52,25 @@ def test_every_header_entry_point_cites_a_passage():
                 bad.append(m.group(1))
     assert n >= 40
     assert not bad, bad
+
+
+def test_golden_values_carry_their_citation():
+    """Each stored value of tests/golden/ is the paper's, with the passage it comes from in
+    the comment lines right above it (no value there comes from the CUDA path)."""
+    gdir = os.path.join(ROOT, "tests", "golden")
+    n = 0
+    for fn in sorted(os.listdir(gdir)):
+        comment = ""
+        for line in open(os.path.join(gdir, fn)):
+            line = line.strip()
+            if line.startswith("#"):
+                comment += " " + line
+                continue
+            if not line:
+                continue
+            name, *vals = line.split()
+            assert vals and all(float(v) == float(v) for v in vals), (fn, line)
+            assert any(k in comment for k in ("Sec.", "Eq", "Fig.", "Table")), (fn, name)
+            n += 1
+            comment = ""
+    assert n >= 3
