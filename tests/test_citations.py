@@ -60,11 +60,12 @@ def test_golden_values_carry_their_citation():
     gdir = os.path.join(ROOT, "tests", "golden")
     n = 0
     for fn in sorted(os.listdir(gdir)):
-        comment = ""
+        comment, after_value = "", False   # a comment block covers the values that follow it
         for line in open(os.path.join(gdir, fn)):
             line = line.strip()
             if line.startswith("#"):
-                comment += " " + line
+                comment = (line if after_value else comment + " " + line)
+                after_value = False
                 continue
             if not line:
                 continue
@@ -72,5 +73,5 @@ def test_golden_values_carry_their_citation():
             assert vals and all(float(v) == float(v) for v in vals), (fn, line)
             assert any(k in comment for k in ("Sec.", "Eq", "Fig.", "Table")), (fn, name)
             n += 1
-            comment = ""
+            after_value = True
     assert n >= 3
