@@ -67,6 +67,15 @@ def test_reference_arm_line():
     assert d["impl"] == "reference" and d["unit"] == "orbitals/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    # the base contract's keys, with the GPU arm's metric, unit and direction
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert key in d, key
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["higher_is_better"] is True
+    assert d["steps"] == 1 and d["n_gpus"] == 1 and d["config"]["workload"].startswith("lattice32")
+    assert d["e2e"]["value"] == d["value"] == d["cpu_baseline"]["value"]
 
 
 def test_traffic_record_voided_by_source_change(tmp_path, monkeypatch):
