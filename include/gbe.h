@@ -232,7 +232,8 @@ enum {
 
 enum {
     GBE_BRANCH_GLOBAL_TRACE = 0, /* branch from the global FP64 traces every iteration     */
-    GBE_BRANCH_REPLAY       = 1  /* apply seq_in[0..seq_len) and stop after it             */
+    GBE_BRANCH_REPLAY       = 1  /* apply seq_in[0..seq_len) and stop after it; seq_len
+                                    above n_max is rejected (GBE_EINVAL)                   */
 };
 
 enum {
@@ -516,10 +517,14 @@ int gbe_free_mlp(gbe_mlp* mlp);
  *           (the same values gbe_sp2_run uses); both NaN when H holds a NaN or Inf.
  *   H:      device CSR (on_device = 1); 1 <= n <= 4,194,304 rows, else GBE_EINVAL with a
  *           message naming the limit.
+ * bounds, H->rowptr, H->col and H->val must be device memory of the context's GPU (or
+ * managed memory); a host pointer is refused with GBE_EINVAL before anything is enqueued.
  * Scratch: a fixed file-scope device array of 16384 per-block partials (about 256 KB),
  * held by every GPU that loads the library until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress, with the device
- * current); make that first call before any stream capture.  Every call shares the one
+ * current), and the lookup is repeated when the device's current context has changed
+ * since (after cudaDeviceReset); make the first call on a device, and the first call
+ * after a reset, before any stream capture.  Every call shares the one
  * array and overwrites it, so calls that overlap on the GPU (different streams or
  * contexts on the same device) race and must be serialised by the caller.
  * Enqueues on the context stream and returns without synchronising. */

@@ -7,6 +7,24 @@ NumPy arrays are passed as host buffers where the ABI accepts them.
 
 There is no CPU fallback: importing works without a GPU, but creating a context fails
 loudly when the library or a usable sm_103 device is missing.
+
+Example (one density matrix of the 32^3 lattice; every step runs in the library's kernels)::
+
+    import torch, synth
+    import paper_1603_00937_gb300 as gbe
+
+    w = synth.lattice(32, seed=0)                                   # 32^3 sites, N = 32,768
+    ctx = gbe.Context(0)
+    st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
+    H = gbe.build_hamiltonian(ctx, st)                              # device CSR H
+    S = gbe.build_graph(ctx, H.csr(), gbe.GRAPH_H2_THRESH, thresh=0.15)     # Eq. 2 on H^2
+    parts = gbe.partition(ctx, S, gbe.PART_SPATIAL_CELLS, ncell=(8, 8, 8), site_struct=st)
+    X, rep = gbe.sp2_submatrices(ctx, H.csr(), parts, gbe.sp2_params(16384, prec=gbe.PREC_FP16X6))
+    n, width = gbe.assemble_width(ctx, X, parts)
+    col = torch.empty((n, width), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, width), dtype=torch.float64, device="cuda")
+    gbe.assemble_D(ctx, X, parts, col, val)                         # row i of the ELL = column i of D (Eq. 6)
+    print(rep["iters"], rep["stop"])
 """
 import ctypes
 import os

@@ -4,6 +4,8 @@
 // e_max = max_i H_ii + sum_{j!=i}|H_ij|, one warp per row summing in the same order), but
 // the per-block partial results live in a fixed file-scope device array instead of
 // memory obtained from cudaMalloc, so the call works for callers that may not allocate.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -91,9 +93,14 @@ __global__ void __launch_bounds__(1024) gersh_reduce_kernel(const unsigned long 
     }
 }
 
-// Device address of the scratch array, looked up once per device with that device current.
+// Device address of the scratch array, looked up once per device with that device current,
+// and again whenever the device's current context is another one than at the lookup (after
+// cudaDeviceReset the primary context is new and the array has a new address).
 std::mutex g_mu;
 unsigned long long* g_scratch_addr[64] = {nullptr};
+CUcontext g_scratch_ctx[64] = {nullptr};
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+CtxGetCurrentFn g_ctx_get = nullptr;
 
 int scratch_for(int device, unsigned long long** out) {
     std::lock_guard<std::mutex> lock(g_mu);
@@ -101,7 +108,22 @@ int scratch_for(int device, unsigned long long** out) {
         gbe_set_error("device index %d out of range for the no-allocation scratch table", device);
         return GBE_EINVAL;
     }
-    if (!g_scratch_addr[device]) {
+    if (!g_ctx_get) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        const cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+            gbe_set_error("cuCtxGetCurrent not available: %s", cudaGetErrorString(e));
+            return GBE_ECUDA;
+        }
+        g_ctx_get = (CtxGetCurrentFn)fn;
+    }
+    CUcontext cur = nullptr;
+    if (g_ctx_get(&cur) != CUDA_SUCCESS || cur == nullptr) {
+        gbe_set_error("no current CUDA context on device %d", device);
+        return GBE_ECUDA;
+    }
+    if (!g_scratch_addr[device] || g_scratch_ctx[device] != cur) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_gersh_scratch);
         if (e != cudaSuccess || p == nullptr) {
@@ -109,9 +131,22 @@ int scratch_for(int device, unsigned long long** out) {
             return GBE_ECUDA;
         }
         g_scratch_addr[device] = (unsigned long long*)p;
+        g_scratch_ctx[device] = cur;
     }
     *out = g_scratch_addr[device];
     return GBE_OK;
+}
+
+// Device (or managed) memory that `device` can address; host memory, registered or not, is
+// refused: a kernel given a host pointer would fault or read the wrong memory.
+bool device_memory_of(const void* p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
@@ -128,6 +163,11 @@ extern "C" int gbe_gershgorin_noalloc(gbe_ctx* ctx, const gbe_csr* H, double* bo
         return GBE_EINVAL;
     }
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    // the pointers are checked before anything is enqueued (no allocation, no synchronisation)
+    GBE_CHECK_ARG(device_memory_of(bounds, ctx->device), "bounds is not device memory of the context's GPU");
+    GBE_CHECK_ARG(device_memory_of(H->rowptr, ctx->device) && device_memory_of(H->col, ctx->device) &&
+                      device_memory_of(H->val, ctx->device),
+                  "H arrays are not device memory of the context's GPU (on_device = 1 needs device pointers)");
     unsigned long long* scratch = nullptr;
     GBE_TRY(scratch_for(ctx->device, &scratch));
     const int nblocks = (int)((H->n + kRowsPerBlock - 1) / kRowsPerBlock);

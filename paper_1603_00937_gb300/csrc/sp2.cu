@@ -1186,6 +1186,10 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     GBE_CHECK_ARG(prm->branch_mode == GBE_BRANCH_GLOBAL_TRACE || prm->branch_mode == GBE_BRANCH_REPLAY, "branch_mode");
     GBE_CHECK_ARG(prm->branch_mode != GBE_BRANCH_REPLAY || (prm->seq_in && prm->seq_len >= 0 && prm->seq_len <= GBE_SEQ_MAX),
                   "replay needs seq_in / seq_len <= GBE_SEQ_MAX");
+    // a replayed sequence is applied whole: a longer one than n_max would be cut silently
+    // (and its FP64 tail, placed at its end, never reached)
+    GBE_CHECK_ARG(prm->branch_mode != GBE_BRANCH_REPLAY || prm->seq_len <= prm->n_max,
+                  "replay sequence longer than n_max");
     GBE_CHECK_ARG(parts->max_m <= 8192, "subgraph larger than 8192");
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;

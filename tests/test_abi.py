@@ -189,19 +189,20 @@ def test_oracle_and_inputs_never_touch_the_package():
                 assert not re.search(r"^\s*(from|import)\s+(oracle|\.)", text, re.M), fn
 
 
-def test_readme_example_uses_the_binding():
-    """The README's Python example parses and every gbe.* name it uses exists in the binding
-    (it runs only on a GPU; its calls are the ones the full-size parity test makes)."""
+def test_docstring_example_uses_the_binding():
+    """The package docstring's usage example parses and every gbe.* name it uses exists in
+    the binding (it runs only on a GPU; its calls are the ones the full-size parity test
+    makes)."""
     import ast
+    import textwrap
     import paper_1603_00937_gb300 as gbe
-    text = open(os.path.join(ROOT, "README.md")).read()
-    blocks = re.findall(r"```python\n(.*?)```", text, re.S)
-    assert blocks
+    doc = gbe.__doc__
+    start = doc.index("::\n") + 3
+    block = textwrap.dedent(doc[start:])
     names = set()
-    for b in blocks:
-        for node in ast.walk(ast.parse(b)):
-            if isinstance(node, ast.Attribute) and isinstance(node.value, ast.Name) and node.value.id == "gbe":
-                names.add(node.attr)
+    for node in ast.walk(ast.parse(block)):
+        if isinstance(node, ast.Attribute) and isinstance(node.value, ast.Name) and node.value.id == "gbe":
+            names.add(node.attr)
     assert {"Context", "build_graph", "partition", "sp2_submatrices", "assemble_D"} <= names
     missing = sorted(n for n in names if not hasattr(gbe, n))
     assert not missing, missing

@@ -6,6 +6,8 @@
   reduces to the scalar recursion on each diagonal entry of X0, compared with the oracle.
 - A subgraph larger than the gather's shared memory holds (2433 vertices) is rejected with
   GBE_ECAPACITY before any kernel runs, and the context stays usable.
+- A replayed branch sequence longer than n_max is rejected with GBE_EINVAL (it would be cut
+  short without notice), and one of exactly n_max steps runs whole.
 """
 import numpy as np
 import pytest
@@ -117,3 +119,16 @@ def test_device_wait_timeout_is_reported(ctx):
     assert rep["status"] == 0 and rep["iters"] == len(seq)
     D1, _, _ = assembled_dense(ctx, X, parts, N)
     assert np.array_equal(D0, D1)
+
+
+def test_replay_longer_than_n_max_rejected(ctx):
+    w, H, _, subs, nc = lattice_case(6, seed=4, thr=1e-2, ncell=(3, 3, 3))
+    N = H.shape[0]
+    parts = import_parts(ctx, N, subs, nc)
+    Hd = device_csr(H)
+    seq = [1, 0, 1, 0, 1, 0]
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=seq, n_max=5))
+    assert e.value.code == gbe.GBE_EINVAL and "n_max" in str(e.value)
+    X, rep = gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=seq, n_max=6))
+    assert rep["iters"] == 6 and rep["seq"] == seq and rep["stop"] == "replay"
