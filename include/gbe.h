@@ -52,6 +52,7 @@ extern "C" {
 #define GBE_ENUMERIC   -6   /* NaN or Inf met in H or in an SP2 iterate           */
 #define GBE_ECAPACITY  -7   /* a subgraph, ELL row or table exceeded its capacity */
 #define GBE_ENODEV     -8   /* no usable sm_103 device                            */
+#define GBE_EPEER      -9   /* another rank of a sharded run reported an error    */
 
 typedef struct gbe_ctx gbe_ctx;
 typedef struct gbe_graph gbe_graph;
@@ -221,6 +222,44 @@ int gbe_parts_import(gbe_ctx* ctx, int64_t n, int64_t P, const int32_t* core_cou
                      const int64_t* sub_ptr, const int32_t* sub_idx, gbe_parts** parts);
 int gbe_free_parts(gbe_parts* parts);
 
+/* ------------------------------------------- several GPUs: subgraphs sharded over ranks */
+
+/* Assignment of the subgraphs of one partition to `world` ranks (host only, no GPU needed).
+ * The subgraph expansions are independent (Sec. II.A, after Eq. 6; the paper spreads them
+ * over 1, 16 and 32 GPUs, Sec. II.B), so each rank squares only its own subgraphs.  The
+ * cost of subgraph s is m_s^3 (its dense squaring, the cost model of Sec. II.B) with
+ * m_s = sub_ptr[s+1] - sub_ptr[s]; subgraphs are taken largest cost first (ties: lower
+ * index first) and each goes to the rank with the smallest load so far (ties: lower rank)
+ * -- greedy longest-processing-time, deterministic, the same on every rank.
+ *   sub_ptr: host int64[P+1]; owner: host int32[P] receives the rank of each subgraph;
+ *   load: host double[world] (nullable) receives the summed cost per rank.
+ * GBE_EINVAL for P < 1, world < 1 or an empty subgraph. */
+int gbe_shard_assign(int64_t P, const int64_t* sub_ptr, int world, int32_t* owner, double* load);
+
+/* The shard of a partition that `rank` owns (the independent subgraph expansions of
+ * Sec. II.A spread over GPUs as in Sec. II.B): its subgraphs (owner[s] == rank) in their
+ * global order, as a partition of the same n vertices that remembers the global index of
+ * each subgraph.  An SP2 run on a shard squares only these subgraphs; its traces are
+ * combined with the other ranks' through gbe_sp2_params.exchange (global-trace mode) and
+ * its assembly fills only the ELL rows of its own cores (the other rows are emptied).
+ *   owner: host int32[P] (gbe_shard_assign or any other assignment); a rank that owns no
+ *   subgraph gets GBE_EINVAL.  *local: library-owned, freed with gbe_free_parts; `parts`
+ *   may be freed after the call. */
+int gbe_parts_shard(gbe_ctx* ctx, const gbe_parts* parts, const int32_t* owner, int rank, gbe_parts** local);
+
+/* Trace exchange of a sharded SP2 run.  Called by gbe_sp2_run on the calling thread, once
+ * after the gather and once after every SP2 step in global-trace mode (never in replay
+ * mode: a pre-determined sequence needs no exchange, Sec. II.C).  `buf` is device memory of
+ * `count` doubles: this rank's per-subgraph trace sums at the global positions of its
+ * subgraphs, zeros elsewhere, and an error flag in the last element.  The function must
+ * replace buf by its element-wise sum over all ranks, ordered on `stream` (a cudaStream_t):
+ * either by enqueuing an all-reduce on that stream (NCCL), or by synchronising the stream,
+ * exchanging on the host and copying the sum back before it returns.  Every position has
+ * one contributing rank, so the sum is exact whatever the reduction order, and every rank
+ * takes the same branch decisions as a single-rank run of the whole partition.  Return 0
+ * on success; anything else stops the run with GBE_EPEER. */
+typedef int (*gbe_exchange_fn)(void* user, double* buf, int64_t count, void* stream);
+
 /* ------------------------------------------------------ SP2 (a4 - a7) */
 
 enum {
@@ -259,6 +298,12 @@ typedef struct {
     int eps_given;         /* 1: use eps_min / eps_max below instead of Gershgorin bounds           */
     double eps_min, eps_max;
     double timeout_ms;     /* bound for device-side waits (0: library default, 2000 ms)             */
+    /* sharded runs (parts from gbe_parts_shard): the trace exchange between ranks; NULL for a
+       run on a whole partition.  A run with an exchange is launched step by step (never as a
+       CUDA graph) and reads the stop flag back after every step, so that all ranks stop
+       after the same step and make the same number of exchanges. */
+    gbe_exchange_fn exchange;
+    void* exchange_user;
 } gbe_sp2_params;
 
 typedef struct {

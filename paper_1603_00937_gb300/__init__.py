@@ -35,7 +35,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgbe.so")
 
 GBE_OK, GBE_EINVAL, GBE_ENOMEM, GBE_ECUDA, GBE_ETIMEOUT = 0, -1, -2, -3, -4
-GBE_ENOCONV, GBE_ENUMERIC, GBE_ECAPACITY, GBE_ENODEV = -5, -6, -7, -8
+GBE_ENOCONV, GBE_ENUMERIC, GBE_ECAPACITY, GBE_ENODEV, GBE_EPEER = -5, -6, -7, -8, -9
 
 GRAPH_H2_THRESH, GRAPH_D_THRESH, GRAPH_EQ8_SYMBOLIC, GRAPH_HK_PATTERN, GRAPH_MLP = 0, 1, 2, 3, 4
 PART_SPATIAL_CELLS, PART_INDEX_BLOCKS = 0, 1
@@ -59,7 +59,11 @@ EXPORTS = [
     "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_free_mlp",
     "gbe_sp2_gap_estimate", "gbe_sp2_sequence", "gbe_fermi_coefficients", "gbe_foe_run", "gbe_foe_report_get",
     "gbe_subs_get_config", "gbe_subs_set_config", "gbe_sp2_autotune", "gbe_partition_autotune",
+    "gbe_shard_assign", "gbe_parts_shard",
 ]
+
+# gbe_exchange_fn: int (*)(void* user, double* buf, int64_t count, void* stream)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p)
 
 
 class GbeError(RuntimeError):
@@ -104,7 +108,8 @@ class Sp2Params(ctypes.Structure):
                 ("n_max", ctypes.c_int), ("prec", ctypes.c_int), ("fp64_tail", ctypes.c_int),
                 ("tail_switch", ctypes.c_double), ("branch_mode", ctypes.c_int),
                 ("seq_in", ctypes.c_void_p), ("seq_len", ctypes.c_int), ("eps_given", ctypes.c_int),
-                ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double), ("timeout_ms", ctypes.c_double)]
+                ("eps_min", ctypes.c_double), ("eps_max", ctypes.c_double), ("timeout_ms", ctypes.c_double),
+                ("exchange", EXCHANGE_FN), ("exchange_user", ctypes.c_void_p)]
 
 
 class Sp2Report(ctypes.Structure):
@@ -184,6 +189,7 @@ def load_library(path=LIB_PATH):
         "gbe_subs_get_config": (I32, [P, P]), "gbe_subs_set_config": (I32, [P, P, P]),
         "gbe_sp2_autotune": (I32, [P, P, P, P, P, I32, P]),
         "gbe_partition_autotune": (I32, [P, P, P, I32, P, I32, P, P, P]),
+        "gbe_shard_assign": (I32, [I64, P, I32, P, P]), "gbe_parts_shard": (I32, [P, P, P, I32, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -413,7 +419,10 @@ def parts_import(ctx, n, core_count, sub_ptr, sub_idx):
 
 
 def sp2_params(n_occ, prec=PREC_FP64, idem_tol=1e-10, n_min=10, n_max=100, fp64_tail=0, tail_switch=0.0,
-               seq=None, eps=None, timeout_ms=0.0):
+               seq=None, eps=None, timeout_ms=0.0, exchange=None):
+    """gbe_sp2_params.  exchange: for a sharded run (parts from parts_shard), a callable
+    (buf_ptr, count, stream_ptr) that replaces the `count` doubles at the device address
+    buf_ptr by their sum over all ranks, ordered on the stream (see dist_exchange)."""
     buf = None
     if seq is not None:
         buf = np.ascontiguousarray(np.asarray(seq, dtype=np.uint8))
@@ -424,8 +433,60 @@ def sp2_params(n_occ, prec=PREC_FP64, idem_tol=1e-10, n_min=10, n_max=100, fp64_
                   eps[1] if eps is not None else 0.0, timeout_ms)
     if buf is not None and len(buf) == 0:
         p.seq_in = ctypes.cast(ctypes.create_string_buffer(1), ctypes.c_void_p)
-    p._keep = buf
+    cb = None
+    if exchange is not None:
+        def _cb(user, ptr, count, stream):
+            try:
+                exchange(ptr, count, stream)
+                return 0
+            except Exception:
+                return 1
+        cb = EXCHANGE_FN(_cb)
+        p.exchange = cb
+    p._keep = (buf, cb)
     return p
+
+
+def shard_assign(sub_ptr, world):
+    """(owner[P], load[world]): subgraphs dealt to ranks by greedy longest-processing-time on
+    m_s^3 (gbe_shard_assign; host only)."""
+    sp = np.ascontiguousarray(sub_ptr, dtype=np.int64)
+    P = len(sp) - 1
+    owner = np.zeros(P, dtype=np.int32)
+    load = np.zeros(world, dtype=np.float64)
+    check(load_library().gbe_shard_assign(P, _ptr(sp), int(world), _ptr(owner), _ptr(load)), "gbe_shard_assign")
+    return owner, load
+
+
+def parts_shard(ctx, parts, owner, rank):
+    """The subgraphs of `parts` that `rank` owns, as a shard (gbe_parts_shard)."""
+    ow = np.ascontiguousarray(owner, dtype=np.int32)
+    h = ctypes.c_void_p()
+    check(load_library().gbe_parts_shard(ctx.handle, parts.handle, _ptr(ow), int(rank), ctypes.byref(h)),
+          "gbe_parts_shard")
+    return Parts(ctx, h)
+
+
+def dist_exchange(group=None):
+    """Trace exchange of a sharded run over torch.distributed: an in-place all-reduce (sum)
+    of the library's exchange buffer.  With NCCL the buffer is device memory and the
+    all-reduce is ordered after the library's kernels on the current CUDA stream (the
+    context must use that stream); with gloo (host ranks) the buffer is host memory."""
+    import torch
+    import torch.distributed as dist
+
+    def fn(ptr, count, stream):
+        if dist.get_backend(group) == "nccl":
+            class _A:
+                pass
+            a = _A()
+            a.__cuda_array_interface__ = {"shape": (int(count),), "typestr": "<f8", "data": (int(ptr), False),
+                                          "version": 3}
+            t = torch.as_tensor(a, device="cuda")
+        else:
+            t = torch.from_numpy(np.ctypeslib.as_array((ctypes.c_double * int(count)).from_address(int(ptr))))
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return fn
 
 
 def subs_create(ctx, parts, prec):

@@ -29,6 +29,7 @@ extern "C" const char* gbe_strerror(int code) {
         case GBE_ENUMERIC: return "NaN or Inf encountered";
         case GBE_ECAPACITY: return "capacity exceeded";
         case GBE_ENODEV: return "no usable sm_103 device";
+        case GBE_EPEER: return "another rank reported an error";
         default: return "unknown error";
     }
 }

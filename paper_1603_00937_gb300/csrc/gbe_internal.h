@@ -82,6 +82,13 @@ struct gbe_parts {
     int32_t* d_sub_idx = nullptr;     // [total]
     std::vector<int32_t> h_core_count;
     std::vector<int64_t> h_sub_ptr;
+    // a shard of a larger partition (gbe_parts_shard): the whole partition has P_global
+    // subgraphs, local subgraph s is global subgraph h_global_id[s], and d_local_of maps a
+    // global index to the local one (-1: another rank's).  Not a shard: P_global = P and
+    // the maps are the identity (h_global_id empty, d_local_of NULL).
+    int64_t P_global = 0;
+    std::vector<int64_t> h_global_id;
+    int32_t* d_local_of = nullptr;   // [P_global]
 };
 
 // Device control block of one SP2 run (one per gbe_subs).
@@ -147,6 +154,13 @@ struct gbe_subs {
     TileItem* d_items_tc_full = nullptr;  int n_items_tc_full = 0;   // all (I, J), for products x b
     TileItem* d_items_64_full = nullptr;  int n_items_64_full = 0;
     double* d_partials = nullptr;    int max_units = 0;    // [2][max_units] (t1, t2)
+    // work units of each subgraph in the partials array, per decision kind (0: gather, one
+    // unit per subgraph; 1: tensor-core tiles; 2: FP64 tiles): first unit and count
+    int2* d_ranges[3] = {nullptr, nullptr, nullptr};
+    // per-subgraph trace sums at global subgraph positions, exchanged between the ranks of
+    // a sharded run: [0, P_global) t1, [P_global, 2 P_global) t2, [2 P_global] error flag
+    double* d_sums = nullptr;
+    int64_t P_global = 0;
     Sp2Ctrl* d_ctrl = nullptr;
     Sp2Ctrl* h_ctrl = nullptr;       // pinned
     // tensor maps for the split planes (opaque 128-byte CUtensorMap blobs)

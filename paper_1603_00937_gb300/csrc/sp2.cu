@@ -294,20 +294,60 @@ __global__ void init_ctrl_kernel(Sp2Ctrl* C, Sp2Init in) {
 }
 
 // ----------------------------------------------------------------------------- decide
+// Trace sums of one subgraph over its work units, in unit order.  A single-rank decision and
+// the per-subgraph sums a sharded run exchanges use this same arithmetic, so both see the
+// same per-subgraph values and take the same decisions.
+__device__ __forceinline__ void sub_trace(const double* __restrict__ partials, int max_units, int2 r, double& a,
+                                          double& b) {
+    double x = 0.0, y = 0.0;
+    for (int u = r.x; u < r.x + r.y; ++u) {
+        x += partials[u];
+        y += partials[max_units + u];
+    }
+    a = x;
+    b = y;
+}
+
+// Per-subgraph trace sums of this rank at global subgraph positions (zeros at other ranks'
+// positions) and its error flag: the buffer a sharded run's exchange sums over the ranks.
+__global__ void __launch_bounds__(256) sub_sums_kernel(const Sp2Ctrl* ctrl, const double* __restrict__ partials,
+                                                       int max_units, const int2* __restrict__ ranges,
+                                                       const int32_t* __restrict__ local_of, int64_t P_global,
+                                                       double* sums) {
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < P_global; g += (int64_t)gridDim.x * blockDim.x) {
+        const int s = local_of ? local_of[g] : (int)g;
+        double a = 0.0, b = 0.0;
+        if (s >= 0) sub_trace(partials, max_units, ranges[s], a, b);
+        sums[g] = a;
+        sums[P_global + g] = b;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) sums[2 * P_global] = (ctrl->status != GBE_OK) ? 1.0 : 0.0;
+}
+
 // Global FP64 traces over core positions -> stop rule and branch of the next step.
 // kind: 0 after the gather (X_0), 1 after a tensor-core step, 2 after an FP64 step.
+// The traces are the per-subgraph sums (sub_trace) added in global subgraph order, taken
+// from this rank's partials (sums == NULL) or from the exchanged buffer of a sharded run.
 // In a graph-launched run the last decision of a loop iteration (set_cond) also sets the
 // loop node's condition: continue while the run has not stopped, and never beyond
 // n_max + 8 iterations of the loop.
-__device__ void decide_body(Sp2Ctrl* ctrl, const double* __restrict__ partials, int max_units, int n_units, int kind,
-                            double* red, int* run);
+struct DecideIn {
+    const double* partials;
+    int max_units;
+    const int2* ranges;   // [P] work units of each subgraph for this kind
+    int P;
+    const double* sums;   // exchanged sums [2 P_global + 1], or NULL
+    int64_t P_global;
+    int kind;
+};
 
-__global__ void __launch_bounds__(512) decide_kernel(Sp2Ctrl* ctrl, const double* __restrict__ partials,
-                                                     int max_units, int n_units, int kind,
-                                                     cudaGraphConditionalHandle cond, int set_cond) {
+__device__ void decide_body(Sp2Ctrl* ctrl, const DecideIn& in, double* red, int* run);
+
+__global__ void __launch_bounds__(512) decide_kernel(Sp2Ctrl* ctrl, DecideIn in, cudaGraphConditionalHandle cond,
+                                                     int set_cond) {
     __shared__ double red[16];
     __shared__ int run;
-    decide_body(ctrl, partials, max_units, n_units, kind, red, &run);
+    decide_body(ctrl, in, red, &run);
     if (set_cond && threadIdx.x == 0) {
         __threadfence_block();
         Sp2Ctrl* C = ctrl;
@@ -316,16 +356,25 @@ __global__ void __launch_bounds__(512) decide_kernel(Sp2Ctrl* ctrl, const double
     }
 }
 
-__device__ void decide_body(Sp2Ctrl* ctrl, const double* __restrict__ partials, int max_units, int n_units, int kind,
-                            double* red, int* run_flag) {
+__device__ void decide_body(Sp2Ctrl* ctrl, const DecideIn& in, double* red, int* run_flag) {
     int& run = *run_flag;
+    const int kind = in.kind;
     if (threadIdx.x == 0) run = (kind == 0) ? 1 : ctrl->pending;
     __syncthreads();
     if (!run) return;
     double a = 0.0, b = 0.0;
-    for (int i = threadIdx.x; i < n_units; i += 512) {
-        a += partials[i];
-        b += partials[max_units + i];
+    if (in.sums) {
+        for (int64_t g = threadIdx.x; g < in.P_global; g += 512) {
+            a += in.sums[g];
+            b += in.sums[in.P_global + g];
+        }
+    } else {
+        for (int s = threadIdx.x; s < in.P; s += 512) {
+            double x, y;
+            sub_trace(in.partials, in.max_units, in.ranges[s], x, y);
+            a += x;
+            b += y;
+        }
     }
     double t1 = block_sum_d<512>(a, red);
     double t2 = block_sum_d<512>(b, red);
@@ -343,6 +392,7 @@ __device__ void decide_body(Sp2Ctrl* ctrl, const double* __restrict__ partials, 
     const int n = C->iter;
     C->t1[n] = t1;
     C->t2[n] = t2;
+    if (in.sums && in.sums[2 * in.P_global] != 0.0 && C->status == GBE_OK) C->status = GBE_EPEER;
     if (C->status != GBE_OK || !isfinite(t1) || !isfinite(t2)) {
         if (C->status == GBE_OK) C->status = GBE_ENUMERIC;
         C->stop = GBE_STOP_ERROR;
@@ -799,7 +849,74 @@ extern "C" int gbe_free_parts(gbe_parts* p) {
     gbe_free(p->d_core_count);
     gbe_free(p->d_sub_ptr);
     gbe_free(p->d_sub_idx);
+    gbe_free(p->d_local_of);
     delete p;
+    return GBE_OK;
+}
+
+extern "C" int gbe_shard_assign(int64_t P, const int64_t* sub_ptr, int world, int32_t* owner, double* load) {
+    GBE_CHECK_ARG(sub_ptr && owner && P >= 1 && world >= 1, "bad argument");
+    std::vector<double> cost(P);
+    for (int64_t s = 0; s < P; ++s) {
+        const double m = (double)(sub_ptr[s + 1] - sub_ptr[s]);
+        GBE_CHECK_ARG(m >= 1, "empty subgraph");
+        cost[s] = m * m * m;
+    }
+    std::vector<int64_t> order(P);
+    for (int64_t s = 0; s < P; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    std::vector<double> ld(world, 0.0);
+    for (int64_t s : order) {
+        int best = 0;
+        for (int r = 1; r < world; ++r)
+            if (ld[r] < ld[best]) best = r;
+        owner[s] = best;
+        ld[best] += cost[s];
+    }
+    if (load)
+        for (int r = 0; r < world; ++r) load[r] = ld[r];
+    return GBE_OK;
+}
+
+extern "C" int gbe_parts_shard(gbe_ctx* ctx, const gbe_parts* parts, const int32_t* owner, int rank, gbe_parts** local) {
+    AllocScope alloc_scope_(ctx);
+    GBE_CHECK_ARG(ctx && parts && owner && local, "NULL argument");
+    GBE_CHECK_ARG(parts->h_global_id.empty(), "a shard cannot be sharded again");
+    const int64_t P = parts->P;
+    std::vector<int32_t> idx(parts->total);
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    GBE_CUDA_TRY(cudaMemcpyAsync(idx.data(), parts->d_sub_idx, parts->total * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    std::vector<int32_t> cc;
+    std::vector<int64_t> sp(1, 0), gid;
+    std::vector<int32_t> si;
+    std::vector<int32_t> local_of(P, -1);
+    for (int64_t s = 0; s < P; ++s) {
+        if (owner[s] != rank) continue;
+        local_of[s] = (int32_t)gid.size();
+        gid.push_back(s);
+        cc.push_back(parts->h_core_count[s]);
+        si.insert(si.end(), idx.begin() + parts->h_sub_ptr[s], idx.begin() + parts->h_sub_ptr[s + 1]);
+        sp.push_back((int64_t)si.size());
+    }
+    GBE_CHECK_ARG(!gid.empty(), "this rank owns no subgraph");
+    gbe_parts* p = nullptr;
+    GBE_TRY(gbe_parts_import(ctx, parts->n, (int64_t)gid.size(), cc.data(), sp.data(), si.data(), &p));
+    p->P_global = P;
+    p->h_global_id = gid;
+    int r = gbe_alloc((void**)&p->d_local_of, P * 4);
+    if (r != GBE_OK) {
+        gbe_free_parts(p);
+        return r;
+    }
+    cudaError_t e = cudaMemcpyAsync(p->d_local_of, local_of.data(), P * 4, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        gbe_free_parts(p);
+        gbe_set_error("gbe_parts_shard: %s", cudaGetErrorString(e));
+        return GBE_ECUDA;
+    }
+    *local = p;
     return GBE_OK;
 }
 
@@ -812,6 +929,8 @@ extern "C" int gbe_free_subs(gbe_subs* X) {
     gbe_free(X->d_items_tc); gbe_free(X->d_items_64); gbe_free(X->d_partials); gbe_free(X->d_ctrl);
     gbe_free(X->d_items_tc_full); gbe_free(X->d_items_64_full);
     gbe_free(X->d_cta_ptr);
+    for (int k = 0; k < 3; ++k) gbe_free(X->d_ranges[k]);
+    gbe_free(X->d_sums);
     if (X->h_ctrl) cudaFreeHost(X->h_ctrl);
     for (int i = 0; i < 3; ++i) if (X->ev[i]) cudaEventDestroy(X->ev[i]);
     for (auto e : X->ev_tc) cudaEventDestroy(e);
@@ -895,6 +1014,19 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     X->n_items_tc_full = (int)ft_tc.size();
     X->n_items_64_full = (int)ft_64.size();
     X->max_units = (int)std::max<int64_t>(X->P, std::max(X->n_items_tc_full, X->n_items_64_full));
+    // work units of each subgraph per decision kind (the tiles of a subgraph are contiguous)
+    std::vector<int2> rg[3];
+    for (int k = 0; k < 3; ++k) rg[k].assign(X->P, make_int2(0, 0));
+    for (int64_t q = 0; q < X->P; ++q) rg[0][q] = make_int2((int)q, 1);
+    for (int k = 1; k < 3; ++k) {
+        const std::vector<TileItem>& its = k == 1 ? it_tc : it_64;
+        for (int i = 0; i < (int)its.size(); ++i) {
+            int2& e = rg[k][its[i].s];
+            if (e.y == 0) e.x = i;
+            ++e.y;
+        }
+    }
+    X->P_global = parts->h_global_id.empty() ? X->P : parts->P_global;
     int r = GBE_OK;
 #define ALLOC(ptr, bytes) \
     do { if (r == GBE_OK) r = gbe_alloc((void**)&(ptr), (bytes)); } while (0)
@@ -908,6 +1040,8 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     ALLOC(X->d_items_64_full, std::max<int64_t>(1, X->n_items_64_full) * sizeof(TileItem));
     ALLOC(X->d_partials, 2 * (int64_t)X->max_units * 8);
     ALLOC(X->d_ctrl, sizeof(Sp2Ctrl));
+    for (int k = 0; k < 3; ++k) ALLOC(X->d_ranges[k], X->P * sizeof(int2));
+    ALLOC(X->d_sums, (2 * X->P_global + 1) * 8);
     // FP64 iterates exist from the start only in FP64 states; mixed states allocate them when
     // a run first needs FP64 steps (ensure_f64)
     for (int i = 0; i < 2; ++i) {
@@ -937,6 +1071,7 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
         cudaMemcpyAsync(X->d_items_tc_full, ft_tc.data(), ft_tc.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
     if (X->n_items_64_full)
         cudaMemcpyAsync(X->d_items_64_full, ft_64.data(), ft_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
+    for (int k = 0; k < 3; ++k) cudaMemcpyAsync(X->d_ranges[k], rg[k].data(), X->P * sizeof(int2), cudaMemcpyHostToDevice, st);
     // The split planes need no clearing: the gather writes every stored (upper) block of side 0,
     // padding included, and each squaring writes every stored block of the side it produces
     // before any launch reads it.
@@ -1070,8 +1205,40 @@ static int check_gather_fits(const gbe_ctx* ctx, const gbe_subs* X) {
     return GBE_OK;
 }
 
+// Decision after the gather (kind 0) or a squaring (1 tensor-core, 2 FP64).  With a trace
+// exchange (sharded global-trace run) this rank's per-subgraph sums are written at their
+// global positions, summed over the ranks by the caller's exchange, and decided from.
+static int enqueue_decide(gbe_ctx* ctx, gbe_subs* X, int kind, const gbe_sp2_params* xp, cudaGraphConditionalHandle cond,
+                          bool set_cond) {
+    cudaStream_t st = ctx->stream;
+    DecideIn in;
+    in.partials = X->d_partials;
+    in.max_units = X->max_units;
+    in.ranges = X->d_ranges[kind];
+    in.P = (int)X->P;
+    in.sums = nullptr;
+    in.P_global = X->P_global;
+    in.kind = kind;
+    if (xp && xp->exchange) {
+        const int blocks = (int)std::min<int64_t>(ctx->sm_count, (X->P_global + 255) / 256);
+        sub_sums_kernel<<<std::max(1, blocks), 256, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->d_ranges[kind],
+                                                              X->parts->d_local_of, X->P_global, X->d_sums);
+        GBE_CUDA_TRY(cudaGetLastError());
+        const int rc = xp->exchange(xp->exchange_user, X->d_sums, 2 * X->P_global + 1, (void*)st);
+        if (rc != 0) {
+            gbe_set_error("trace exchange returned %d", rc);
+            return GBE_EPEER;
+        }
+        in.sums = X->d_sums;
+    }
+    decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, in, cond, set_cond ? 1 : 0);
+    GBE_CUDA_TRY(cudaGetLastError());
+    return GBE_OK;
+}
+
 // Control init, spectral bounds, gather and the first decision of a run (on ctx->stream).
-static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, gbe_subs* X) {
+static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, gbe_subs* X,
+                            const gbe_sp2_params* xp = nullptr) {
     cudaStream_t st = ctx->stream;
     init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
     GBE_CUDA_TRY(cudaGetLastError());
@@ -1084,16 +1251,14 @@ static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, g
                                              geom_of(X), X->max_mpad, X->planes[0], X->total_elems, X->f64[0],
                                              X->d_partials, X->max_units, L.htab_off, L.hbits);
     GBE_CUDA_TRY(cudaGetLastError());
-    decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, (int)X->P, 0, 0, 0);
-    GBE_CUDA_TRY(cudaGetLastError());
-    return GBE_OK;
+    return enqueue_decide(ctx, X, 0, xp, 0, false);
 }
 
 // One SP2 step: the tensor-core squaring and/or the FP64 squaring, each followed by its
 // decision (kernels whose turn it is not exit at once).  slot >= 0 records profiling
 // events; in a graph body slot = -1 and the last decision sets the loop condition.
 static int enqueue_step(gbe_ctx* ctx, gbe_subs* X, bool fp64_steps, int slot, cudaGraphConditionalHandle cond,
-                        bool set_cond) {
+                        bool set_cond, const gbe_sp2_params* xp = nullptr) {
     cudaStream_t st = ctx->stream;
     const bool prof = slot >= 0 && ctx->profile != 0;
     const bool has_tc = X->prec != GBE_PREC_FP64;
@@ -1101,8 +1266,7 @@ static int enqueue_step(gbe_ctx* ctx, gbe_subs* X, bool fp64_steps, int slot, cu
         if (prof) cudaEventRecord(X->ev_tc[2 * slot], st);
         GBE_TRY(gbe_tc_launch_square(ctx, X, slot));
         if (prof) cudaEventRecord(X->ev_tc[2 * slot + 1], st);
-        decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_tc, 1, cond,
-                                         set_cond && !fp64_steps ? 1 : 0);
+        GBE_TRY(enqueue_decide(ctx, X, 1, xp, cond, set_cond && !fp64_steps));
     }
     if (fp64_steps) {
         const int grid64 = std::max(1, std::min(X->n_items_64, ctx->sm_count * 4));
@@ -1111,10 +1275,9 @@ static int enqueue_step(gbe_ctx* ctx, gbe_subs* X, bool fp64_steps, int slot, cu
                                                    X->planes[1], X->total_elems, X->f64[0], X->f64[1], X->d_partials,
                                                    X->max_units, slot);
         if (prof) cudaEventRecord(X->ev_64[2 * slot + 1], st);
-        decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->n_items_64, 2, cond,
-                                         set_cond ? 1 : 0);
+        GBE_CUDA_TRY(cudaGetLastError());
+        GBE_TRY(enqueue_decide(ctx, X, 2, xp, cond, set_cond));
     }
-    GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }
 
@@ -1225,7 +1388,11 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
         GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     }
     const bool prof = ctx->profile != 0;
-    if (ctx->graphs && !prof) {
+    // a sharded global-trace run exchanges traces through the caller after every decision
+    const gbe_sp2_params* xp = (prm->exchange && in.branch_mode == GBE_BRANCH_GLOBAL_TRACE) ? prm : nullptr;
+    GBE_CHECK_ARG(!prm->exchange || !X->parts->h_global_id.empty() || X->P_global == X->P,
+                  "exchange given for a partition that is not a shard");
+    if (ctx->graphs && !prof && !xp) {
         // graph launch: the loop runs exactly as many steps as the device decides
         std::vector<unsigned char> key(sizeof(in) + 5 * sizeof(int64_t) + 1);
         unsigned char* k = key.data();
@@ -1256,7 +1423,7 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
         X->gkey = key;
     }
     cudaEventRecord(X->ev[0], st);
-    GBE_TRY(enqueue_prologue(ctx, H, in, X));
+    GBE_TRY(enqueue_prologue(ctx, H, in, X, xp));
     cudaEventRecord(X->ev[1], st);
     if (prof && (int)X->ev_tc.size() < 2 * prm->n_max) {
         for (int i = (int)X->ev_tc.size(); i < 2 * prm->n_max; ++i) {
@@ -1271,7 +1438,19 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     // the device's stop decision exit at once)
     const int slots = in.branch_mode == GBE_BRANCH_REPLAY ? std::min(prm->n_max, in.seq_len) : prm->n_max;
     X->last_slots = slots;
-    for (int slot = 0; slot < slots; ++slot) GBE_TRY(enqueue_step(ctx, X, fp64_steps, slot, 0, false));
+    for (int slot = 0; slot < slots; ++slot) {
+        GBE_TRY(enqueue_step(ctx, X, fp64_steps, slot, 0, false, xp));
+        if (xp) {
+            // every rank takes the same decisions, so all stop after the same step and make
+            // the same number of exchanges
+            GBE_CUDA_TRY(cudaMemcpyAsync(&X->h_ctrl->stop, &X->d_ctrl->stop, sizeof(int), cudaMemcpyDeviceToHost, st));
+            GBE_CUDA_TRY(cudaStreamSynchronize(st));
+            if (X->h_ctrl->stop != 0) {
+                X->last_slots = slot + 1;
+                break;
+            }
+        }
+    }
     X->last_prof = prof;
     GBE_CUDA_TRY(cudaGetLastError());
     cudaEventRecord(X->ev[2], st);

@@ -80,21 +80,27 @@ def test_reference_arm_line():
 
 def test_traffic_record_voided_by_source_change(tmp_path, monkeypatch):
     """The roofline's DRAM-traffic figure comes from a committed ncu record only while the
-    squaring kernel's sources hash to the value stored with it; any change voids it (null)."""
+    squaring kernel's sources hash to the value stored with it; any change voids it (null).
+    The record here is a stand-in written for the current sources in a scratch copy."""
+    import hashlib
     import shutil
     sys.path.insert(0, ROOT)
     import bench
-    rec = json.load(open(os.path.join(ROOT, "profiles", "traffic_sp2_square_tc_fp16x6_lattice32.json")))
+    srcs = bench.TRAFFIC_SOURCES["sp2_square_tc_fp16x6"]
     root = tmp_path / "repo"
     (root / "profiles").mkdir(parents=True)
-    shutil.copy(os.path.join(ROOT, "profiles", "traffic_sp2_square_tc_fp16x6_lattice32.json"), root / "profiles")
-    for src in rec["sources"]:
+    h = hashlib.sha256()
+    for src in srcs:
         (root / src).parent.mkdir(parents=True, exist_ok=True)
         shutil.copy(os.path.join(ROOT, src), root / src)
+        h.update(open(os.path.join(ROOT, src), "rb").read())
+    rec = {"kernel": "sp2_square_tc_fp16x6", "workload": "lattice32", "dram_bytes_per_launch": [100, 300],
+           "sources": srcs, "sha256": h.hexdigest(), "capture": "stand-in"}
+    with open(root / "profiles" / "traffic_sp2_square_tc_fp16x6_lattice32.json", "w") as f:
+        json.dump(rec, f)
     monkeypatch.setattr(bench, "ROOT", str(root))
-    t = bench.captured_traffic("sp2_square_tc_fp16x6", "lattice32")
-    assert t == sum(rec["dram_bytes_per_launch"]) / len(rec["dram_bytes_per_launch"])
-    with open(root / rec["sources"][0], "a") as f:
+    assert bench.captured_traffic("sp2_square_tc_fp16x6", "lattice32") == 200
+    with open(root / srcs[0], "a") as f:
         f.write("\n// changed\n")
     assert bench.captured_traffic("sp2_square_tc_fp16x6", "lattice32") is None
     assert bench.captured_traffic("sp2_square_tc_fp16x6", "no_such_workload") is None
