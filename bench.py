@@ -60,7 +60,8 @@ WORKLOADS = {
     "mlp1m": dict(kind="disordered", N=1 << 20, seed=2024, mlp=dict(rcand=4.0, cut=0.0)),
 }
 PRECS = {"fp16x6": ("FP16X6", "f16-split(x6)/f32-acc/f64-trace"),
-         "bf16x3": ("BF16X3", "bf16-split(x3)/f32-acc/f64-trace")}
+         "bf16x3": ("BF16X3", "bf16-split(x3)/f32-acc/f64-trace"),
+         "fp64tc": ("FP64TC", "f16-fixed-point-slices(x18 products)/f32-acc, FP64-grade")}
 
 
 def make_system(wl, seed):

@@ -266,7 +266,10 @@ enum {
     GBE_PREC_FP64    = 0, /* every squaring in FP64 on the FP64 pipe                          */
     GBE_PREC_FP16X6  = 1, /* tensor cores: 3-level fp16 split, 6 products, FP32 accumulation,
                              exact accumulation of the fixed-point leading part               */
-    GBE_PREC_BF16X3  = 2  /* tensor cores: per-element bf16 hi/lo split, 3 products            */
+    GBE_PREC_BF16X3  = 2, /* tensor cores: per-element bf16 hi/lo split, 3 products            */
+    GBE_PREC_FP64TC  = 3  /* tensor cores at FP64 grade: x held to 2^-50 as five fixed-point
+                             fp16 slices (an Ozaki-type slicing; not in the paper), 18 fp16
+                             products in four FP32 accumulators, the three leading ones exact */
 };
 
 enum {

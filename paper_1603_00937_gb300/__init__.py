@@ -39,7 +39,7 @@ GBE_ENOCONV, GBE_ENUMERIC, GBE_ECAPACITY, GBE_ENODEV, GBE_EPEER = -5, -6, -7, -8
 
 GRAPH_H2_THRESH, GRAPH_D_THRESH, GRAPH_EQ8_SYMBOLIC, GRAPH_HK_PATTERN, GRAPH_MLP = 0, 1, 2, 3, 4
 PART_SPATIAL_CELLS, PART_INDEX_BLOCKS = 0, 1
-PREC_FP64, PREC_FP16X6, PREC_BF16X3 = 0, 1, 2
+PREC_FP64, PREC_FP16X6, PREC_BF16X3, PREC_FP64TC = 0, 1, 2, 3
 BRANCH_GLOBAL_TRACE, BRANCH_REPLAY = 0, 1
 SCHED_ROUND_ROBIN, SCHED_BALANCED_RANGES = 0, 1
 SCHED_NAMES = {0: "round_robin", 1: "balanced_ranges"}

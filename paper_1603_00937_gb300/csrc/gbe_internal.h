@@ -146,7 +146,7 @@ struct gbe_subs {
     // storage
     // sides 0/1: ping-pong iterates; side 2: the fixed x of a Chebyshev expansion (allocated
     // by its first run)
-    uint16_t* planes[3] = {nullptr, nullptr, nullptr};  // tensor-core path: 4 planes x total_elems
+    uint16_t* planes[3] = {nullptr, nullptr, nullptr};  // tensor-core path: gbe_subs_planes(prec) planes x total_elems
     double* f64[3] = {nullptr, nullptr, nullptr};       // FP64 iterates
     // work lists
     TileItem* d_items_tc = nullptr;  int n_items_tc = 0;   // 128x128 tiles
@@ -208,6 +208,9 @@ __host__ __device__ inline int64_t blk_index(int64_t off, int mpad, int r, int c
 __host__ __device__ inline int64_t sym_index(int64_t off, int mpad, int r, int c) {
     return ((r >> 7) > (c >> 7)) ? blk_index(off, mpad, c, r) : blk_index(off, mpad, r, c);
 }
+
+// split planes of a tensor-core state (each plane total_elems fp16 / bf16 values)
+inline int gbe_subs_planes(int prec) { return prec == GBE_PREC_FP64TC ? 10 : 4; }
 
 // ----------------------------------------------------------------------------- launchers
 int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X);

@@ -181,14 +181,20 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                     if (b < 0) continue;
                     const double h = hv[u];
                     uint2 packed;
-                    if constexpr (prec == GBE_PREC_FP64) {
+                    if constexpr (prec == GBE_PREC_FP64 || prec == GBE_PREC_FP64TC) {
                         // the exact quotients, as the FP64 oracle computes them
                         const double x = foe ? (h - (a == b ? centre : 0.0)) / half : ((a == b ? emax : 0.0) - h) / range;
                         if (a < c) {
                             t2 += x * x;
                             if (a == b) t1 += x;
                         }
-                        packed = make_uint2((uint32_t)__double2loint(x), (uint32_t)__double2hiint(x));
+                        if constexpr (prec == GBE_PREC_FP64) {
+                            packed = make_uint2((uint32_t)__double2loint(x), (uint32_t)__double2hiint(x));
+                        } else {
+                            // FP64TC: x on the fixed-point grid 2^-50 (digits cut at write-out)
+                            const long long V = __double2ll_rn(x * 1125899906842624.0);
+                            packed = make_uint2((uint32_t)(unsigned long long)V, (uint32_t)((unsigned long long)V >> 32));
+                        }
                     } else {
                         // split paths need x to ~2^-35: off-diagonal x = -h / range as an FP32 pair
                         // product (no FP64 arithmetic: this part's FP64 pipe is narrow); the diagonal
@@ -236,6 +242,23 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                 uint2 u[8];
 #pragma unroll
                 for (int k = 0; k < 8; ++k) u[k] = rows8[(size_t)k * max_mpad + r];
+                if constexpr (prec == GBE_PREC_FP64TC) {
+                    // ten digit planes of the 8 values (split.cuh)
+                    uint32_t w10[GBE_F64TC_PLANES][4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const long long V0 = (long long)(((unsigned long long)u[2 * k].y << 32) | u[2 * k].x);
+                        const long long V1 = (long long)(((unsigned long long)u[2 * k + 1].y << 32) | u[2 * k + 1].x);
+                        uint32_t t[GBE_F64TC_PLANES];
+                        f64tc_planes2(f64tc_digits(V0), f64tc_digits(V1), t);
+#pragma unroll
+                        for (int q = 0; q < GBE_F64TC_PLANES; ++q) w10[q][k] = t[q];
+                    }
+                    const int64_t e = blk_index(off, mpad, r, a0);
+#pragma unroll
+                    for (int q = 0; q < GBE_F64TC_PLANES; ++q)
+                        *reinterpret_cast<uint4*>(planes + e + q * plane_stride) = make_uint4(w10[q][0], w10[q][1], w10[q][2], w10[q][3]);
+                } else {
                 uint32_t w[4][4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -249,11 +272,12 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
                     if (q < np) *reinterpret_cast<uint4*>(planes + e + q * plane_stride) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+                }
             }
             __syncthreads();
         }
     }
-    if constexpr (prec != GBE_PREC_FP64) t2 = (double)t2h + (double)t2l;
+    if constexpr (prec != GBE_PREC_FP64 && prec != GBE_PREC_FP64TC) t2 = (double)t2h + (double)t2l;
     double s1 = block_sum_d<256>(t1, red);
     double s2 = block_sum_d<256>(t2, red + 8);
     if (threadIdx.x == 0) {
@@ -399,7 +423,7 @@ __device__ void decide_body(Sp2Ctrl* ctrl, const DecideIn& in, double* red, int*
         return;
     }
     const double e = fabs(t1 - t2);
-    const bool mixed = (C->prec != GBE_PREC_FP64);
+    const bool mixed = (C->prec == GBE_PREC_FP16X6 || C->prec == GBE_PREC_BF16X3);   // FP64TC is FP64-grade
     if (C->branch_mode == GBE_BRANCH_REPLAY) {
         if (n >= C->seq_len || n >= C->n_max) { C->stop = GBE_STOP_REPLAY; return; }
         C->branch = C->seq_in[n] ? 1 : 0;
@@ -462,6 +486,9 @@ __device__ __forceinline__ double load_x(int fmt, int prec, const uint16_t* pl, 
     if (fmt == 1) return f[blk_index(off, mpad, r, c)];
     const int64_t e = sym_index(off, mpad, r, c);
     if (prec == GBE_PREC_FP16X6) return oz_value(pl[e], pl[e + ps], pl[e + 2 * ps]);
+    if (prec == GBE_PREC_FP64TC)
+        return (double)f64tc_from_planes(pl[e + ps], pl[e + 2 * ps], pl[e + 3 * ps], pl[e + 4 * ps], pl[e + 8 * ps]) *
+               8.881784197001252e-16;   // 2^-50
     return bf_value(pl[e], pl[e + ps]);
 }
 
@@ -673,6 +700,20 @@ __global__ void __launch_bounds__(256) assemble_kernel(const Sp2Ctrl* ctrl, cons
                         const double2 d2 = reinterpret_cast<const double2*>(f + e)[t];
                         v[2 * t] = d2.x;
                         v[2 * t + 1] = d2.y;
+                    }
+                } else if (prec == GBE_PREC_FP64TC) {
+                    uint4 dg[5];
+#pragma unroll
+                    for (int p = 0; p < 5; ++p) dg[p] = *reinterpret_cast<const uint4*>(pl + (p < 4 ? p + 1 : 8) * plane_stride + e);
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        const int sh = 16 * (t & 1);
+                        auto hw = [&](const uint4& u) {
+                            const int q = t >> 1;
+                            return (uint16_t)((q == 0 ? u.x : (q == 1 ? u.y : (q == 2 ? u.z : u.w))) >> sh);
+                        };
+                        v[t] = (double)f64tc_from_planes(hw(dg[0]), hw(dg[1]), hw(dg[2]), hw(dg[3]), hw(dg[4])) *
+                               8.881784197001252e-16;
                     }
                 } else if (prec == GBE_PREC_FP16X6) {
                     const uint4 a = *reinterpret_cast<const uint4*>(pl + e);
@@ -969,7 +1010,8 @@ static void make_items(const std::vector<int32_t>& dim, const std::vector<int32_
 extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, gbe_subs** out) {
     AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && parts && out, "NULL argument");
-    GBE_CHECK_ARG(prec == GBE_PREC_FP64 || prec == GBE_PREC_FP16X6 || prec == GBE_PREC_BF16X3, "unknown prec");
+    GBE_CHECK_ARG(prec == GBE_PREC_FP64 || prec == GBE_PREC_FP16X6 || prec == GBE_PREC_BF16X3 || prec == GBE_PREC_FP64TC,
+                  "unknown prec");
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     gbe_subs* X = new gbe_subs();
     X->parts = parts;
@@ -978,7 +1020,8 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     X->h_off.resize(X->P); X->h_mpad.resize(X->P); X->h_m.resize(X->P); X->h_c.resize(X->P);
     int64_t total = 0;
     double alg = 0.0, mma = 0.0, f64 = 0.0, mma_full = 0.0, f64_full = 0.0;
-    const int nprod = (prec == GBE_PREC_FP16X6) ? 6 : 3;
+    const int nprod = (prec == GBE_PREC_FP16X6) ? 6 : (prec == GBE_PREC_FP64TC ? 18 : 3);
+    const int kcw = (prec == GBE_PREC_FP64TC) ? 16 : 32;   // K-chunk width of the tensor-core kernel
     for (int64_t s = 0; s < X->P; ++s) {
         const int m = (int)(parts->h_sub_ptr[s + 1] - parts->h_sub_ptr[s]);
         const int mpad = (m + 127) & ~127;
@@ -987,8 +1030,12 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
         total += (int64_t)mpad * mpad;
         X->max_mpad = std::max(X->max_mpad, mpad);
         alg += 2.0 * (double)m * m * m;
-        const int T = mpad / 128, kk = (m + 31) & ~31;
-        mma += (double)nprod * 2.0 * 128.0 * 128.0 * kk * (T * (T + 1) / 2);
+        // executed MMA work: K in steps of 16 (a squaring skips an all-padding second half of
+        // its last chunk), the last column block only up to the next multiple of 16 past m;
+        // a Chebyshev step runs whole chunks and whole tiles
+        const int T = mpad / 128, kk = (m + kcw - 1) / kcw * kcw, kt = (m + 15) & ~15;
+        const int nlast = ((m - 128 * (T - 1) + 15) >> 4) << 4;
+        mma += (double)nprod * 2.0 * 128.0 * kt * (128.0 * (T - 1) * T / 2 + (double)nlast * T);
         mma_full += (double)nprod * 2.0 * 128.0 * 128.0 * kk * (T * T);
         const int T64 = (m + 63) / 64, k16 = (m + 15) & ~15;
         f64 += 2.0 * 64.0 * 64.0 * k16 * (T64 * (T64 + 1) / 2);
@@ -1048,7 +1095,7 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
         if (prec == GBE_PREC_FP64) {
             ALLOC(X->f64[i], total * 8);
         } else {
-            ALLOC(X->planes[i], 4 * total * 2);
+            ALLOC(X->planes[i], (int64_t)gbe_subs_planes(prec) * total * 2);
         }
     }
     if (r == GBE_OK && prec != GBE_PREC_FP64 && !(X->planes[0] && X->planes[1])) r = GBE_ENOMEM;
@@ -1072,11 +1119,13 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     if (X->n_items_64_full)
         cudaMemcpyAsync(X->d_items_64_full, ft_64.data(), ft_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
     for (int k = 0; k < 3; ++k) cudaMemcpyAsync(X->d_ranges[k], rg[k].data(), X->P * sizeof(int2), cudaMemcpyHostToDevice, st);
-    // The split planes need no clearing: the gather writes every stored (upper) block of side 0,
-    // padding included, and each squaring writes every stored block of the side it produces
-    // before any launch reads it.
-    for (int i = 0; i < 2; ++i)
+    // Both sides of the split planes start at zero: the gather writes every stored (upper)
+    // block of side 0, padding included, but a squaring leaves the columns of a subgraph's
+    // last block past the next multiple of 16 above m unwritten, and they must read as zero.
+    for (int i = 0; i < 2; ++i) {
         if (X->f64[i]) cudaMemsetAsync(X->f64[i], 0, total * 8, st);
+        if (X->planes[i]) cudaMemsetAsync(X->planes[i], 0, (size_t)gbe_subs_planes(prec) * total * 2, st);
+    }
     GBE_CUDA_TRY(cudaStreamSynchronize(st));
     if (prec != GBE_PREC_FP64) {
         r = gbe_tc_make_tmaps(X);
@@ -1112,6 +1161,7 @@ std::vector<int64_t> gbe_subs_shape_key(const gbe_ctx* ctx, const gbe_subs* X) {
 int gbe_subs_apply_config(gbe_ctx* ctx, gbe_subs* X, const gbe_tc_config& cfg) {
     GBE_CHECK_ARG(cfg.schedule == GBE_SCHED_ROUND_ROBIN || cfg.schedule == GBE_SCHED_BALANCED_RANGES, "schedule");
     GBE_CHECK_ARG(cfg.kchunk == 0 || cfg.kchunk == 16 || cfg.kchunk == 32, "kchunk must be 0, 16 or 32");
+    GBE_CHECK_ARG(X->prec != GBE_PREC_FP64TC || cfg.kchunk != 32, "the FP64TC squaring runs 16-column K-chunks only");
     if (X->prec != GBE_PREC_FP64 && cfg.stages != 0) {
         int opt[8];
         const int n = gbe_tc_stage_options(X->prec, cfg.kchunk, opt, 8);
@@ -1175,6 +1225,17 @@ int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X) {
     gershgorin_kernel<<<blocks, 256, 0, ctx->stream>>>(H->rowptr, H->col, H->val, H->n, X->d_ctrl);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
+}
+
+typedef void (*GatherFn)(Sp2Ctrl*, const int64_t*, const int32_t*, const double*, const int64_t*, const int32_t*,
+                         SubsGeom, int, uint16_t*, int64_t, double*, double*, int, int, int);
+static GatherFn gather_for(int prec) {
+    switch (prec) {
+        case GBE_PREC_FP64: return gather_kernel<GBE_PREC_FP64>;
+        case GBE_PREC_FP16X6: return gather_kernel<GBE_PREC_FP16X6>;
+        case GBE_PREC_FP64TC: return gather_kernel<GBE_PREC_FP64TC>;
+        default: return gather_kernel<GBE_PREC_BF16X3>;
+    }
 }
 
 // Dynamic shared memory of the gather: 8 dense rows, the local->global list, and a hash
@@ -1245,8 +1306,7 @@ static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, g
     if (!in.eps_given) GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
     const gbe_parts* parts = X->parts;
     const GatherLayout L = gather_layout(X);
-    auto gk = X->prec == GBE_PREC_FP64 ? gather_kernel<GBE_PREC_FP64>
-            : (X->prec == GBE_PREC_FP16X6 ? gather_kernel<GBE_PREC_FP16X6> : gather_kernel<GBE_PREC_BF16X3>);
+    auto gk = gather_for(X->prec);
     gk<<<(unsigned)X->P, 256, L.smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
                                              geom_of(X), X->max_mpad, X->planes[0], X->total_elems, X->f64[0],
                                              X->d_partials, X->max_units, L.htab_off, L.hbits);
@@ -1364,7 +1424,7 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     in.n_max = prm->n_max;
     in.branch_mode = prm->branch_mode;
     in.seq_len = prm->branch_mode == GBE_BRANCH_REPLAY ? prm->seq_len : 0;
-    in.fp64_tail = prm->fp64_tail;
+    in.fp64_tail = prm->prec == GBE_PREC_FP64TC ? 0 : prm->fp64_tail;   // FP64TC is FP64-grade throughout
     in.prec = prm->prec;
     in.eps_given = prm->eps_given;
     in.eps_min = prm->eps_min;
@@ -1377,14 +1437,13 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     in.out_scale = 1.0;
     if (in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len) memcpy(in.seq_in, prm->seq_in, in.seq_len);
     if (in.prec != GBE_PREC_FP64 && in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len <= in.fp64_tail) in.mode = 1;
-    const bool fp64_steps = X->prec == GBE_PREC_FP64 || prm->fp64_tail > 0;
+    const bool fp64_steps = X->prec == GBE_PREC_FP64 || in.fp64_tail > 0;
     GBE_TRY(check_gather_fits(ctx, X));
     if (fp64_steps) GBE_TRY(ensure_f64(X, st));
     // kernel attributes are set outside any capture
     {
         const GatherLayout L = gather_layout(X);
-        auto gk = X->prec == GBE_PREC_FP64 ? gather_kernel<GBE_PREC_FP64>
-                : (X->prec == GBE_PREC_FP16X6 ? gather_kernel<GBE_PREC_FP16X6> : gather_kernel<GBE_PREC_BF16X3>);
+        auto gk = gather_for(X->prec);
         GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     }
     const bool prof = ctx->profile != 0;

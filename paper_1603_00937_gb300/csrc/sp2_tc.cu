@@ -121,6 +121,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr)
         : "memory");
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
@@ -162,47 +168,90 @@ __device__ __forceinline__ uint64_t sdesc_mnmajor(uint32_t saddr) {
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator, A/B type (0 fp16, 1 bf16),
-// K-major operands (bits 15/16 select MN-major per operand), N = 128, M = 128.
-__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type) {
-    return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// K-major operands (bits 15/16 select MN-major per operand), N = n (a multiple of 16, at
+// most 128 here), M = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t ab_type, uint32_t n = 128) {
+    return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// Columns of output tile (I, J) that a squaring computes: in a subgraph's last column block
+// only up to the first multiple of 16 at or past m (every iterate is zero beyond m, and those
+// columns are never written: they keep the zeros the state starts with); all 128 for a
+// Chebyshev step.
+__device__ __forceinline__ int tile_cols(int m, int J, bool foe) {
+    const int rest = m - 128 * J;
+    return (foe || rest >= 128) ? 128 : ((rest + 15) >> 4) << 4;
 }
 
 // ------------------------------------------------------------------ recipes
 // Operand slots of a stage: A slots first, then B slots, each side in storage-plane order
-// so that one 3-D TMA box (planes as its third dimension) fills a side's slots; `plane` is
-// the storage plane, `alias` the A slot holding the same plane on diagonal tiles (-1: always
-// loaded).  On a diagonal tile B's non-aliased slots are the planes kA.. (kDiag of them).
+// so that one 3-D TMA box (planes as its third dimension) fills a side's slots.  A slot i
+// holds plane i; B slot kA + j holds plane kBPlane0 + j.  On a diagonal tile B's planes
+// below kA are A's (the same block), so B loads only its planes kDiagPlane.. (kDiag of
+// them) into their own slots.  pa / pb / pacc: A slot, B slot and accumulator of product p.
+// TMEM: kAcc accumulators of 128 columns per tile, kTmemBufCols columns per buffer, 512 /
+// kTmemBufCols buffers (two: the epilogue of one tile overlaps the next tile's MMAs).
 template <int PREC>
 struct Recipe;
 
-// Tables are packed 4-bit fields indexed by slot / product number.
+__host__ __device__ constexpr int nib(uint32_t v, int i) { return (int)((v >> (4 * i)) & 0xFu); }
+
 template <>
 struct Recipe<GBE_PREC_FP16X6> {
     // slots: A {s0, s1, s2}, B {s0, s1, s2, s1s}; products into acc0: s0 s0^T,
     // into acc1 (units 2^-11): s0 s1^T, s1 s0^T, s1 s1s^T, s0 s2^T, s2 s0^T
     static constexpr int kSlots = 7, kA = 3, kProducts = 6, kPlanes = 4, kStages = 4, kDiag = 1;
+    static constexpr int kAcc = 2, kTmemBufCols = 256, kBPlane0 = 0, kDiagPlane = 3, kStages16 = 8;
     static constexpr uint32_t kType = 0;  // fp16
-    static constexpr uint32_t kPlane = 0x3210210u, kAlias1 = 0x0321000u;
-    static constexpr uint32_t kPa = 0x201100u, kPb = 0x356343u, kPacc = 0x111110u;
+    __host__ __device__ static constexpr int pa(int p) { return nib(0x201100u, p); }
+    __host__ __device__ static constexpr int pb(int p) { return nib(0x356343u, p); }
+    __host__ __device__ static constexpr int pacc(int p) { return nib(0x111110u, p); }
 };
 
 template <>
 struct Recipe<GBE_PREC_BF16X3> {
     // slots: A {hi, lo}, B {hi, lo}; products hi hi^T + hi lo^T + lo hi^T into acc0
     static constexpr int kSlots = 4, kA = 2, kProducts = 3, kPlanes = 2, kStages = 6, kDiag = 0;
+    static constexpr int kAcc = 1, kTmemBufCols = 256, kBPlane0 = 0, kDiagPlane = 2, kStages16 = 12;
     static constexpr uint32_t kType = 1;  // bf16
-    static constexpr uint32_t kPlane = 0x1010u, kAlias1 = 0x2100u;
-    static constexpr uint32_t kPa = 0x100u, kPb = 0x232u, kPacc = 0x0u;
+    __host__ __device__ static constexpr int pa(int p) { return nib(0x100u, p); }
+    __host__ __device__ static constexpr int pb(int p) { return nib(0x232u, p); }
+    __host__ __device__ static constexpr int pacc(int p) { return 0; }
 };
 
-__host__ __device__ constexpr int nib(uint32_t v, int i) { return (int)((v >> (4 * i)) & 0xFu); }
-template <class R> __device__ __forceinline__ int slot_plane(int s) { return nib(R::kPlane, s); }
-template <class R> __device__ __forceinline__ int slot_alias(int s) { return nib(R::kAlias1, s) - 1; }
+template <>
+struct Recipe<GBE_PREC_FP64TC> {
+    // planes 0 u', 1 t0, 2 t1, 3 t2, 4 t3, 5 u, 6 v, 7 t3', 8 t4', 9 t2' (split.cuh); A slots
+    // 0-8 = planes 0-8, B slots 9-17 = planes 1-9 (B slot of plane q: 8 + q).  Four
+    // accumulators fill the TMEM, so the epilogue does not overlap the next tile's MMAs;
+    // only 16-column K-chunks fit (a stage of 18 slots is 72 KB).
+    static constexpr int kSlots = 18, kA = 9, kProducts = 18, kPlanes = 10, kStages = 0, kDiag = 1;
+    static constexpr int kAcc = 4, kTmemBufCols = 512, kBPlane0 = 1, kDiagPlane = 9, kStages16 = 3;
+    static constexpr uint32_t kType = 0;  // fp16
+    //  ACC0: t0 t0 | ACC1: t0 t1, t1 t0, u' u | ACC2: t0 t2, t2 t0, u v, v u, v v |
+    //  ACC3: t0 t3, t3 t0, t1 t2, t2 t1 (2^-30); t0 t4', t4' t0, t1 t3', t3' t1, t2 t2' (2^-40)
+    __host__ __device__ static constexpr int pa(int p) {
+        constexpr int t[18] = {1, 1, 2, 0, 1, 3, 5, 6, 6, 1, 4, 2, 3, 1, 8, 2, 7, 3};
+        return t[p];
+    }
+    __host__ __device__ static constexpr int pb(int p) {
+        constexpr int t[18] = {9, 10, 9, 13, 11, 9, 14, 13, 14, 12, 9, 11, 10, 16, 9, 15, 10, 17};
+        return t[p];
+    }
+    __host__ __device__ static constexpr int pacc(int p) {
+        constexpr int t[18] = {0, 1, 1, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+        return t[p];
+    }
+};
 
-// Default ring depth: the recipe's for 32-column chunks, twice that for 16-column ones (the
-// same bytes in flight).
+// A slot holding the same plane as B slot b on a diagonal tile, or -1 (loaded).
+template <class R> __host__ __device__ constexpr int slot_alias(int b) {
+    return (b >= R::kA && R::kBPlane0 + (b - R::kA) < R::kA) ? R::kBPlane0 + (b - R::kA) : -1;
+}
+
+// Default ring depth for a K-chunk width.
 template <int PREC, int KC>
-constexpr int default_stages() { return Recipe<PREC>::kStages * (32 / KC); }
+constexpr int default_stages() { return KC == 32 ? Recipe<PREC>::kStages : Recipe<PREC>::kStages16; }
 
 // Shared memory of a CTA with an NS-deep ring of KC-column chunks (NS = 0: the default).
 template <int PREC, int NS = 0, int KC = 32>
@@ -371,8 +420,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const int Rt = side == 0 ? w.I : w.J;
                         const int bx = side == 0 ? 0 : (diag ? 2 : 1);
                         if (side == 1 && diag && R::kDiag == 0) continue;
-                        const int slot0 = side == 0 ? 0 : (diag ? R::kA + R::kA : R::kA);
-                        const int z = side == 1 && diag ? R::kA : 0;
+                        // B: planes kBPlane0.. into slots kA..; on a diagonal tile only planes
+                        // kDiagPlane.. (the others are A's) into their own slots
+                        const int slot0 = side == 0 ? 0 : (diag ? R::kA + R::kDiagPlane - R::kBPlane0 : R::kA);
+                        const int z = side == 0 ? 0 : (diag ? R::kDiagPlane : R::kBPlane0);
                         unsigned char* dst = st + (size_t)slot0 * kTileBytes;
                         const CUtensorMap(*tm)[3] = side == 0 ? tmA : tmB;
                         // a Chebyshev step's b is not symmetric to the last bit: its block (kb, J)
@@ -408,7 +459,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ MMA issuer
         // The whole warp runs the loop (every operand is warp-uniform); one elected lane
         // issues each tcgen05 instruction and lane 0 waits on the barriers for the warp.
-        constexpr uint32_t idesc = idesc_f16(R::kType);
         int stage = 0;
         uint32_t phase = 0;
         int tb = 0;
@@ -428,6 +478,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int m = args.g.m[w.s];
             const int nk = (m + KC - 1) / KC;
             const bool diag = (w.I == w.J) && !FOE;
+            const uint32_t idesc = idesc_f16(R::kType, (uint32_t)tile_cols(m, w.J, FOE));
 #ifdef GBE_TC_STATS
             st_acc[6] += (unsigned long long)(clock64() - ts0);
 #endif
@@ -439,7 +490,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!got) { ok = false; break; }
             tc_fence_after();
-            const uint32_t dacc0 = tmem_base + (uint32_t)(tb * 256);
+            const uint32_t dacc0 = tmem_base + (uint32_t)(tb * R::kTmemBufCols);
             for (int kc = 0; kc < nk; ++kc) {
                 {
                     TC_T0();
@@ -455,12 +506,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int kb = kc / kCPB;
                 const bool tA = w.I > kb, tB = FOE || w.J > kb;   // operand loaded transposed (MN-major)
                 const uint32_t idesc_t = idesc | ((uint32_t)tA << 15) | ((uint32_t)tB << 16);
+                // k-steps of 16 holding columns below m (a squaring skips the last chunk's second
+                // half when it is all padding; a Chebyshev step runs every k-step)
+                const int ksn = FOE ? KC / 16 : min(KC / 16, (m - kc * KC + 15) >> 4);
 #pragma unroll
                 for (int ks = 0; ks < KC / 16; ++ks) {
+                    if (ks >= ksn) break;
 #pragma unroll
                     for (int p = 0; p < R::kProducts; ++p) {
-                        const int a = nib(R::kPa, p), acc = nib(R::kPacc, p);
-                        int b = nib(R::kPb, p);
+                        const int a = R::pa(p), acc = R::pacc(p);
+                        int b = R::pb(p);
                         if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);   // never for FOE
                         const uint32_t aa = sbase + a * kTileBytes, ba = sbase + b * kTileBytes;
                         const uint64_t da = tA ? sdesc_mnmajor<KC>(aa + ks * 256) : sdesc_kmajor(aa + ks * 4096);
@@ -469,7 +524,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         bool first = (kc == 0 && ks == 0);
                         if (first) {
                             for (int q = 0; q < p; ++q)
-                                if (nib(R::kPacc, q) == acc) first = false;
+                                if (R::pacc(q) == acc) first = false;
                         }
                         umma_f16(dacc0 + acc * 128, da, db, idesc_t, first ? 0u : 1u);
                     }
@@ -482,8 +537,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
             umma_commit(&tfull[tb]);
-            tb ^= 1;
-            if (tb == 0) tph ^= 1;
+            if (++tb == 512 / R::kTmemBufCols) { tb = 0; tph ^= 1; }
         }
         if (!ok && lane == 0) {
             *abort_flag = 1;
@@ -515,6 +569,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int row = 128 * w.I + a;
             const bool core_row = row < c;
             const bool offdiag = (w.I != w.J);
+            const int ncol = tile_cols(args.g.m[w.s], w.J, FOE);   // columns the MMAs computed
+            // this warp's 16-column chunks (FP64TC: 8-column chunks) inside them, 0..4 (0..8)
+            const int nch = max(0, min(4, (ncol - 64 * half + 15) >> 4));
+            const int nch8 = max(0, min(8, (ncol - 64 * half + 7) >> 3));
             // X_n of the first chunk, fetched before the accumulator is ready
             uint32_t xn[kXP][8];
             auto fetch_x = [&](int ch) {
@@ -527,7 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     xn[p][4] = v1.x; xn[p][5] = v1.y; xn[p][6] = v1.z; xn[p][7] = v1.w;
                 }
             };
-            if (use_c) fetch_x(4 * half);
+            if (use_c && PREC != GBE_PREC_FP64TC && nch > 0) fetch_x(4 * half);
             bool ok;
             {
                 TC_T0();
@@ -542,20 +600,91 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             float sh = 0.f, sl = 0.f, dP = 0.f, dQ = 0.f;
-            for (int cc = 0; cc < 4; ++cc) {
+            if ((PREC == GBE_PREC_FP64TC ? nch8 : nch) == 0) {
+                // no column of this warp's half was computed: nothing to read or write
+                tc_fence_before();
+                mbar_arrive(&tempty[tb]);
+            }
+            if constexpr (PREC == GBE_PREC_FP64TC) {
+                // X^2 = ACC0 + 2^-10 ACC1 + 2^-20 ACC2 + 2^-30 ACC3 as an integer V in units of
+                // 2^-50 (ACC0..2 hold exact multiples of 2^-20; ACC3 is rounded there), the branch
+                // 2 X_n - X^2 in the same integers, then the digits of the next iterate
+                for (int cc = 0; cc < nch8; ++cc) {
+                    const int col0 = 128 * w.J + 64 * half + 8 * cc;
+                    const uint32_t ta = lane_addr + (uint32_t)(tb * R::kTmemBufCols + 64 * half + 8 * cc);
+                    uint32_t r0[8], r1[8], r2[8], r3[8];
+                    tmem_ld8(ta, r0);
+                    tmem_ld8(ta + 128, r1);
+                    tmem_ld8(ta + 256, r2);
+                    tmem_ld8(ta + 384, r3);
+                    const int64_t e0 = blk_index(off, mpad, row, col0);
+                    uint4 xv[5] = {};
+                    if (use_c) {
+                        // X_n digits t0, t1, t2, t3 (planes 1-4) and t4' (plane 8)
+#pragma unroll
+                        for (int p = 0; p < 5; ++p)
+                            xv[p] = *reinterpret_cast<const uint4*>(pin + (p < 4 ? p + 1 : 8) * ps + e0);
+                    }
+                    tmem_wait_ld();
+                    if (cc == nch8 - 1) {
+                        tc_fence_before();
+                        mbar_arrive(&tempty[tb]);
+                    }
+                    uint32_t ow[GBE_F64TC_PLANES][4];
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        F64Digits d[2];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int j = 2 * jj + e;
+                            const int n0 = __float2int_rn(__uint_as_float(r0[j]) * 1048576.0f);
+                            const int n1 = __float2int_rn(__uint_as_float(r1[j]) * 1048576.0f);
+                            const int n2 = __float2int_rn(__uint_as_float(r2[j]) * 1048576.0f);
+                            const int n3 = __float2int_rn(__uint_as_float(r3[j]) * 1048576.0f);
+                            long long V = ((long long)n0 << 30) + ((long long)n1 << 20) + ((long long)n2 << 10) + (long long)n3;
+                            if (use_c) {
+                                const int sh16 = 16 * e;
+                                auto hw = [&](const uint4& u) {
+                                    const uint32_t wd = jj == 0 ? u.x : (jj == 1 ? u.y : (jj == 2 ? u.z : u.w));
+                                    return (uint16_t)(wd >> sh16);
+                                };
+                                const long long Vn = f64tc_from_planes(hw(xv[0]), hw(xv[1]), hw(xv[2]), hw(xv[3]), hw(xv[4]));
+                                V = 2 * Vn - V;
+                            }
+                            d[e] = f64tc_digits(V);
+                            float P, Q;
+                            f64tc_pair(d[e], P, Q);
+                            const int colg = col0 + j;
+                            const float wgt = (float)((int)core_row + (int)(offdiag && colg < c));
+                            if (wgt != 0.0f) df_add_sq(sh, sl, P, Q, wgt);
+                            const bool dg = (colg == row);
+                            dP = dg ? P : dP;
+                            dQ = dg ? Q : dQ;
+                        }
+                        uint32_t w10[GBE_F64TC_PLANES];
+                        f64tc_planes2(d[0], d[1], w10);
+#pragma unroll
+                        for (int p = 0; p < GBE_F64TC_PLANES; ++p) ow[p][jj] = w10[p];
+                    }
+#pragma unroll
+                    for (int p = 0; p < GBE_F64TC_PLANES; ++p)
+                        *reinterpret_cast<uint4*>(pout + p * ps + e0) = make_uint4(ow[p][0], ow[p][1], ow[p][2], ow[p][3]);
+                }
+            } else
+            for (int cc = 0; cc < nch; ++cc) {
                 const int ch = 4 * half + cc;
                 const int col0 = 128 * w.J + 16 * ch;
                 uint32_t ra[16], rb[16];
-                tmem_ld16(lane_addr + (uint32_t)(tb * 256 + 16 * ch), ra);
-                if (R::kPlanes == 4) tmem_ld16(lane_addr + (uint32_t)(tb * 256 + 128 + 16 * ch), rb);
+                tmem_ld16(lane_addr + (uint32_t)(tb * R::kTmemBufCols + 16 * ch), ra);
+                if (R::kPlanes == 4) tmem_ld16(lane_addr + (uint32_t)(tb * R::kTmemBufCols + 128 + 16 * ch), rb);
                 uint32_t xw[kXP][8];
 #pragma unroll
                 for (int p = 0; p < kXP; ++p)
 #pragma unroll
                     for (int k = 0; k < 8; ++k) xw[p][k] = xn[p][k];
-                if (use_c && cc < 3) fetch_x(ch + 1);
+                if (use_c && cc < nch - 1) fetch_x(ch + 1);
                 tmem_wait_ld();
-                if (cc == 3) {
+                if (cc == nch - 1) {
                     tc_fence_before();
                     mbar_arrive(&tempty[tb]);
                 }
@@ -659,8 +788,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #ifdef GBE_TC_STATS
             if (lane == 0) st_acc[4] += 1ull;
 #endif
-            tb ^= 1;
-            if (tb == 0) tph ^= 1;
+            if (++tb == 512 / R::kTmemBufCols) { tb = 0; tph ^= 1; }
         }
         tc_fence_before();
     }
@@ -712,15 +840,19 @@ static const TcVariant kVariants[] = {
     GBE_TC_VARIANT(GBE_PREC_FP16X6, true, 0, 32),  GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 0, 32),
     GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 4, 32), GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 7, 32),
     GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 0, 16), GBE_TC_VARIANT(GBE_PREC_BF16X3, false, 14, 16),
+    GBE_TC_VARIANT(GBE_PREC_FP64TC, false, 0, 16),
 };
 #undef GBE_TC_VARIANT
 
 // stages = 0: the default depth for the chunk width; kc = 0: 32 columns
+static int default_kchunk(int prec) { return prec == GBE_PREC_FP64TC ? 16 : 32; }
+
 static const TcVariant* find_variant(int prec, bool foe, int stages, int kc) {
-    if (kc == 0) kc = 32;
+    if (kc == 0) kc = default_kchunk(prec);
     if (stages == 0) {
-        const int base = prec == GBE_PREC_FP16X6 ? Recipe<GBE_PREC_FP16X6>::kStages : Recipe<GBE_PREC_BF16X3>::kStages;
-        stages = base * (32 / kc);
+        if (prec == GBE_PREC_FP16X6) stages = kc == 32 ? default_stages<GBE_PREC_FP16X6, 32>() : default_stages<GBE_PREC_FP16X6, 16>();
+        else if (prec == GBE_PREC_BF16X3) stages = kc == 32 ? default_stages<GBE_PREC_BF16X3, 32>() : default_stages<GBE_PREC_BF16X3, 16>();
+        else stages = default_stages<GBE_PREC_FP64TC, 16>();
     }
     for (const TcVariant& v : kVariants)
         if (v.prec == prec && v.foe == foe && v.kc == kc && v.stages == stages) return &v;
@@ -753,7 +885,7 @@ int gbe_tc_prepare(gbe_ctx* ctx) {
 }
 
 int gbe_tc_stage_options(int prec, int kc, int* stages, int cap) {
-    if (kc == 0) kc = 32;
+    if (kc == 0) kc = default_kchunk(prec);
     int n = 0;
     for (const TcVariant& v : kVariants)
         if (v.prec == prec && !v.foe && v.kc == kc && n < cap) stages[n++] = v.stages;
@@ -765,9 +897,16 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
         gbe_set_error("tensor maps requested before gbe_tc_prepare");
         return GBE_ECUDA;
     }
-    const int nplanes = 4;   // plane buffers hold 4 planes of total_elems for every split format
+    // plane buffers hold gbe_subs_planes(prec) planes of total_elems (4 for the two split
+    // formats, 10 for FP64TC); boxes: A planes, B planes, a diagonal tile's own B planes
+    const int nplanes = gbe_subs_planes(X->prec);
     const bool fp16 = X->prec != GBE_PREC_BF16X3;
-    const int depth[3] = {fp16 ? 3 : 2, fp16 ? 4 : 2, fp16 ? 1 : 1};
+    int depth[3] = {fp16 ? 3 : 2, fp16 ? 4 : 2, 1};
+    if (X->prec == GBE_PREC_FP64TC) {
+        depth[0] = Recipe<GBE_PREC_FP64TC>::kA;
+        depth[1] = Recipe<GBE_PREC_FP64TC>::kSlots - Recipe<GBE_PREC_FP64TC>::kA;
+        depth[2] = Recipe<GBE_PREC_FP64TC>::kDiag;
+    }
     for (int w = 0; w < 2; ++w)   // ring stages of 32 (w = 0) or 16 (w = 1) columns of K
     for (int side = 0; side < 3; ++side)
         for (int view = 0; view < 2; ++view)
@@ -785,7 +924,8 @@ int gbe_tc_make_tmaps(gbe_subs* X) {
                 cuuint64_t strides[2] = {inner * 2, (cuuint64_t)X->total_elems * 2};
                 cuuint32_t box[3] = {view == 0 ? 256u : 8u * kc, view == 0 ? kc / 2u : 16u, (cuuint32_t)depth[bx]};
                 cuuint32_t estr[3] = {1, 1, 1};
-                if (!X->planes[side]) {   // side 2 exists only once a Chebyshev expansion ran
+                // side 2 exists only once a Chebyshev expansion ran; FP64TC runs 16-column chunks only
+                if (!X->planes[side] || (X->prec == GBE_PREC_FP64TC && w == 0)) {
                     memset(slot, 0, 128);
                     continue;
                 }

@@ -142,6 +142,11 @@ double step_time_us(int prec, int sm_count, const std::vector<int64_t>& sub_ptr)
         if (prec == GBE_PREC_FP64) {
             const double T = std::ceil(m / 64.0), k = 16.0 * std::ceil(m / 16.0);
             t += 2.0 * 64.0 * 64.0 * k * T * (T + 1.0) / 2.0 / 1.2e6;   // flops / (1.2e12 / 1e6)
+        } else if (prec == GBE_PREC_FP64TC) {
+            // 18 products per K-chunk (three times FP16X6's six) and an epilogue that does not
+            // overlap the MMAs (the four accumulators fill the TMEM)
+            const double T = std::ceil(m / 128.0), nk = std::ceil(m / 32.0);
+            t += T * (T + 1.0) / 2.0 * (1.8 * nk + 10.0) / (double)sm_count;
         } else {
             const double T = std::ceil(m / 128.0), nk = std::ceil(m / 32.0);
             const double c = prec == GBE_PREC_FP16X6 ? 0.6 : 0.3;
@@ -158,7 +163,8 @@ extern "C" int gbe_partition_autotune(gbe_ctx* ctx, const gbe_graph* S, const gb
     AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && S && params && candidates && cost && best && parts, "NULL argument");
     GBE_CHECK_ARG(ncand >= 1, "no candidates");
-    GBE_CHECK_ARG(prec == GBE_PREC_FP64 || prec == GBE_PREC_FP16X6 || prec == GBE_PREC_BF16X3, "unknown prec");
+    GBE_CHECK_ARG(prec == GBE_PREC_FP64 || prec == GBE_PREC_FP16X6 || prec == GBE_PREC_BF16X3 || prec == GBE_PREC_FP64TC,
+                  "unknown prec");
     GBE_CHECK_ARG(params->mode == GBE_PART_SPATIAL_CELLS || params->mode == GBE_PART_INDEX_BLOCKS, "partition mode");
     *parts = nullptr;
     *best = -1;

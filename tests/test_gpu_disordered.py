@@ -11,7 +11,12 @@ the submatrix sizes over several 128-wide buckets.
     checked on sampled submatrices that the oracle computes one by one (its H from a
     k-d-tree neighbour search, the sampled halos from rows of H^2, and the SP2 polynomial
     of (a)'s branch sequence applied to each sampled submatrix).
-Tolerances: FP64 1e-10.  This model is near-metallic (HOMO-LUMO gap ~0.02 eV against a
+Tolerances: FP64 1e-10.  FP64TC (the FP64-grade tensor-core squaring) 1e-10 on the full-size
+sampled subgraphs and 5e-10 on the 4096-site sample, whose amplification is the largest:
+one FP32 rounding per MMA into its fourth accumulator (|value| ~ 4 in units of 2^-30, so
+~2^-52 of an element per addition, 9 products x K/16 additions) and the dropped 2^-50
+level leave a squaring within a few 1e-15, about ten times the FP64 DFMA path's own
+rounding, and the same amplification turns that into ~1.5e-10.  This model is near-metallic (HOMO-LUMO gap ~0.02 eV against a
 Gershgorin range of ~50 eV; 56 SP2 steps before the idempotency error stalls), and an SP2
 expansion amplifies a perturbation of an early iterate near the chemical potential by the
 slope of the remaining polynomial: the FP64 path's own rounding (~1e-16) reaches ~1e-12 in D.
@@ -31,7 +36,8 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_helpers import assembled_dense, gbe, torch  # noqa: E402
 
 THRESH = 0.1
-TOL = {0: 1e-10, 1: 1e-5, 2: 5e-2}
+TOL = {0: 1e-10, 1: 1e-5, 2: 5e-2, 3: 1e-10}
+TOL_SAMPLE = {**TOL, 3: 5e-10}
 
 
 @pytest.fixture(scope="module")
@@ -68,7 +74,7 @@ def test_sample_partition_is_uneven_and_exact(ctx, sample):
     assert len(np.unique((ms + 127) // 128)) >= 2, (ms.min(), ms.max())
 
 
-@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6, gbe.PREC_BF16X3])
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6, gbe.PREC_BF16X3, gbe.PREC_FP64TC])
 def test_sample_chain_parity(ctx, sample, prec):
     st, Hg, parts = gpu_chain(ctx, sample["w"], (4, 4, 4))
     X, rep = gbe.sp2_submatrices(ctx, Hg.csr(), parts, gbe.sp2_params(2048, prec=prec, seq=sample["seq"]))
@@ -76,7 +82,7 @@ def test_sample_chain_parity(ctx, sample, prec):
     D, _, _ = assembled_dense(ctx, X, parts, 4096)
     err = np.abs(D - sample["D"]).max()
     print(f"disordered 4096, prec {prec}: {len(sample['seq'])} steps ({sample['stop']}), max|dD| {err:.3e}")
-    assert err <= TOL[prec], err
+    assert err <= TOL_SAMPLE[prec], err
 
 
 def test_sample_free_running_decisions(ctx, sample):
@@ -115,7 +121,7 @@ def test_full_size_partition_sampled(full):
         np.testing.assert_array_equal(full["sub_idx"][full["sub_ptr"][s]:full["sub_ptr"][s + 1]], ref)
 
 
-@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6, gbe.PREC_BF16X3])
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6, gbe.PREC_BF16X3, gbe.PREC_FP64TC])
 def test_full_size_sp2_sampled(ctx, full, sample, prec):
     N = full["N"]
     seq = sample["seq"]

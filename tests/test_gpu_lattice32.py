@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_helpers import gbe, torch  # noqa: E402
 
 L, THRESH, NCELL = 32, 0.15, (8, 8, 8)
-TOL = {gbe.PREC_FP64: 1e-10, gbe.PREC_FP16X6: 1e-6}
+TOL = {gbe.PREC_FP64: 1e-10, gbe.PREC_FP16X6: 1e-6, gbe.PREC_FP64TC: 1e-10}
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +59,7 @@ def test_full_size_partition_sampled(full):
         np.testing.assert_array_equal(full["sub_idx"][full["sub_ptr"][s]:full["sub_ptr"][s + 1]], ref)
 
 
-@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6])
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6, gbe.PREC_FP64TC])
 def test_full_size_sp2_sampled(ctx, full, prec):
     N, seq = full["N"], full["seq"]
     assert full["stop"] in ("stall", "tol") and len(seq) >= 10

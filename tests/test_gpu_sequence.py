@@ -1,0 +1,80 @@
+"""A pre-determined SP2 sequence (Sec. II.C) driving the GPU run.
+
+The paper's MD run fixes the branch sequence of a step beforehand from a HOMO-LUMO gap
+estimated at the previous step, so no trace is exchanged while the subgraphs are
+squared.  Here, on the 8^3 lattice:
+- a converged GPU run (the complete graph: one subgraph of every site, so the run reaches
+  the two-level regime the estimate needs) gives its report to gbe_sp2_gap_estimate; the
+  estimate lies inside the exact gap and matches the oracle's estimate from its own run;
+- gbe_sp2_sequence turns it into a branch sequence equal to the oracle's
+  sequence_from_gap of the oracle's estimate;
+- the GPU replays that sequence on the complete graph (D against exact diagonalisation)
+  and on the |H^2| > 1e-5 graph with cores of 8 (D against the oracle's graph SP2 driven by
+  the oracle's sequence), FP64 and FP64TC to 1e-10, FP16X6 to 1e-6.
+"""
+import numpy as np
+import pytest
+
+from oracle import exact, sp2
+
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_helpers import assembled_dense, device_csr, gbe, import_parts, lattice_case, oracle_graph_sp2  # noqa: E402
+
+E_LO, E_HI, TOL_SEQ = 1e-8, 1e-3, 1e-12
+
+
+@pytest.fixture(scope="module")
+def case():
+    w, H, S, subs, nc = lattice_case(8, seed=0, thr=1e-5)
+    N = H.shape[0]
+    eps = sp2.gershgorin(H)
+    Dex, ev = exact.density_matrix(H, N // 2)
+    _, logd = sp2.sp2_dense(H, N // 2, idem_tol=1e-11, n_max=80)
+    ho, lo = sp2.gap_estimate(logd.t1, logd.t2, logd.seq, N // 2, eps, E_LO, E_HI)
+    seq_o = sp2.sequence_from_gap(eps, ho, lo, TOL_SEQ)
+    return dict(H=H, subs=subs, nc=nc, N=N, eps=eps, Dex=Dex, ev=ev, oracle_gap=(ho, lo), seq_o=seq_o)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return gbe.Context(0)
+
+
+def gpu_sequence(ctx, case):
+    N = case["N"]
+    full = import_parts(ctx, N, [np.arange(N)], np.array([N]))
+    _, rep = gbe.sp2_submatrices(ctx, device_csr(case["H"]), full,
+                                 gbe.sp2_params(N // 2, prec=gbe.PREC_FP64, idem_tol=1e-11, n_max=80))
+    assert rep["stop"] == "tol"
+    homo, lumo = gbe.sp2_gap_estimate(rep, N // 2, E_LO, E_HI)
+    return (homo, lumo), gbe.sp2_sequence(rep["eps"], homo, lumo, TOL_SEQ), full
+
+
+def test_gap_estimate_and_sequence_from_a_gpu_run(ctx, case):
+    (homo, lumo), seq, _ = gpu_sequence(ctx, case)
+    ev, N = case["ev"], case["N"]
+    assert ev[N // 2 - 1] <= homo < lumo <= ev[N // 2]
+    np.testing.assert_allclose((homo, lumo), case["oracle_gap"], rtol=0, atol=1e-8)
+    assert seq == case["seq_o"]
+    print(f"gap estimate [{homo:.6f}, {lumo:.6f}] eV (exact [{ev[N // 2 - 1]:.6f}, {ev[N // 2]:.6f}]), "
+          f"{len(seq)} steps")
+
+
+@pytest.mark.parametrize("prec,tol", [(gbe.PREC_FP64, 1e-10), (gbe.PREC_FP64TC, 1e-10), (gbe.PREC_FP16X6, 1e-6)])
+def test_replayed_gap_sequence(ctx, case, prec, tol):
+    _, seq, full = gpu_sequence(ctx, case)
+    N, Hd = case["N"], device_csr(case["H"])
+    # complete graph: the sequence converges the dense expansion to theta(mu - H)
+    X, rep = gbe.sp2_submatrices(ctx, Hd, full, gbe.sp2_params(N // 2, prec=prec, seq=seq))
+    assert rep["iters"] == len(seq) and rep["stop"] == "replay"
+    D, _, _ = assembled_dense(ctx, X, full, N)
+    err_ex = np.abs(D - case["Dex"]).max()
+    # truncated graph: every subgraph follows the same pre-determined sequence
+    parts = import_parts(ctx, N, case["subs"], case["nc"])
+    X2, rep2 = gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=prec, seq=seq))
+    D2, _, _ = assembled_dense(ctx, X2, parts, N)
+    Dref, _, _ = oracle_graph_sp2(case["H"], case["subs"], case["nc"], seq=case["seq_o"])
+    err_or = np.abs(D2 - Dref).max()
+    print(f"prec {prec}: {len(seq)} steps, complete graph vs eigh {err_ex:.3e}, |H^2| graph vs oracle {err_or:.3e}")
+    assert err_ex <= tol and err_or <= tol

@@ -2,8 +2,9 @@
 
 Partitions come from the oracle and enter libgbe through gbe_parts_import, so these tests
 isolate the SP2 kernels; the graph and partition kernels have their own parity tests.
-Tolerances: FP64 path 1e-10 (max |dD| against the FP64 oracle on the same graph and
-branch sequence); FP16X6 tensor-core path 1e-6; BF16X3 reported, bounded loosely.
+Tolerances: FP64 path and the FP64-grade tensor-core path (FP64TC) 1e-10 (max |dD| against
+the FP64 oracle on the same graph and branch sequence); FP16X6 tensor-core path 1e-6;
+BF16X3 reported, bounded loosely.
 """
 import numpy as np
 import pytest
@@ -52,13 +53,26 @@ def test_fp64_replay_parity(ctx, c1):
     assert abs(rep["eps"][0] - lo) < 1e-12 and abs(rep["eps"][1] - hi) < 1e-12
 
 
-def test_fp64_free_running_matches_oracle_decisions(ctx, c1):
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP64TC])
+def test_fp64_free_running_matches_oracle_decisions(ctx, c1, prec):
     H = c1["H"]
     N = H.shape[0]
     _, logo, _ = oracle_graph_sp2(H, c1["subs"], c1["nc"], seq=None)
-    _, rep, _, _ = run(ctx, c1, gbe.PREC_FP64, seq=None, n_max=60)
+    _, rep, _, _ = run(ctx, c1, prec, seq=None, n_max=60)
     assert rep["stop"] == logo.stop
     assert rep["seq"] == logo.seq
+
+
+def test_fp64tc_replay_parity(ctx, c1):
+    """The FP64-grade tensor-core squaring (five fixed-point fp16 slices, 18 products in four
+    FP32 accumulators, the three leading ones exact) against the FP64 oracle."""
+    D, rep, _, _ = run(ctx, c1, gbe.PREC_FP64TC, seq=c1["seq"])
+    assert rep["iters"] == len(c1["seq"]) and rep["stop"] == "replay" and rep["fp64_iters"] == 0
+    err = np.abs(D - c1["Dref"]).max()
+    print(f"FP64TC 8^3: {rep['iters']} steps, max|dD| {err:.3e}")
+    assert err <= 1e-10, err
+    np.testing.assert_allclose(rep["t1"], c1["logr"].t1, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(rep["t2"], c1["logr"].t2, rtol=0, atol=1e-9)
 
 
 def test_fp64_host_csr_e2e(ctx, c1):
@@ -89,7 +103,7 @@ def test_bf16x3_replay_bounded(ctx, c1):
     assert err <= 1e-3, err
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 3e-9), (2, 3e-4)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-13), (1, 3e-9), (2, 3e-4), (3, 1e-13)])
 @pytest.mark.parametrize("b", [1, 0])
 def test_single_step(ctx, c1, prec, tol, b):
     """One squaring X_1 = X_0^2 (b=1) or 2 X_0 - X_0^2 (b=0): dense per-subgraph check."""
@@ -106,7 +120,8 @@ def test_single_step(ctx, c1, prec, tol, b):
         else:
             # off-diagonal tiles are mirrored (exact); inside diagonal tiles (a,b) and (b,a)
             # accumulate their split products in different orders
-            assert np.abs(got - got.T).max() <= (1e-9 if prec == gbe.PREC_FP16X6 else 1e-7)
+            sym = {gbe.PREC_FP16X6: 1e-9, gbe.PREC_BF16X3: 1e-7, gbe.PREC_FP64TC: 1e-14}[prec]
+            assert np.abs(got - got.T).max() <= sym
 
 
 def ragged_case(seed=3, thr=0.3):
@@ -129,7 +144,7 @@ def ragged_case(seed=3, thr=0.3):
     return dict(H=H, subs=subs, nc=nc)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6), (3, 1e-10)])
 def test_ragged_subgraphs(ctx, prec, tol):
     case = ragged_case()
     H = case["H"]
@@ -142,7 +157,7 @@ def test_ragged_subgraphs(ctx, prec, tol):
     assert np.abs(D - Dref).max() <= tol
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-6), (3, 1e-10)])
 def test_tiny_subgraphs(ctx, prec, tol):
     """Very sparse graph: subgraphs of fewer than 32 vertices (a single K-chunk)."""
     case = ragged_case(seed=5, thr=1.5)
@@ -154,14 +169,15 @@ def test_tiny_subgraphs(ctx, prec, tol):
     assert np.abs(D - Dref).max() <= tol
 
 
-def test_complete_graph_matches_eigh(ctx):
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP64TC])
+def test_complete_graph_matches_eigh(ctx, prec):
     """One subgraph covering everything: graph SP2 is dense SP2, which is theta(mu - H)."""
     from oracle import exact
     w, H, _, _, _ = lattice_case(6, seed=4)
     N = H.shape[0]
     case = dict(H=H, subs=[np.arange(N)], nc=np.array([N]))
     Dex, _ = exact.density_matrix(H, N // 2)
-    D, rep, _, _ = run(ctx, case, gbe.PREC_FP64, n_max=80, idem_tol=1e-11)
+    D, rep, _, _ = run(ctx, case, prec, n_max=80, idem_tol=1e-11)
     assert rep["stop"] == "tol"
     assert np.abs(D - Dex).max() <= 1e-10
 
@@ -181,7 +197,7 @@ def test_drop_tolerance_and_width_query(ctx, c1):
         assert np.all(col1[r, :k] >= 0) and np.all(col1[r, k:] == -1)
 
 
-@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6])
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6, gbe.PREC_FP64TC])
 def test_graph_launch_matches_step_launch(prec):
     """The CUDA-graph path (device-driven loop) and the step-by-step launch path run the same
     kernels: identical decisions and bit-identical D.  A state's first run with given inputs

@@ -25,7 +25,8 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_helpers import assembled_dense, device_csr, gbe, import_parts, torch  # noqa: E402,F401
 
 # ring depths each precision is built with, per K-chunk width
-STAGES = {gbe.PREC_FP16X6: {32: [3, 4], 16: [6, 8]}, gbe.PREC_BF16X3: {32: [4, 6, 7], 16: [12, 14]}}
+STAGES = {gbe.PREC_FP16X6: {32: [3, 4], 16: [6, 8]}, gbe.PREC_BF16X3: {32: [4, 6, 7], 16: [12, 14]},
+          gbe.PREC_FP64TC: {16: [3]}}
 N = 4096
 
 
@@ -52,7 +53,7 @@ def run(ctx, Hd, parts, params, X):
     return D, rep
 
 
-@pytest.mark.parametrize("prec", [gbe.PREC_FP16X6, gbe.PREC_BF16X3])
+@pytest.mark.parametrize("prec", [gbe.PREC_FP16X6, gbe.PREC_BF16X3, gbe.PREC_FP64TC])
 def test_every_config_gives_identical_D(ctx, case, prec):
     parts = import_parts(ctx, N, case["subs"], case["nc"])
     Hd = device_csr(case["H"])
@@ -70,9 +71,11 @@ def test_every_config_gives_identical_D(ctx, case, prec):
                 D, rep = run(ctx, Hd, parts, params, X)
                 assert np.array_equal(D, D0), (kc, stages, sched, np.abs(D - D0).max())
                 assert rep["t1"] == rep0["t1"] and rep["t2"] == rep0["t2"], (kc, stages, sched)
-    if prec == gbe.PREC_FP16X6:
+    if prec in (gbe.PREC_FP16X6, gbe.PREC_FP64TC):
         err = np.abs(D0 - case["D"]).max()
-        assert err <= 1e-5, err
+        print(f"disordered 4096, prec {prec}: max|dD| {err:.3e}")
+        # the mixed and FP64-grade bounds of this near-metallic sample (test_gpu_disordered.py)
+        assert err <= (1e-5 if prec == gbe.PREC_FP16X6 else 5e-10), err
 
 
 def test_autotune_installs_fastest_and_caches(case):
