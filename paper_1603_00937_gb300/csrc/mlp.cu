@@ -193,185 +193,396 @@ __global__ void __launch_bounds__(32 * kH2Warps) h2_feature_kernel(int64_t n, co
 }
 
 // ------------------------------------------------------------------ MLP
+__device__ __forceinline__ uint32_t h2_bits_mlp(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+
 __global__ void round_params_kernel(const float* __restrict__ p, float* pw) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kNParams; i += gridDim.x * blockDim.x)
         pw[i] = __half2float(__float2half_rn(p[i]));
 }
 
-__global__ void __launch_bounds__(256) mlp_forward_kernel(const float* __restrict__ feat, int64_t npairs,
-                                                          const float* __restrict__ pw, float* logits) {
-    __shared__ __align__(16) float W[kNParams];
-    for (int i = threadIdx.x; i < kNParams; i += blockDim.x) W[i] = pw[i];
+// ------------------------------------------------------------------ forward on the tensor cores
+// The 64 x 64 layer as mma.sync m16n8k16 (fp16 operands, FP32 accumulation): a warp takes 16
+// pairs at a time (the M rows), the hidden units are K (4 k-steps of 16) and the outputs N
+// (8 tiles of 8).  W2 is fp16-rounded already, so its fragments are exact; h1 is carried as
+// hi = fp16(h1) plus lo = fp16(h1 - hi) (relative error 2^-22), two MMAs per fragment, so
+// the layer keeps FP32-class accuracy.  Layer 1 (5 inputs) runs on the FP32 pipe straight
+// into the A-fragment layout; layer 3 is a dot product finished across the 4 lanes of a
+// fragment row.  (|h1| must stay below the fp16 range, 65504.)
+__device__ __forceinline__ uint32_t pack_h2(float lo_elem, float hi_elem) {
+    return h2_bits_mlp(__floats2half2_rn(lo_elem, hi_elem));
+}
+
+__device__ __forceinline__ void mma_16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256) mlp_forward_tc_kernel(const float* __restrict__ feat, int64_t npairs,
+                                                             const float* __restrict__ pw, float* logits) {
+    __shared__ float W1s[kHid * kNF], B1s[kHid], B2s[kHid], W3s[kHid];
+    for (int i = threadIdx.x; i < kHid * kNF; i += blockDim.x) W1s[i] = pw[OW1 + i];
+    for (int i = threadIdx.x; i < kHid; i += blockDim.x) {
+        B1s[i] = pw[OB1 + i];
+        B2s[i] = pw[OB2 + i];
+        W3s[i] = pw[OW3 + i];
+    }
     __syncthreads();
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < npairs; t += (int64_t)gridDim.x * blockDim.x) {
-        // base pointer the compiler cannot treat as loop-invariant (t < 2^40), so that the
-        // weight loads stay in the loop instead of being hoisted into hundreds of registers
-        const float* Wt = W + (int)(t >> 40);
-        float f[kNF], h1[kHid];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    // B fragments of W2^T (k = input unit, n = output unit): rows 2t, 2t+1 and 2t+8, 2t+9 of
+    // each 16 x 8 block, column g
+    uint32_t bf[4][8][2];
 #pragma unroll
-        for (int q = 0; q < kNF; ++q) f[q] = feat[t * kNF + q];
+    for (int ks = 0; ks < 4; ++ks)
 #pragma unroll
-        for (int k = 0; k < kHid; ++k) {  // h1 stays in registers (64)
-            float a = Wt[OB1 + k];
-#pragma unroll
-            for (int q = 0; q < kNF; ++q) a = fmaf(Wt[OW1 + k * kNF + q], f[q], a);
-            h1[k] = fmaxf(a, 0.0f);
+        for (int nt = 0; nt < 8; ++nt) {
+            const float* r = pw + OW2 + (8 * nt + g) * kHid + 16 * ks + 2 * t;
+            bf[ks][nt][0] = pack_h2(r[0], r[1]);
+            bf[ks][nt][1] = pack_h2(r[8], r[9]);
         }
-        float z = Wt[OB3];
-#pragma unroll 1
-        for (int o = 0; o < kHid; ++o) {
-            const float4* w4 = reinterpret_cast<const float4*>(Wt + OW2 + o * kHid);
-            float a0 = Wt[OB2 + o], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    const float b3 = pw[OB3];
+    const int64_t ngroups = (npairs + 15) / 16;
+    for (int64_t grp = (int64_t)blockIdx.x * 8 + warp; grp < ngroups; grp += (int64_t)gridDim.x * 8) {
+        const int64_t p0 = grp * 16 + g, p1 = p0 + 8;   // the two fragment rows of this lane
+        float f[2][kNF];
 #pragma unroll
-            for (int k4 = 0; k4 < kHid / 4; ++k4) {
-                const float4 wv = w4[k4];
-                a0 = fmaf(wv.x, h1[4 * k4], a0);
-                a1 = fmaf(wv.y, h1[4 * k4 + 1], a1);
-                a2 = fmaf(wv.z, h1[4 * k4 + 2], a2);
-                a3 = fmaf(wv.w, h1[4 * k4 + 3], a3);
+        for (int q = 0; q < kNF; ++q) {
+            f[0][q] = p0 < npairs ? feat[p0 * kNF + q] : 0.0f;
+            f[1][q] = p1 < npairs ? feat[p1 * kNF + q] : 0.0f;
+        }
+        float acc[8][4];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            acc[nt][0] = acc[nt][2] = B2s[8 * nt + 2 * t];
+            acc[nt][1] = acc[nt][3] = B2s[8 * nt + 2 * t + 1];
+        }
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+            // h1 of units 16 ks + 2t + {0, 1, 8, 9} for both rows, split into fp16 hi + lo
+            float hi[2][4], lo[2][4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int u = 16 * ks + 2 * t + (e & 1) + 8 * (e >> 1);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    float a = B1s[u];
+#pragma unroll
+                    for (int q = 0; q < kNF; ++q) a = fmaf(W1s[u * kNF + q], f[r][q], a);
+                    const float h = fmaxf(a, 0.0f);
+                    hi[r][e] = __half2float(__float2half_rn(h));
+                    lo[r][e] = h - hi[r][e];
+                }
             }
-            z = fmaf(Wt[OW3 + o], fmaxf((a0 + a1) + (a2 + a3), 0.0f), z);
+            const uint32_t ah[4] = {pack_h2(hi[0][0], hi[0][1]), pack_h2(hi[1][0], hi[1][1]), pack_h2(hi[0][2], hi[0][3]),
+                                    pack_h2(hi[1][2], hi[1][3])};
+            const uint32_t al[4] = {pack_h2(lo[0][0], lo[0][1]), pack_h2(lo[1][0], lo[1][1]), pack_h2(lo[0][2], lo[0][3]),
+                                    pack_h2(lo[1][2], lo[1][3])};
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                mma_16816(acc[nt], ah, bf[ks][nt][0], bf[ks][nt][1]);
+                mma_16816(acc[nt], al, bf[ks][nt][0], bf[ks][nt][1]);
+            }
         }
-        logits[t] = z;
+        float z0 = 0.0f, z1 = 0.0f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            const float w0 = W3s[8 * nt + 2 * t], w1 = W3s[8 * nt + 2 * t + 1];
+            z0 = fmaf(w0, fmaxf(acc[nt][0], 0.0f), z0);
+            z0 = fmaf(w1, fmaxf(acc[nt][1], 0.0f), z0);
+            z1 = fmaf(w0, fmaxf(acc[nt][2], 0.0f), z1);
+            z1 = fmaf(w1, fmaxf(acc[nt][3], 0.0f), z1);
+        }
+        z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
+        z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
+        z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
+        z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
+        if (t == 0) {
+            if (p0 < npairs) logits[p0] = z0 + b3;
+            if (p1 < npairs) logits[p1] = z1 + b3;
+        }
     }
 }
 
+// Gradient on the tensor cores.  Per batch of 128 pairs (4 warps x 2 tiles of 16 rows):
+//   forward   h1 (FP32 pipe, A-fragment layout, fp16 hi + lo), a2 = W2 h1 + b2 (mma), h2, z
+//   backward  dz' = sigmoid(z) - y (the 1/n of the mean is applied at the end, so that the
+//             small values stay in fp16's range), d2' = (h2 > 0) dz' w3,
+//             d1' = (h1 > 0) (d2' W2) (mma: the layer-2 accumulator fragments are the A
+//             fragments of this product), and per warp gW2 rows += d2'^T h1 over the batch
+//             (mma with the batch as K, from the hi/lo halves staged in shared memory:
+//             hi hi + hi lo + lo hi, relative error ~2^-21)
+//   the small blocks (w3, b3, b2, W1, b1) are reduced over the batch by owner threads in a
+//   fixed order, as on the FP32 pipe; gW2 stays in each warp's registers across batches.
 struct GradSmem {
     float W[kNParams];
     float G[kNParams];
-    float H1[kBatch][kLd];
-    float H2[kBatch][kLd];      // activations h2, then dL/dh2
-    float D1[kBatch][kLd];      // dL/dh1
+    uint32_t w2t[4][8][2][32];   // B fragments of W2^T (forward), per lane
+    uint32_t w2n[4][8][2][32];   // B fragments of W2 (backward to h1), per lane
+    __half H1h[kBatch][kHid + 8], H1l[kBatch][kHid + 8];   // h1 = hi + lo
+    __half D2h[kBatch][kHid + 8], D2l[kBatch][kHid + 8];   // d2' = hi + lo
+    float H2[kBatch][kLd];
+    float D1[kBatch][kLd];      // dL/dh1 (with the 1/n)
     float F[kBatch][8];
-    float dz[kBatch];
+    float dz[kBatch];           // dL/dz (with the 1/n)
 };
 
-// Forward + BCE + backward over batches of 128 pairs; each CTA accumulates the gradient of
-// the mean loss in shared memory (every entry owned by one thread, no atomics) and writes
-// it to its partial slot; loss terms likewise.
+__device__ __forceinline__ uint32_t ld_pair(const __half* p0, const __half* p1) {
+    return (uint32_t)__half_as_ushort(*p0) | ((uint32_t)__half_as_ushort(*p1) << 16);
+}
+
 __global__ void __launch_bounds__(kBatch) mlp_grad_kernel(const float* __restrict__ feat,
                                                           const uint8_t* __restrict__ labels, int64_t npairs,
                                                           const float* __restrict__ pw, float inv_n, float* partials,
                                                           double* loss_part) {
     extern __shared__ unsigned char gsm_raw[];
     GradSmem& S = *reinterpret_cast<GradSmem*>(gsm_raw);
-    const int t = threadIdx.x;
-    for (int i = t; i < kNParams; i += kBatch) { S.W[i] = pw[i]; S.G[i] = 0.0f; }
-    double lsum = 0.0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    for (int i = tid; i < kNParams; i += kBatch) { S.W[i] = pw[i]; S.G[i] = 0.0f; }
     __syncthreads();
+    // this lane's B fragments: W2^T (k = input unit, n = output) and W2 (k = output, n = input)
+    for (int e = tid; e < 4 * 8 * 2 * 32; e += kBatch) {
+        const int ln = e & 31, reg = (e >> 5) & 1, nt = (e >> 6) & 7, ks = e >> 9;
+        const int gg = ln >> 2, tt = ln & 3;
+        const int k0 = 16 * ks + 2 * tt + 8 * reg, n = 8 * nt + gg;
+        S.w2t[ks][nt][reg][ln] = pack_h2(S.W[OW2 + n * kHid + k0], S.W[OW2 + n * kHid + k0 + 1]);
+        S.w2n[ks][nt][reg][ln] = pack_h2(S.W[OW2 + k0 * kHid + n], S.W[OW2 + (k0 + 1) * kHid + n]);
+    }
+    __syncthreads();
+    float gw2[8][4];   // gW2 rows 16 warp + {g, g + 8}, columns 8 nt + 2t + {0, 1}
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) gw2[nt][0] = gw2[nt][1] = gw2[nt][2] = gw2[nt][3] = 0.0f;
+    double lsum = 0.0;
     for (int64_t b0 = (int64_t)blockIdx.x * kBatch; b0 < npairs; b0 += (int64_t)gridDim.x * kBatch) {
-        const int64_t pidx = b0 + t;
-        const bool valid = pidx < npairs;
-        float f[kNF], h1[kHid];
+#pragma unroll 1
+        for (int rt = 0; rt < 2; ++rt) {
+            const int r0 = 32 * warp + 16 * rt + g, r1 = r0 + 8;     // rows of the batch
+            const int64_t q0 = b0 + r0, q1 = b0 + r1;
+            const bool v0 = q0 < npairs, v1 = q1 < npairs;
+            float f[2][kNF];
 #pragma unroll
-        for (int q = 0; q < kNF; ++q) f[q] = valid ? feat[pidx * kNF + q] : 0.0f;
-        const float y = valid ? (float)labels[pidx] : 0.0f;
-        // forward, keeping h1 and h2 for the backward pass
-#pragma unroll
-        for (int k = 0; k < kHid; ++k) {
-            float a = S.W[OB1 + k];
-#pragma unroll
-            for (int q = 0; q < kNF; ++q) a = fmaf(S.W[OW1 + k * kNF + q], f[q], a);
-            h1[k] = fmaxf(a, 0.0f);
-            S.H1[t][k] = h1[k];
-        }
-        float z = S.W[OB3];
-        for (int o = 0; o < kHid; ++o) {
-            float a = S.W[OB2 + o];
-#pragma unroll
-            for (int k = 0; k < kHid; ++k) a = fmaf(S.W[OW2 + o * kHid + k], h1[k], a);
-            const float h2 = fmaxf(a, 0.0f);
-            S.H2[t][o] = h2;
-            z = fmaf(S.W[OW3 + o], h2, z);
-        }
-        const float sig = 1.0f / (1.0f + __expf(-z));
-        const float dz = valid ? (sig - y) * inv_n : 0.0f;
-        if (valid) lsum += (double)(fmaxf(z, 0.0f) - y * z + log1pf(__expf(-fabsf(z))));
-#pragma unroll
-        for (int q = 0; q < kNF; ++q) S.F[t][q] = f[q];
-        S.dz[t] = dz;
-        __syncthreads();
-        // gradients of the output layer (thread o < 64 owns w3[o]; thread 64 owns b3)
-        if (t < kHid) {
-            float acc = 0.0f;
-            for (int b = 0; b < kBatch; ++b) acc = fmaf(S.dz[b], S.H2[b][t], acc);
-            S.G[OW3 + t] += acc;
-        } else if (t == kHid) {
-            float acc = 0.0f;
-            for (int b = 0; b < kBatch; ++b) acc += S.dz[b];
-            S.G[OB3] += acc;
-        }
-        __syncthreads();
-        // backward through layer 2 for this thread's pair: dh2 (overwrites h2), dh1
-        {
-            float d1[kHid];
-#pragma unroll
-            for (int k = 0; k < kHid; ++k) d1[k] = 0.0f;
-            for (int o = 0; o < kHid; ++o) {
-                const float d2 = S.H2[t][o] > 0.0f ? dz * S.W[OW3 + o] : 0.0f;
-                S.H2[t][o] = d2;
-#pragma unroll
-                for (int k = 0; k < kHid; ++k) d1[k] = fmaf(d2, S.W[OW2 + o * kHid + k], d1[k]);
+            for (int q = 0; q < kNF; ++q) {
+                f[0][q] = v0 ? feat[q0 * kNF + q] : 0.0f;
+                f[1][q] = v1 ? feat[q1 * kNF + q] : 0.0f;
             }
+            if (t == 0) {
 #pragma unroll
-            for (int k = 0; k < kHid; ++k) S.D1[t][k] = S.H1[t][k] > 0.0f ? d1[k] : 0.0f;
-        }
-        __syncthreads();
-        // weight gradients: thread owns a 4 (out) x 8 (in) block of W2, plus b2 for its
-        // 4 outputs when it holds the first input block
-        {
-            const int o0 = (t >> 3) * 4, k0 = (t & 7) * 8;
-            float acc[4][8];
-            float accb[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int q = 0; q < kNF; ++q) { S.F[r0][q] = f[0][q]; S.F[r1][q] = f[1][q]; }
+            }
+            // forward: h1 (hi/lo A fragments, also staged for gW2), a2 = W2 h1 + b2
+            float acc[8][4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int nt = 0; nt < 8; ++nt) {
+                acc[nt][0] = acc[nt][2] = S.W[OB2 + 8 * nt + 2 * t];
+                acc[nt][1] = acc[nt][3] = S.W[OB2 + 8 * nt + 2 * t + 1];
+            }
+            uint32_t h1pos = 0;   // bit (4 ks + e) * 2 + row: h1 > 0
 #pragma unroll
-                for (int c = 0; c < 8; ++c) acc[a][c] = 0.0f;
-            for (int b = 0; b < kBatch; ++b) {
-                float d[4], h[8];
+            for (int ks = 0; ks < 4; ++ks) {
+                float hi[2][4], lo[2][4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) d[a] = S.H2[b][o0 + a];
+                for (int e = 0; e < 4; ++e) {
+                    const int u = 16 * ks + 2 * t + (e & 1) + 8 * (e >> 1);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) h[c] = S.H1[b][k0 + c];
+                    for (int r = 0; r < 2; ++r) {
+                        float a = S.W[OB1 + u];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    accb[a] += d[a];
+                        for (int q = 0; q < kNF; ++q) a = fmaf(S.W[OW1 + u * kNF + q], f[r][q], a);
+                        const float h = fmaxf(a, 0.0f);
+                        if (h > 0.0f) h1pos |= 1u << ((4 * ks + e) * 2 + r);
+                        hi[r][e] = __half2float(__float2half_rn(h));
+                        lo[r][e] = h - hi[r][e];
+                    }
+                }
+                const uint32_t ah[4] = {pack_h2(hi[0][0], hi[0][1]), pack_h2(hi[1][0], hi[1][1]),
+                                        pack_h2(hi[0][2], hi[0][3]), pack_h2(hi[1][2], hi[1][3])};
+                const uint32_t al[4] = {pack_h2(lo[0][0], lo[0][1]), pack_h2(lo[1][0], lo[1][1]),
+                                        pack_h2(lo[0][2], lo[0][3]), pack_h2(lo[1][2], lo[1][3])};
+                *reinterpret_cast<uint32_t*>(&S.H1h[r0][16 * ks + 2 * t]) = ah[0];
+                *reinterpret_cast<uint32_t*>(&S.H1h[r1][16 * ks + 2 * t]) = ah[1];
+                *reinterpret_cast<uint32_t*>(&S.H1h[r0][16 * ks + 2 * t + 8]) = ah[2];
+                *reinterpret_cast<uint32_t*>(&S.H1h[r1][16 * ks + 2 * t + 8]) = ah[3];
+                *reinterpret_cast<uint32_t*>(&S.H1l[r0][16 * ks + 2 * t]) = al[0];
+                *reinterpret_cast<uint32_t*>(&S.H1l[r1][16 * ks + 2 * t]) = al[1];
+                *reinterpret_cast<uint32_t*>(&S.H1l[r0][16 * ks + 2 * t + 8]) = al[2];
+                *reinterpret_cast<uint32_t*>(&S.H1l[r1][16 * ks + 2 * t + 8]) = al[3];
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) acc[a][c] = fmaf(d[a], h[c], acc[a][c]);
+                for (int nt = 0; nt < 8; ++nt) {
+                    const uint32_t bb0 = S.w2t[ks][nt][0][lane], bb1 = S.w2t[ks][nt][1][lane];
+                    mma_16816(acc[nt], ah, bb0, bb1);
+                    mma_16816(acc[nt], al, bb0, bb1);
                 }
             }
+            // h2, z, loss, dz'
+            float z0 = 0.0f, z1 = 0.0f;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
+            for (int nt = 0; nt < 8; ++nt) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) S.G[OW2 + (o0 + a) * kHid + k0 + c] += acc[a][c];
-                if (k0 == 0) S.G[OB2 + o0 + a] += accb[a];
+                for (int e = 0; e < 4; ++e) acc[nt][e] = fmaxf(acc[nt][e], 0.0f);
+                const float w0 = S.W[OW3 + 8 * nt + 2 * t], w1 = S.W[OW3 + 8 * nt + 2 * t + 1];
+                z0 = fmaf(w0, acc[nt][0], z0);
+                z0 = fmaf(w1, acc[nt][1], z0);
+                z1 = fmaf(w0, acc[nt][2], z1);
+                z1 = fmaf(w1, acc[nt][3], z1);
+                S.H2[r0][8 * nt + 2 * t] = acc[nt][0];
+                S.H2[r0][8 * nt + 2 * t + 1] = acc[nt][1];
+                S.H2[r1][8 * nt + 2 * t] = acc[nt][2];
+                S.H2[r1][8 * nt + 2 * t + 1] = acc[nt][3];
             }
+            z0 += __shfl_xor_sync(0xffffffffu, z0, 1);
+            z1 += __shfl_xor_sync(0xffffffffu, z1, 1);
+            z0 += __shfl_xor_sync(0xffffffffu, z0, 2);
+            z1 += __shfl_xor_sync(0xffffffffu, z1, 2);
+            z0 += S.W[OB3];
+            z1 += S.W[OB3];
+            const float y0 = v0 ? (float)labels[q0] : 0.0f, y1 = v1 ? (float)labels[q1] : 0.0f;
+            const float d0 = v0 ? 1.0f / (1.0f + __expf(-z0)) - y0 : 0.0f;
+            const float d1 = v1 ? 1.0f / (1.0f + __expf(-z1)) - y1 : 0.0f;
+            if (t == 0) {
+                if (v0) lsum += (double)(fmaxf(z0, 0.0f) - y0 * z0 + log1pf(__expf(-fabsf(z0))));
+                if (v1) lsum += (double)(fmaxf(z1, 0.0f) - y1 * z1 + log1pf(__expf(-fabsf(z1))));
+                S.dz[r0] = d0 * inv_n;
+                S.dz[r1] = d1 * inv_n;
+            }
+            // d2' = (h2 > 0) dz' w3 as hi/lo A fragments of the product d2' W2 (the C fragment
+            // tiles 2 ks and 2 ks + 1 are the k = 16 ks .. 16 ks + 15 columns), staged for gW2
+            float acc1[8][4];
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) acc1[nt][0] = acc1[nt][1] = acc1[nt][2] = acc1[nt][3] = 0.0f;
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+                float dv[2][2][2];   // [tile 2ks + j][row][col pair]
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int nt = 2 * ks + j;
+                    const float w0 = S.W[OW3 + 8 * nt + 2 * t], w1 = S.W[OW3 + 8 * nt + 2 * t + 1];
+                    dv[j][0][0] = acc[nt][0] > 0.0f ? d0 * w0 : 0.0f;
+                    dv[j][0][1] = acc[nt][1] > 0.0f ? d0 * w1 : 0.0f;
+                    dv[j][1][0] = acc[nt][2] > 0.0f ? d1 * w0 : 0.0f;
+                    dv[j][1][1] = acc[nt][3] > 0.0f ? d1 * w1 : 0.0f;
+                }
+                float hh[2][2][2], ll[2][2][2];
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            hh[j][r][c] = __half2float(__float2half_rn(dv[j][r][c]));
+                            ll[j][r][c] = dv[j][r][c] - hh[j][r][c];
+                        }
+                const uint32_t ah[4] = {pack_h2(hh[0][0][0], hh[0][0][1]), pack_h2(hh[0][1][0], hh[0][1][1]),
+                                        pack_h2(hh[1][0][0], hh[1][0][1]), pack_h2(hh[1][1][0], hh[1][1][1])};
+                const uint32_t al[4] = {pack_h2(ll[0][0][0], ll[0][0][1]), pack_h2(ll[0][1][0], ll[0][1][1]),
+                                        pack_h2(ll[1][0][0], ll[1][0][1]), pack_h2(ll[1][1][0], ll[1][1][1])};
+                *reinterpret_cast<uint32_t*>(&S.D2h[r0][16 * ks + 2 * t]) = ah[0];
+                *reinterpret_cast<uint32_t*>(&S.D2h[r1][16 * ks + 2 * t]) = ah[1];
+                *reinterpret_cast<uint32_t*>(&S.D2h[r0][16 * ks + 2 * t + 8]) = ah[2];
+                *reinterpret_cast<uint32_t*>(&S.D2h[r1][16 * ks + 2 * t + 8]) = ah[3];
+                *reinterpret_cast<uint32_t*>(&S.D2l[r0][16 * ks + 2 * t]) = al[0];
+                *reinterpret_cast<uint32_t*>(&S.D2l[r1][16 * ks + 2 * t]) = al[1];
+                *reinterpret_cast<uint32_t*>(&S.D2l[r0][16 * ks + 2 * t + 8]) = al[2];
+                *reinterpret_cast<uint32_t*>(&S.D2l[r1][16 * ks + 2 * t + 8]) = al[3];
+#pragma unroll
+                for (int nt = 0; nt < 8; ++nt) {
+                    const uint32_t bb0 = S.w2n[ks][nt][0][lane], bb1 = S.w2n[ks][nt][1][lane];
+                    mma_16816(acc1[nt], ah, bb0, bb1);
+                    mma_16816(acc1[nt], al, bb0, bb1);
+                }
+            }
+            // d1 = (h1 > 0) d1' / n, columns 8 nt + 2t + {0, 1}: A-fragment unit 16 ks + 2t + e
+            // of layer 1 is C tile nt = 2 ks + (e >> 1), column 2t + (e & 1)
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int e = (c & 1) + 2 * (nt & 1), ks = nt >> 1;
+                    const bool p0 = (h1pos >> ((4 * ks + e) * 2)) & 1u, p1 = (h1pos >> ((4 * ks + e) * 2 + 1)) & 1u;
+                    S.D1[r0][8 * nt + 2 * t + c] = p0 ? acc1[nt][c] * inv_n : 0.0f;
+                    S.D1[r1][8 * nt + 2 * t + c] = p1 ? acc1[nt][2 + c] * inv_n : 0.0f;
+                }
         }
-        // layer-1 gradients: 64 x (5 + 1) entries, threads 0..63 own one hidden unit each
-        if (t < kHid) {
+        __syncthreads();
+        // small blocks, each entry owned by one thread, batch order fixed
+        if (tid < kHid) {
+            float acc = 0.0f;
+            for (int b = 0; b < kBatch; ++b) acc = fmaf(S.dz[b], S.H2[b][tid], acc);
+            S.G[OW3 + tid] += acc;
             float gw[kNF] = {0.f, 0.f, 0.f, 0.f, 0.f};
             float gb = 0.0f;
             for (int b = 0; b < kBatch; ++b) {
-                const float d = S.D1[b][t];
+                const float d = S.D1[b][tid];
                 gb += d;
 #pragma unroll
                 for (int q = 0; q < kNF; ++q) gw[q] = fmaf(d, S.F[b][q], gw[q]);
             }
 #pragma unroll
-            for (int q = 0; q < kNF; ++q) S.G[OW1 + t * kNF + q] += gw[q];
-            S.G[OB1 + t] += gb;
+            for (int q = 0; q < kNF; ++q) S.G[OW1 + tid * kNF + q] += gw[q];
+            S.G[OB1 + tid] += gb;
+        } else {
+            const int o = tid - kHid;
+            float acc = 0.0f;
+            for (int b = 0; b < kBatch; ++b) acc += __half2float(S.D2h[b][o]) + __half2float(S.D2l[b][o]);
+            S.G[OB2 + o] += acc * inv_n;
+            if (o == 0) {
+                float a3 = 0.0f;
+                for (int b = 0; b < kBatch; ++b) a3 += S.dz[b];
+                S.G[OB3] += a3;
+            }
+        }
+        // gW2 rows 16 warp .. 16 warp + 15: d2'^T h1 with the batch as K (hi hi + hi lo + lo hi)
+#pragma unroll 1
+        for (int kb = 0; kb < kBatch / 16; ++kb) {
+            const int bA = 16 * kb + 2 * t, o0 = 16 * warp + g;
+            uint32_t dh[4], dl[4];
+            dh[0] = ld_pair(&S.D2h[bA][o0], &S.D2h[bA + 1][o0]);
+            dh[1] = ld_pair(&S.D2h[bA][o0 + 8], &S.D2h[bA + 1][o0 + 8]);
+            dh[2] = ld_pair(&S.D2h[bA + 8][o0], &S.D2h[bA + 9][o0]);
+            dh[3] = ld_pair(&S.D2h[bA + 8][o0 + 8], &S.D2h[bA + 9][o0 + 8]);
+            dl[0] = ld_pair(&S.D2l[bA][o0], &S.D2l[bA + 1][o0]);
+            dl[1] = ld_pair(&S.D2l[bA][o0 + 8], &S.D2l[bA + 1][o0 + 8]);
+            dl[2] = ld_pair(&S.D2l[bA + 8][o0], &S.D2l[bA + 9][o0]);
+            dl[3] = ld_pair(&S.D2l[bA + 8][o0 + 8], &S.D2l[bA + 9][o0 + 8]);
+#pragma unroll
+            for (int nt = 0; nt < 8; ++nt) {
+                const int i = 8 * nt + g;
+                const uint32_t hh0 = ld_pair(&S.H1h[bA][i], &S.H1h[bA + 1][i]);
+                const uint32_t hh1 = ld_pair(&S.H1h[bA + 8][i], &S.H1h[bA + 9][i]);
+                const uint32_t hl0 = ld_pair(&S.H1l[bA][i], &S.H1l[bA + 1][i]);
+                const uint32_t hl1 = ld_pair(&S.H1l[bA + 8][i], &S.H1l[bA + 9][i]);
+                mma_16816(gw2[nt], dh, hh0, hh1);
+                mma_16816(gw2[nt], dh, hl0, hl1);
+                mma_16816(gw2[nt], dl, hh0, hh1);
+            }
         }
         __syncthreads();
     }
-    for (int i = t; i < kNParams; i += kBatch) partials[(int64_t)blockIdx.x * kNParams + i] = S.G[i];
+    for (int i = tid; i < kNParams; i += kBatch)
+        if (i < OW2 || i >= OB2) partials[(int64_t)blockIdx.x * kNParams + i] = S.G[i];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+        const int o = 16 * warp + g, i = 8 * nt + 2 * t;
+        float* dst = partials + (int64_t)blockIdx.x * kNParams + OW2;
+        dst[o * kHid + i] = gw2[nt][0] * inv_n;
+        dst[o * kHid + i + 1] = gw2[nt][1] * inv_n;
+        dst[(o + 8) * kHid + i] = gw2[nt][2] * inv_n;
+        dst[(o + 8) * kHid + i + 1] = gw2[nt][3] * inv_n;
+    }
     // fixed-order loss reduction within the CTA
     __shared__ double lred[kBatch];
-    lred[t] = lsum;
+    lred[tid] = lsum;
     __syncthreads();
-    if (t == 0) {
-        double s = 0.0;
-        for (int b = 0; b < kBatch; ++b) s += lred[b];
-        loss_part[blockIdx.x] = s;
+    if (tid == 0) {
+        double sum = 0.0;
+        for (int b = 0; b < kBatch; ++b) sum += lred[b];
+        loss_part[blockIdx.x] = sum;
     }
 }
 
@@ -619,8 +830,9 @@ extern "C" int gbe_mlp_get_params(gbe_ctx* ctx, const gbe_mlp* M, float* host_pa
 
 static int mlp_forward_dev(gbe_ctx* ctx, const gbe_mlp* M, const gbe_pairs* P, float* logits) {
     round_params_kernel<<<8, 256, 0, ctx->stream>>>(M->p, M->pw);
-    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((P->npairs + 255) / 256, (int64_t)ctx->sm_count * 8));
-    if (P->npairs) mlp_forward_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(P->feat, P->npairs, M->pw, logits);
+    // 8 warps per CTA, 16 pairs per warp and iteration
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((P->npairs + 127) / 128, (int64_t)ctx->sm_count * 8));
+    if (P->npairs) mlp_forward_tc_kernel<<<(unsigned)blocks, 256, 0, ctx->stream>>>(P->feat, P->npairs, M->pw, logits);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }
