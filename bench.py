@@ -587,12 +587,14 @@ def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
         "metric": "learned graph proposal: sites/s (candidate pairs, features, network, selection)",
         "value": N * world / sec, "unit": "sites/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * sec, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (fp16-rounded weights)", "data": "synthetic (random weights)",
+        "vs_baseline": None, "dtype": "f16 tensor-core 64x64 layer (hi+lo activations), f32 accumulation; fp16-rounded weights",
+        "data": "synthetic (random weights)",
         "config": {"workload": args.workload, "N": N, "box_a": float(w["box"][0]), "rcand_a": cfg["rcand"],
                    "pairs": int(npairs), "graph_edges_per_site": edges / N,
                    "timing": "wall clock of gbe_build_graph(GBE_GRAPH_MLP); pairs and forward timed apart"},
         "phase_ms": {k: 1000.0 * v / args.steps for k, v in phases.items()},
-        "pairs_per_s_forward": npairs / fwd, "forward_tflops_fp32": flops / fwd / 1e12,
+        "pairs_per_s_forward": npairs / fwd,
+        "forward_tflops": flops / fwd / 1e12,   # the network's 2 x 4,480 flop per pair; 64x64 layer on mma.sync
         "e2e": None, "gpu_launches": None, "clocks": clk,
     }
     if rank == 0:

@@ -586,6 +586,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             };
             if (use_c && PREC != GBE_PREC_FP64TC && nch > 0) fetch_x(4 * half);
+            // FP64TC: X_n's digits t0..t3 (planes 1-4) and t4' (plane 8) of an 8-column chunk,
+            // the first chunk fetched before the accumulators are ready, later ones one ahead
+            uint4 xv[5] = {};
+            auto fetch_dig = [&](int cc) {
+                const int64_t e = blk_index(off, mpad, row, 128 * w.J + 64 * half + 8 * cc);
+#pragma unroll
+                for (int p = 0; p < 5; ++p) xv[p] = *reinterpret_cast<const uint4*>(pin + (p < 4 ? p + 1 : 8) * ps + e);
+            };
+            if (PREC == GBE_PREC_FP64TC && use_c && nch8 > 0) fetch_dig(0);
             bool ok;
             {
                 TC_T0();
@@ -618,13 +627,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_ld8(ta + 256, r2);
                     tmem_ld8(ta + 384, r3);
                     const int64_t e0 = blk_index(off, mpad, row, col0);
-                    uint4 xv[5] = {};
-                    if (use_c) {
-                        // X_n digits t0, t1, t2, t3 (planes 1-4) and t4' (plane 8)
+                    uint4 xw[5];
 #pragma unroll
-                        for (int p = 0; p < 5; ++p)
-                            xv[p] = *reinterpret_cast<const uint4*>(pin + (p < 4 ? p + 1 : 8) * ps + e0);
-                    }
+                    for (int p = 0; p < 5; ++p) xw[p] = xv[p];
+                    if (use_c && cc + 1 < nch8) fetch_dig(cc + 1);
                     tmem_wait_ld();
                     if (cc == nch8 - 1) {
                         tc_fence_before();
@@ -648,7 +654,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                     const uint32_t wd = jj == 0 ? u.x : (jj == 1 ? u.y : (jj == 2 ? u.z : u.w));
                                     return (uint16_t)(wd >> sh16);
                                 };
-                                const long long Vn = f64tc_from_planes(hw(xv[0]), hw(xv[1]), hw(xv[2]), hw(xv[3]), hw(xv[4]));
+                                const long long Vn = f64tc_from_planes(hw(xw[0]), hw(xw[1]), hw(xw[2]), hw(xw[3]), hw(xw[4]));
                                 V = 2 * Vn - V;
                             }
                             d[e] = f64tc_digits(V);

@@ -2,8 +2,10 @@
 network's forward pass, its BCE gradient, Adam, the GBE_GRAPH_MLP graph, GPU training,
 and what the trained network gains over the H^k-pattern graph.
 
-Tolerances.  The kernels compute in FP32 with fp16-rounded weights; the oracle in FP64
-with the same rounded weights.  A logit is a sum of products through three layers, so
+Tolerances.  The kernels compute in FP32 with fp16-rounded weights (the 64 x 64 layer on
+the tensor cores, its activations and back-propagated errors carried as fp16 hi + lo pairs,
+relative error ~2^-21, with FP32 accumulation); the oracle in FP64 with the same rounded
+weights.  A logit is a sum of products through three layers, so
 its FP32 error is bounded by about (terms per dot product) x 2^-24 times the same
 expression evaluated with absolute values (``abs_scale``); 1e-5 x abs_scale covers the
 133-term depth with margin.  Features are FP32 roundings of FP64 values (log10f within
