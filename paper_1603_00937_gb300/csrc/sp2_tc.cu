@@ -87,20 +87,24 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// MMA and commit, issued by the calling thread alone: the MMA warp's lane 0 issues every MMA
-// (tcgen05.mma is a single-thread instruction) and the commits that track them.
-__device__ __forceinline__ void umma_f16_1t(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accum) {
+// MMA and commit, executed by a whole warp with warp-uniform operands: one elected lane
+// issues the instruction (tcgen05.mma is a single-thread instruction).
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
+        "{\n\t.reg .pred p, e;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
         : "memory");
 }
-__device__ __forceinline__ void umma_commit_1t(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -234,13 +238,6 @@ struct Recipe<GBE_PREC_FP64TC> {
         return t[p];
     }
 };
-
-// Whether product p is the first into its accumulator (its first k-step overwrites it).
-template <class R> __host__ __device__ constexpr bool first_of_acc(int p) {
-    for (int q = 0; q < p; ++q)
-        if (R::pacc(q) == R::pacc(p)) return false;
-    return true;
-}
 
 // A slot holding the same plane as B slot b on a diagonal tile, or -1 (loaded).
 template <class R> __host__ __device__ constexpr int slot_alias(int b) {
@@ -456,8 +453,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
-        // The whole warp runs the loop (every operand is warp-uniform); lane 0 waits on the
-        // barriers for the warp and issues every tcgen05 instruction.
+        // The whole warp runs the loop (every operand is warp-uniform); one elected lane
+        // issues each tcgen05 instruction and lane 0 waits on the barriers for the warp.
         int stage = 0;
         uint32_t phase = 0;
         int tb = 0;
@@ -508,48 +505,42 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // k-steps of 16 holding columns below m (a squaring skips the last chunk's second
                 // half when it is all padding; a Chebyshev step runs every k-step)
                 const int ksn = FOE ? KC / 16 : min(KC / 16, (m - kc * KC + 15) >> 4);
-                // descriptors of the stage's slot 0, K-major and MN-major: a slot's and a k-step's
-                // byte offsets are added to their 14-bit address field (shared-memory addresses
-                // stay below 2^18, so the field does not overflow)
-                const uint64_t dA = tA ? sdesc_mnmajor<KC>(sbase) : sdesc_kmajor(sbase);
-                const uint64_t dB = tB ? sdesc_mnmajor<KC>(sbase) : sdesc_kmajor(sbase);
-                const uint32_t stA = tA ? 256u : 4096u, stB = tB ? 256u : 4096u;   // bytes per k-step of 16
-                if (lane == 0) {
 #pragma unroll
-                    for (int ks = 0; ks < KC / 16; ++ks) {
-                        if (ks >= ksn) break;
+                for (int ks = 0; ks < KC / 16; ++ks) {
+                    if (ks >= ksn) break;
 #pragma unroll
-                        for (int p = 0; p < R::kProducts; ++p) {
-                            const int a = R::pa(p), acc = R::pacc(p);
-                            int b = R::pb(p);
-                            if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);   // never for FOE
-                            const uint64_t da = dA + (uint64_t)(((uint32_t)a * kTileBytes + (uint32_t)ks * stA) >> 4);
-                            const uint64_t db = dB + (uint64_t)(((uint32_t)b * kTileBytes + (uint32_t)ks * stB) >> 4);
-                            // the first product into each accumulator overwrites it
-                            const bool first = kc == 0 && ks == 0 && first_of_acc<R>(p);
-                            umma_f16_1t(dacc0 + acc * 128, da, db, idesc_t, first ? 0u : 1u);
+                    for (int p = 0; p < R::kProducts; ++p) {
+                        const int a = R::pa(p), acc = R::pacc(p);
+                        int b = R::pb(p);
+                        if (diag && slot_alias<R>(b) >= 0) b = slot_alias<R>(b);   // never for FOE
+                        const uint32_t aa = sbase + a * kTileBytes, ba = sbase + b * kTileBytes;
+                        const uint64_t da = tA ? sdesc_mnmajor<KC>(aa + ks * 256) : sdesc_kmajor(aa + ks * 4096);
+                        const uint64_t db = tB ? sdesc_mnmajor<KC>(ba + ks * 256) : sdesc_kmajor(ba + ks * 4096);
+                        // the first product into each accumulator overwrites it
+                        bool first = (kc == 0 && ks == 0);
+                        if (first) {
+                            for (int q = 0; q < p; ++q)
+                                if (R::pacc(q) == acc) first = false;
                         }
+                        umma_f16(dacc0 + acc * 128, da, db, idesc_t, first ? 0u : 1u);
                     }
-                    umma_commit_1t(&empty[stage]);
                 }
-                __syncwarp();
+                umma_commit(&empty[stage]);
 #ifdef GBE_TC_STATS
                 st_acc[7] += (unsigned long long)(clock64() - ti0);
 #endif
                 if (++stage == NS) { stage = 0; phase ^= 1; }
             }
             if (!ok) break;
-            if (lane == 0) umma_commit_1t(&tfull[tb]);
-            __syncwarp();
+            umma_commit(&tfull[tb]);
             if (++tb == 512 / R::kTmemBufCols) { tb = 0; tph ^= 1; }
         }
         if (!ok && lane == 0) {
             *abort_flag = 1;
             atomicExch(&ctrl->status, GBE_ETIMEOUT);
         }
-        // all issued MMAs complete before TMEM is released (lane 0 issued them)
-        if (lane == 0) umma_commit_1t(drain);
-        __syncwarp();
+        // all issued MMAs complete before TMEM is released
+        umma_commit(drain);
         if (lane == 0) {
             const long long t0 = clock64();
             while (!mbar_try_wait(drain, 0) && clock64() - t0 < drain_budget) {
