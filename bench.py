@@ -616,6 +616,8 @@ def parse_args(argv=None):
                     help="with several ranks: one system, its subgraphs dealt to the ranks, the global traces "
                          "all-reduced every SP2 step (strong scaling); default: an independent system per rank")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-fp64tc", action="store_true",
+                    help="skip the FP64-grade tensor-core comparison run (default: timed beside the FP64 path)")
     ap.add_argument("--prec", default="fp16x6", choices=sorted(PRECS))
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch SP2 runs step by step instead of as CUDA graphs (profilers do not see "
@@ -785,6 +787,24 @@ def main():
         out["max_abs_dD_vs_fp64_free_running"] = dD_free
         out["branch_sequences_equal"] = seq_equal
         out["speedup_vs_fp64"] = ms_d / ms_m
+        if PREC != gbe.PREC_FP64TC and not args.no_fp64tc:
+            # the FP64-grade tensor-core path on the same workload and sequence as the FP64 run
+            Xt = gbe.subs_create(ctx, parts, gbe.PREC_FP64TC)
+            col_t, val_t = torch.empty_like(col_m), torch.empty_like(val_m)
+            pt = params(gbe.PREC_FP64TC, seq=rep_d["seq"])
+            ms_t, rep_t = timed(Xt, pt, col_t, val_t, max(3, args.fp64_steps), 3)
+            ctx.set_profiling(True)
+            gbe.sp2_run(ctx, Hv, parts, pt, Xt)
+            rep_tp = gbe.sp2_report_get(ctx, Xt).as_dict()
+            ctx.set_profiling(False)
+            tl = rep_tp["ms_tc"] / max(1, rep_tp["n_tc"])
+            out["fp64tc"] = {"value": N * systems / (ms_t / 1000.0), "unit": UNIT, "ms_per_step": ms_t,
+                             "iters": rep_t["iters"], "max_abs_dD_vs_fp64": float((val_t - val_d).abs().max().item()),
+                             "speedup_vs_fp64": ms_d / ms_t, "ms_per_squaring_launch": tl,
+                             "alg_tflops_in_squarings": rep_tp["alg_flops"] / max(1, rep_tp["iters"]) / (tl / 1000.0) / 1e12
+                             if tl > 0 else None,
+                             "precision": "FP64TC: five fixed-point fp16 slices, 18 products, FP32 accumulators"}
+            del Xt, col_t, val_t
 
     # ---------------------------------------------------------------- end to end (host buffers)
     def dev_to_host(ptr, count, typestr):
