@@ -40,7 +40,8 @@ def test_bad_partitions_rejected(ctx):
     assert imp(4, [1], [0, 2], [-1, 0]) == gbe.GBE_EINVAL
 
 
-@pytest.mark.parametrize("prec,tol", [(gbe.PREC_FP64, 1e-12), (gbe.PREC_FP16X6, 1e-6), (gbe.PREC_BF16X3, 2e-4)])
+@pytest.mark.parametrize("prec,tol", [(gbe.PREC_FP64, 1e-12), (gbe.PREC_FP16X6, 1e-6), (gbe.PREC_BF16X3, 2e-4),
+                                      (gbe.PREC_FP64TC, 1e-12)])
 def test_singleton_subgraphs(ctx, prec, tol):
     w, H, _, _, _ = lattice_case(6, seed=2)
     N = H.shape[0]

@@ -6,7 +6,7 @@ on the host (synchronise the stream, copy the buffer out, add the two buffers in
 order, copy the sum back).  The threads' kernels never wait on each other; only the host
 does.  Checked against one run of the whole partition on the same GPU:
 - global-trace mode: the same branch sequence and traces bit for bit, and the union of
-  the ranks' ELL rows equals the whole run's D bit for bit (FP64 and FP16X6);
+  the ranks' ELL rows equals the whole run's D bit for bit (FP64, FP16X6 and FP64TC);
 - replay mode (a pre-determined sequence): no exchange is made, and D is again identical;
 - a rank whose exchange fails makes both ranks return GBE_EPEER instead of hanging, and
   the contexts stay usable.
@@ -119,7 +119,7 @@ class _View:
                                          "version": 3}
 
 
-@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6])
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6, gbe.PREC_FP64TC])
 def test_global_trace_shards_match_whole_run(case, prec):
     rep, col, val = whole_run(case, prec)
     out = sharded_run(case, prec)
