@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "decide.cuh"
 #include "gbe_internal.h"
 #include "split.cuh"
 
@@ -318,20 +319,6 @@ __global__ void init_ctrl_kernel(Sp2Ctrl* C, Sp2Init in) {
 }
 
 // ----------------------------------------------------------------------------- decide
-// Trace sums of one subgraph over its work units, in unit order.  A single-rank decision and
-// the per-subgraph sums a sharded run exchanges use this same arithmetic, so both see the
-// same per-subgraph values and take the same decisions.
-__device__ __forceinline__ void sub_trace(const double* __restrict__ partials, int max_units, int2 r, double& a,
-                                          double& b) {
-    double x = 0.0, y = 0.0;
-    for (int u = r.x; u < r.x + r.y; ++u) {
-        x += partials[u];
-        y += partials[max_units + u];
-    }
-    a = x;
-    b = y;
-}
-
 // Per-subgraph trace sums of this rank at global subgraph positions (zeros at other ranks'
 // positions) and its error flag: the buffer a sharded run's exchange sums over the ranks.
 __global__ void __launch_bounds__(256) sub_sums_kernel(const Sp2Ctrl* ctrl, const double* __restrict__ partials,
@@ -348,100 +335,27 @@ __global__ void __launch_bounds__(256) sub_sums_kernel(const Sp2Ctrl* ctrl, cons
     if (blockIdx.x == 0 && threadIdx.x == 0) sums[2 * P_global] = (ctrl->status != GBE_OK) ? 1.0 : 0.0;
 }
 
-// Global FP64 traces over core positions -> stop rule and branch of the next step.
-// kind: 0 after the gather (X_0), 1 after a tensor-core step, 2 after an FP64 step.
-// The traces are the per-subgraph sums (sub_trace) added in global subgraph order, taken
+// Global FP64 traces over core positions -> stop rule and branch of the next step
+// (decide.cuh).  The traces are the per-subgraph sums added in global subgraph order, taken
 // from this rank's partials (sums == NULL) or from the exchanged buffer of a sharded run.
-// In a graph-launched run the last decision of a loop iteration (set_cond) also sets the
-// loop node's condition: continue while the run has not stopped, and never beyond
-// n_max + 8 iterations of the loop.
-struct DecideIn {
-    const double* partials;
-    int max_units;
-    const int2* ranges;   // [P] work units of each subgraph for this kind
-    int P;
-    const double* sums;   // exchanged sums [2 P_global + 1], or NULL
-    int64_t P_global;
-    int kind;
-};
-
-__device__ void decide_body(Sp2Ctrl* ctrl, const DecideIn& in, double* red, int* run);
-
-__global__ void __launch_bounds__(512) decide_kernel(Sp2Ctrl* ctrl, DecideIn in, cudaGraphConditionalHandle cond,
-                                                     int set_cond) {
+// A kernel whose step did no work (the run had stopped, or the other precision's kernel
+// ran) leaves the state alone.  In a graph-launched
+// run the last decision of a loop iteration (set_cond) also sets the loop node's condition.
+__global__ void __launch_bounds__(kDecideThreads) decide_kernel(Sp2Ctrl* ctrl, DecideIn in,
+                                                                cudaGraphConditionalHandle cond, int set_cond) {
     __shared__ double red[16];
     __shared__ int run;
-    decide_body(ctrl, in, red, &run);
+    if (threadIdx.x == 0) run = (in.kind == 0) ? 1 : ctrl->pending;
+    __syncthreads();
+    if (run) {
+        double t1, t2;
+        decide_traces(in, threadIdx.x, red, [] { __syncthreads(); }, t1, t2);
+        if (threadIdx.x == 0) decide_apply(ctrl, in, t1, t2);
+    }
     if (set_cond && threadIdx.x == 0) {
         __threadfence_block();
-        Sp2Ctrl* C = ctrl;
-        if (++C->loops > C->n_max + 8 && C->stop == 0) C->stop = GBE_STOP_NMAX;
-        cudaGraphSetConditional(cond, C->stop == 0 ? 1u : 0u);
+        decide_set_condition(ctrl, cond);
     }
-}
-
-__device__ void decide_body(Sp2Ctrl* ctrl, const DecideIn& in, double* red, int* run_flag) {
-    int& run = *run_flag;
-    const int kind = in.kind;
-    if (threadIdx.x == 0) run = (kind == 0) ? 1 : ctrl->pending;
-    __syncthreads();
-    if (!run) return;
-    double a = 0.0, b = 0.0;
-    if (in.sums) {
-        for (int64_t g = threadIdx.x; g < in.P_global; g += 512) {
-            a += in.sums[g];
-            b += in.sums[in.P_global + g];
-        }
-    } else {
-        for (int s = threadIdx.x; s < in.P; s += 512) {
-            double x, y;
-            sub_trace(in.partials, in.max_units, in.ranges[s], x, y);
-            a += x;
-            b += y;
-        }
-    }
-    double t1 = block_sum_d<512>(a, red);
-    double t2 = block_sum_d<512>(b, red);
-    if (threadIdx.x != 0) return;
-    Sp2Ctrl* C = ctrl;
-    C->pending = 0;
-    if (kind != 0) {
-        const int n_prev = C->iter;
-        C->seq[n_prev] = (uint8_t)C->branch;
-        C->iter = n_prev + 1;
-        C->cur ^= 1;
-        C->fmt = (kind == 2) ? 1 : 0;
-        if (kind == 2) C->fp64_iters++;
-    }
-    const int n = C->iter;
-    C->t1[n] = t1;
-    C->t2[n] = t2;
-    if (in.sums && in.sums[2 * in.P_global] != 0.0 && C->status == GBE_OK) C->status = GBE_EPEER;
-    if (C->status != GBE_OK || !isfinite(t1) || !isfinite(t2)) {
-        if (C->status == GBE_OK) C->status = GBE_ENUMERIC;
-        C->stop = GBE_STOP_ERROR;
-        return;
-    }
-    const double e = fabs(t1 - t2);
-    const bool mixed = (C->prec == GBE_PREC_FP16X6 || C->prec == GBE_PREC_BF16X3);   // FP64TC is FP64-grade
-    if (C->branch_mode == GBE_BRANCH_REPLAY) {
-        if (n >= C->seq_len || n >= C->n_max) { C->stop = GBE_STOP_REPLAY; return; }
-        C->branch = C->seq_in[n] ? 1 : 0;
-        if (mixed && C->mode == 0 && n >= C->seq_len - C->fp64_tail) { C->mode = 1; C->switch_iter = n; }
-        return;
-    }
-    const bool stalled = (n >= C->n_min && n >= 2 && e >= fabs(C->t1[n - 2] - C->t2[n - 2]));
-    if (mixed && C->mode == 0 && C->fp64_tail > 0) {
-        if (e <= C->tail_switch || e <= C->idem_tol || stalled) { C->mode = 1; C->switch_iter = n; }
-    } else {
-        const int since = (C->switch_iter >= 0) ? n - C->switch_iter : n;
-        const bool tail_done = !mixed || C->fp64_tail == 0 || since >= C->fp64_tail;
-        const bool stall_ok = (C->switch_iter < 0) || (since >= 2);
-        if (e <= C->idem_tol && tail_done) { C->stop = GBE_STOP_TOL; return; }
-        if (stalled && stall_ok && tail_done) { C->stop = GBE_STOP_STALL; return; }
-    }
-    if (n >= C->n_max) { C->stop = GBE_STOP_NMAX; return; }
-    C->branch = (fabs(t2 - C->n_occ) < fabs(2.0 * t1 - t2 - C->n_occ)) ? 1 : 0;
 }
 
 // ----------------------------------------------------------------------------- FP64 squaring
@@ -1269,9 +1183,7 @@ static int check_gather_fits(const gbe_ctx* ctx, const gbe_subs* X) {
 // Decision after the gather (kind 0) or a squaring (1 tensor-core, 2 FP64).  With a trace
 // exchange (sharded global-trace run) this rank's per-subgraph sums are written at their
 // global positions, summed over the ranks by the caller's exchange, and decided from.
-static int enqueue_decide(gbe_ctx* ctx, gbe_subs* X, int kind, const gbe_sp2_params* xp, cudaGraphConditionalHandle cond,
-                          bool set_cond) {
-    cudaStream_t st = ctx->stream;
+static DecideIn decide_in(const gbe_subs* X, int kind) {
     DecideIn in;
     in.partials = X->d_partials;
     in.max_units = X->max_units;
@@ -1280,6 +1192,13 @@ static int enqueue_decide(gbe_ctx* ctx, gbe_subs* X, int kind, const gbe_sp2_par
     in.sums = nullptr;
     in.P_global = X->P_global;
     in.kind = kind;
+    return in;
+}
+
+static int enqueue_decide(gbe_ctx* ctx, gbe_subs* X, int kind, const gbe_sp2_params* xp, cudaGraphConditionalHandle cond,
+                          bool set_cond) {
+    cudaStream_t st = ctx->stream;
+    DecideIn in = decide_in(X, kind);
     if (xp && xp->exchange) {
         const int blocks = (int)std::min<int64_t>(ctx->sm_count, (X->P_global + 255) / 256);
         sub_sums_kernel<<<std::max(1, blocks), 256, 0, st>>>(X->d_ctrl, X->d_partials, X->max_units, X->d_ranges[kind],
@@ -1292,7 +1211,7 @@ static int enqueue_decide(gbe_ctx* ctx, gbe_subs* X, int kind, const gbe_sp2_par
         }
         in.sums = X->d_sums;
     }
-    decide_kernel<<<1, 512, 0, st>>>(X->d_ctrl, in, cond, set_cond ? 1 : 0);
+    decide_kernel<<<1, kDecideThreads, 0, st>>>(X->d_ctrl, in, cond, set_cond ? 1 : 0);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }
