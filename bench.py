@@ -57,7 +57,19 @@ WORKLOADS = {
     "foe32": dict(kind="lattice", L=32, seed=0, thresh=0.15, ncell=(8, 8, 8), foe=dict(beta=4.0, mu=0.0, order=300)),
     # learned graph proposal at 1,048,576 disordered sites (box 101.6a): candidate pairs
     # r < 4a with features, the width-64 network over every pair, selection + union with H
-    "mlp1m": dict(kind="disordered", N=1 << 20, seed=2024, mlp=dict(rcand=4.0, cut=0.0)),
+    # learned graph proposal at 1,048,576 disordered sites (box 101.6a): the network is trained
+    # on seeded 4096-site systems of the same model (box 16a; labels |D_ij| >= 1e-2 from the
+    # library's FP64-grade SP2 on each one's complete graph), then proposes the graph of the
+    # big system, whose FP64-grade graph SP2 is compared with the H^1 and H^2 pattern graphs'
+    # (cores from 25^3 cells of ~67 sites, the branch sequence of one global-trace run replayed
+    # on every graph, subgraphs in batches that fit the device)
+    "mlp1m": dict(kind="disordered", N=1 << 20, seed=2024,
+                  mlp=dict(rcand=4.0, cut=-2.0, tau=1e-2, train_n=4096, train_seed0=20000, test_seed=29999,
+                           passes=40, lr=3e-3, ncell=(25, 25, 25), n_max=100)),
+    # the same at 65,536 sites (box 40.3a, cores from 10^3 cells): a quick case of the pipeline
+    "mlp64k": dict(kind="disordered", N=1 << 16, seed=2024,
+                   mlp=dict(rcand=4.0, cut=-2.0, tau=1e-2, train_n=4096, train_seed0=20000, test_seed=29999,
+                            passes=40, lr=3e-3, ncell=(10, 10, 10), n_max=100)),
 }
 PRECS = {"fp16x6": ("FP16X6", "f16-split(x6)/f32-acc/f64-trace"),
          "bf16x3": ("BF16X3", "bf16-split(x3)/f32-acc/f64-trace"),
@@ -534,20 +546,188 @@ def run_foe(args, wl, gbe, torch, ctx, local, rank, world):
 
 
 # ----------------------------------------------------------------------------- learned graph proposal
+def mlp_init_params(seed):
+    """He-normal initial weights of the width-64 network: W1[64x5], b1, W2[64x64], b2, w3, b3."""
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.normal(0.0, (2.0 / 5) ** 0.5, 320), np.zeros(64),
+                           rng.normal(0.0, (2.0 / 64) ** 0.5, 4096), np.zeros(64),
+                           rng.normal(0.0, (1.0 / 64) ** 0.5, 64), np.zeros(1)]).astype(np.float32)
+
+
+def mlp_labelled_system(gbe, torch, ctx, cfg, seed):
+    """One seeded training system: candidate pairs with features, and labels |D_ij| >= tau
+    from the library's FP64-grade SP2 on its complete graph (one subgraph of every site)."""
+    import synth
+    n = cfg["train_n"]
+    w = synth.disordered(n, seed=seed)
+    st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
+    Hh = gbe.build_hamiltonian(ctx, st)
+    full = gbe.parts_import(ctx, n, np.array([n], np.int32), np.array([0, n], np.int64), np.arange(n, dtype=np.int32))
+    X, rep = gbe.sp2_submatrices(ctx, Hh.csr(), full, gbe.sp2_params(n / 2.0, prec=gbe.PREC_FP64TC, n_max=100))
+    col = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    gbe.assemble_D(ctx, X, full, col, val)
+    P = gbe.pairs_build(ctx, st, Hh.csr(), cfg["rcand"])
+    lab = torch.empty(P.info()[1], dtype=torch.uint8, device="cuda")
+    gbe.mlp_labels(ctx, P, col, val, cfg["tau"], lab)
+    torch.cuda.synchronize()
+    return P, lab, rep["iters"]
+
+
+def mlp_train(args, gbe, torch, ctx, cfg):
+    """Train the network on the GPU: args.train_systems labelled systems, one Adam step per
+    system in turn, cfg passes; accuracy on an unseen system."""
+    t0 = time.perf_counter()
+    sets = [mlp_labelled_system(gbe, torch, ctx, cfg, cfg["train_seed0"] + k)[:2] for k in range(args.train_systems)]
+    t_lab = time.perf_counter() - t0
+    M = gbe.mlp_create(ctx)
+    M.set_params(mlp_init_params(0))
+    loss0 = float(np.mean([M.gradient(P, lab)[0] for P, lab in sets]))
+    t0 = time.perf_counter()
+    for _ in range(cfg["passes"]):
+        for P, lab in sets:
+            M.train(P, lab, 1, cfg["lr"])
+    t_train = time.perf_counter() - t0
+    loss = float(np.mean([M.gradient(P, lab)[0] for P, lab in sets]))
+    Pt, labt, _ = mlp_labelled_system(gbe, torch, ctx, cfg, cfg["test_seed"])
+    z = torch.empty(Pt.info()[1], dtype=torch.float32, device="cuda")
+    M.forward(Pt, z)
+    acc = float(((z >= 0) == (labt > 0)).float().mean())
+    pos = float(np.mean([float(lab.float().mean()) for _, lab in sets]))
+    return M, {"systems": len(sets), "system": "%d disordered sites, box %.1fa, seeds %d.." % (
+                   cfg["train_n"], cfg["train_n"] ** (1.0 / 3.0), cfg["train_seed0"]),
+               "labels": "|D_ij| >= %g, D from FP64TC SP2 on the complete graph" % cfg["tau"],
+               "positive_rate": pos, "passes": cfg["passes"], "lr": cfg["lr"], "loss_initial": loss0,
+               "loss_final": loss, "unseen_accuracy": acc, "labels_s": t_lab, "train_s": t_train}
+
+
+def ell_rows_maxdiff(torch, rows, ca, va, cb, vb, n, chunk=8192):
+    """max |A - B| over the union of the entries of the given rows of two ELL matrices
+    (row i = column i of D; an entry absent from one side counts as zero there)."""
+    mx = 0.0
+    for r0 in range(0, len(rows), chunk):
+        r = rows[r0:r0 + chunk]
+        a_c, a_v, b_c, b_v = ca[r], va[r], cb[r], vb[r]
+        loc = torch.arange(len(r), device=a_c.device, dtype=torch.int64).unsqueeze(1)
+        ma, mb = a_c >= 0, b_c >= 0
+        keys = torch.cat([(loc * n + a_c)[ma], (loc * n + b_c)[mb]])
+        vals = torch.cat([a_v[ma], -b_v[mb]])
+        uk, inv = torch.unique(keys, return_inverse=True)
+        d = torch.zeros(len(uk), dtype=torch.float64, device=a_c.device).index_add_(0, inv, vals)
+        mx = max(mx, float(d.abs().max()) if len(d) else 0.0)
+    return mx
+
+
+def graph_sp2_batched(gbe, torch, ctx, Hv, parts, N, seq, budget, keep=None, compare=None):
+    """FP64-grade graph SP2 (FP64TC) of a partition that need not fit the device at once: the
+    subgraphs are dealt to batches (gbe_shard_assign, largest m_s^3 first) whose split planes
+    fit `budget` bytes, and each batch replays the branch sequence `seq` (no traces need to be
+    combined, Sec. II.C) and assembles the D rows of its own cores.  keep: (col, val) to fill
+    with the whole D; compare: {name: (col, val)} D's compared row by row with this one."""
+    P, total, max_m = parts.info()
+    cc, sptr, _ = parts.export()
+    ms = np.diff(sptr)
+    mpad = (ms + 127) // 128 * 128
+    need = float(np.sum(mpad.astype(np.float64) ** 2)) * 40.0      # 10 planes x 2 bytes x 2 sides
+    B = max(1, int(np.ceil(need / budget)))
+    owner, load = gbe.shard_assign(sptr, B)
+    col = torch.empty((N, max_m), dtype=torch.int32, device="cuda") if keep is None else keep[0]
+    val = torch.empty((N, max_m), dtype=torch.float64, device="cuda") if keep is None else keep[1]
+    prm = gbe.sp2_params(N / 2.0, prec=gbe.PREC_FP64TC, n_max=max(len(seq), 10), seq=seq)
+    t_sp2, diffs = 0.0, {k: 0.0 for k in (compare or {})}
+    for b in range(B):
+        local = gbe.parts_shard(ctx, parts, owner, b)
+        X = gbe.subs_create(ctx, local, gbe.PREC_FP64TC)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gbe.sp2_run(ctx, Hv, local, prm, X)
+        torch.cuda.synchronize()
+        t_sp2 += time.perf_counter() - t0
+        if keep is None:
+            gbe.assemble_D(ctx, X, local, col, val)
+            rows = torch.nonzero(col[:, 0] >= 0).squeeze(1)
+            for k, (cb, vb) in (compare or {}).items():
+                diffs[k] = max(diffs[k], ell_rows_maxdiff(torch, rows, col, val, cb, vb, N))
+        else:
+            cb = torch.empty_like(col)
+            vb = torch.empty_like(val)
+            gbe.assemble_D(ctx, X, local, cb, vb)
+            rows = torch.nonzero(cb[:, 0] >= 0).squeeze(1)
+            col[rows] = cb[rows]
+            val[rows] = vb[rows]
+            del cb, vb
+        del X, local
+    info = {"subgraphs": int(P), "m_s_min": int(ms.min()), "m_s_median": float(np.median(ms)), "m_s_max": int(ms.max()),
+            "sum_m3": float(np.sum(ms.astype(np.float64) ** 3)), "batches": B, "planes_gb": need / 1e9,
+            "sp2_s": t_sp2, "alg_tflops": 2.0 * float(np.sum(ms.astype(np.float64) ** 3)) * len(seq) / t_sp2 / 1e12}
+    return info, diffs
+
+
+def mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M):
+    """The trained network's graph of the big system against the H^k pattern graphs: each
+    graph's FP64-grade graph SP2 (the same replayed branch sequence), D compared with the
+    conservative H^2 graph's D, with each graph's sum of m_s^3 and SP2 time."""
+    N = w["pos"].shape[0]
+    graphs = {"H^1": lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_HK_PATTERN, k=1),
+              "MLP": lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_MLP, site_struct=st, mlp=M, rcand=cfg["rcand"],
+                                             logit_cut=cfg["cut"]),
+              "H^2": lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_HK_PATTERN, k=2)}
+    res, parts_of = {}, {}
+    for name, make in graphs.items():
+        t0 = time.perf_counter()
+        G = make()
+        parts_of[name] = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=cfg["ncell"], site_struct=st)
+        torch.cuda.synchronize()
+        res[name] = {"edges_per_site": G.size()[1] / N, "graph_and_partition_s": time.perf_counter() - t0}
+        del G
+    # the branch sequence: one global-trace run (FP16X6, every subgraph resident: 4 planes x 2
+    # bytes x 2 sides per padded element) of the MLP graph, or of H^1 when the MLP graph's
+    # planes would not fit beside the rest
+    budget = args.batch_gb * 1e9
+
+    def planes16(parts):
+        ms = np.diff(parts.export()[1])
+        return float(np.sum(((ms + 127) // 128 * 128).astype(np.float64) ** 2)) * 16.0
+
+    src = "MLP" if planes16(parts_of["MLP"]) <= 1.5 * budget else "H^1"
+    t0 = time.perf_counter()
+    XS = gbe.subs_create(ctx, parts_of[src], gbe.PREC_FP16X6)
+    gbe.sp2_run(ctx, Hv, parts_of[src], gbe.sp2_params(N / 2.0, prec=gbe.PREC_FP16X6, n_max=cfg["n_max"]), XS)
+    rep = gbe.sp2_report_get(ctx, XS).as_dict()
+    del XS
+    seq = rep["seq"]
+    seq_info = {"from": "global-trace FP16X6 run of the %s graph" % src, "steps": len(seq), "stop": rep["stop"],
+                "s": time.perf_counter() - t0}
+    stored = {}
+    for name in ("H^1", "MLP"):
+        _, _, max_m = parts_of[name].info()
+        stored[name] = (torch.empty((N, max_m), dtype=torch.int32, device="cuda"),
+                        torch.empty((N, max_m), dtype=torch.float64, device="cuda"))
+        info, _ = graph_sp2_batched(gbe, torch, ctx, Hv, parts_of[name], N, seq, budget, keep=stored[name])
+        res[name].update(info)
+    info, diffs = graph_sp2_batched(gbe, torch, ctx, Hv, parts_of["H^2"], N, seq, budget, compare=stored)
+    res["H^2"].update(info)
+    for name in ("H^1", "MLP"):
+        res[name]["max_abs_dD_vs_H2"] = diffs[name]
+        res[name]["sum_m3_vs_H2"] = res[name]["sum_m3"] / res["H^2"]["sum_m3"]
+    return {"graphs": res, "sequence": seq_info, "cores": "spatial cells %s" % (cfg["ncell"],),
+            "precision": "FP64TC (FP64-grade tensor-core squarings) in every graph's SP2",
+            "reference": "the H^2 pattern graph (every pair with (H^2)_ij != 0)"}
+
+
 def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
     """Graph proposal by the edge classifier at full size: per step the candidate pairs and
     their features, the network's logits for every pair, and the selected graph (union
-    with H).  Reported: sites/s and pairs/s of the whole proposal; the phases apart."""
-    import numpy as np
+    with H).  Reported: sites/s and pairs/s of the whole proposal; the phases apart.  The
+    network is first trained on the GPU (mlp_train); unless --no-compare, the proposed
+    graph's FP64-grade SP2 is then compared with the H^k pattern graphs' (mlp_compare)."""
     w = make_system(wl, wl["seed"] + rank)
     N = w["pos"].shape[0]
     st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
     Hh = gbe.build_hamiltonian(ctx, st)
     Hv = Hh.csr()
     cfg = wl["mlp"]
-    M = gbe.mlp_create(ctx)
-    rng = np.random.default_rng(0)
-    M.set_params((rng.normal(0, 0.2, M.param_count)).astype(np.float32))
+    M, train = mlp_train(args, gbe, torch, ctx, cfg)
     phases = {"pairs_features": 0.0, "forward": 0.0, "graph": 0.0}
     npairs = 0
 
@@ -580,6 +760,7 @@ def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
         G = step(True)
     clk = clocks.stop()
     edges = G.size()[1]
+    del G
     sec = max_over_ranks(phases["graph"] / args.steps, world)
     fwd = phases["forward"] / args.steps
     flops = 2.0 * npairs * (5 * 64 + 64 * 64 + 64)
@@ -588,15 +769,18 @@ def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
         "value": N * world / sec, "unit": "sites/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * sec, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f16 tensor-core 64x64 layer (hi+lo activations), f32 accumulation; fp16-rounded weights",
-        "data": "synthetic (random weights)",
+        "data": "synthetic (seeded systems; network trained on the GPU in this run)",
         "config": {"workload": args.workload, "N": N, "box_a": float(w["box"][0]), "rcand_a": cfg["rcand"],
-                   "pairs": int(npairs), "graph_edges_per_site": edges / N,
+                   "logit_cut": cfg["cut"], "pairs": int(npairs), "graph_edges_per_site": edges / N,
                    "timing": "wall clock of gbe_build_graph(GBE_GRAPH_MLP); pairs and forward timed apart"},
         "phase_ms": {k: 1000.0 * v / args.steps for k, v in phases.items()},
         "pairs_per_s_forward": npairs / fwd,
         "forward_tflops": flops / fwd / 1e12,   # the network's 2 x 4,480 flop per pair; 64x64 layer on mma.sync
+        "training": train,
         "e2e": None, "gpu_launches": None, "clocks": clk,
     }
+    if not args.no_compare:
+        line["comparison"] = mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -631,6 +815,12 @@ def parse_args(argv=None):
                     help="force the squaring kernel's launch configuration instead of autotuning, e.g. 4,0 "
                          "(schedule 0 round-robin, 1 balanced ranges; K-chunk 32 or 16); used to profile the "
                          "tuned choice")
+    ap.add_argument("--train-systems", type=int, default=200,
+                    help="mlp1m: seeded 4096-site systems the network is trained on")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="mlp1m: skip the FP64-grade graph SP2 comparison of the proposed graph with H^1 and H^2")
+    ap.add_argument("--batch-gb", type=float, default=96.0,
+                    help="mlp1m comparison: split-plane bytes per batch of subgraphs (GB)")
     ap.add_argument("--record-traffic", metavar="REPORT",
                     help="write the DRAM traffic record of the FP16X6 squaring kernel for --workload "
                          "from this ncu report (no GPU needed), then exit")

@@ -551,6 +551,13 @@ int gbe_mlp_adam_step(gbe_ctx* ctx, gbe_mlp* mlp, float lr, float beta1, float b
  * nullable) is the mean loss of the last epoch before its update.  Synchronises. */
 int gbe_mlp_train(gbe_ctx* ctx, gbe_mlp* mlp, const gbe_pairs* pairs, const uint8_t* labels, int epochs, float lr,
                   double* final_loss);
+/* Training labels of the candidate pairs from a density matrix (not in the paper; the
+ * labels are the thresholded pattern floor(D)_tau whose graph Sec. II.A builds): labels[p]
+ * = 1 when |D_ij| >= tau for pair p = (i, j), 0 otherwise, 0 also where D holds no entry
+ * (i, j).  D: device ELL as gbe_assemble_D fills it (row j = column j of D, so D_ij is read
+ * from row j), D->n = the pairs' n.  labels: device uint8[npairs].  GBE_EINVAL for a host
+ * ELL, mismatched n or tau < 0.  Enqueue only. */
+int gbe_mlp_labels(gbe_ctx* ctx, const gbe_pairs* pairs, const gbe_ell* D, double tau, uint8_t* labels);
 int gbe_free_mlp(gbe_mlp* mlp);
 
 /* ----------------------------------------------- allocation-free Gershgorin bounds */

@@ -56,7 +56,7 @@ EXPORTS = [
     "gbe_free_subs", "gbe_sp2_run", "gbe_sp2_report_get", "gbe_sp2_submatrices", "gbe_assemble_D",
     "gbe_subs_export", "gbe_gershgorin_noalloc", "gbe_pairs_build", "gbe_pairs_info", "gbe_pairs_export", "gbe_pairs_device",
     "gbe_free_pairs", "gbe_mlp_create", "gbe_mlp_param_count", "gbe_mlp_set_params", "gbe_mlp_get_params",
-    "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_free_mlp",
+    "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_mlp_labels", "gbe_free_mlp",
     "gbe_sp2_gap_estimate", "gbe_sp2_sequence", "gbe_fermi_coefficients", "gbe_foe_run", "gbe_foe_report_get",
     "gbe_subs_get_config", "gbe_subs_set_config", "gbe_sp2_autotune", "gbe_partition_autotune",
     "gbe_shard_assign", "gbe_parts_shard",
@@ -183,6 +183,7 @@ def load_library(path=LIB_PATH):
         "gbe_mlp_forward": (I32, [P, P, P, P]), "gbe_mlp_gradient": (I32, [P, P, P, P, P, P]),
         "gbe_mlp_adam_step": (I32, [P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
         "gbe_mlp_train": (I32, [P, P, P, P, I32, ctypes.c_float, P]), "gbe_free_mlp": (I32, [P]),
+        "gbe_mlp_labels": (I32, [P, P, P, D, P]),
         "gbe_sp2_gap_estimate": (I32, [P, D, D, D, P, P]), "gbe_sp2_sequence": (I32, [D, D, D, D, D, I32, P, P]),
         "gbe_fermi_coefficients": (I32, [D, D, D, D, I32, P]), "gbe_foe_run": (I32, [P, P, P, P, P]),
         "gbe_foe_report_get": (I32, [P, P, P]),
@@ -705,6 +706,14 @@ def pairs_build(ctx, site_struct, H, rcand):
     check(load_library().gbe_pairs_build(ctx.handle, ctypes.byref(site_struct), ctypes.byref(H), float(rcand),
                                          ctypes.byref(h)), "gbe_pairs_build")
     return Pairs(ctx, h)
+
+
+def mlp_labels(ctx, pairs, col, val, tau, labels):
+    """Enqueue the training labels of the pairs (device uint8[npairs]) from a device ELL D."""
+    e = ell_struct(col, val)
+    check(load_library().gbe_mlp_labels(ctx.handle, pairs.handle, ctypes.byref(e), float(tau), _ptr(labels)),
+          "gbe_mlp_labels")
+    return labels
 
 
 def mlp_create(ctx, hidden=64):

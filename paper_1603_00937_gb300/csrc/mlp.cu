@@ -890,6 +890,48 @@ extern "C" int gbe_mlp_train(gbe_ctx* ctx, gbe_mlp* M, const gbe_pairs* P, const
     return GBE_OK;
 }
 
+// Training labels from an assembled density matrix (the thresholded D patterns the network
+// learns, Sec. II.A's floor(D)_tau): y_p = 1 when |D_ij| >= tau for pair p = (i, j), else 0
+// (also when D has no entry (i, j)).  Row j of the ELL holds column j of D, so D_ij is the
+// entry of row j whose column index is i.  One block per site i; each warp takes pairs of
+// row i in turn, its lanes scanning row j 32 entries at a time up to the row's padding.
+__global__ void pair_labels_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ pj,
+                                   const int32_t* __restrict__ ecol, const double* __restrict__ eval, int64_t width,
+                                   double tau, uint8_t* __restrict__ labels) {
+    const int64_t i = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t p1 = rowptr[i + 1];
+    for (int64_t p = rowptr[i] + warp; p < p1; p += blockDim.x >> 5) {
+        const int64_t base = (int64_t)pj[p] * width;
+        uint8_t y = 0;
+        for (int64_t k0 = 0; k0 < width; k0 += 32) {
+            const int64_t k = k0 + lane;
+            const int32_t ck = k < width ? ecol[base + k] : -1;
+            const unsigned hit = __ballot_sync(0xffffffffu, ck == (int32_t)i);
+            if (hit) {
+                const int src = __ffs(hit) - 1;
+                const double v = __shfl_sync(0xffffffffu, lane == src ? eval[base + k] : 0.0, src);
+                y = fabs(v) >= tau ? 1 : 0;
+                break;
+            }
+            if (__ballot_sync(0xffffffffu, ck < 0)) break;   // padding: row j holds no more entries
+        }
+        if (lane == 0) labels[p] = y;
+    }
+}
+
+extern "C" int gbe_mlp_labels(gbe_ctx* ctx, const gbe_pairs* P, const gbe_ell* D, double tau, uint8_t* labels) {
+    AllocScope alloc_scope_(ctx);
+    GBE_CHECK_ARG(ctx && P && D && labels, "NULL argument");
+    GBE_CHECK_ARG(D->on_device == 1 && D->col && D->val, "D must be a device ELL");
+    GBE_CHECK_ARG(D->n == P->n && D->width >= 1, "D must have one row per site of the pairs");
+    GBE_CHECK_ARG(tau >= 0.0, "tau must be >= 0");
+    if (P->npairs == 0) return GBE_OK;
+    pair_labels_kernel<<<(unsigned)P->n, 256, 0, ctx->stream>>>(P->rowptr, P->j, D->col, D->val, D->width, tau, labels);
+    GBE_CUDA_TRY(cudaGetLastError());
+    return GBE_OK;
+}
+
 // GBE_GRAPH_MLP: pairs within rcand scored by the network, kept when logit >= cut; the
 // graph adds the pattern of H and the diagonal (union and symmetrisation in graph.cu).
 int gbe_graph_mlp_select(gbe_ctx* ctx, const gbe_csr* H, const gbe_graph_params* p, int64_t** rp_out, int32_t** ci_out) {

@@ -179,3 +179,40 @@ def test_clock_sampler_with_fake_smi(tmp_path, monkeypatch):
     s.start()
     clk = s.stop()
     assert clk["reasons"] == ["nvidia-smi unavailable"] and bench.clock_verdict(clk) is None
+
+
+def test_ell_rows_maxdiff_against_dense():
+    """bench.ell_rows_maxdiff (the D comparison of the mlp workloads' graphs) against the dense
+    difference: ELL rows with different patterns and widths, entries absent on one side
+    counting as zero, only the selected rows compared."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    rng = np.random.default_rng(3)
+    n = 40
+
+    def random_ell(width, fill):
+        col = np.full((n, width), -1, dtype=np.int32)
+        val = np.zeros((n, width))
+        for i in range(n):
+            k = rng.integers(1, min(fill, width) + 1)
+            col[i, :k] = rng.choice(n, k, replace=False)
+            val[i, :k] = rng.normal(size=k)
+        return col, val
+
+    def dense(col, val):
+        D = np.zeros((n, n))
+        for i in range(n):
+            m = col[i] >= 0
+            D[col[i][m], i] = val[i][m]
+        return D
+
+    ca, va = random_ell(12, 12)
+    cb, vb = random_ell(20, 18)
+    rows = np.sort(rng.choice(n, 25, replace=False))
+    want = np.abs(dense(ca, va) - dense(cb, vb))[:, rows].max()
+    t = torch.from_numpy
+    got = bench.ell_rows_maxdiff(torch, t(rows), t(ca), t(va), t(cb), t(vb), n, chunk=7)
+    assert got == want
+    assert bench.ell_rows_maxdiff(torch, t(rows), t(ca), t(va), t(ca), t(va), n) == 0.0
+    assert bench.mlp_init_params(0).shape == (4609,)

@@ -211,6 +211,31 @@ def graph_sp2_error(ctx, Hg, G, st, N, D_exact, ncell, prec=gbe.PREC_FP64):
                 edges=G.size()[1] / N, iters=rep["iters"])
 
 
+@pytest.mark.parametrize("tau", [1e-2, 1e-5])
+def test_labels_from_assembled_D(ctx, dis, tau):
+    """gbe_mlp_labels against the oracle's labels of the same D: the GPU's graph SP2 D of the
+    1500-site disordered system (|H^2| >= 0.1 graph, cores from 3^3 cells), copied to the
+    host.  Pairs outside a core's subgraph have no entry in D and get label 0.  Bit for bit."""
+    N, st, Hg, P, I, J = 1500, dis["st"], dis["Hg"], dis["P"], dis["I"], dis["J"]
+    G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_H2_THRESH, thresh=0.1)
+    parts = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=(3, 3, 3), site_struct=st)
+    X, _ = gbe.sp2_submatrices(ctx, Hg.csr(), parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP64))
+    n, width = gbe.assemble_width(ctx, X, parts)
+    col = torch.empty((n, width), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, width), dtype=torch.float64, device="cuda")
+    gbe.assemble_D(ctx, X, parts, col, val)
+    lab = torch.full((len(I),), 7, dtype=torch.uint8, device="cuda")
+    gbe.mlp_labels(ctx, P, col, val, tau, lab)
+    torch.cuda.synchronize()
+    D = gbe.ell_to_dense(col.cpu().numpy(), val.cpu().numpy(), N)
+    y = mlp.labels(D, I, J, tau).astype(np.uint8)
+    assert np.array_equal(lab.cpu().numpy(), y)
+    absent = D[I, J] == 0.0
+    assert absent.any() and 0.0 < y.mean() < 1.0
+    with pytest.raises(gbe.GbeError):
+        gbe.mlp_labels(ctx, P, col.cpu(), val.cpu(), tau, lab)
+
+
 TRAIN_SEEDS = range(1000, 1008)   # eight seeded, jittered 16^3 lattices (4096 sites each)
 
 
