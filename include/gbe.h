@@ -203,7 +203,7 @@ int gbe_partition(gbe_ctx* ctx, const gbe_graph* S, const gbe_partition_params* 
  * max(7.5, c ceil(m_s / 32)) / (number of SMs), c = 0.6 (FP16X6) or 0.3 (BF16X3): a tile's
  * epilogue against its MMAs, fitted to GB300 runs; GBE_PREC_FP64 the FP64 flops
  * 2 x 64^2 x 16 ceil(m_s / 16) per upper 64 x 64 tile at 1.2 TFLOP/s.  A candidate whose
- * partition fails (a subgraph above max_sub or above the 2432 vertices the gather holds)
+ * partition fails (a subgraph above max_sub or above the 8192 vertices the gather holds)
  * costs +inf; any other error of gbe_partition (an invalid candidate) is returned.
  * cost[ncand] receives the costs, *best the index of the cheapest and *parts its partition
  * (library-owned; NULL and GBE_ECAPACITY when every candidate failed).  Not in the paper as
@@ -347,9 +347,10 @@ int gbe_free_subs(gbe_subs* X);
  * Gershgorin bounds of H (FP64, a4), gather + scale of every x[s] (a4), and the SP2
  * loop (a5 squarings, a6 global FP64 trace + branch, a7 branch apply in the squaring
  * epilogue), with convergence decided on the device.  `H` must be device CSR.
- * GBE_ECAPACITY (before any launch) when a subgraph has more than 2432 vertices: the
- * gather stages whole dense rows and an index hash table in one CTA's 227 KB of shared
- * memory (the same bound applies to gbe_foe_run). */
+ * GBE_ECAPACITY (before any launch) when a subgraph has more than 8192 vertices: the
+ * gather keeps an index hash table of the subgraph in one CTA's 227 KB of shared memory,
+ * with the dense rows it stages beside it up to 2432 vertices and in global memory above
+ * (the same bound applies to gbe_foe_run). */
 int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* params,
                 gbe_subs* X);
 /* Synchronise and read the report of the last run on X (the traces and branch sequence of

@@ -148,6 +148,9 @@ struct gbe_subs {
     // by its first run)
     uint16_t* planes[3] = {nullptr, nullptr, nullptr};  // tensor-core path: gbe_subs_planes(prec) planes x total_elems
     double* f64[3] = {nullptr, nullptr, nullptr};       // FP64 iterates
+    // the gather's dense-row staging in global memory, for subgraphs whose rows do not fit
+    // shared memory: [P][8][max_mpad] uint2 (allocated by the first run that needs it)
+    void* d_gather_rows = nullptr;
     // work lists
     TileItem* d_items_tc = nullptr;  int n_items_tc = 0;   // 128x128 tiles
     TileItem* d_items_64 = nullptr;  int n_items_64 = 0;   // 64x64 tiles

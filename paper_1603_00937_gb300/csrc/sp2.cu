@@ -104,8 +104,9 @@ __device__ __forceinline__ int hash_local(const int2* htab, int hbits, int g) {
 
 // One CTA (8 warps) per subgraph, 8 consecutive rows a0..a0+7 at a time, one per warp:
 // lanes map the row's H entries to local columns (a shared-memory hash table of the
-// subgraph's sites), split them and scatter them into the warp's dense row buffer in shared memory (4
-// split planes packed in 8 bytes per column, or the FP64 value).  X_0 is symmetric, so the
+// subgraph's sites), split them and scatter them into the warp's dense row buffer (4 split
+// planes packed in 8 bytes per column, or the FP64 value; in shared memory, or for
+// subgraphs too large for it in this CTA's slice rows_g of a global buffer).  X_0 is symmetric, so the
 // 8 rows are also columns a0..a0+7: for the split planes the whole CTA then writes that
 // 8-column group of every stored (upper) block, each thread one row r of it (16 contiguous
 // bytes per plane; a warp covers 512 contiguous bytes).  The FP64 iterate (stored in full)
@@ -117,7 +118,8 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                                                      const int64_t* __restrict__ sub_ptr,
                                                      const int32_t* __restrict__ sub_idx, SubsGeom g, int max_mpad,
                                                      uint16_t* planes, int64_t plane_stride, double* f,
-                                                     double* partials, int max_units, int htab_off, int hbits) {
+                                                     double* partials, int max_units, int htab_off, int hbits,
+                                                     uint2* rows_g) {
     extern __shared__ unsigned char gsm[];
     __shared__ double red[16];
     const int s = blockIdx.x;
@@ -125,9 +127,10 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     const int64_t off = g.off[s];
     const int64_t base = sub_ptr[s];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint2* rows8 = reinterpret_cast<uint2*>(gsm);                                      // [8][max_mpad]
+    // [8][max_mpad] dense rows, then the m_s local -> global list
+    uint2* rows8 = rows_g ? rows_g + (size_t)blockIdx.x * 8 * max_mpad : reinterpret_cast<uint2*>(gsm);
     uint2* rowbuf = rows8 + (size_t)warp * max_mpad;
-    int32_t* sidx = reinterpret_cast<int32_t*>(gsm + (size_t)8 * max_mpad * 8);         // m_s local -> global
+    int32_t* sidx = reinterpret_cast<int32_t*>(gsm + (rows_g ? (size_t)0 : (size_t)8 * max_mpad * 8));
     int2* htab = reinterpret_cast<int2*>(gsm + htab_off);
     for (int i = threadIdx.x; i < (1 << hbits); i += blockDim.x) htab[i] = make_int2(-1, 0);
     __syncthreads();
@@ -886,6 +889,7 @@ extern "C" int gbe_free_subs(gbe_subs* X) {
     gbe_free(X->d_cta_ptr);
     for (int k = 0; k < 3; ++k) gbe_free(X->d_ranges[k]);
     gbe_free(X->d_sums);
+    gbe_free(X->d_gather_rows);
     if (X->h_ctrl) cudaFreeHost(X->h_ctrl);
     for (int i = 0; i < 3; ++i) if (X->ev[i]) cudaEventDestroy(X->ev[i]);
     for (auto e : X->ev_tc) cudaEventDestroy(e);
@@ -1142,7 +1146,7 @@ int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X) {
 }
 
 typedef void (*GatherFn)(Sp2Ctrl*, const int64_t*, const int32_t*, const double*, const int64_t*, const int32_t*,
-                         SubsGeom, int, uint16_t*, int64_t, double*, double*, int, int, int);
+                         SubsGeom, int, uint16_t*, int64_t, double*, double*, int, int, int, uint2*);
 static GatherFn gather_for(int prec) {
     switch (prec) {
         case GBE_PREC_FP64: return gather_kernel<GBE_PREC_FP64>;
@@ -1153,31 +1157,46 @@ static GatherFn gather_for(int prec) {
 }
 
 // Dynamic shared memory of the gather: 8 dense rows, the local->global list, and a hash
-// table of >= 2 m slots (global -> local).
+// table of >= 2 m slots (global -> local).  Subgraphs up to 2432 vertices keep the rows in
+// the 227 KB of a GB300 CTA; larger ones stage them in global memory (L2) and keep the list
+// and the hash table in shared memory, up to 8192 vertices.
 struct GatherLayout {
     size_t smem;
     int htab_off, hbits;
+    bool rows_global;
 };
-static GatherLayout gather_layout(const gbe_subs* X) {
+static GatherLayout gather_layout(const gbe_ctx* ctx, const gbe_subs* X) {
     GatherLayout L;
     const int64_t max_m = X->parts->max_m;
     L.hbits = 6;
     while ((1ll << L.hbits) < 2 * max_m) ++L.hbits;
+    L.rows_global = false;
     L.htab_off = (int)((((size_t)8 * X->max_mpad * 8 + (size_t)max_m * 4) + 7) & ~(size_t)7);
     L.smem = (size_t)L.htab_off + ((size_t)8 << L.hbits);
+    if ((int64_t)L.smem > (int64_t)ctx->smem_optin) {
+        L.rows_global = true;
+        L.htab_off = (int)(((size_t)max_m * 4 + 7) & ~(size_t)7);
+        L.smem = (size_t)L.htab_off + ((size_t)8 << L.hbits);
+    }
     return L;
 }
 
-// The gather stages whole dense rows and the subgraph's index hash table in shared memory:
-// subgraphs up to 2432 vertices fit the 227 KB of a GB300 CTA.
-static int check_gather_fits(const gbe_ctx* ctx, const gbe_subs* X) {
-    const GatherLayout L = gather_layout(X);
+// Checks that the gather fits and allocates its global row staging when it needs one (called
+// before any launch or capture of a run).
+static int prepare_gather(const gbe_ctx* ctx, gbe_subs* X) {
+    const GatherLayout L = gather_layout(ctx, X);
     if ((int64_t)L.smem > (int64_t)ctx->smem_optin) {
         gbe_set_error("a subgraph of %lld vertices needs %zu bytes of gather shared memory, the device allows %d",
                       (long long)X->parts->max_m, L.smem, ctx->smem_optin);
         return GBE_ECAPACITY;
     }
+    if (L.rows_global && !X->d_gather_rows)
+        GBE_TRY(gbe_alloc(&X->d_gather_rows, (size_t)X->P * 8 * X->max_mpad * sizeof(uint2)));
     return GBE_OK;
+}
+
+static uint2* gather_rows_arg(const GatherLayout& L, const gbe_subs* X) {
+    return L.rows_global ? static_cast<uint2*>(X->d_gather_rows) : nullptr;
 }
 
 // Decision after the gather (kind 0) or a squaring (1 tensor-core, 2 FP64).  With a trace
@@ -1224,11 +1243,11 @@ static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, g
     GBE_CUDA_TRY(cudaGetLastError());
     if (!in.eps_given) GBE_TRY(gbe_launch_gershgorin(ctx, H, X));
     const gbe_parts* parts = X->parts;
-    const GatherLayout L = gather_layout(X);
+    const GatherLayout L = gather_layout(ctx, X);
     auto gk = gather_for(X->prec);
     gk<<<(unsigned)X->P, 256, L.smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
                                              geom_of(X), X->max_mpad, X->planes[0], X->total_elems, X->f64[0],
-                                             X->d_partials, X->max_units, L.htab_off, L.hbits);
+                                             X->d_partials, X->max_units, L.htab_off, L.hbits, gather_rows_arg(L, X));
     GBE_CUDA_TRY(cudaGetLastError());
     return enqueue_decide(ctx, X, 0, xp, 0, false);
 }
@@ -1357,11 +1376,11 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     if (in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len) memcpy(in.seq_in, prm->seq_in, in.seq_len);
     if (in.prec != GBE_PREC_FP64 && in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len <= in.fp64_tail) in.mode = 1;
     const bool fp64_steps = X->prec == GBE_PREC_FP64 || in.fp64_tail > 0;
-    GBE_TRY(check_gather_fits(ctx, X));
+    GBE_TRY(prepare_gather(ctx, X));
     if (fp64_steps) GBE_TRY(ensure_f64(X, st));
     // kernel attributes are set outside any capture
     {
-        const GatherLayout L = gather_layout(X);
+        const GatherLayout L = gather_layout(ctx, X);
         auto gk = gather_for(X->prec);
         GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     }
@@ -1701,15 +1720,15 @@ extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     in.eps_min = emin;
     in.eps_max = emax;
     in.out_scale = B;
-    GBE_TRY(check_gather_fits(ctx, X));
-    const GatherLayout L = gather_layout(X);
+    GBE_TRY(prepare_gather(ctx, X));
+    const GatherLayout L = gather_layout(ctx, X);
     auto gk = fp64 ? gather_kernel<GBE_PREC_FP64> : gather_kernel<GBE_PREC_FP16X6>;
     GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     cudaEventRecord(X->ev[0], st);
     init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
     gk<<<(unsigned)X->P, 256, L.smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
                                              geom_of(X), X->max_mpad, X->planes[2], X->total_elems, X->f64[2],
-                                             X->d_partials, X->max_units, L.htab_off, L.hbits);
+                                             X->d_partials, X->max_units, L.htab_off, L.hbits, gather_rows_arg(L, X));
     GBE_CUDA_TRY(cudaGetLastError());
     for (int s = 0; s < 2; ++s) {
         if (fp64) GBE_CUDA_TRY(cudaMemsetAsync(X->f64[s], 0, X->total_elems * 8, st));

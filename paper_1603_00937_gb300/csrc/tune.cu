@@ -183,7 +183,7 @@ extern "C" int gbe_partition_autotune(gbe_ctx* ctx, const gbe_graph* S, const gb
             gbe_free_parts(keep);
             return r;
         }
-        if (P->max_m > 2432) {   // beyond what the gather's shared memory holds
+        if (P->max_m > 8192) {   // beyond what the gather's hash table holds
             gbe_free_parts(P);
             continue;
         }

@@ -4,8 +4,10 @@
   index outside H) are rejected on the host with GBE_EINVAL, before any device work.
 - Singleton subgraphs (m_s = 1, every vertex its own core and no halo): the graph SP2
   reduces to the scalar recursion on each diagonal entry of X0, compared with the oracle.
-- A subgraph larger than the gather's shared memory holds (2433 vertices) is rejected with
-  GBE_ECAPACITY before any kernel runs, and the context stays usable.
+- A subgraph whose dense rows exceed the gather's shared memory (more than 2432 vertices)
+  has them staged in global memory: the 2600-site complete graph, FP64 and FP64TC, against
+  the oracle's dense SP2.  One whose hash table exceeds it too (8193 vertices) is rejected
+  with GBE_ECAPACITY before any kernel runs, and the context stays usable.
 - A replayed branch sequence longer than n_max is rejected with GBE_EINVAL (it would be cut
   short without notice), and one of exactly n_max steps runs whole.
 """
@@ -59,20 +61,37 @@ def test_singleton_subgraphs(ctx, prec, tol):
     assert np.abs(D - Dref).max() <= tol
 
 
-def test_oversized_subgraph_rejected(ctx):
-    w, H, _, _, _ = lattice_case(16, seed=0, thr=0.15)
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP64TC])
+def test_large_subgraph_rows_staged_in_global_memory(ctx, prec):
+    import synth
+    from oracle import hamiltonian
+    w = synth.disordered(2600, seed=11)
+    H = hamiltonian.build_h(w["pos"], w["box"], w["onsite"])
     N = H.shape[0]
-    big = np.arange(2433)
-    subs = [big] + [np.array([i]) for i in range(2433, N)]
-    nc = np.array([2433] + [1] * (N - 2433), dtype=np.int32)
+    Xo, log = sp2.sp2_dense(H, N // 2, n_max=100)
+    Xo = np.asarray(Xo.todense() if hasattr(Xo, "todense") else Xo)
+    full = import_parts(ctx, N, [np.arange(N)], np.array([N]))
+    seq = list(log.seq)
+    X, rep = gbe.sp2_submatrices(ctx, device_csr(H), full, gbe.sp2_params(N // 2, prec=prec, seq=seq, n_max=len(seq)))
+    assert rep["iters"] == len(seq) and rep["status"] == 0
+    Dg, _, _ = assembled_dense(ctx, X, full, N)
+    assert np.abs(Dg - Xo).max() < 1e-10
+
+
+def test_oversized_subgraph_rejected(ctx):
+    w, H, _, _, _ = lattice_case(21, seed=0, thr=0.15)
+    N = H.shape[0]
+    big = np.arange(8193)
+    subs = [big] + [np.array([i]) for i in range(8193, N)]
+    nc = np.array([8193] + [1] * (N - 8193), dtype=np.int32)
     parts = import_parts(ctx, N, subs, nc)
     Hd = device_csr(H)
     with pytest.raises(gbe.GbeError) as e:
         gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP64, n_max=4))
     assert e.value.code == gbe.GBE_ECAPACITY
     # the context still works: a partition at the bound runs
-    ok = [np.arange(2432)] + [np.array([i]) for i in range(2432, N)]
-    nc2 = np.array([2432] + [1] * (N - 2432), dtype=np.int32)
+    ok = [np.arange(8192)] + [np.array([i]) for i in range(8192, N)]
+    nc2 = np.array([8192] + [1] * (N - 8192), dtype=np.int32)
     parts2 = import_parts(ctx, N, ok, nc2)
     X, rep = gbe.sp2_submatrices(ctx, Hd, parts2, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=[1, 0]))
     assert rep["iters"] == 2 and rep["status"] == 0
