@@ -64,12 +64,12 @@ WORKLOADS = {
     # (cores from 25^3 cells of ~67 sites, the branch sequence of one global-trace run replayed
     # on every graph, subgraphs in batches that fit the device)
     "mlp1m": dict(kind="disordered", N=1 << 20, seed=2024,
-                  mlp=dict(rcand=4.0, cut=-2.0, tau=1e-2, train_n=4096, train_seed0=20000, test_seed=29999,
-                           passes=40, lr=3e-3, ncell=(25, 25, 25), n_max=100)),
+                  mlp=dict(rcand=4.0, cut=-2.0, cuts=(-6.0, -4.0, -2.0), tau=1e-2, train_n=4096, train_seed0=20000,
+                           test_seed=29999, passes=40, lr=3e-3, ncell=(25, 25, 25), n_max=100)),
     # the same at 65,536 sites (box 40.3a, cores from 10^3 cells): a quick case of the pipeline
     "mlp64k": dict(kind="disordered", N=1 << 16, seed=2024,
-                   mlp=dict(rcand=4.0, cut=-2.0, tau=1e-2, train_n=4096, train_seed0=20000, test_seed=29999,
-                            passes=40, lr=3e-3, ncell=(10, 10, 10), n_max=100)),
+                   mlp=dict(rcand=4.0, cut=-2.0, cuts=(-6.0, -4.0, -2.0), tau=1e-2, train_n=4096, train_seed0=20000,
+                            test_seed=29999, passes=40, lr=3e-3, ncell=(10, 10, 10), n_max=100)),
 }
 PRECS = {"fp16x6": ("FP16X6", "f16-split(x6)/f32-acc/f64-trace"),
          "bf16x3": ("BF16X3", "bf16-split(x3)/f32-acc/f64-trace"),
@@ -601,10 +601,11 @@ def mlp_train(args, gbe, torch, ctx, cfg):
                "loss_final": loss, "unseen_accuracy": acc, "labels_s": t_lab, "train_s": t_train}
 
 
-def ell_rows_maxdiff(torch, rows, ca, va, cb, vb, n, chunk=8192):
-    """max |A - B| over the union of the entries of the given rows of two ELL matrices
-    (row i = column i of D; an entry absent from one side counts as zero there)."""
-    mx = 0.0
+def ell_rows_diff(torch, rows, ca, va, cb, vb, n, chunk=8192):
+    """(max |A - B|, sum of (A - B)^2, entries) over the union of the entries of the given rows
+    of two ELL matrices (row i = column i of D; an entry absent from one side counts as zero
+    there)."""
+    mx, ss, cnt = 0.0, 0.0, 0
     for r0 in range(0, len(rows), chunk):
         r = rows[r0:r0 + chunk]
         a_c, a_v, b_c, b_v = ca[r], va[r], cb[r], vb[r]
@@ -614,8 +615,11 @@ def ell_rows_maxdiff(torch, rows, ca, va, cb, vb, n, chunk=8192):
         vals = torch.cat([a_v[ma], -b_v[mb]])
         uk, inv = torch.unique(keys, return_inverse=True)
         d = torch.zeros(len(uk), dtype=torch.float64, device=a_c.device).index_add_(0, inv, vals)
-        mx = max(mx, float(d.abs().max()) if len(d) else 0.0)
-    return mx
+        if len(d):
+            mx = max(mx, float(d.abs().max()))
+            ss += float((d * d).sum())
+            cnt += len(d)
+    return mx, ss, cnt
 
 
 def graph_sp2_batched(gbe, torch, ctx, Hv, parts, N, seq, budget, keep=None, compare=None):
@@ -634,7 +638,7 @@ def graph_sp2_batched(gbe, torch, ctx, Hv, parts, N, seq, budget, keep=None, com
     col = torch.empty((N, max_m), dtype=torch.int32, device="cuda") if keep is None else keep[0]
     val = torch.empty((N, max_m), dtype=torch.float64, device="cuda") if keep is None else keep[1]
     prm = gbe.sp2_params(N / 2.0, prec=gbe.PREC_FP64TC, n_max=max(len(seq), 10), seq=seq)
-    t_sp2, diffs = 0.0, {k: 0.0 for k in (compare or {})}
+    t_sp2, diffs = 0.0, {k: [0.0, 0.0, 0] for k in (compare or {})}
     for b in range(B):
         local = gbe.parts_shard(ctx, parts, owner, b)
         X = gbe.subs_create(ctx, local, gbe.PREC_FP64TC)
@@ -647,7 +651,8 @@ def graph_sp2_batched(gbe, torch, ctx, Hv, parts, N, seq, budget, keep=None, com
             gbe.assemble_D(ctx, X, local, col, val)
             rows = torch.nonzero(col[:, 0] >= 0).squeeze(1)
             for k, (cb, vb) in (compare or {}).items():
-                diffs[k] = max(diffs[k], ell_rows_maxdiff(torch, rows, col, val, cb, vb, N))
+                mx, ss, cnt = ell_rows_diff(torch, rows, col, val, cb, vb, N)
+                diffs[k] = [max(diffs[k][0], mx), diffs[k][1] + ss, diffs[k][2] + cnt]
         else:
             cb = torch.empty_like(col)
             vb = torch.empty_like(val)
@@ -664,16 +669,23 @@ def graph_sp2_batched(gbe, torch, ctx, Hv, parts, N, seq, budget, keep=None, com
 
 
 def mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M):
-    """The trained network's graph of the big system against the H^k pattern graphs: each
-    graph's FP64-grade graph SP2 (the same replayed branch sequence), D compared with the
-    conservative H^2 graph's D, with each graph's sum of m_s^3 and SP2 time."""
+    """The trained network's graphs of the big system (one per logit cut) against the H^k
+    pattern graphs and the whole candidate ball: each graph's FP64-grade graph SP2 (the
+    same replayed branch sequence), D compared with the conservative H^2 graph's D, with
+    each graph's sum of m_s^3 and SP2 time."""
     N = w["pos"].shape[0]
-    graphs = {"H^1": lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_HK_PATTERN, k=1),
-              "MLP": lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_MLP, site_struct=st, mlp=M, rcand=cfg["rcand"],
-                                             logit_cut=cfg["cut"]),
-              "H^2": lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_HK_PATTERN, k=2)}
+
+    def hk(k):
+        return lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_HK_PATTERN, k=k)
+
+    def learned(cut):
+        return lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_MLP, site_struct=st, mlp=M, rcand=cfg["rcand"],
+                                       logit_cut=cut)
+
+    graphs = [("H^1", hk(1))] + [("MLP cut %g" % c, learned(c)) for c in cfg["cuts"]] + \
+             [("ball r<%g" % cfg["rcand"], learned(-1e30)), ("H^2", hk(2))]
     res, parts_of = {}, {}
-    for name, make in graphs.items():
+    for name, make in graphs:
         t0 = time.perf_counter()
         G = make()
         parts_of[name] = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=cfg["ncell"], site_struct=st)
@@ -681,7 +693,7 @@ def mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M):
         res[name] = {"edges_per_site": G.size()[1] / N, "graph_and_partition_s": time.perf_counter() - t0}
         del G
     # the branch sequence: one global-trace run (FP16X6, every subgraph resident: 4 planes x 2
-    # bytes x 2 sides per padded element) of the MLP graph, or of H^1 when the MLP graph's
+    # bytes x 2 sides per padded element) of the first learned graph, or of H^1 when its
     # planes would not fit beside the rest
     budget = args.batch_gb * 1e9
 
@@ -689,7 +701,8 @@ def mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M):
         ms = np.diff(parts.export()[1])
         return float(np.sum(((ms + 127) // 128 * 128).astype(np.float64) ** 2)) * 16.0
 
-    src = "MLP" if planes16(parts_of["MLP"]) <= 1.5 * budget else "H^1"
+    first = graphs[1][0]
+    src = first if planes16(parts_of[first]) <= 1.5 * budget else "H^1"
     t0 = time.perf_counter()
     XS = gbe.subs_create(ctx, parts_of[src], gbe.PREC_FP16X6)
     gbe.sp2_run(ctx, Hv, parts_of[src], gbe.sp2_params(N / 2.0, prec=gbe.PREC_FP16X6, n_max=cfg["n_max"]), XS)
@@ -698,18 +711,20 @@ def mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M):
     seq = rep["seq"]
     seq_info = {"from": "global-trace FP16X6 run of the %s graph" % src, "steps": len(seq), "stop": rep["stop"],
                 "s": time.perf_counter() - t0}
-    stored = {}
-    for name in ("H^1", "MLP"):
-        _, _, max_m = parts_of[name].info()
-        stored[name] = (torch.empty((N, max_m), dtype=torch.int32, device="cuda"),
-                        torch.empty((N, max_m), dtype=torch.float64, device="cuda"))
-        info, _ = graph_sp2_batched(gbe, torch, ctx, Hv, parts_of[name], N, seq, budget, keep=stored[name])
-        res[name].update(info)
-    info, diffs = graph_sp2_batched(gbe, torch, ctx, Hv, parts_of["H^2"], N, seq, budget, compare=stored)
+    # the reference first (its D kept), then every other graph compared with it batch by batch
+    _, _, max_m = parts_of["H^2"].info()
+    ref = (torch.empty((N, max_m), dtype=torch.int32, device="cuda"),
+           torch.empty((N, max_m), dtype=torch.float64, device="cuda"))
+    info, _ = graph_sp2_batched(gbe, torch, ctx, Hv, parts_of["H^2"], N, seq, budget, keep=ref)
     res["H^2"].update(info)
-    for name in ("H^1", "MLP"):
-        res[name]["max_abs_dD_vs_H2"] = diffs[name]
+    for name, _ in graphs[:-1]:
+        info, diffs = graph_sp2_batched(gbe, torch, ctx, Hv, parts_of[name], N, seq, budget, compare={"H^2": ref})
+        res[name].update(info)
+        mx, ss, cnt = diffs["H^2"]
+        res[name]["max_abs_dD_vs_H2"] = mx
+        res[name]["rms_dD_vs_H2"] = (ss / cnt) ** 0.5 if cnt else 0.0   # over the union of both patterns
         res[name]["sum_m3_vs_H2"] = res[name]["sum_m3"] / res["H^2"]["sum_m3"]
+        del parts_of[name]
     return {"graphs": res, "sequence": seq_info, "cores": "spatial cells %s" % (cfg["ncell"],),
             "precision": "FP64TC (FP64-grade tensor-core squarings) in every graph's SP2",
             "reference": "the H^2 pattern graph (every pair with (H^2)_ij != 0)"}
@@ -726,7 +741,11 @@ def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
     st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
     Hh = gbe.build_hamiltonian(ctx, st)
     Hv = Hh.csr()
-    cfg = wl["mlp"]
+    cfg = dict(wl["mlp"])
+    if args.mlp_tau is not None:
+        cfg["tau"] = args.mlp_tau
+    if args.mlp_cuts:
+        cfg["cuts"] = tuple(float(c) for c in args.mlp_cuts.split(","))
     M, train = mlp_train(args, gbe, torch, ctx, cfg)
     phases = {"pairs_features": 0.0, "forward": 0.0, "graph": 0.0}
     npairs = 0
@@ -817,6 +836,10 @@ def parse_args(argv=None):
                          "tuned choice")
     ap.add_argument("--train-systems", type=int, default=200,
                     help="mlp1m: seeded 4096-site systems the network is trained on")
+    ap.add_argument("--mlp-tau", type=float, default=None,
+                    help="mlp workloads: label threshold |D_ij| >= tau (default 1e-2)")
+    ap.add_argument("--mlp-cuts", default=None,
+                    help="mlp workloads: comma-separated logit cuts of the compared learned graphs")
     ap.add_argument("--no-compare", action="store_true",
                     help="mlp1m: skip the FP64-grade graph SP2 comparison of the proposed graph with H^1 and H^2")
     ap.add_argument("--batch-gb", type=float, default=96.0,

@@ -1351,7 +1351,10 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     // (and its FP64 tail, placed at its end, never reached)
     GBE_CHECK_ARG(prm->branch_mode != GBE_BRANCH_REPLAY || prm->seq_len <= prm->n_max,
                   "replay sequence longer than n_max");
-    GBE_CHECK_ARG(parts->max_m <= 8192, "subgraph larger than 8192");
+    if (parts->max_m > 8192) {
+        gbe_set_error("a subgraph of %lld vertices exceeds the 8192 the gather holds", (long long)parts->max_m);
+        return GBE_ECAPACITY;
+    }
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     Sp2Init in;
@@ -1674,7 +1677,10 @@ extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     GBE_CHECK_ARG(X->prec == GBE_PREC_FP64 || X->prec == GBE_PREC_FP16X6, "Chebyshev expansion supports FP64 and FP16X6");
     GBE_CHECK_ARG(prm->order >= 1 && prm->order <= 100000, "order out of range");
     GBE_CHECK_ARG(prm->coeffs || prm->beta > 0.0, "beta must be positive (or coefficients given)");
-    GBE_CHECK_ARG(parts->max_m <= 8192, "subgraph larger than 8192");
+    if (parts->max_m > 8192) {
+        gbe_set_error("a subgraph of %lld vertices exceeds the 8192 the gather holds", (long long)parts->max_m);
+        return GBE_ECAPACITY;
+    }
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const bool fp64 = X->prec == GBE_PREC_FP64;

@@ -181,8 +181,8 @@ def test_clock_sampler_with_fake_smi(tmp_path, monkeypatch):
     assert clk["reasons"] == ["nvidia-smi unavailable"] and bench.clock_verdict(clk) is None
 
 
-def test_ell_rows_maxdiff_against_dense():
-    """bench.ell_rows_maxdiff (the D comparison of the mlp workloads' graphs) against the dense
+def test_ell_rows_diff_against_dense():
+    """bench.ell_rows_diff (the D comparison of the mlp workloads' graphs) against the dense
     difference: ELL rows with different patterns and widths, entries absent on one side
     counting as zero, only the selected rows compared."""
     import numpy as np
@@ -210,9 +210,11 @@ def test_ell_rows_maxdiff_against_dense():
     ca, va = random_ell(12, 12)
     cb, vb = random_ell(20, 18)
     rows = np.sort(rng.choice(n, 25, replace=False))
-    want = np.abs(dense(ca, va) - dense(cb, vb))[:, rows].max()
+    dd = (dense(ca, va) - dense(cb, vb))[:, rows]
+    both = ((dense(ca, np.where(ca >= 0, 1.0, 0.0)) + dense(cb, np.where(cb >= 0, 1.0, 0.0))) > 0)[:, rows]
     t = torch.from_numpy
-    got = bench.ell_rows_maxdiff(torch, t(rows), t(ca), t(va), t(cb), t(vb), n, chunk=7)
-    assert got == want
-    assert bench.ell_rows_maxdiff(torch, t(rows), t(ca), t(va), t(ca), t(va), n) == 0.0
+    mx, ss, cnt = bench.ell_rows_diff(torch, t(rows), t(ca), t(va), t(cb), t(vb), n, chunk=7)
+    assert mx == np.abs(dd).max() and cnt == int(both.sum())
+    assert abs(ss - float((dd ** 2).sum())) < 1e-12 * max(1.0, ss)
+    assert bench.ell_rows_diff(torch, t(rows), t(ca), t(va), t(ca), t(va), n)[:2] == (0.0, 0.0)
     assert bench.mlp_init_params(0).shape == (4609,)
