@@ -160,23 +160,48 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     f64_to_f32_pair(gsc, ih, il);
     double t1 = 0.0, t2 = 0.0;
     float t2h = 0.f, t2l = 0.f;             // double-float Tr X_0^2 (split paths)
+    // A lane takes the entries p0, p0 + 32, p0 + 64 of a row together (their loads issued at
+    // once), then the next 96, in that order (the order the traces add them).  The first 96
+    // entries of the warp's next row are loaded one iteration ahead and its row range two
+    // iterations ahead, so that their latency overlaps the current rows' write-out.
+    auto row_range = [&](int ar, int64_t& r0, int64_t& r1) {
+        if (ar < m) {
+            const int64_t gi = sidx[ar];
+            r0 = rowptr[gi];
+            r1 = rowptr[gi + 1];
+        } else {
+            r0 = 0;
+            r1 = 0;
+        }
+    };
+    auto load3 = [&](int64_t p0, int64_t r1, int (&cj)[3], double (&hv)[3]) {
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int64_t p = p0 + 32 * u;
+            cj[u] = p < r1 ? col[p] : -1;
+            hv[u] = p < r1 ? val[p] : 0.0;
+        }
+    };
+    int64_t r0c, r1c, r0n, r1n;
+    int cjc[3];
+    double hvc[3];
+    row_range(warp, r0c, r1c);
+    load3(r0c + lane, r1c, cjc, hvc);
+    row_range(warp + 8, r0n, r1n);
     for (int a0 = 0; a0 < mpad; a0 += 8) {
         const int a = a0 + warp;
         for (int b = lane; b < mpad; b += 32) rowbuf[b] = make_uint2(0u, 0u);
         __syncwarp();
-        if (a < m) {
-            const int64_t gi = sidx[a];
-            const int64_t r0 = rowptr[gi], r1 = rowptr[gi + 1];
+        {
+            const int64_t r0 = r0c, r1 = r1c;   // empty for a >= m
             for (int64_t p0 = r0 + lane; p0 < r1; p0 += 96) {
-                // this lane's entries p0, p0 + 32, p0 + 64: their loads are issued together,
-                // then the entries are taken in that order (the order the traces add them)
                 int cj[3];
                 double hv[3];
+                if (p0 == r0 + lane) {
 #pragma unroll
-                for (int u = 0; u < 3; ++u) {
-                    const int64_t p = p0 + 32 * u;
-                    cj[u] = p < r1 ? col[p] : -1;
-                    hv[u] = p < r1 ? val[p] : 0.0;
+                    for (int u = 0; u < 3; ++u) { cj[u] = cjc[u]; hv[u] = hvc[u]; }
+                } else {
+                    load3(p0, r1, cj, hv);
                 }
 #pragma unroll
                 for (int u = 0; u < 3; ++u) {
@@ -227,6 +252,11 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                 }
             }
         }
+        // the next row's first entries and the range of the row after it
+        load3(r0n + lane, r1n, cjc, hvc);
+        r0c = r0n;
+        r1c = r1n;
+        row_range(a + 16, r0n, r1n);
         if constexpr (prec == GBE_PREC_FP64) {
             __syncwarp();
             // row a, all column groups: 64 contiguous bytes per lane and group

@@ -188,16 +188,16 @@ def test_partition_capacity_error(ctx, lat):
 
 @pytest.mark.parametrize("prec", [gbe.PREC_FP16X6, gbe.PREC_FP64])
 def test_partition_autotune_picks_cheapest(ctx, prec):
-    """Cost-driven partition size on the 16^3 lattice (|H^2| >= 0.15 graph): every candidate
+    """Cost-driven partition size on the 21^3 lattice (|H^2| >= 0.15 graph): every candidate
     cell grid is partitioned and costed by the modelled squaring time of one SP2 step
     (checked here against the formula on the exported subgraph sizes); a grid whose
-    subgraphs exceed what the gather holds (one cell: 4096 sites) is infeasible; the cheapest
-    one is returned."""
-    w = synth.lattice(16, seed=3)
+    subgraphs exceed what the gather holds (one cell: 9261 sites, above 8192) is infeasible;
+    the cheapest one is returned."""
+    w = synth.lattice(21, seed=3)
     st = gbe.sites(torch.from_numpy(w["pos"]).cuda(), torch.from_numpy(w["onsite"]).cuda(), w["box"])
     Hg = gbe.build_hamiltonian(ctx, st)
     G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_H2_THRESH, thresh=0.15)
-    cands = [(1, 1, 1), (2, 2, 2), (4, 4, 4), (8, 8, 8), (16, 16, 16)]
+    cands = [(1, 1, 1), (3, 3, 3), (7, 7, 7), (21, 21, 21)]
     parts, best, cost = gbe.partition_autotune(ctx, G, cands, prec=prec, site_struct=st)
     assert np.isinf(cost[0]) and np.all(np.isfinite(cost[1:]))
     for i, c in enumerate(cands[1:], start=1):
