@@ -2,18 +2,19 @@
 // tiles staged by TMA (cp.async.bulk.tensor), branch X^2 / 2X - X^2 applied in the
 // epilogue, next split written directly, FP64-grade core traces fused.
 //
-// One CTA per SM (persistent), 10 warps:
+// One CTA per SM (persistent), 10 warps (14 for FP64TC):
 //   warp 0  TMA producer      : K-chunks of 32 (16) for every split plane an MMA needs (one
 //                               contiguous 8 KB (4 KB) box each, already in MMA operand order)
 //   warp 1  MMA issuer        : 128xNx16 tcgen05.mma per product and k-step (N = 128, less in a
 //                               subgraph's last column block) into the recipe's TMEM
 //                               accumulators: two, double-buffered (4 x 128 cols), for the
 //                               split formats; four, single-buffered, for FP64TC
-//   warps 2-9 epilogue        : TMEM -> registers, X_{n+1} = S or 2 X_n - S, split,
+//   warps 2.. epilogue        : TMEM -> registers, X_{n+1} = S or 2 X_n - S, split,
 //                               store the tile, partial traces of core rows (counting the
 //                               implied mirror of off-diagonal tiles); two warps per TMEM lane
-//                               quarter, each taking half of the tile's columns.  X_n
-//                               values for the next chunk are fetched ahead.
+//                               quarter, each taking half of the tile's columns (three for
+//                               FP64TC, whose epilogue does not overlap the MMAs, each taking
+//                               a third).  X_n values for the next chunk are fetched ahead.
 // Only upper-triangular 128x128 blocks of each iterate are stored; a K-chunk that falls in
 // a lower block is loaded from the mirror block as a transposed (MN-major) operand tile.
 // Work items are upper-triangular output tiles (I <= J) of every subgraph.
@@ -32,8 +33,6 @@
 
 namespace {
 
-constexpr int kEpiWarps = 8;                       // two per TMEM lane quarter
-constexpr int kThreads = 64 + 32 * kEpiWarps;      // producer, MMA issuer, epilogue
 // One operand slot holds a K-chunk of KC columns (32 or 16) of a 128-row block: KC/8 column
 // groups of 128 rows x 16 bytes, contiguous in the blocked layout.
 template <int KC>
@@ -124,17 +123,20 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-// Named barrier over the 256 epilogue threads that also ORs a flag across them.
+// Named barrier over the NT epilogue threads.
+template <int NT>
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory"); }
+// The same barrier, ORing a flag across the epilogue threads.
+template <int NT>
 __device__ __forceinline__ bool epi_bar_any(bool v) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, 1, 256, p;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}\n"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(NT)
         : "memory");
     return r != 0;
 }
@@ -197,6 +199,7 @@ struct Recipe<GBE_PREC_FP16X6> {
     // into acc1 (units 2^-11): s0 s1^T, s1 s0^T, s1 s1s^T, s0 s2^T, s2 s0^T
     static constexpr int kSlots = 7, kA = 3, kProducts = 6, kPlanes = 4, kStages = 4, kDiag = 1;
     static constexpr int kAcc = 2, kTmemBufCols = 256, kBPlane0 = 0, kDiagPlane = 3, kStages16 = 8;
+    static constexpr int kEpiWarps = 8;
     static constexpr uint32_t kType = 0;  // fp16
     __host__ __device__ static constexpr int pa(int p) { return nib(0x201100u, p); }
     __host__ __device__ static constexpr int pb(int p) { return nib(0x356343u, p); }
@@ -208,6 +211,7 @@ struct Recipe<GBE_PREC_BF16X3> {
     // slots: A {hi, lo}, B {hi, lo}; products hi hi^T + hi lo^T + lo hi^T into acc0
     static constexpr int kSlots = 4, kA = 2, kProducts = 3, kPlanes = 2, kStages = 6, kDiag = 0;
     static constexpr int kAcc = 1, kTmemBufCols = 256, kBPlane0 = 0, kDiagPlane = 2, kStages16 = 12;
+    static constexpr int kEpiWarps = 8;
     static constexpr uint32_t kType = 1;  // bf16
     __host__ __device__ static constexpr int pa(int p) { return nib(0x100u, p); }
     __host__ __device__ static constexpr int pb(int p) { return nib(0x232u, p); }
@@ -222,6 +226,7 @@ struct Recipe<GBE_PREC_FP64TC> {
     // only 16-column K-chunks fit (a stage of 18 slots is 72 KB).
     static constexpr int kSlots = 18, kA = 9, kProducts = 18, kPlanes = 10, kStages = 0, kDiag = 1;
     static constexpr int kAcc = 4, kTmemBufCols = 512, kBPlane0 = 1, kDiagPlane = 9, kStages16 = 3;
+    static constexpr int kEpiWarps = 12;
     static constexpr uint32_t kType = 0;  // fp16
     //  ACC0: t0 t0 | ACC1: t0 t1, t1 t0, u' u | ACC2: t0 t2, t2 t0, u v, v u, v v |
     //  ACC3: t0 t3, t3 t0, t1 t2, t2 t1 (2^-30); t0 t4', t4' t0, t1 t3', t3' t1, t2 t2' (2^-40)
@@ -239,6 +244,10 @@ struct Recipe<GBE_PREC_FP64TC> {
     }
 };
 
+// Threads of a CTA: producer warp, MMA warp, the recipe's epilogue warps.
+template <int PREC>
+constexpr int threads_of() { return 64 + 32 * Recipe<PREC>::kEpiWarps; }
+
 // A slot holding the same plane as B slot b on a diagonal tile, or -1 (loaded).
 template <class R> __host__ __device__ constexpr int slot_alias(int b) {
     return (b >= R::kA && R::kBPlane0 + (b - R::kA) < R::kA) ? R::kBPlane0 + (b - R::kA) : -1;
@@ -248,12 +257,16 @@ template <class R> __host__ __device__ constexpr int slot_alias(int b) {
 template <int PREC, int KC>
 constexpr int default_stages() { return KC == 32 ? Recipe<PREC>::kStages : Recipe<PREC>::kStages16; }
 
+// Bytes after the operand ring: 2 NS + 5 mbarriers, the TMEM address, abort flag and header
+// words, then the per-tile trace reduction (two parities x 4 floats per epilogue warp).
+constexpr size_t bar_area_bytes(int ns, int epi_warps) { return (size_t)(2 * ns + 8) * 8 + (size_t)32 * epi_warps; }
+
 // Shared memory of a CTA with an NS-deep ring of KC-column chunks (NS = 0: the default).
 template <int PREC, int NS = 0, int KC = 32>
 constexpr size_t smem_bytes() {
     using R = Recipe<PREC>;
     constexpr int ns = NS ? NS : default_stages<PREC, KC>();
-    return 1024 /*align slack*/ + (size_t)ns * R::kSlots * tile_bytes<KC>() + 512 /*barriers, flags, reduction*/;
+    return 1024 /*align slack*/ + (size_t)ns * R::kSlots * tile_bytes<KC>() + bar_area_bytes(ns, R::kEpiWarps);
 }
 
 // Optional wait-time counters (build with -DGBE_TC_STATS): cycles each role spends in
@@ -304,9 +317,11 @@ struct TcArgs {
 // NS_: depth of the operand ring (0: the default for KC); KC: columns of K per ring stage
 // (32, or 16 for twice as many stages in the same shared memory).
 template <int PREC, bool FOE, int NS_, int KC>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_of<PREC>(), 1)
     sp2_square_tc_kernel(const __grid_constant__ TcMaps maps, TcArgs args) {
     using R = Recipe<PREC>;
+    constexpr int EW = R::kEpiWarps, ENT = 32 * EW;   // epilogue warps and threads
+    static_assert(EW == 8 || EW == 12, "two or three epilogue warps per TMEM lane quarter");
     static_assert(R::kAcc * 128 <= R::kTmemBufCols && 512 % R::kTmemBufCols == 0, "accumulators must fit a TMEM buffer");
     constexpr int NS = NS_ ? NS_ : default_stages<PREC, KC>();
     constexpr int kTileBytes = tile_bytes<KC>();
@@ -337,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         hdr[2] = ctrl->branch;
         *abort_flag = 0;
         for (int i = 0; i < NS; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], 32 * kEpiWarps); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], ENT); }
         mbar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -550,8 +565,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ------------------------------------------------------------ epilogue (warps 2..9)
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int ew = warp - 2;                // 0..7
-        const int half = ew >> 2;               // column half of the tile
+        const int ew = warp - 2;                // 0..EW-1
+        const int part = ew >> 2;               // this warp's share of the tile's columns
+        // columns [cbeg, cend): halves (16-column chunks) for the split recipes; for FP64TC
+        // thirds of its sixteen 8-column chunks (6, 5, 5)
+        constexpr int kParts = EW / 4;
+        const int cbeg = kParts == 2 ? 64 * part : 8 * (part == 0 ? 0 : 1 + 5 * part);
+        const int cend = kParts == 2 ? cbeg + 64 : 8 * (6 + 5 * part);
         const int a = 32 * q + lane;
         const uint32_t lane_addr = tmem_base + ((uint32_t)(32 * q) << 16);
         constexpr int kXP = (R::kPlanes == 4) ? 3 : 2;   // planes of X_n the update reads
@@ -567,8 +587,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool offdiag = (w.I != w.J);
             const int ncol = tile_cols(args.g.m[w.s], w.J, FOE);   // columns the MMAs computed
             // this warp's 16-column chunks (FP64TC: 8-column chunks) inside them, 0..4 (0..8)
-            const int nch = max(0, min(4, (ncol - 64 * half + 15) >> 4));
-            const int nch8 = max(0, min(8, (ncol - 64 * half + 7) >> 3));
+            const int nch = max(0, min((cend - cbeg) >> 4, (ncol - cbeg + 15) >> 4));
+            const int nch8 = max(0, min((cend - cbeg) >> 3, (ncol - cbeg + 7) >> 3));
             // X_n of the first chunk, fetched before the accumulator is ready
             uint32_t xn[kXP][8];
             auto fetch_x = [&](int ch) {
@@ -581,12 +601,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     xn[p][4] = v1.x; xn[p][5] = v1.y; xn[p][6] = v1.z; xn[p][7] = v1.w;
                 }
             };
-            if (use_c && PREC != GBE_PREC_FP64TC && nch > 0) fetch_x(4 * half);
+            if (use_c && PREC != GBE_PREC_FP64TC && nch > 0) fetch_x(cbeg >> 4);
             // FP64TC: X_n's digits t0..t3 (planes 1-4) and t4' (plane 8) of an 8-column chunk,
             // the first chunk fetched before the accumulators are ready, later ones one ahead
             uint4 xv[5] = {};
             auto fetch_dig = [&](int cc) {
-                const int64_t e = blk_index(off, mpad, row, 128 * w.J + 64 * half + 8 * cc);
+                const int64_t e = blk_index(off, mpad, row, 128 * w.J + cbeg + 8 * cc);
 #pragma unroll
                 for (int p = 0; p < 5; ++p) xv[p] = *reinterpret_cast<const uint4*>(pin + (p < 4 ? p + 1 : 8) * ps + e);
             };
@@ -598,7 +618,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (lane == 0) TC_ACC(3);
             }
             // all epilogue warps leave together, so no named barrier is left waiting
-            if (epi_bar_any(!ok)) {
+            if (epi_bar_any<ENT>(!ok)) {
                 *abort_flag = 1;
                 atomicExch(&ctrl->status, GBE_ETIMEOUT);
                 break;
@@ -606,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             float sh = 0.f, sl = 0.f, dP = 0.f, dQ = 0.f;
             if ((PREC == GBE_PREC_FP64TC ? nch8 : nch) == 0) {
-                // no column of this warp's half was computed: nothing to read or write
+                // no column of this warp's share was computed: nothing to read or write
                 tc_fence_before();
                 mbar_arrive(&tempty[tb]);
             }
@@ -615,8 +635,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // 2^-50 (ACC0..2 hold exact multiples of 2^-20; ACC3 is rounded there), the branch
                 // 2 X_n - X^2 in the same integers, then the digits of the next iterate
                 for (int cc = 0; cc < nch8; ++cc) {
-                    const int col0 = 128 * w.J + 64 * half + 8 * cc;
-                    const uint32_t ta = lane_addr + (uint32_t)(tb * R::kTmemBufCols + 64 * half + 8 * cc);
+                    const int col0 = 128 * w.J + cbeg + 8 * cc;
+                    const uint32_t ta = lane_addr + (uint32_t)(tb * R::kTmemBufCols + cbeg + 8 * cc);
                     uint32_t r0[8], r1[8], r2[8], r3[8];
                     tmem_ld8(ta, r0);
                     tmem_ld8(ta + 128, r1);
@@ -674,7 +694,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             } else
             for (int cc = 0; cc < nch; ++cc) {
-                const int ch = 4 * half + cc;
+                const int ch = (cbeg >> 4) + cc;
                 const int col0 = 128 * w.J + 16 * ch;
                 uint32_t ra[16], rb[16];
                 tmem_ld16(lane_addr + (uint32_t)(tb * R::kTmemBufCols + 16 * ch), ra);
@@ -768,18 +788,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // partial traces of this tile: FP32-pair (TwoSum) reduction in a fixed order over
             // the warp, FP64 only for the final per-tile sum (FP64 is a narrow pipe here)
-            const bool has_diag = core_row && !offdiag && (row >> 7) == w.J && ((row & 127) >> 6) == half;
+            const bool has_diag = core_row && !offdiag && (row >> 7) == w.J && (row & 127) >= cbeg && (row & 127) < cend;
             float d1h = has_diag ? dP : 0.f, d1l = has_diag ? dQ : 0.f;
             for (int o = 16; o > 0; o >>= 1) {
                 df_add(sh, sl, __shfl_xor_sync(0xffffffffu, sh, o), __shfl_xor_sync(0xffffffffu, sl, o));
                 df_add(d1h, d1l, __shfl_xor_sync(0xffffffffu, d1h, o), __shfl_xor_sync(0xffffffffu, d1l, o));
             }
-            float* rd = reinterpret_cast<float*>(red) + 32 * par;
+            float* rd = reinterpret_cast<float*>(red) + 4 * EW * par;
             if (lane == 0) { rd[4 * ew] = d1h; rd[4 * ew + 1] = d1l; rd[4 * ew + 2] = sh; rd[4 * ew + 3] = sl; }
-            epi_bar();
+            epi_bar<ENT>();
             if (ew == 0 && lane == 0) {
                 double r1 = 0.0, r2 = 0.0;
-                for (int k = 0; k < kEpiWarps; ++k) {
+                for (int k = 0; k < EW; ++k) {
                     r1 += (double)rd[4 * k] + (double)rd[4 * k + 1];
                     r2 += (double)rd[4 * k + 2] + (double)rd[4 * k + 3];
                 }
@@ -831,10 +851,12 @@ struct TcVariant {
     int stages;
     const void* fn;
     size_t smem;
+    int threads;
 };
 #define GBE_TC_VARIANT(P, F, N, K)                                                                          \
     TcVariant {                                                                                              \
-        P, F, K, N ? N : default_stages<P, K>(), (const void*)sp2_square_tc_kernel<P, F, N, K>, smem_bytes<P, N, K>() \
+        P, F, K, N ? N : default_stages<P, K>(), (const void*)sp2_square_tc_kernel<P, F, N, K>, smem_bytes<P, N, K>(), \
+            threads_of<P>()                                                                                  \
     }
 static const TcVariant kVariants[] = {
     GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 0, 32), GBE_TC_VARIANT(GBE_PREC_FP16X6, false, 3, 32),
@@ -982,7 +1004,7 @@ int gbe_tc_launch_square(gbe_ctx* ctx, gbe_subs* X, int slot) {
     static_assert(sizeof(maps) == sizeof(X->tmap) && sizeof(maps) == sizeof(X->tmap16), "tensor map set size");
     memcpy(&maps, v->kc == 16 ? X->tmap16 : X->tmap, sizeof(maps));
     void* kargs[2] = {&maps, &a};
-    GBE_CUDA_TRY(cudaLaunchKernel(v->fn, dim3(grid), dim3(kThreads), kargs, v->smem, ctx->stream));
+    GBE_CUDA_TRY(cudaLaunchKernel(v->fn, dim3(grid), dim3(v->threads), kargs, v->smem, ctx->stream));
     return GBE_OK;
 }
 
@@ -1005,7 +1027,7 @@ int gbe_tc_launch_foe(gbe_ctx* ctx, gbe_subs* X, int a_side, int b_side, int c_s
     memcpy(&maps, X->tmap, sizeof(maps));
     const int gridf = std::max(1, std::min(X->n_items_tc_full, ctx->sm_count));
     sp2_square_tc_kernel<GBE_PREC_FP16X6, true, 0, 32>
-        <<<gridf, kThreads, smem_bytes<GBE_PREC_FP16X6, 0, 32>(), ctx->stream>>>(maps, a);
+        <<<gridf, threads_of<GBE_PREC_FP16X6>(), smem_bytes<GBE_PREC_FP16X6, 0, 32>(), ctx->stream>>>(maps, a);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;
 }
