@@ -1074,7 +1074,7 @@ def main():
                 "frac_alg": achieved / peak if achieved else None,
                 "achieved_exec": achieved_exec, "frac_exec": achieved_exec / peak if achieved_exec else None,
                 "work_exec": "executed: %d split products on the padded upper 128x128 tiles (%.4g flop per launch)"
-                             % (6 if prec_name == "FP16X6" else 3, tc_flops),
+                             % ({"FP16X6": 6, "BF16X3": 3, "FP64TC": 18}[prec_name], tc_flops),
                 "kernel": "sp2_square_tc_kernel<%s>" % prec_name, "peak_kind": peak_kind + " dense bf16/fp16 burst",
                 "launches": rep_prof["n_tc"], "ms_per_launch": tc_ms,
                 "timing": "CUDA events around every squaring of a step-by-step launched run of the same workload"}
