@@ -52,6 +52,13 @@ WORKLOADS = {
     # comes from the previous step's |D| >= 1e-2 (first step: |H^2| >= 0.15), the SP2
     # sequence is the previous step's, replayed (no trace exchange during a step)
     "qmd32": dict(kind="lattice", L=32, seed=0, thresh=0.15, ncell=(8, 8, 8), qmd=True, tau=1e-2),
+    # QMD-like run of the 16^3 lattice on its complete graph (one subgraph of all 4096 sites,
+    # where SP2 converges and the gap estimate has its window): each step's branch sequence
+    # comes from the HOMO-LUMO gap estimated at the previous step (Sec. II.C), FP64-grade;
+    # the estimate reads the traces where the idempotency error is 1e-6 .. 1e-2, above the
+    # FP64TC squarings' floor (~1e-9 over 4096 core positions)
+    "qmd16gap": dict(kind="lattice", L=16, seed=0, qmd=True, complete=True, sequence="gap", prec="fp64tc",
+                     gap_window=(1e-6, 1e-2), seq_tol=1e-12),
     # finite temperature on the 32^3 workload: Fermi function at kT = 0.25 eV (beta = 4/eV),
     # mu = 0, Chebyshev order 300 (coefficients below 1e-8 beyond it for this spectral width)
     "foe32": dict(kind="lattice", L=32, seed=0, thresh=0.15, ncell=(8, 8, 8), foe=dict(beta=4.0, mu=0.0, order=300)),
@@ -362,9 +369,13 @@ def configure(args, gbe, ctx, H, parts, prm, X):
 def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
     """MD steps of the lattice: every step rebuilds H from the new positions, the graph from
     the previous step's D, the partition, the SP2 state, runs SP2 with the previous step's
-    branch sequence replayed, and assembles D (the next step's graph input).  A step's
-    inputs are the positions, copied in from pinned host memory; its output read back is
-    the SP2 report.  Timed: the whole step, wall clock, K steps after W warm-up steps."""
+    branch sequence replayed, and assembles D (the next step's graph input).  With
+    wl["sequence"] == "gap" (Sec. II.C's other source of a sequence) the graph is the
+    complete one and each step's sequence comes from the HOMO-LUMO gap estimated from the
+    previous step's traces (gbe_sp2_gap_estimate, then gbe_sp2_sequence on the new step's
+    Gershgorin bounds).  A step's inputs are the positions, copied in from pinned host
+    memory; its output read back is the SP2 report.  Timed: the whole step, wall clock, K
+    steps after W warm-up steps."""
     import synth
     prec_name, dtype_name = PRECS[args.prec]
     PREC = getattr(gbe, "PREC_" + prec_name)
@@ -375,11 +386,15 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
     ons = torch.from_numpy(w["onsite"]).cuda()
     pos_h = torch.empty((N, 3), dtype=torch.float64).pin_memory()
     pos_d = torch.empty((N, 3), dtype=torch.float64, device="cuda")
-    state = {"D": None, "seq": None}
+    gap_mode = wl.get("sequence") == "gap"
+    full = (gbe.parts_import(ctx, N, np.array([N], np.int32), np.array([0, N], np.int64),
+                             np.arange(N, dtype=np.int32)) if wl.get("complete") else None)
+    bounds = torch.empty(2, dtype=torch.float64, device="cuda")
+    state = {"D": None, "seq": None, "gap": None, "gap_steps": 0, "gap_missed": 0}
     phase = {k: 0.0 for k in ("h_build", "graph", "partition", "sp2_state", "sp2", "assemble")}
     last = {}
 
-    def step(t, timed):
+    def step(t, timed, free=False):
         def mark(name, t0):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -392,20 +407,33 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
         st = gbe.sites(pos_d, ons, box)
         Hg = gbe.build_hamiltonian(ctx, st)
         t0 = mark("h_build", t0)
-        if state["D"] is None:
-            G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_H2_THRESH, thresh=wl["thresh"])
+        if full is not None:
+            parts = full
         else:
-            G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_D_THRESH, thresh=wl["tau"], D_prev=state["D"])
-        t0 = mark("graph", t0)
-        parts = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=wl["ncell"], site_struct=st)
+            if state["D"] is None:
+                G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_H2_THRESH, thresh=wl["thresh"])
+            else:
+                G = gbe.build_graph(ctx, Hg.csr(), gbe.GRAPH_D_THRESH, thresh=wl["tau"], D_prev=state["D"])
+            t0 = mark("graph", t0)
+            parts = gbe.partition(ctx, G, gbe.PART_SPATIAL_CELLS, ncell=wl["ncell"], site_struct=st)
         P, total, max_m = parts.info()
         t0 = mark("partition", t0)
         X = gbe.subs_create(ctx, parts, PREC)
         col = torch.empty((N, max_m), dtype=torch.int32, device="cuda")
         val = torch.empty((N, max_m), dtype=torch.float64, device="cuda")
         t0 = mark("sp2_state", t0)
-        prm = gbe.sp2_params(N / 2.0, prec=PREC, n_max=64, n_min=10, idem_tol=1e-10, seq=state["seq"],
-                             fp64_tail=args.fp64_tail)
+        if gap_mode and state["gap"] is not None and not free:
+            # the sequence that converges the estimated gap on this step's spectral bounds
+            gbe.gershgorin_noalloc(ctx, Hg.csr(), bounds)
+            eps = tuple(bounds.cpu().tolist())
+            seq = gbe.sp2_sequence(eps, state["gap"][0], state["gap"][1], wl["seq_tol"])
+            prm = gbe.sp2_params(N / 2.0, prec=PREC, n_max=len(seq), seq=seq, eps=eps)
+            used_gap = True
+        else:
+            seq = None if (gap_mode or free) else state["seq"]
+            prm = gbe.sp2_params(N / 2.0, prec=PREC, n_max=64, n_min=10, idem_tol=1e-10, seq=seq,
+                                 fp64_tail=args.fp64_tail)
+            used_gap = False
         if not timed and "tune" not in last:
             # first warm-up step: tune once; later states of the same shape start with the choice
             last["tune"] = configure(args, gbe, ctx, Hg.csr(), parts, prm, X)
@@ -415,11 +443,19 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
         t0 = mark("sp2", t0)
         gbe.assemble_D(ctx, X, parts, col, val)
         mark("assemble", t0)
-        if state["seq"] is None:
+        if free:
+            return col, val
+        if gap_mode:
+            try:
+                state["gap"] = gbe.sp2_gap_estimate(rep, N / 2.0, *wl["gap_window"])
+            except gbe.GbeError:
+                state["gap_missed"] += int(timed)   # no step in the window: keep the last estimate
+            state["gap_steps"] += int(timed and used_gap)
+        elif state["seq"] is None:
             state["seq"] = rep["seq"]
         state["D"] = gbe.ell_struct(col, val)
         cc, sptr, _ = parts.export()
-        last.update(rep=rep, ms=np.diff(sptr), P=P, cc=cc)
+        last.update(rep=rep, ms=np.diff(sptr), P=P, cc=cc, col=col, val=val, t=t)
 
     W = max(args.warmup, 3)
     for t in range(W):
@@ -442,6 +478,13 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
     step(W + args.steps, False)
     ctx.set_profiling(False)
     rep, ms = last["rep"], last["ms"]
+    gap_check = None
+    if gap_mode:
+        # the same positions once more, free running (global traces): the D it converges to
+        # against the one the gap-derived sequence gave
+        col_f, val_f = step(last["t"], False, free=True)
+        gap_check = {"max_abs_dD_vs_free_running": float((val_f - last["val"]).abs().max().item()),
+                     "same_pattern": bool(torch.equal(col_f, last["col"]))}
     peaks, peak_kind = load_peaks()
     tc_ms = rep["ms_tc"] / max(1, rep["n_tc"])
     mixed = max(1, rep["iters"] - rep["fp64_iters"])
@@ -453,8 +496,10 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
         "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": dtype_name, "data": "synthetic",
         "config": {"workload": args.workload, "N": N, "L": wl["L"], "md_steps_timed": args.steps,
-                   "graph": "first step |H^2|>=%g, then |D_prev|>=%g" % (wl["thresh"], wl["tau"]),
-                   "branch": "previous step's sequence replayed", "sp2_iters": rep["iters"],
+                   "graph": ("complete (one subgraph of every site)" if full is not None else
+                             "first step |H^2|>=%g, then |D_prev|>=%g" % (wl["thresh"], wl["tau"])),
+                   "branch": ("sequence from the previous step's HOMO-LUMO gap estimate (first step free running)"
+                              if gap_mode else "previous step's sequence replayed"), "sp2_iters": rep["iters"],
                    "precision": prec_name, "fp64_tail": args.fp64_tail, "cores": int(last["P"]),
                    "m_s_min": int(ms.min()), "m_s_median": float(np.median(ms)), "m_s_max": int(ms.max()),
                    "l2": "inputs larger than L2 (GB-scale split planes); no flush",
@@ -462,6 +507,10 @@ def run_qmd(args, wl, gbe, torch, dist, ctx, local, rank, world):
                              "CUDA graphs, assembly), positions copied in from pinned host memory each step; "
                              "roofline from one further step launched step by step with CUDA events"},
         "phase_ms_per_step": {k: 1000.0 * v / args.steps for k, v in phase.items()},
+        "gap_sequence": None if not gap_mode else {
+            "timed_steps_on_a_gap_sequence": state["gap_steps"], "timed_steps_without_estimate": state["gap_missed"],
+            "last_gap_estimate_eV": list(state["gap"]) if state["gap"] else None, "window": list(wl["gap_window"]),
+            "tol": wl["seq_tol"], **(gap_check or {})},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak if achieved else None, "traffic": None,
                      "kernel": "sp2_square_tc_kernel<%s>" % prec_name,
@@ -854,7 +903,7 @@ def main():
     args = parse_args()
     disordered = WORKLOADS[args.workload]["kind"] == "disordered" and not WORKLOADS[args.workload].get("mlp")
     if args.prec is None:
-        args.prec = "fp64tc" if disordered else "fp16x6"
+        args.prec = WORKLOADS[args.workload].get("prec") or ("fp64tc" if disordered else "fp16x6")
     if args.fp64_steps is None:
         args.fp64_steps = 1 if disordered else 3
     if args.record_traffic:

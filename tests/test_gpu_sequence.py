@@ -22,7 +22,7 @@ from oracle import exact, sp2
 
 pytestmark = pytest.mark.gpu
 
-from tests.gpu_helpers import assembled_dense, device_csr, gbe, import_parts, lattice_case, oracle_graph_sp2  # noqa: E402
+from tests.gpu_helpers import assembled_dense, device_csr, gbe, import_parts, lattice_case, oracle_graph_sp2, torch  # noqa: E402
 
 E_LO, E_HI, TOL_SEQ = 1e-8, 1e-3, 1e-12
 
@@ -82,3 +82,45 @@ def test_replayed_gap_sequence(ctx, case, prec, tol):
     err_or = np.abs(D2 - Dref).max()
     print(f"prec {prec}: {len(seq)} steps, complete graph vs eigh {err_ex:.3e}, |H^2| graph vs oracle {err_or:.3e}")
     assert err_ex <= tol and err_or <= tol
+
+
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP64TC])
+def test_gap_from_previous_md_step(ctx, prec):
+    """Sec. II.C's MD use: the gap estimated from one step's run fixes the next step's
+    sequence.  The 8^3 lattice on its complete graph at t = 0 (free running), then the
+    positions advanced by one step of seeded velocities: the sequence from the t = 0 estimate
+    on the t = 1 Gershgorin bounds (from gbe_gershgorin_noalloc, passed to the run) gives D
+    within 1e-10 of exact diagonalisation at t = 1, and the t = 1 run's own traces give the
+    next estimate.  The estimate reads idempotency errors in [1e-6, 1e-2], above the
+    FP64-grade tensor-core path's floor."""
+    import synth
+    from oracle import hamiltonian
+    w = synth.lattice(8, seed=0)
+    N = w["pos"].shape[0]
+    vel = synth.velocities(N, seed=1)
+    full = import_parts(ctx, N, [np.arange(N)], np.array([N]))
+
+    def system(t):
+        pos = synth.advance(w["pos"], vel, w["box"], t)
+        return pos, hamiltonian.build_h(pos, w["box"], w["onsite"])
+
+    _, H0 = system(0)
+    _, rep0 = gbe.sp2_submatrices(ctx, device_csr(H0), full,
+                                  gbe.sp2_params(N // 2, prec=prec, idem_tol=1e-11, n_max=80))
+    gap = gbe.sp2_gap_estimate(rep0, N // 2, 1e-6, 1e-2)
+    pos1, H1 = system(1)
+    Hd = device_csr(H1)
+    bounds = torch.empty(2, dtype=torch.float64, device="cuda")
+    gbe.gershgorin_noalloc(ctx, Hd, bounds)
+    eps = tuple(bounds.cpu().tolist())
+    np.testing.assert_allclose(eps, sp2.gershgorin(H1), rtol=0, atol=1e-12)
+    seq = gbe.sp2_sequence(eps, gap[0], gap[1], TOL_SEQ)
+    X, rep1 = gbe.sp2_submatrices(ctx, Hd, full, gbe.sp2_params(N // 2, prec=prec, seq=seq, eps=eps,
+                                                               n_max=len(seq)))
+    assert rep1["iters"] == len(seq) and rep1["eps"] == eps
+    D1, _, _ = assembled_dense(ctx, X, full, N)
+    Dex, ev = exact.density_matrix(H1, N // 2)
+    assert ev[N // 2 - 1] <= gap[0] < gap[1] <= ev[N // 2]
+    assert np.abs(D1 - Dex).max() < 1e-10
+    homo, lumo = gbe.sp2_gap_estimate(rep1, N // 2, 1e-6, 1e-2)
+    assert ev[N // 2 - 1] <= homo < lumo <= ev[N // 2]
