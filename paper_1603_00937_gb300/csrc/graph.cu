@@ -342,6 +342,124 @@ __global__ void __launch_bounds__(256) rowset_kernel(int mode, int64_t n, const 
     }
 }
 
+// Rows of |(H^2)_ij| >= thresh (rowset_kernel's mode 0) by accumulation instead of one merge
+// per candidate: a warp per row i sums (H^2)_il = sum_k H_ik H_kl into a shared-memory hash
+// table keyed by l, taking k in ascending order (one row k at a time, its entries across the
+// lanes: a row's columns are distinct, so each slot has one writer per k).  That is the same
+// sequence of products and additions as row_dot's ordered merge of rows i and l, so the kept
+// set is the same.  The kept columns (i itself always) are compacted in slot order, sorted in
+// the warp, and written as rowset_kernel's passes 1 and 2 write them.  A row of H^2 with more
+// distinct columns than the table holds sets overflow[2] (the host then builds the graph with
+// rowset_kernel).
+constexpr int kH2RowSlots = 1024;
+constexpr int kH2RowWarps = 4;
+constexpr size_t kH2RowSmem = (size_t)kH2RowWarps * kH2RowSlots * (4 + 8);
+
+__device__ __forceinline__ unsigned h2row_hash(int l) { return ((unsigned)l * 2654435761u) >> 22; }   // 10 bits
+
+__global__ void __launch_bounds__(32 * kH2RowWarps) h2_rowset_kernel(int64_t n, const int64_t* __restrict__ hrp,
+                                                                     const int32_t* __restrict__ hci,
+                                                                     const double* __restrict__ hva, double thresh,
+                                                                     int pass, int32_t* cnt,
+                                                                     const int64_t* __restrict__ outrp, int32_t* outci,
+                                                                     int* overflow, int stage_cap) {
+    extern __shared__ unsigned char h2rsm[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * kH2RowWarps + w;
+    if (row >= n) return;   // whole warps only: nothing below synchronises the block
+    const int i = (int)row;
+    int* keys = reinterpret_cast<int*>(h2rsm) + w * kH2RowSlots;
+    double* vals = reinterpret_cast<double*>(h2rsm + (size_t)kH2RowWarps * kH2RowSlots * 4) + w * kH2RowSlots;
+    for (int t = lane; t < kH2RowSlots; t += 32) {
+        keys[t] = -1;
+        vals[t] = 0.0;
+    }
+    __syncwarp();
+    bool ok = true;
+    // row i's entries 32 at a time, each lane holding one k with its H_ik and the range of row
+    // k (loaded together), then taken in ascending order across the warp
+    const int64_t p0 = hrp[i], p1 = hrp[i + 1];
+    for (int64_t pb = p0; pb < p1; pb += 32) {
+        const int64_t pl = pb + lane;
+        int kl = 0;
+        double hl = 0.0;
+        int64_t ql0 = 0, ql1 = 0;
+        if (pl < p1) {
+            kl = hci[pl];
+            hl = hva[pl];
+            ql0 = hrp[kl];
+            ql1 = hrp[kl + 1];
+        }
+        const int nk = (p1 - pb) < 32 ? (int)(p1 - pb) : 32;
+        for (int u = 0; u < nk; ++u) {
+            const double hik = __shfl_sync(0xffffffffu, hl, u);
+            const int64_t q0 = __shfl_sync(0xffffffffu, ql0, u), q1 = __shfl_sync(0xffffffffu, ql1, u);
+            for (int64_t q = q0 + lane; q < q1; q += 32) {
+                const int l = hci[q];
+                unsigned h = h2row_hash(l);
+                int probes = 0;
+                while (true) {
+                    const int old = atomicCAS(&keys[h], -1, l);
+                    if (old == -1 || old == l) break;
+                    if (++probes == kH2RowSlots) break;
+                    h = (h + 1) & (kH2RowSlots - 1);
+                }
+                if (probes < kH2RowSlots) vals[h] = __dadd_rn(vals[h], __dmul_rn(hik, hva[q]));
+                else ok = false;
+            }
+            __syncwarp();
+        }
+    }
+    if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicExch(overflow + 2, 1);
+        return;
+    }
+    // kept columns to keys[0..m) in slot order (a chunk's slots are read before any is written)
+    int m = 0;
+    for (int t0 = 0; t0 < kH2RowSlots; t0 += 32) {
+        const int key = keys[t0 + lane];
+        const bool keep = key >= 0 && (key == i || fabs(vals[t0 + lane]) >= thresh);
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) keys[m + __popc(bal & ((1u << lane) - 1u))] = key;
+        m += __popc(bal);
+        __syncwarp();
+    }
+    // bitonic sort of keys[0..m) within the warp (padded to a power of two)
+    int size = 1;
+    while (size < m) size <<= 1;
+    for (int t = m + lane; t < size; t += 32) keys[t] = INT32_MAX;
+    __syncwarp();
+    for (int kk = 2; kk <= size; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int t = lane; t < size; t += 32) {
+                const int l = t ^ j;
+                if (l > t) {
+                    const bool up = ((t & kk) == 0);
+                    const int x = keys[t], y = keys[l];
+                    if ((x > y) == up) { keys[t] = y; keys[l] = x; }
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (pass == 0) {
+        if (lane == 0) cnt[i] = m;
+    } else if (pass == 2) {
+        if (lane == 0) {
+            cnt[i] = m;
+            if (m > stage_cap) atomicExch(overflow + 1, 1);
+        }
+        if (m <= stage_cap) {
+            const int64_t base = (int64_t)i * stage_cap;
+            for (int t = lane; t < m; t += 32) outci[base + t] = keys[t];
+        }
+    } else {
+        const int64_t base = outrp[i];
+        for (int t = lane; t < m; t += 32) outci[base + t] = keys[t];
+    }
+}
+
 // Staged rows (stage_cap apart) -> CSR column indices, one warp per row.
 __global__ void compact_set_rows_kernel(const int32_t* __restrict__ stage, int64_t n, int stage_cap,
                                         const int64_t* __restrict__ rp, int32_t* ci) {
@@ -474,8 +592,10 @@ int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thres
                int hops, int64_t** rp_out, int32_t** ci_out, int64_t* nnz_out) {
     DevBuf cnt, flag, stage;
     GBE_TRY(gbe_alloc(&cnt.p, n * 4));
-    GBE_TRY(gbe_alloc(&flag.p, 8));   // [0] a row above kSetMax, [1] a row above the staging slot
-    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 8, ctx->stream));
+    // [0] a row above kSetMax, [1] a row above the staging slot, [2] a row of H^2 above the
+    // accumulation table of h2_rowset_kernel
+    GBE_TRY(gbe_alloc(&flag.p, 12));
+    GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 12, ctx->stream));
     // one set construction per row into staging slots (at most 64 Mi entries in all), then a
     // compaction; a row longer than its slot falls back to a second construction pass
     const int stage_cap = (int)std::min<int64_t>(kSetMax, std::max<int64_t>(128, ((int64_t)64 << 20) / n));
@@ -486,9 +606,31 @@ int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thres
     const int64_t* hrp = H ? H->rowptr : nullptr;
     const int32_t* hci = H ? H->col : nullptr;
     const double* hva = H ? H->val : nullptr;
-    rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp, s3ci,
-                                                  hops, 2, cnt.as<int32_t>(), nullptr, stage.as<int32_t>(), flag.as<int>(),
-                                                  stage_cap);
+    // mode 0 by accumulation (a warp per row), unless a row of H^2 overflows its table
+    bool h2acc = mode == 0;
+    auto launch = [&](int pass, const int64_t* outrp, int32_t* outci) {
+        if (h2acc)
+            h2_rowset_kernel<<<(unsigned)((n + kH2RowWarps - 1) / kH2RowWarps), 32 * kH2RowWarps, kH2RowSmem,
+                               ctx->stream>>>(n, hrp, hci, hva, thresh, pass, cnt.as<int32_t>(), outrp, outci,
+                                              flag.as<int>(), stage_cap);
+        else
+            rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp,
+                                                          s3ci, hops, pass, cnt.as<int32_t>(), outrp, outci,
+                                                          flag.as<int>(), stage_cap);
+    };
+    if (h2acc) {
+        GBE_CUDA_TRY(cudaFuncSetAttribute(h2_rowset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kH2RowSmem));
+        launch(2, nullptr, stage.as<int32_t>());
+        int ovf2 = 0;
+        GBE_CUDA_TRY(cudaGetLastError());
+        GBE_CUDA_TRY(cudaMemcpyAsync(&ovf2, flag.as<int>() + 2, 4, cudaMemcpyDeviceToHost, ctx->stream));
+        GBE_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        if (ovf2) {
+            h2acc = false;
+            GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 12, ctx->stream));
+        }
+    }
+    if (!h2acc) launch(2, nullptr, stage.as<int32_t>());
     GBE_CUDA_TRY(cudaGetLastError());
     int64_t* rp = nullptr;
     GBE_TRY(gbe_alloc((void**)&rp, (n + 1) * 8));
@@ -514,8 +656,7 @@ int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thres
         compact_set_rows_kernel<<<(unsigned)((n + 7) / 8), 256, 0, ctx->stream>>>(stage.as<int32_t>(), n, stage_cap, rp,
                                                                                 ci);
     else
-        rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp,
-                                                      s3ci, hops, 1, cnt.as<int32_t>(), rp, ci, flag.as<int>(), stage_cap);
+        launch(1, rp, ci);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
