@@ -168,24 +168,50 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
         if (g.nc[d] >= 3) { lo[d] = -1; hi[d] = 1; }
         else { lo[d] = -cc[d]; hi[d] = g.nc[d] - 1 - cc[d]; }
     }
-    for (int dx = lo[0]; dx <= hi[0]; ++dx)
-        for (int dy = lo[1]; dy <= hi[1]; ++dy)
-            for (int dz = lo[2]; dz <= hi[2]; ++dz) {
-                const int ax = (cc[0] + dx + g.nc[0]) % g.nc[0];
-                const int ay = (cc[1] + dy + g.nc[1]) % g.nc[1];
-                const int az = (cc[2] + dz + g.nc[2]) % g.nc[2];
-                const int cell = (ax * g.nc[1] + ay) * g.nc[2] + az;
-                for (int64_t p = cstart[cell] + lane; p < cstart[cell + 1]; p += 32) {
-                    const int j = members[p];
-                    // FP32 pre-filter, then r^2 < rcut^2 in FP64 (differs from r < rcut only within
-                    // an ulp of the cutoff)
-                    if (j == i || (near_f32(pi, pos4[j], bx, by, bz, ix, iy, iz, lim2) &&
-                                   pair_dist2(pos, xi, yi, zi, j, g) < mdl.rcut2)) {
-                        const int k = atomicAdd(&bcount[w], 1);
-                        if (k < kRowCap) buf[w][k] = j;
-                    }
-                }
+    // The (at most 27) neighbour cells' member ranges, one per lane, and their exclusive prefix
+    // sums: the candidates of all cells are then one flat range across the lanes, whose loads
+    // do not wait on one another (the row is sorted afterwards, so the order found is free).
+    const int ncx = hi[0] - lo[0] + 1, ncy = hi[1] - lo[1] + 1, ncz = hi[2] - lo[2] + 1;
+    const int ncell = ncx * ncy * ncz;
+    int64_t c0 = 0;
+    int clen = 0;
+    if (lane < ncell) {
+        const int dx = lo[0] + lane / (ncy * ncz), dy = lo[1] + (lane / ncz) % ncy, dz = lo[2] + lane % ncz;
+        const int ax = (cc[0] + dx + g.nc[0]) % g.nc[0];
+        const int ay = (cc[1] + dy + g.nc[1]) % g.nc[1];
+        const int az = (cc[2] + dz + g.nc[2]) % g.nc[2];
+        const int cell = (ax * g.nc[1] + ay) * g.nc[2] + az;
+        c0 = cstart[cell];
+        clen = (int)(cstart[cell + 1] - c0);
+    }
+    int incl = clen;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - clen;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    // (every lane runs every iteration: the shuffles need the whole warp)
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        // the candidate's cell: the last one whose range starts at or before t
+        int c = 0;
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(0xffffffffu, excl, (c + step) & 31);
+            if (c + step < ncell && e <= t) c += step;
+        }
+        const int64_t p = __shfl_sync(0xffffffffu, c0, c) + (t - __shfl_sync(0xffffffffu, excl, c));
+        if (t < total) {
+            const int j = members[p];
+            // FP32 pre-filter, then r^2 < rcut^2 in FP64 (differs from r < rcut only within an ulp
+            // of the cutoff)
+            if (j == i ||
+                (near_f32(pi, pos4[j], bx, by, bz, ix, iy, iz, lim2) && pair_dist2(pos, xi, yi, zi, j, g) < mdl.rcut2)) {
+                const int k = atomicAdd(&bcount[w], 1);
+                if (k < kRowCap) buf[w][k] = j;
             }
+        }
+    }
     __syncwarp();
     const int m = bcount[w];
     if (m > kRowCap) {
@@ -342,27 +368,45 @@ __global__ void __launch_bounds__(256) rowset_kernel(int mode, int64_t n, const 
     }
 }
 
-// Rows of |(H^2)_ij| >= thresh (rowset_kernel's mode 0) by accumulation instead of one merge
-// per candidate: a warp per row i sums (H^2)_il = sum_k H_ik H_kl into a shared-memory hash
-// table keyed by l, taking k in ascending order (one row k at a time, its entries across the
-// lanes: a row's columns are distinct, so each slot has one writer per k).  That is the same
-// sequence of products and additions as row_dot's ordered merge of rows i and l, so the kept
-// set is the same.  The kept columns (i itself always) are compacted in slot order, sorted in
-// the warp, and written as rowset_kernel's passes 1 and 2 write them.  A row of H^2 with more
-// distinct columns than the table holds sets overflow[2] (the host then builds the graph with
-// rowset_kernel).
+// A warp per row, for rowset_kernel's modes 0 and 1 on rows that fit a warp's table.
+// MODE 0, rows of |(H^2)_ij| >= thresh by accumulation instead of one merge per candidate:
+// the warp sums (H^2)_il = sum_k H_ik H_kl into a shared-memory hash table keyed by l, taking k
+// in ascending order (one row k at a time, its entries across the lanes: a row's columns are
+// distinct, so each slot has one writer per k).  That is the same sequence of products and
+// additions as row_dot's ordered merge of rows i and l, so the kept set is the same.
+// MODE 1, the union of row i of up to three CSR lists and i itself.
+// The kept columns (i itself always) are compacted in slot order, sorted in the warp, and
+// written as rowset_kernel's passes 1 and 2 write them.  A row with more distinct columns than
+// the table holds sets overflow[2] (the host then builds the graph with rowset_kernel).
 constexpr int kH2RowSlots = 1024;
 constexpr int kH2RowWarps = 4;
 constexpr size_t kH2RowSmem = (size_t)kH2RowWarps * kH2RowSlots * (4 + 8);
 
 __device__ __forceinline__ unsigned h2row_hash(int l) { return ((unsigned)l * 2654435761u) >> 22; }   // 10 bits
 
-__global__ void __launch_bounds__(32 * kH2RowWarps) h2_rowset_kernel(int64_t n, const int64_t* __restrict__ hrp,
-                                                                     const int32_t* __restrict__ hci,
-                                                                     const double* __restrict__ hva, double thresh,
-                                                                     int pass, int32_t* cnt,
-                                                                     const int64_t* __restrict__ outrp, int32_t* outci,
-                                                                     int* overflow, int stage_cap) {
+// Insert l into a warp's hash table; the slot, or -1 when the table is full.
+__device__ __forceinline__ int h2row_insert(int* keys, int l) {
+    unsigned h = h2row_hash(l);
+    for (int probes = 0; probes < kH2RowSlots; ++probes) {
+        const int old = atomicCAS(&keys[h], -1, l);
+        if (old == -1 || old == l) return (int)h;
+        h = (h + 1) & (kH2RowSlots - 1);
+    }
+    return -1;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * kH2RowWarps) warp_rowset_kernel(int64_t n, const int64_t* __restrict__ hrp,
+                                                                       const int32_t* __restrict__ hci,
+                                                                       const double* __restrict__ hva, double thresh,
+                                                                       const int64_t* __restrict__ s1rp,
+                                                                       const int32_t* __restrict__ s1ci,
+                                                                       const int64_t* __restrict__ s2rp,
+                                                                       const int32_t* __restrict__ s2ci,
+                                                                       const int64_t* __restrict__ s3rp,
+                                                                       const int32_t* __restrict__ s3ci, int pass,
+                                                                       int32_t* cnt, const int64_t* __restrict__ outrp,
+                                                                       int32_t* outci, int* overflow, int stage_cap) {
     extern __shared__ unsigned char h2rsm[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t row = (int64_t)blockIdx.x * kH2RowWarps + w;
@@ -376,39 +420,43 @@ __global__ void __launch_bounds__(32 * kH2RowWarps) h2_rowset_kernel(int64_t n, 
     }
     __syncwarp();
     bool ok = true;
-    // row i's entries 32 at a time, each lane holding one k with its H_ik and the range of row
-    // k (loaded together), then taken in ascending order across the warp
-    const int64_t p0 = hrp[i], p1 = hrp[i + 1];
-    for (int64_t pb = p0; pb < p1; pb += 32) {
-        const int64_t pl = pb + lane;
-        int kl = 0;
-        double hl = 0.0;
-        int64_t ql0 = 0, ql1 = 0;
-        if (pl < p1) {
-            kl = hci[pl];
-            hl = hva[pl];
-            ql0 = hrp[kl];
-            ql1 = hrp[kl + 1];
-        }
-        const int nk = (p1 - pb) < 32 ? (int)(p1 - pb) : 32;
-        for (int u = 0; u < nk; ++u) {
-            const double hik = __shfl_sync(0xffffffffu, hl, u);
-            const int64_t q0 = __shfl_sync(0xffffffffu, ql0, u), q1 = __shfl_sync(0xffffffffu, ql1, u);
-            for (int64_t q = q0 + lane; q < q1; q += 32) {
-                const int l = hci[q];
-                unsigned h = h2row_hash(l);
-                int probes = 0;
-                while (true) {
-                    const int old = atomicCAS(&keys[h], -1, l);
-                    if (old == -1 || old == l) break;
-                    if (++probes == kH2RowSlots) break;
-                    h = (h + 1) & (kH2RowSlots - 1);
-                }
-                if (probes < kH2RowSlots) vals[h] = __dadd_rn(vals[h], __dmul_rn(hik, hva[q]));
-                else ok = false;
+    if constexpr (MODE == 0) {
+        // row i's entries 32 at a time, each lane holding one k with its H_ik and the range of
+        // row k (loaded together), then taken in ascending order across the warp
+        const int64_t p0 = hrp[i], p1 = hrp[i + 1];
+        for (int64_t pb = p0; pb < p1; pb += 32) {
+            const int64_t pl = pb + lane;
+            double hl = 0.0;
+            int64_t ql0 = 0, ql1 = 0;
+            if (pl < p1) {
+                const int kl = hci[pl];
+                hl = hva[pl];
+                ql0 = hrp[kl];
+                ql1 = hrp[kl + 1];
             }
-            __syncwarp();
+            const int nk = (p1 - pb) < 32 ? (int)(p1 - pb) : 32;
+            for (int u = 0; u < nk; ++u) {
+                const double hik = __shfl_sync(0xffffffffu, hl, u);
+                const int64_t q0 = __shfl_sync(0xffffffffu, ql0, u), q1 = __shfl_sync(0xffffffffu, ql1, u);
+                for (int64_t q = q0 + lane; q < q1; q += 32) {
+                    const int h = h2row_insert(keys, hci[q]);
+                    if (h >= 0) vals[h] = __dadd_rn(vals[h], __dmul_rn(hik, hva[q]));
+                    else ok = false;
+                }
+                __syncwarp();
+            }
         }
+    } else {
+        if (lane == 0 && h2row_insert(keys, i) < 0) ok = false;
+        const int64_t* rps[3] = {s1rp, s2rp, s3rp};
+        const int32_t* cis[3] = {s1ci, s2ci, s3ci};
+#pragma unroll
+        for (int src = 0; src < 3; ++src) {
+            if (!rps[src]) continue;
+            for (int64_t q = rps[src][i] + lane; q < rps[src][i + 1]; q += 32)
+                if (h2row_insert(keys, cis[src][q]) < 0) ok = false;
+        }
+        __syncwarp();
     }
     if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) atomicExch(overflow + 2, 1);
@@ -418,7 +466,7 @@ __global__ void __launch_bounds__(32 * kH2RowWarps) h2_rowset_kernel(int64_t n, 
     int m = 0;
     for (int t0 = 0; t0 < kH2RowSlots; t0 += 32) {
         const int key = keys[t0 + lane];
-        const bool keep = key >= 0 && (key == i || fabs(vals[t0 + lane]) >= thresh);
+        const bool keep = key >= 0 && (MODE == 1 || key == i || fabs(vals[t0 + lane]) >= thresh);
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
         if (keep) keys[m + __popc(bal & ((1u << lane) - 1u))] = key;
@@ -593,7 +641,7 @@ int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thres
     DevBuf cnt, flag, stage;
     GBE_TRY(gbe_alloc(&cnt.p, n * 4));
     // [0] a row above kSetMax, [1] a row above the staging slot, [2] a row of H^2 above the
-    // accumulation table of h2_rowset_kernel
+    // warp table of warp_rowset_kernel
     GBE_TRY(gbe_alloc(&flag.p, 12));
     GBE_CUDA_TRY(cudaMemsetAsync(flag.p, 0, 12, ctx->stream));
     // one set construction per row into staging slots (at most 64 Mi entries in all), then a
@@ -606,20 +654,26 @@ int rowset_csr(gbe_ctx* ctx, int mode, int64_t n, const gbe_csr* H, double thres
     const int64_t* hrp = H ? H->rowptr : nullptr;
     const int32_t* hci = H ? H->col : nullptr;
     const double* hva = H ? H->val : nullptr;
-    // mode 0 by accumulation (a warp per row), unless a row of H^2 overflows its table
-    bool h2acc = mode == 0;
+    // modes 0 and 1 a warp per row, unless a row overflows the warp's table
+    bool h2acc = mode == 0 || mode == 1;
     auto launch = [&](int pass, const int64_t* outrp, int32_t* outci) {
-        if (h2acc)
-            h2_rowset_kernel<<<(unsigned)((n + kH2RowWarps - 1) / kH2RowWarps), 32 * kH2RowWarps, kH2RowSmem,
-                               ctx->stream>>>(n, hrp, hci, hva, thresh, pass, cnt.as<int32_t>(), outrp, outci,
-                                              flag.as<int>(), stage_cap);
+        const unsigned wb = (unsigned)((n + kH2RowWarps - 1) / kH2RowWarps);
+        if (h2acc && mode == 0)
+            warp_rowset_kernel<0><<<wb, 32 * kH2RowWarps, kH2RowSmem, ctx->stream>>>(
+                n, hrp, hci, hva, thresh, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, pass, cnt.as<int32_t>(),
+                outrp, outci, flag.as<int>(), stage_cap);
+        else if (h2acc)
+            warp_rowset_kernel<1><<<wb, 32 * kH2RowWarps, kH2RowSmem, ctx->stream>>>(
+                n, nullptr, nullptr, nullptr, 0.0, s1rp, s1ci, s2rp, s2ci, s3rp, s3ci, pass, cnt.as<int32_t>(), outrp,
+                outci, flag.as<int>(), stage_cap);
         else
             rowset_kernel<<<grid, 256, sm, ctx->stream>>>(mode, n, hrp, hci, hva, thresh, s1rp, s1ci, s2rp, s2ci, s3rp,
                                                           s3ci, hops, pass, cnt.as<int32_t>(), outrp, outci,
                                                           flag.as<int>(), stage_cap);
     };
     if (h2acc) {
-        GBE_CUDA_TRY(cudaFuncSetAttribute(h2_rowset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kH2RowSmem));
+        GBE_CUDA_TRY(cudaFuncSetAttribute(warp_rowset_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kH2RowSmem));
+        GBE_CUDA_TRY(cudaFuncSetAttribute(warp_rowset_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kH2RowSmem));
         launch(2, nullptr, stage.as<int32_t>());
         int ovf2 = 0;
         GBE_CUDA_TRY(cudaGetLastError());
