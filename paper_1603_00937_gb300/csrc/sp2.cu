@@ -1067,13 +1067,13 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     if (X->n_items_64_full)
         cudaMemcpyAsync(X->d_items_64_full, ft_64.data(), ft_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
     for (int k = 0; k < 3; ++k) cudaMemcpyAsync(X->d_ranges[k], rg[k].data(), X->P * sizeof(int2), cudaMemcpyHostToDevice, st);
-    // Both sides of the split planes start at zero: the gather writes every stored (upper)
-    // block of side 0, padding included, but a squaring leaves the columns of a subgraph's
-    // last block past the next multiple of 16 above m unwritten, and they must read as zero.
-    for (int i = 0; i < 2; ++i) {
-        if (X->f64[i]) cudaMemsetAsync(X->f64[i], 0, total * 8, st);
-        if (X->planes[i]) cudaMemsetAsync(X->planes[i], 0, (size_t)gbe_subs_planes(prec) * total * 2, st);
-    }
+    // Side 1 starts at zero: a squaring leaves the columns of a subgraph's last block past the
+    // next multiple of 16 above m unwritten, and they must read as zero.  Side 0 needs no
+    // clear: every SP2 run starts with the gather, which writes every stored (upper) block of
+    // side 0, padding included (the FP64 iterate in full); lower blocks are never read.  A
+    // Chebyshev expansion clears its sides itself.
+    if (X->f64[1]) cudaMemsetAsync(X->f64[1], 0, total * 8, st);
+    if (X->planes[1]) cudaMemsetAsync(X->planes[1], 0, (size_t)gbe_subs_planes(prec) * total * 2, st);
     GBE_CUDA_TRY(cudaStreamSynchronize(st));
     if (prec != GBE_PREC_FP64) {
         r = gbe_tc_make_tmaps(X);
