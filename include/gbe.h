@@ -357,6 +357,19 @@ int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gb
  * the Sec. II.A recursion, timings, flops). */
 int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_report* rep);
 
+/* Replayed SP2 of a partition whose iterates need not fit the device together, and its D.
+ * With a pre-determined branch sequence (Sec. II.C) no trace is shared between subgraphs,
+ * and their expansions are independent (Sec. II.A, after Eq. 6), so they may run one batch
+ * after another: the subgraphs are dealt to the fewest batches whose two ping-pong iterates
+ * take at most budget_bytes each (gbe_shard_assign over the batches, largest m_s^3 first),
+ * and each batch is created, runs gbe_sp2_run with `params` and writes the columns of its
+ * own cores into D (Eq. 6) before it is freed.  D is as gbe_assemble_D fills it (device or
+ * host ELL, width >= max m_s); *batches (nullable) receives the number of batches.  H must
+ * be device CSR.  GBE_EINVAL unless params is in replay mode without an exchange;
+ * GBE_ECAPACITY when one subgraph's iterates alone exceed the budget.  Synchronises. */
+int gbe_sp2_replay_batched(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* params,
+                           int64_t budget_bytes, double drop_tol, gbe_ell* D, int* batches);
+
 /* gbe_sp2_run + gbe_sp2_report_get (Sec. II.A, Eq. 6).  *X NULL: allocate a new state; otherwise reuse it
  * (it must come from the same partition and precision).  H may be host CSR (copied in).
  * Returns GBE_ENOCONV when the run stopped at n_max, GBE_ENUMERIC / GBE_ETIMEOUT when

@@ -53,7 +53,7 @@ EXPORTS = [
     "gbe_last_error_message", "gbe_build_hamiltonian", "gbe_hamiltonian_csr", "gbe_free_hamiltonian",
     "gbe_build_graph", "gbe_graph_size", "gbe_graph_export", "gbe_free_graph", "gbe_partition",
     "gbe_parts_info", "gbe_parts_export", "gbe_parts_import", "gbe_free_parts", "gbe_subs_create",
-    "gbe_free_subs", "gbe_sp2_run", "gbe_sp2_report_get", "gbe_sp2_submatrices", "gbe_assemble_D",
+    "gbe_free_subs", "gbe_sp2_run", "gbe_sp2_report_get", "gbe_sp2_replay_batched", "gbe_sp2_submatrices", "gbe_assemble_D",
     "gbe_subs_export", "gbe_gershgorin_noalloc", "gbe_pairs_build", "gbe_pairs_info", "gbe_pairs_export", "gbe_pairs_device",
     "gbe_free_pairs", "gbe_mlp_create", "gbe_mlp_param_count", "gbe_mlp_set_params", "gbe_mlp_get_params",
     "gbe_mlp_forward", "gbe_mlp_gradient", "gbe_mlp_adam_step", "gbe_mlp_train", "gbe_mlp_labels", "gbe_free_mlp",
@@ -174,6 +174,7 @@ def load_library(path=LIB_PATH):
         "gbe_subs_create": (I32, [P, P, I32, P]), "gbe_free_subs": (I32, [P]),
         "gbe_sp2_run": (I32, [P, P, P, P, P]), "gbe_sp2_report_get": (I32, [P, P, P]),
         "gbe_sp2_submatrices": (I32, [P, P, P, P, P, P]), "gbe_assemble_D": (I32, [P, P, P, D, P]),
+        "gbe_sp2_replay_batched": (I32, [P, P, P, P, ctypes.c_int64, D, P, P]),
         "gbe_subs_export": (I32, [P, P, I64, P]), "gbe_gershgorin_noalloc": (I32, [P, P, P]),
         "gbe_pairs_build": (I32, [P, P, P, D, P]), "gbe_pairs_info": (I32, [P, P, P]),
         "gbe_pairs_export": (I32, [P, P, P, P, P]), "gbe_free_pairs": (I32, [P]),
@@ -499,6 +500,18 @@ def subs_create(ctx, parts, prec):
 def sp2_run(ctx, H, parts, params, X):
     check(load_library().gbe_sp2_run(ctx.handle, ctypes.byref(H), parts.handle, ctypes.byref(params), X.handle),
           "gbe_sp2_run")
+
+
+def sp2_replay_batched(ctx, H, parts, params, budget_bytes, col, val, drop_tol=0.0):
+    """Replayed SP2 in batches of subgraphs whose iterates fit budget_bytes, D into the
+    caller's ELL buffers col[n, width], val[n, width]; returns the number of batches."""
+    n, width = col.shape
+    e = Ell(n, width, _ptr(col), _ptr(val), 1 if _is_device(col) else 0)
+    b = ctypes.c_int()
+    check(load_library().gbe_sp2_replay_batched(ctx.handle, ctypes.byref(H), parts.handle, ctypes.byref(params),
+                                                int(budget_bytes), float(drop_tol), ctypes.byref(e), ctypes.byref(b)),
+          "gbe_sp2_replay_batched")
+    return b.value
 
 
 def sp2_report_get(ctx, X):

@@ -1581,6 +1581,57 @@ extern "C" int gbe_sp2_submatrices(gbe_ctx* ctx, const gbe_csr* H, const gbe_par
     return GBE_OK;
 }
 
+// Core columns of every subgraph of X into a device ELL (col, val of width `width`); rows
+// outside X's cores are emptied first when `clear` is set.  Enqueue only.
+static int assemble_device(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, double drop_tol, int64_t width,
+                           int32_t* col, double* val, bool clear) {
+    cudaStream_t st = ctx->stream;
+    const int64_t total = parts->n * width;
+    // rows outside every core keep the empty entry (the assembly pads the rows it writes)
+    if (clear && !parts->cores_cover) fill_ell_kernel<<<ctx->sm_count * 4, 256, 0, st>>>(total, col, val);
+    int max_c = 1;
+    for (int64_t q = 0; q < X->P; ++q) max_c = std::max(max_c, X->h_c[q]);
+    const int jblocks = (max_c + 7) / 8;
+    assemble_kernel<<<(unsigned)(X->P * jblocks), 256, 0, st>>>(X->d_ctrl, parts->d_sub_ptr, parts->d_sub_idx, geom_of(X),
+                                                                 X->planes[0], X->planes[1], X->total_elems, X->f64[0],
+                                                                 X->f64[1], width, col, val, drop_tol, jblocks);
+    GBE_CUDA_TRY(cudaGetLastError());
+    return GBE_OK;
+}
+
+// Device ELL buffers for D: D's own when on the device, else a staging pair (tmp).
+static int ell_device_buffers(const gbe_ell* D, void** tmp, int32_t** col, double** val) {
+    const int64_t total = D->n * D->width;
+    *tmp = nullptr;
+    *col = D->col;
+    *val = D->val;
+    if (!D->on_device) {
+        const int64_t col_bytes = ((total * 4 + 15) / 16) * 16;
+        GBE_TRY(gbe_alloc(tmp, col_bytes + total * 8));
+        *col = (int32_t*)*tmp;
+        *val = (double*)((char*)*tmp + col_bytes);
+    }
+    return GBE_OK;
+}
+
+// A host D from its device staging pair (the copy engines move it over the host link faster
+// than the kernels' own stores to page-locked host memory), then the stream is synchronised.
+static int ell_finish(gbe_ctx* ctx, const gbe_ell* D, const int32_t* col, const double* val) {
+    cudaStream_t st = ctx->stream;
+    const int64_t total = D->n * D->width;
+    cudaError_t e = cudaSuccess;
+    if (!D->on_device) {
+        e = cudaMemcpyAsync(D->col, col, total * 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(D->val, val, total * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) {
+        gbe_set_error("assemble: %s", cudaGetErrorString(e));
+        return GBE_ECUDA;
+    }
+    return GBE_OK;
+}
+
 extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* parts, double drop_tol, gbe_ell* D) {
     AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && X && parts && D, "NULL argument");
@@ -1596,40 +1647,90 @@ extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* 
         return GBE_ECAPACITY;
     }
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
-    cudaStream_t st = ctx->stream;
-    const int64_t total = D->n * D->width;
-    int32_t* col = D->col;
-    double* val = D->val;
     void* tmp = nullptr;
-    // host D: assembled on the device and copied out (the copy engines move it over the host
-    // link faster than the kernels' own stores to page-locked host memory)
-    const bool staged = !D->on_device;
-    if (staged) {
-        const int64_t col_bytes = ((total * 4 + 15) / 16) * 16;
-        GBE_TRY(gbe_alloc(&tmp, col_bytes + total * 8));
-        col = (int32_t*)tmp;
-        val = (double*)((char*)tmp + col_bytes);
-    }
-    // rows outside every core keep the empty entry (the assembly pads the rows it writes)
-    if (!parts->cores_cover) fill_ell_kernel<<<ctx->sm_count * 4, 256, 0, st>>>(total, col, val);
-    int max_c = 1;
-    for (int64_t q = 0; q < X->P; ++q) max_c = std::max(max_c, X->h_c[q]);
-    const int jblocks = (max_c + 7) / 8;
-    assemble_kernel<<<(unsigned)(X->P * jblocks), 256, 0, st>>>(X->d_ctrl, parts->d_sub_ptr, parts->d_sub_idx, geom_of(X),
-                                                                 X->planes[0], X->planes[1], X->total_elems, X->f64[0],
-                                                                 X->f64[1], D->width, col, val, drop_tol, jblocks);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && staged) {
-        e = cudaMemcpyAsync(D->col, col, total * 4, cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(D->val, val, total * 8, cudaMemcpyDeviceToHost, st);
-    }
-    if (e == cudaSuccess && !D->on_device) e = cudaStreamSynchronize(st);
+    int32_t* col;
+    double* val;
+    GBE_TRY(ell_device_buffers(D, &tmp, &col, &val));
+    int r = assemble_device(ctx, X, parts, drop_tol, D->width, col, val, true);
+    if (r == GBE_OK) r = ell_finish(ctx, D, col, val);
     if (tmp) gbe_free(tmp);
-    if (e != cudaSuccess) {
-        gbe_set_error("assemble: %s", cudaGetErrorString(e));
-        return GBE_ECUDA;
+    return r;
+}
+
+// Bytes of the two ping-pong iterates of a subgraph with padded size mpad.
+static int64_t iterate_bytes(int prec, int64_t mpad, bool fp64_also) {
+    const int64_t e = mpad * mpad;
+    int64_t b = prec == GBE_PREC_FP64 ? 2 * 8 * e : 2 * (int64_t)gbe_subs_planes(prec) * 2 * e;
+    if (fp64_also && prec != GBE_PREC_FP64) b += 2 * 8 * e;
+    return b;
+}
+
+extern "C" int gbe_sp2_replay_batched(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts,
+                                      const gbe_sp2_params* prm, int64_t budget_bytes, double drop_tol, gbe_ell* D,
+                                      int* batches) {
+    AllocScope alloc_scope_(ctx);
+    GBE_CHECK_ARG(ctx && H && parts && prm && D && D->col && D->val, "NULL argument");
+    GBE_CHECK_ARG(prm->branch_mode == GBE_BRANCH_REPLAY && prm->seq_in && prm->seq_len > 0,
+                  "a batched run replays a pre-determined sequence");
+    GBE_CHECK_ARG(prm->exchange == nullptr, "a batched run exchanges no traces");
+    GBE_CHECK_ARG(parts->h_global_id.empty(), "parts is a shard");
+    GBE_CHECK_ARG(D->n == parts->n, "D rows");
+    if (D->width < parts->max_m) {
+        gbe_set_error("ELL width %lld < max subgraph size %lld", (long long)D->width, (long long)parts->max_m);
+        return GBE_ECAPACITY;
     }
-    return GBE_OK;
+    const int64_t P = parts->P;
+    const int prec = prm->prec;
+    const bool tail = prm->fp64_tail > 0;
+    std::vector<int64_t> bytes(P);
+    int64_t total = 0, largest = 0;
+    for (int64_t s = 0; s < P; ++s) {
+        const int64_t m = parts->h_sub_ptr[s + 1] - parts->h_sub_ptr[s];
+        bytes[s] = iterate_bytes(prec, (m + 127) / 128 * 128, tail);
+        total += bytes[s];
+        largest = std::max(largest, bytes[s]);
+    }
+    if (largest > budget_bytes) {
+        gbe_set_error("a subgraph's iterates take %lld bytes, above the budget of %lld", (long long)largest,
+                      (long long)budget_bytes);
+        return GBE_ECAPACITY;
+    }
+    // the fewest batches, dealt by m_s^3, whose iterates each fit the budget
+    std::vector<int32_t> owner(P);
+    int B = (int)std::max<int64_t>(1, (total + budget_bytes - 1) / budget_bytes);
+    for (;; ++B) {
+        GBE_TRY(gbe_shard_assign(P, parts->h_sub_ptr.data(), B, owner.data(), nullptr));
+        std::vector<int64_t> per(B, 0);
+        for (int64_t s = 0; s < P; ++s) per[owner[s]] += bytes[s];
+        if (*std::max_element(per.begin(), per.end()) <= budget_bytes) break;
+        if (B >= P) break;   // one subgraph per batch fits (largest <= budget)
+    }
+    GBE_CUDA_TRY(cudaSetDevice(ctx->device));
+    void* tmp = nullptr;
+    int32_t* col;
+    double* val;
+    GBE_TRY(ell_device_buffers(D, &tmp, &col, &val));
+    int r = GBE_OK;
+    if (!parts->cores_cover) fill_ell_kernel<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(D->n * D->width, col, val);
+    for (int b = 0; b < B && r == GBE_OK; ++b) {
+        gbe_parts* local = nullptr;
+        gbe_subs* X = nullptr;
+        r = gbe_parts_shard(ctx, parts, owner.data(), b, &local);
+        if (r == GBE_OK) r = gbe_subs_create(ctx, local, prec, &X);
+        if (r == GBE_OK) r = gbe_sp2_run(ctx, H, local, prm, X);
+        // each batch writes the rows of its own cores; no batch clears the others'
+        if (r == GBE_OK) r = assemble_device(ctx, X, local, drop_tol, D->width, col, val, false);
+        if (r == GBE_OK) {
+            const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+            if (e != cudaSuccess) { gbe_set_error("batched replay: %s", cudaGetErrorString(e)); r = GBE_ECUDA; }
+        }
+        if (X) gbe_free_subs(X);
+        if (local) gbe_free_parts(local);
+    }
+    if (r == GBE_OK) r = ell_finish(ctx, D, col, val);
+    if (tmp) gbe_free(tmp);
+    if (r == GBE_OK && batches) *batches = B;
+    return r;
 }
 
 extern "C" int gbe_subs_export(gbe_ctx* ctx, const gbe_subs* X, int64_t s, double* out) {

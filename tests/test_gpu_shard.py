@@ -9,7 +9,9 @@ does.  Checked against one run of the whole partition on the same GPU:
   the ranks' ELL rows equals the whole run's D bit for bit (FP64, FP16X6 and FP64TC);
 - replay mode (a pre-determined sequence): no exchange is made, and D is again identical;
 - a rank whose exchange fails makes both ranks return GBE_EPEER instead of hanging, and
-  the contexts stay usable.
+  the contexts stay usable;
+- the same independence on one GPU: gbe_sp2_replay_batched runs a replayed partition in
+  batches that fit a memory budget, with D identical to one whole run.
 """
 import threading
 
@@ -157,3 +159,37 @@ def test_failed_exchange_stops_both_ranks(case):
     gbe.sp2_run(ctx, out["Hd"], sh, gbe.sp2_params(case["N"] // 2, prec=gbe.PREC_FP64, seq=[1, 0, 1]), X)
     r = gbe.sp2_report_get(ctx, X).as_dict()
     assert r["status"] == gbe.GBE_OK and r["iters"] == 3
+
+
+@pytest.mark.parametrize("prec", [gbe.PREC_FP64, gbe.PREC_FP16X6, gbe.PREC_FP64TC])
+def test_replay_in_batches_matches_whole_run(case, prec):
+    """gbe_sp2_replay_batched: a partition replayed in batches of subgraphs whose iterates
+    fit a budget (here a quarter of the whole, so at least four batches) gives, row for row,
+    the D of one run over the whole partition with the same sequence, into device and host
+    ELL buffers; a global-trace run and a budget below one subgraph's iterates are refused."""
+    rep, _, _ = whole_run(case, prec)
+    seq = rep["seq"]
+    _, col2, val2 = whole_run(case, prec, seq=seq)
+    ctx = gbe.Context(0, torch.cuda.current_stream().cuda_stream)
+    parts = import_parts(ctx, case["N"], case["subs"], case["nc"])
+    Hd = device_csr(case["H"])
+    mpad = [(len(s) + 127) // 128 * 128 for s in case["subs"]]
+    per = {gbe.PREC_FP64: 16, gbe.PREC_FP16X6: 16, gbe.PREC_FP64TC: 40}[prec]
+    need = sum(p * p * per for p in mpad)
+    prm = gbe.sp2_params(case["N"] // 2, prec=prec, seq=seq, n_max=len(seq))
+    n, width = col2.shape
+    col = torch.empty((n, width), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, width), dtype=torch.float64, device="cuda")
+    nb = gbe.sp2_replay_batched(ctx, Hd, parts, prm, need // 4, col, val)
+    assert nb >= 4
+    assert np.array_equal(col.cpu().numpy(), col2) and np.array_equal(val.cpu().numpy(), val2)
+    colh = np.empty((n, width), np.int32)
+    valh = np.empty((n, width), np.float64)
+    assert gbe.sp2_replay_batched(ctx, Hd, parts, prm, need, colh, valh) == 1
+    assert np.array_equal(colh, col2) and np.array_equal(valh, val2)
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.sp2_replay_batched(ctx, Hd, parts, gbe.sp2_params(case["N"] // 2, prec=prec), need, col, val)
+    assert e.value.code == gbe.GBE_EINVAL
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.sp2_replay_batched(ctx, Hd, parts, prm, min(mpad) ** 2 * per - 1, col, val)
+    assert e.value.code == gbe.GBE_ECAPACITY
