@@ -672,45 +672,27 @@ def ell_rows_diff(torch, rows, ca, va, cb, vb, n, chunk=8192):
 
 
 def graph_sp2_batched(gbe, torch, ctx, Hv, parts, N, seq, budget, keep=None, compare=None):
-    """FP64-grade graph SP2 (FP64TC) of a partition that need not fit the device at once: the
-    subgraphs are dealt to batches (gbe_shard_assign, largest m_s^3 first) whose split planes
-    fit `budget` bytes, and each batch replays the branch sequence `seq` (no traces need to be
-    combined, Sec. II.C) and assembles the D rows of its own cores.  keep: (col, val) to fill
-    with the whole D; compare: {name: (col, val)} D's compared row by row with this one."""
+    """FP64-grade graph SP2 (FP64TC) of a partition that need not fit the device at once,
+    through gbe_sp2_replay_batched: the subgraphs run in batches whose iterates fit `budget`
+    bytes, each replaying the branch sequence `seq` (no traces need to be combined,
+    Sec. II.C), and D is assembled column by column.  keep: (col, val) to fill with D;
+    compare: {name: (col, val)} D's compared row by row with this one."""
     P, total, max_m = parts.info()
     cc, sptr, _ = parts.export()
     ms = np.diff(sptr)
-    mpad = (ms + 127) // 128 * 128
-    need = float(np.sum(mpad.astype(np.float64) ** 2)) * 40.0      # 10 planes x 2 bytes x 2 sides
-    B = max(1, int(np.ceil(need / budget)))
-    owner, load = gbe.shard_assign(sptr, B)
+    need = float(np.sum(((ms + 127) // 128 * 128).astype(np.float64) ** 2)) * 40.0   # 10 planes x 2 B x 2 sides
     col = torch.empty((N, max_m), dtype=torch.int32, device="cuda") if keep is None else keep[0]
     val = torch.empty((N, max_m), dtype=torch.float64, device="cuda") if keep is None else keep[1]
     prm = gbe.sp2_params(N / 2.0, prec=gbe.PREC_FP64TC, n_max=max(len(seq), 10), seq=seq)
-    t_sp2, diffs = 0.0, {k: [0.0, 0.0, 0] for k in (compare or {})}
-    for b in range(B):
-        local = gbe.parts_shard(ctx, parts, owner, b)
-        X = gbe.subs_create(ctx, local, gbe.PREC_FP64TC)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        gbe.sp2_run(ctx, Hv, local, prm, X)
-        torch.cuda.synchronize()
-        t_sp2 += time.perf_counter() - t0
-        if keep is None:
-            gbe.assemble_D(ctx, X, local, col, val)
-            rows = torch.nonzero(col[:, 0] >= 0).squeeze(1)
-            for k, (cb, vb) in (compare or {}).items():
-                mx, ss, cnt = ell_rows_diff(torch, rows, col, val, cb, vb, N)
-                diffs[k] = [max(diffs[k][0], mx), diffs[k][1] + ss, diffs[k][2] + cnt]
-        else:
-            cb = torch.empty_like(col)
-            vb = torch.empty_like(val)
-            gbe.assemble_D(ctx, X, local, cb, vb)
-            rows = torch.nonzero(cb[:, 0] >= 0).squeeze(1)
-            col[rows] = cb[rows]
-            val[rows] = vb[rows]
-            del cb, vb
-        del X, local
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    B = gbe.sp2_replay_batched(ctx, Hv, parts, prm, int(budget), col, val)
+    torch.cuda.synchronize()
+    t_sp2 = time.perf_counter() - t0
+    diffs = {}
+    rows = torch.arange(N, device="cuda")
+    for k, (cb, vb) in (compare or {}).items():
+        diffs[k] = list(ell_rows_diff(torch, rows, col, val, cb, vb, N))
     info = {"subgraphs": int(P), "m_s_min": int(ms.min()), "m_s_median": float(np.median(ms)), "m_s_max": int(ms.max()),
             "sum_m3": float(np.sum(ms.astype(np.float64) ** 3)), "batches": B, "planes_gb": need / 1e9,
             "sp2_s": t_sp2, "alg_tflops": 2.0 * float(np.sum(ms.astype(np.float64) ** 3)) * len(seq) / t_sp2 / 1e12}
