@@ -603,9 +603,10 @@ def mlp_init_params(seed):
                            rng.normal(0.0, (1.0 / 64) ** 0.5, 64), np.zeros(1)]).astype(np.float32)
 
 
-def mlp_labelled_system(gbe, torch, ctx, cfg, seed):
-    """One seeded training system: candidate pairs with features, and labels |D_ij| >= tau
-    from the library's FP64-grade SP2 on its complete graph (one subgraph of every site)."""
+def mlp_labelled_system(gbe, torch, ctx, cfg, seed, taus):
+    """One seeded training system: candidate pairs with features, and for each tau the labels
+    |D_ij| >= tau from the library's FP64-grade SP2 on its complete graph (one subgraph of
+    every site)."""
     import synth
     n = cfg["train_n"]
     w = synth.disordered(n, seed=seed)
@@ -617,37 +618,49 @@ def mlp_labelled_system(gbe, torch, ctx, cfg, seed):
     val = torch.empty((n, n), dtype=torch.float64, device="cuda")
     gbe.assemble_D(ctx, X, full, col, val)
     P = gbe.pairs_build(ctx, st, Hh.csr(), cfg["rcand"])
-    lab = torch.empty(P.info()[1], dtype=torch.uint8, device="cuda")
-    gbe.mlp_labels(ctx, P, col, val, cfg["tau"], lab)
+    labs = {}
+    for tau in taus:
+        labs[tau] = torch.empty(P.info()[1], dtype=torch.uint8, device="cuda")
+        gbe.mlp_labels(ctx, P, col, val, tau, labs[tau])
     torch.cuda.synchronize()
-    return P, lab, rep["iters"]
+    return P, labs
 
 
 def mlp_train(args, gbe, torch, ctx, cfg):
-    """Train the network on the GPU: args.train_systems labelled systems, one Adam step per
-    system in turn, cfg passes; accuracy on an unseen system."""
+    """Train one network per label threshold on the GPU (the configuration's tau = 1e-5 and
+    the pruning threshold cfg["tau"]): args.train_systems labelled systems, one Adam step per
+    system in turn, cfg passes; accuracy on an unseen system.  Returns the cfg["tau"]
+    network, the 1e-5 one and the training reports."""
+    taus = [1e-5, cfg["tau"]] if cfg["tau"] != 1e-5 else [1e-5]
     t0 = time.perf_counter()
-    sets = [mlp_labelled_system(gbe, torch, ctx, cfg, cfg["train_seed0"] + k)[:2] for k in range(args.train_systems)]
+    sets = [mlp_labelled_system(gbe, torch, ctx, cfg, cfg["train_seed0"] + k, taus) for k in range(args.train_systems)]
     t_lab = time.perf_counter() - t0
-    M = gbe.mlp_create(ctx)
-    M.set_params(mlp_init_params(0))
-    loss0 = float(np.mean([M.gradient(P, lab)[0] for P, lab in sets]))
-    t0 = time.perf_counter()
-    for _ in range(cfg["passes"]):
-        for P, lab in sets:
-            M.train(P, lab, 1, cfg["lr"])
-    t_train = time.perf_counter() - t0
-    loss = float(np.mean([M.gradient(P, lab)[0] for P, lab in sets]))
-    Pt, labt, _ = mlp_labelled_system(gbe, torch, ctx, cfg, cfg["test_seed"])
-    z = torch.empty(Pt.info()[1], dtype=torch.float32, device="cuda")
-    M.forward(Pt, z)
-    acc = float(((z >= 0) == (labt > 0)).float().mean())
-    pos = float(np.mean([float(lab.float().mean()) for _, lab in sets]))
-    return M, {"systems": len(sets), "system": "%d disordered sites, box %.1fa, seeds %d.." % (
-                   cfg["train_n"], cfg["train_n"] ** (1.0 / 3.0), cfg["train_seed0"]),
-               "labels": "|D_ij| >= %g, D from FP64TC SP2 on the complete graph" % cfg["tau"],
-               "positive_rate": pos, "passes": cfg["passes"], "lr": cfg["lr"], "loss_initial": loss0,
-               "loss_final": loss, "unseen_accuracy": acc, "labels_s": t_lab, "train_s": t_train}
+    Pt, labt = mlp_labelled_system(gbe, torch, ctx, cfg, cfg["test_seed"], taus)
+    nets, reports = {}, {}
+    for tau in taus:
+        M = gbe.mlp_create(ctx)
+        M.set_params(mlp_init_params(0))
+        loss0 = float(np.mean([M.gradient(P, labs[tau])[0] for P, labs in sets]))
+        t0 = time.perf_counter()
+        for _ in range(cfg["passes"]):
+            for P, labs in sets:
+                M.train(P, labs[tau], 1, cfg["lr"])
+        t_train = time.perf_counter() - t0
+        loss = float(np.mean([M.gradient(P, labs[tau])[0] for P, labs in sets]))
+        z = torch.empty(Pt.info()[1], dtype=torch.float32, device="cuda")
+        M.forward(Pt, z)
+        acc = float(((z >= 0) == (labt[tau] > 0)).float().mean())
+        pos = float(np.mean([float(labs[tau].float().mean()) for _, labs in sets]))
+        nets[tau] = M
+        reports["tau=%g" % tau] = {"positive_rate": pos, "loss_initial": loss0, "loss_final": loss,
+                                   "unseen_accuracy": acc, "train_s": t_train}
+    return nets[cfg["tau"]], nets[1e-5], {
+        "systems": len(sets), "system": "%d disordered sites, box %.1fa, seeds %d.." % (
+            cfg["train_n"], cfg["train_n"] ** (1.0 / 3.0), cfg["train_seed0"]),
+        "labels": "|D_ij| >= tau, D from FP64TC SP2 on the complete graph", "passes": cfg["passes"],
+        "lr": cfg["lr"], "labels_s": t_lab, "networks": reports,
+        "used_for_the_graphs": "tau=%g (tau = 1e-5 labels almost every candidate, so its network keeps "
+                               "nearly the whole ball)" % cfg["tau"]}
 
 
 def ell_rows_diff(torch, rows, ca, va, cb, vb, n, chunk=8192):
@@ -699,7 +712,7 @@ def graph_sp2_batched(gbe, torch, ctx, Hv, parts, N, seq, budget, keep=None, com
     return info, diffs
 
 
-def mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M):
+def mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M, M5=None):
     """The trained network's graphs of the big system (one per logit cut) against the H^k
     pattern graphs and the whole candidate ball: each graph's FP64-grade graph SP2 (the
     same replayed branch sequence), D compared with the conservative H^2 graph's D, with
@@ -713,8 +726,11 @@ def mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M):
         return lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_MLP, site_struct=st, mlp=M, rcand=cfg["rcand"],
                                        logit_cut=cut)
 
-    graphs = [("H^1", hk(1))] + [("MLP cut %g" % c, learned(c)) for c in cfg["cuts"]] + \
-             [("ball r<%g" % cfg["rcand"], learned(-1e30)), ("H^2", hk(2))]
+    graphs = [("H^1", hk(1))] + [("MLP cut %g" % c, learned(c)) for c in cfg["cuts"]]
+    if M5 is not None:
+        graphs.append(("MLP tau=1e-5 cut 0", lambda: gbe.build_graph(ctx, Hv, gbe.GRAPH_MLP, site_struct=st, mlp=M5,
+                                                                    rcand=cfg["rcand"], logit_cut=0.0)))
+    graphs += [("ball r<%g" % cfg["rcand"], learned(-1e30)), ("H^2", hk(2))]
     res, parts_of = {}, {}
     for name, make in graphs:
         t0 = time.perf_counter()
@@ -777,7 +793,7 @@ def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
         cfg["tau"] = args.mlp_tau
     if args.mlp_cuts:
         cfg["cuts"] = tuple(float(c) for c in args.mlp_cuts.split(","))
-    M, train = mlp_train(args, gbe, torch, ctx, cfg)
+    M, M5, train = mlp_train(args, gbe, torch, ctx, cfg)
     phases = {"pairs_features": 0.0, "forward": 0.0, "graph": 0.0}
     npairs = 0
 
@@ -830,7 +846,7 @@ def run_mlp(args, wl, gbe, torch, ctx, local, rank, world):
         "e2e": None, "gpu_launches": None, "clocks": clk,
     }
     if not args.no_compare:
-        line["comparison"] = mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M)
+        line["comparison"] = mlp_compare(args, gbe, torch, ctx, cfg, w, st, Hv, M, M5)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
