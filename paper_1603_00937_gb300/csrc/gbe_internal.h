@@ -151,6 +151,9 @@ struct gbe_subs {
     // the gather's dense-row staging in global memory, for subgraphs whose rows do not fit
     // shared memory: [P][8][max_mpad] uint2 (allocated by the first run that needs it)
     void* d_gather_rows = nullptr;
+    // CTAs of the gather per subgraph (each takes every gather_split-th group of 8 rows and
+    // writes one trace partial); 1 with global row staging
+    int gather_split = 1;
     // work lists
     TileItem* d_items_tc = nullptr;  int n_items_tc = 0;   // 128x128 tiles
     TileItem* d_items_64 = nullptr;  int n_items_64 = 0;   // 64x64 tiles

@@ -81,10 +81,34 @@ __global__ void __launch_bounds__(256) gershgorin_kernel(const int64_t* __restri
         lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(&ctrl->status, GBE_ENUMERIC);
-    if (lane == 0 && lo <= hi) {
-        atomicMin(&ctrl->eps_min_key, dkey(lo));
-        atomicMax(&ctrl->eps_max_key, dkey(hi));
+    // the block's bounds first, then one atomic pair per block (per-warp atomics on the two
+    // words serialise in L2)
+    __shared__ double slo[8], shi[8];
+    __shared__ int sbad;
+    const int w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    const bool wbad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+        slo[w] = lo;
+        shi[w] = hi;
+        if (wbad) sbad = 1;
+    }
+    __syncthreads();
+    if (w == 0) {
+        lo = lane < (int)(blockDim.x >> 5) ? slo[lane] : INFINITY;
+        hi = lane < (int)(blockDim.x >> 5) ? shi[lane] : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            if (sbad) atomicExch(&ctrl->status, GBE_ENUMERIC);
+            if (lo <= hi) {
+                atomicMin(&ctrl->eps_min_key, dkey(lo));
+                atomicMax(&ctrl->eps_max_key, dkey(hi));
+            }
+        }
     }
 }
 
@@ -102,7 +126,8 @@ __device__ __forceinline__ int hash_local(const int2* htab, int hbits, int g) {
     }
 }
 
-// One CTA (8 warps) per subgraph, 8 consecutive rows a0..a0+7 at a time, one per warp:
+// G CTAs (8 warps each) per subgraph, CTA `part` taking the groups of 8 consecutive rows
+// a0..a0+7 with a0 = 8 part, 8 (part + G), ..., one row per warp:
 // lanes map the row's H entries to local columns (a shared-memory hash table of the
 // subgraph's sites), split them and scatter them into the warp's dense row buffer (4 split
 // planes packed in 8 bytes per column, or the FP64 value; in shared memory, or for
@@ -111,7 +136,8 @@ __device__ __forceinline__ int hash_local(const int2* htab, int hbits, int g) {
 // 8-column group of every stored (upper) block, each thread one row r of it (16 contiguous
 // bytes per plane; a warp covers 512 contiguous bytes).  The FP64 iterate (stored in full)
 // is written row by row.  Every element of the padded tile is written, zeros included, so
-// the planes need no separate clear.
+// the planes need no separate clear.  Each CTA builds its own copy of the hash table and
+// writes the trace sums of its rows as one partial (work unit s G + part).
 template <int prec>
 __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_t* __restrict__ rowptr,
                                                      const int32_t* __restrict__ col, const double* __restrict__ val,
@@ -119,10 +145,10 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
                                                      const int32_t* __restrict__ sub_idx, SubsGeom g, int max_mpad,
                                                      uint16_t* planes, int64_t plane_stride, double* f,
                                                      double* partials, int max_units, int htab_off, int hbits,
-                                                     uint2* rows_g) {
+                                                     uint2* rows_g, int G) {
     extern __shared__ unsigned char gsm[];
     __shared__ double red[16];
-    const int s = blockIdx.x;
+    const int s = blockIdx.x / G, part = blockIdx.x % G;
     const int m = g.m[s], c = g.c[s], mpad = g.mpad[s];
     const int64_t off = g.off[s];
     const int64_t base = sub_ptr[s];
@@ -185,10 +211,11 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     int64_t r0c, r1c, r0n, r1n;
     int cjc[3];
     double hvc[3];
-    row_range(warp, r0c, r1c);
+    const int step = 8 * G;   // this CTA's groups of 8 rows: 8 part, 8 (part + G), ...
+    row_range(8 * part + warp, r0c, r1c);
     load3(r0c + lane, r1c, cjc, hvc);
-    row_range(warp + 8, r0n, r1n);
-    for (int a0 = 0; a0 < mpad; a0 += 8) {
+    row_range(8 * part + step + warp, r0n, r1n);
+    for (int a0 = 8 * part; a0 < mpad; a0 += step) {
         const int a = a0 + warp;
         for (int b = lane; b < mpad; b += 32) rowbuf[b] = make_uint2(0u, 0u);
         __syncwarp();
@@ -256,7 +283,7 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
         load3(r0n + lane, r1n, cjc, hvc);
         r0c = r0n;
         r1c = r1n;
-        row_range(a + 16, r0n, r1n);
+        row_range(a + 2 * step, r0n, r1n);
         if constexpr (prec == GBE_PREC_FP64) {
             __syncwarp();
             // row a, all column groups: 64 contiguous bytes per lane and group
@@ -315,9 +342,9 @@ __global__ void __launch_bounds__(256) gather_kernel(Sp2Ctrl* ctrl, const int64_
     double s1 = block_sum_d<256>(t1, red);
     double s2 = block_sum_d<256>(t2, red + 8);
     if (threadIdx.x == 0) {
-        partials[s] = s1;
-        partials[max_units + s] = s2;
-        if (s == 0) { ctrl->eps_min = emin; ctrl->eps_max = emax; }
+        partials[blockIdx.x] = s1;
+        partials[max_units + blockIdx.x] = s2;
+        if (blockIdx.x == 0) { ctrl->eps_min = emin; ctrl->eps_max = emax; }
     }
 }
 
@@ -955,6 +982,43 @@ static void make_items(const std::vector<int32_t>& dim, const std::vector<int32_
     }
 }
 
+// Dynamic shared memory of the gather: 8 dense rows, the local->global list, and a hash
+// table of >= 2 m slots (global -> local).  Subgraphs up to 2432 vertices keep the rows in
+// the 227 KB of a GB300 CTA; larger ones stage them in global memory (L2) and keep the list
+// and the hash table in shared memory, up to 8192 vertices.
+struct GatherLayout {
+    size_t smem;
+    int htab_off, hbits;
+    bool rows_global;
+};
+static GatherLayout gather_layout(const gbe_ctx* ctx, const gbe_subs* X) {
+    GatherLayout L;
+    const int64_t max_m = X->parts->max_m;
+    L.hbits = 6;
+    while ((1ll << L.hbits) < 2 * max_m) ++L.hbits;
+    L.rows_global = false;
+    L.htab_off = (int)((((size_t)8 * X->max_mpad * 8 + (size_t)max_m * 4) + 7) & ~(size_t)7);
+    L.smem = (size_t)L.htab_off + ((size_t)8 << L.hbits);
+    if ((int64_t)L.smem > (int64_t)ctx->smem_optin) {
+        L.rows_global = true;
+        L.htab_off = (int)(((size_t)max_m * 4 + 7) & ~(size_t)7);
+        L.smem = (size_t)L.htab_off + ((size_t)8 << L.hbits);
+    }
+    return L;
+}
+
+// CTAs of the gather per subgraph: enough CTAs for about eight per SM, each keeping at
+// least two groups of 8 rows of the smallest padded subgraph.
+static int gather_split_of(const gbe_ctx* ctx, const gbe_subs* X, const GatherLayout& L) {
+    if (L.rows_global || X->P <= 0) return 1;
+    int min_mpad = X->max_mpad;
+    for (int64_t s = 0; s < X->P; ++s) min_mpad = std::min(min_mpad, X->h_mpad[s]);
+    const int64_t target = 8ll * ctx->sm_count;
+    int G = (int)std::min<int64_t>(8, (target + X->P - 1) / X->P);
+    G = std::min(G, std::max(1, min_mpad / 16));
+    return std::max(1, G);
+}
+
 extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, gbe_subs** out) {
     AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && parts && out, "NULL argument");
@@ -1008,11 +1072,12 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     make_items(m64, X->h_mpad, 64, ft_64, true);
     X->n_items_tc_full = (int)ft_tc.size();
     X->n_items_64_full = (int)ft_64.size();
-    X->max_units = (int)std::max<int64_t>(X->P, std::max(X->n_items_tc_full, X->n_items_64_full));
+    X->gather_split = gather_split_of(ctx, X, gather_layout(ctx, X));
+    X->max_units = (int)std::max<int64_t>(X->P * X->gather_split, std::max(X->n_items_tc_full, X->n_items_64_full));
     // work units of each subgraph per decision kind (the tiles of a subgraph are contiguous)
     std::vector<int2> rg[3];
     for (int k = 0; k < 3; ++k) rg[k].assign(X->P, make_int2(0, 0));
-    for (int64_t q = 0; q < X->P; ++q) rg[0][q] = make_int2((int)q, 1);
+    for (int64_t q = 0; q < X->P; ++q) rg[0][q] = make_int2((int)q * X->gather_split, X->gather_split);
     for (int k = 1; k < 3; ++k) {
         const std::vector<TileItem>& its = k == 1 ? it_tc : it_64;
         for (int i = 0; i < (int)its.size(); ++i) {
@@ -1176,7 +1241,7 @@ int gbe_launch_gershgorin(gbe_ctx* ctx, const gbe_csr* H, gbe_subs* X) {
 }
 
 typedef void (*GatherFn)(Sp2Ctrl*, const int64_t*, const int32_t*, const double*, const int64_t*, const int32_t*,
-                         SubsGeom, int, uint16_t*, int64_t, double*, double*, int, int, int, uint2*);
+                         SubsGeom, int, uint16_t*, int64_t, double*, double*, int, int, int, uint2*, int);
 static GatherFn gather_for(int prec) {
     switch (prec) {
         case GBE_PREC_FP64: return gather_kernel<GBE_PREC_FP64>;
@@ -1184,31 +1249,6 @@ static GatherFn gather_for(int prec) {
         case GBE_PREC_FP64TC: return gather_kernel<GBE_PREC_FP64TC>;
         default: return gather_kernel<GBE_PREC_BF16X3>;
     }
-}
-
-// Dynamic shared memory of the gather: 8 dense rows, the local->global list, and a hash
-// table of >= 2 m slots (global -> local).  Subgraphs up to 2432 vertices keep the rows in
-// the 227 KB of a GB300 CTA; larger ones stage them in global memory (L2) and keep the list
-// and the hash table in shared memory, up to 8192 vertices.
-struct GatherLayout {
-    size_t smem;
-    int htab_off, hbits;
-    bool rows_global;
-};
-static GatherLayout gather_layout(const gbe_ctx* ctx, const gbe_subs* X) {
-    GatherLayout L;
-    const int64_t max_m = X->parts->max_m;
-    L.hbits = 6;
-    while ((1ll << L.hbits) < 2 * max_m) ++L.hbits;
-    L.rows_global = false;
-    L.htab_off = (int)((((size_t)8 * X->max_mpad * 8 + (size_t)max_m * 4) + 7) & ~(size_t)7);
-    L.smem = (size_t)L.htab_off + ((size_t)8 << L.hbits);
-    if ((int64_t)L.smem > (int64_t)ctx->smem_optin) {
-        L.rows_global = true;
-        L.htab_off = (int)(((size_t)max_m * 4 + 7) & ~(size_t)7);
-        L.smem = (size_t)L.htab_off + ((size_t)8 << L.hbits);
-    }
-    return L;
 }
 
 // Checks that the gather fits and allocates its global row staging when it needs one (called
@@ -1275,9 +1315,10 @@ static int enqueue_prologue(gbe_ctx* ctx, const gbe_csr* H, const Sp2Init& in, g
     const gbe_parts* parts = X->parts;
     const GatherLayout L = gather_layout(ctx, X);
     auto gk = gather_for(X->prec);
-    gk<<<(unsigned)X->P, 256, L.smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
-                                             geom_of(X), X->max_mpad, X->planes[0], X->total_elems, X->f64[0],
-                                             X->d_partials, X->max_units, L.htab_off, L.hbits, gather_rows_arg(L, X));
+    gk<<<(unsigned)(X->P * X->gather_split), 256, L.smem, st>>>(
+        X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx, geom_of(X), X->max_mpad, X->planes[0],
+        X->total_elems, X->f64[0], X->d_partials, X->max_units, L.htab_off, L.hbits, gather_rows_arg(L, X),
+        X->gather_split);
     GBE_CUDA_TRY(cudaGetLastError());
     return enqueue_decide(ctx, X, 0, xp, 0, false);
 }
@@ -1863,9 +1904,10 @@ extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     GBE_CUDA_TRY(cudaFuncSetAttribute(gk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
     cudaEventRecord(X->ev[0], st);
     init_ctrl_kernel<<<1, 256, 0, st>>>(X->d_ctrl, in);
-    gk<<<(unsigned)X->P, 256, L.smem, st>>>(X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx,
-                                             geom_of(X), X->max_mpad, X->planes[2], X->total_elems, X->f64[2],
-                                             X->d_partials, X->max_units, L.htab_off, L.hbits, gather_rows_arg(L, X));
+    gk<<<(unsigned)(X->P * X->gather_split), 256, L.smem, st>>>(
+        X->d_ctrl, H->rowptr, H->col, H->val, parts->d_sub_ptr, parts->d_sub_idx, geom_of(X), X->max_mpad, X->planes[2],
+        X->total_elems, X->f64[2], X->d_partials, X->max_units, L.htab_off, L.hbits, gather_rows_arg(L, X),
+        X->gather_split);
     GBE_CUDA_TRY(cudaGetLastError());
     for (int s = 0; s < 2; ++s) {
         if (fp64) GBE_CUDA_TRY(cudaMemsetAsync(X->f64[s], 0, X->total_elems * 8, st));
