@@ -366,7 +366,9 @@ int gbe_sp2_report_get(gbe_ctx* ctx, const gbe_subs* X, gbe_sp2_report* rep);
  * own cores into D (Eq. 6) before it is freed.  D is as gbe_assemble_D fills it (device or
  * host ELL, width >= max m_s); *batches (nullable) receives the number of batches.  H must
  * be device CSR.  GBE_EINVAL unless params is in replay mode without an exchange;
- * GBE_ECAPACITY when one subgraph's iterates alone exceed the budget.  Synchronises. */
+ * GBE_ECAPACITY when one subgraph's iterates alone exceed the budget; the device status of
+ * the first batch that recorded one (GBE_ENUMERIC for a non-finite H, GBE_ETIMEOUT), and
+ * no further batch runs.  Synchronises. */
 int gbe_sp2_replay_batched(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* parts, const gbe_sp2_params* params,
                            int64_t budget_bytes, double drop_tol, gbe_ell* D, int* batches);
 

@@ -1765,6 +1765,13 @@ extern "C" int gbe_sp2_replay_batched(gbe_ctx* ctx, const gbe_csr* H, const gbe_
             const cudaError_t e = cudaStreamSynchronize(ctx->stream);
             if (e != cudaSuccess) { gbe_set_error("batched replay: %s", cudaGetErrorString(e)); r = GBE_ECUDA; }
         }
+        // the status the batch's kernels recorded (non-finite H, a wait that ran out)
+        gbe_sp2_report R;
+        if (r == GBE_OK) r = gbe_sp2_report_get(ctx, X, &R);
+        if (r == GBE_OK && R.status != GBE_OK) {
+            gbe_set_error("batch %d: device recorded status %d (%s)", b, R.status, gbe_strerror(R.status));
+            r = R.status;
+        }
         if (X) gbe_free_subs(X);
         if (local) gbe_free_parts(local);
     }

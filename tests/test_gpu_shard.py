@@ -193,3 +193,27 @@ def test_replay_in_batches_matches_whole_run(case, prec):
     with pytest.raises(gbe.GbeError) as e:
         gbe.sp2_replay_batched(ctx, Hd, parts, prm, min(mpad) ** 2 * per - 1, col, val)
     assert e.value.code == gbe.GBE_ECAPACITY
+
+
+def test_replay_in_batches_reports_a_non_finite_H(case):
+    """A NaN entry of H (found by the Gershgorin pass of the first batch) comes back from
+    gbe_sp2_replay_batched as GBE_ENUMERIC, as it does from gbe_sp2_submatrices."""
+    rep, _, _ = whole_run(case, gbe.PREC_FP16X6)
+    seq = rep["seq"]
+    ctx = gbe.Context(0, torch.cuda.current_stream().cuda_stream)
+    parts = import_parts(ctx, case["N"], case["subs"], case["nc"])
+    bad = case["H"].tocsr().copy()
+    bad.sort_indices()
+    bad.data[len(bad.data) // 3] = np.nan
+    Hd = device_csr(bad)
+    prm = gbe.sp2_params(case["N"] // 2, prec=gbe.PREC_FP16X6, seq=seq, n_max=len(seq))
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.sp2_submatrices(ctx, Hd, parts, prm)
+    assert e.value.code == gbe.GBE_ENUMERIC
+    n = case["N"]
+    width = max(len(s) for s in case["subs"])
+    col = torch.empty((n, width), dtype=torch.int32, device="cuda")
+    val = torch.empty((n, width), dtype=torch.float64, device="cuda")
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.sp2_replay_batched(ctx, Hd, parts, prm, 1 << 40, col, val)
+    assert e.value.code == gbe.GBE_ENUMERIC
