@@ -5,6 +5,7 @@
 #include <mutex>
 #include <unordered_map>
 
+#include "devmem.h"
 #include "gbe_internal.h"
 
 static thread_local char g_errmsg[1024] = "";
@@ -35,6 +36,44 @@ extern "C" const char* gbe_strerror(int code) {
 }
 
 // ------------------------------------------------------------------ device memory
+bool gbe_device_memory_of(const void* p, int device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
+int gbe_check_device(const gbe_ctx* ctx, const void* p, size_t bytes, const char* what) {
+    if (bytes == 0 || gbe_device_memory_of(p, ctx->device)) return GBE_OK;
+    gbe_set_error("%s is flagged as device memory but is not device memory of GPU %d", what, ctx->device);
+    return GBE_EINVAL;
+}
+
+int gbe_check_device_csr(const gbe_ctx* ctx, const gbe_csr* H, const char* what) {
+    if (!H->on_device) return GBE_OK;
+    if (gbe_check_device(ctx, H->rowptr, (size_t)(H->n + 1) * 8, "CSR rowptr") != GBE_OK ||
+        gbe_check_device(ctx, H->col, (size_t)H->nnz * 4, "CSR col") != GBE_OK ||
+        gbe_check_device(ctx, H->val, (size_t)H->nnz * 8, "CSR val") != GBE_OK) {
+        gbe_set_error("%s: arrays flagged on_device = 1 are not device memory of GPU %d", what, ctx->device);
+        return GBE_EINVAL;
+    }
+    return GBE_OK;
+}
+
+int gbe_check_device_ell(const gbe_ctx* ctx, const gbe_ell* D, const char* what) {
+    if (!D->on_device) return GBE_OK;
+    const size_t total = (size_t)D->n * (size_t)D->width;
+    if (gbe_check_device(ctx, D->col, total * 4, "ELL col") != GBE_OK ||
+        gbe_check_device(ctx, D->val, total * 8, "ELL val") != GBE_OK) {
+        gbe_set_error("%s: arrays flagged on_device = 1 are not device memory of GPU %d", what, ctx->device);
+        return GBE_EINVAL;
+    }
+    return GBE_OK;
+}
+
 namespace {
 thread_local cudaStream_t t_stream = nullptr;
 thread_local cudaMemPool_t t_pool = nullptr;

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "devmem.h"
 #include "gbe_internal.h"
 
 namespace gbe_dev {
@@ -195,7 +196,11 @@ static inline int scan_exclusive(gbe_ctx* ctx, const int32_t* in, int64_t* out, 
 
 // Copy an array to the device when it is on the host.
 static inline int to_device(gbe_ctx* ctx, const void* src, size_t bytes, int on_device, DevBuf& hold, const void** out) {
-    if (on_device) { *out = src; return GBE_OK; }
+    if (on_device) {
+        GBE_TRY(gbe_check_device(ctx, src, bytes, "an input array"));
+        *out = src;
+        return GBE_OK;
+    }
     GBE_TRY(gbe_alloc(&hold.p, bytes));
     GBE_CUDA_TRY(cudaMemcpyAsync(hold.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
     *out = hold.p;

@@ -845,6 +845,7 @@ extern "C" int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* Hin, const gbe_graph
     // H on the device
     DevBuf hrp, hci, hva;
     gbe_csr H = *Hin;
+    GBE_TRY(gbe_check_device_csr(ctx, Hin, "gbe_build_graph H"));
     if (!Hin->on_device) {
         GBE_TRY(to_device(ctx, Hin->rowptr, (n + 1) * 8, 0, hrp, (const void**)&H.rowptr));
         GBE_TRY(to_device(ctx, Hin->col, Hin->nnz * 4, 0, hci, (const void**)&H.col));

@@ -860,6 +860,7 @@ extern "C" int gbe_mlp_gradient(gbe_ctx* ctx, gbe_mlp* M, const gbe_pairs* P, co
                                 float* grad_host) {
     AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && M && P && labels, "NULL argument");
+    GBE_TRY(gbe_check_device(ctx, labels, (size_t)P->npairs, "gbe_mlp_gradient labels"));
     GBE_TRY(mlp_grad_dev(ctx, M, P, labels));
     if (loss) GBE_CUDA_TRY(cudaMemcpyAsync(loss, M->loss, 8, cudaMemcpyDeviceToHost, ctx->stream));
     if (grad_host) GBE_CUDA_TRY(cudaMemcpyAsync(grad_host, M->g, kNParams * 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -881,6 +882,7 @@ extern "C" int gbe_mlp_train(gbe_ctx* ctx, gbe_mlp* M, const gbe_pairs* P, const
                              float lr, double* final_loss) {
     AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && M && P && labels && epochs > 0, "bad argument");
+    GBE_TRY(gbe_check_device(ctx, labels, (size_t)P->npairs, "gbe_mlp_train labels"));
     for (int e = 0; e < epochs; ++e) {
         GBE_TRY(mlp_grad_dev(ctx, M, P, labels));
         GBE_TRY(gbe_mlp_adam_step(ctx, M, lr, 0.9f, 0.999f, 1e-8f));
@@ -927,6 +929,8 @@ extern "C" int gbe_mlp_labels(gbe_ctx* ctx, const gbe_pairs* P, const gbe_ell* D
     GBE_CHECK_ARG(D->n == P->n && D->width >= 1, "D must have one row per site of the pairs");
     GBE_CHECK_ARG(tau >= 0.0, "tau must be >= 0");
     if (P->npairs == 0) return GBE_OK;
+    GBE_TRY(gbe_check_device_ell(ctx, D, "gbe_mlp_labels D"));
+    GBE_TRY(gbe_check_device(ctx, labels, (size_t)P->npairs, "gbe_mlp_labels labels"));
     pair_labels_kernel<<<(unsigned)P->n, 256, 0, ctx->stream>>>(P->rowptr, P->j, D->col, D->val, D->width, tau, labels);
     GBE_CUDA_TRY(cudaGetLastError());
     return GBE_OK;

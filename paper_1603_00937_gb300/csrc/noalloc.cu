@@ -9,6 +9,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "devmem.h"
 #include "gbe_internal.h"
 
 namespace {
@@ -137,18 +138,6 @@ int scratch_for(int device, unsigned long long** out) {
     return GBE_OK;
 }
 
-// Device (or managed) memory that `device` can address; host memory, registered or not, is
-// refused: a kernel given a host pointer would fault or read the wrong memory.
-bool device_memory_of(const void* p, int device) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return false;
-    }
-    if (a.type == cudaMemoryTypeManaged) return true;
-    return a.type == cudaMemoryTypeDevice && a.device == device;
-}
-
 }  // namespace
 
 extern "C" int gbe_gershgorin_noalloc(gbe_ctx* ctx, const gbe_csr* H, double* bounds) {
@@ -164,9 +153,9 @@ extern "C" int gbe_gershgorin_noalloc(gbe_ctx* ctx, const gbe_csr* H, double* bo
     }
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     // the pointers are checked before anything is enqueued (no allocation, no synchronisation)
-    GBE_CHECK_ARG(device_memory_of(bounds, ctx->device), "bounds is not device memory of the context's GPU");
-    GBE_CHECK_ARG(device_memory_of(H->rowptr, ctx->device) && device_memory_of(H->col, ctx->device) &&
-                      device_memory_of(H->val, ctx->device),
+    GBE_CHECK_ARG(gbe_device_memory_of(bounds, ctx->device), "bounds is not device memory of the context's GPU");
+    GBE_CHECK_ARG(gbe_device_memory_of(H->rowptr, ctx->device) && gbe_device_memory_of(H->col, ctx->device) &&
+                      gbe_device_memory_of(H->val, ctx->device),
                   "H arrays are not device memory of the context's GPU (on_device = 1 needs device pointers)");
     unsigned long long* scratch = nullptr;
     GBE_TRY(scratch_for(ctx->device, &scratch));

@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "decide.cuh"
+#include "devmem.h"
 #include "gbe_internal.h"
 #include "split.cuh"
 
@@ -1411,6 +1412,7 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && H && parts && prm && X, "NULL argument");
     GBE_CHECK_ARG(H->on_device, "gbe_sp2_run needs a device CSR (use gbe_sp2_submatrices for host H)");
+    GBE_TRY(gbe_check_device_csr(ctx, H, "gbe_sp2_run H"));
     GBE_CHECK_ARG(X->parts == parts, "state was created for another partition");
     GBE_CHECK_ARG(H->n == parts->n, "H and partition sizes differ");
     GBE_CHECK_ARG(prm->prec == X->prec, "params.prec differs from the state's precision");
@@ -1641,8 +1643,9 @@ static int assemble_device(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* par
 }
 
 // Device ELL buffers for D: D's own when on the device, else a staging pair (tmp).
-static int ell_device_buffers(const gbe_ell* D, void** tmp, int32_t** col, double** val) {
+static int ell_device_buffers(const gbe_ctx* ctx, const gbe_ell* D, void** tmp, int32_t** col, double** val) {
     const int64_t total = D->n * D->width;
+    GBE_TRY(gbe_check_device_ell(ctx, D, "D"));
     *tmp = nullptr;
     *col = D->col;
     *val = D->val;
@@ -1691,7 +1694,7 @@ extern "C" int gbe_assemble_D(gbe_ctx* ctx, const gbe_subs* X, const gbe_parts* 
     void* tmp = nullptr;
     int32_t* col;
     double* val;
-    GBE_TRY(ell_device_buffers(D, &tmp, &col, &val));
+    GBE_TRY(ell_device_buffers(ctx, D, &tmp, &col, &val));
     int r = assemble_device(ctx, X, parts, drop_tol, D->width, col, val, true);
     if (r == GBE_OK) r = ell_finish(ctx, D, col, val);
     if (tmp) gbe_free(tmp);
@@ -1750,7 +1753,7 @@ extern "C" int gbe_sp2_replay_batched(gbe_ctx* ctx, const gbe_csr* H, const gbe_
     void* tmp = nullptr;
     int32_t* col;
     double* val;
-    GBE_TRY(ell_device_buffers(D, &tmp, &col, &val));
+    GBE_TRY(ell_device_buffers(ctx, D, &tmp, &col, &val));
     int r = GBE_OK;
     if (!parts->cores_cover) fill_ell_kernel<<<ctx->sm_count * 4, 256, 0, ctx->stream>>>(D->n * D->width, col, val);
     for (int b = 0; b < B && r == GBE_OK; ++b) {
@@ -1852,6 +1855,7 @@ extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     AllocScope alloc_scope_(ctx);
     GBE_CHECK_ARG(ctx && H && parts && prm && X, "NULL argument");
     GBE_CHECK_ARG(H->on_device, "gbe_foe_run needs a device CSR");
+    GBE_TRY(gbe_check_device_csr(ctx, H, "gbe_foe_run H"));
     GBE_CHECK_ARG(X->parts == parts && H->n == parts->n, "state / partition / H mismatch");
     GBE_CHECK_ARG(X->prec == GBE_PREC_FP64 || X->prec == GBE_PREC_FP16X6, "Chebyshev expansion supports FP64 and FP16X6");
     GBE_CHECK_ARG(prm->order >= 1 && prm->order <= 100000, "order out of range");

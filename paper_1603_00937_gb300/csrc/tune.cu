@@ -10,6 +10,7 @@
 #include <cstring>
 #include <limits>
 
+#include "devmem.h"
 #include "gbe_internal.h"
 
 namespace {
@@ -57,6 +58,7 @@ extern "C" int gbe_sp2_autotune(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts*
     GBE_CHECK_ARG(ctx && H && parts && prm && X && rep, "NULL argument");
     GBE_CHECK_ARG(reps >= 1 && reps <= 1000, "reps must be in 1..1000");
     GBE_CHECK_ARG(H->on_device, "gbe_sp2_autotune needs a device CSR");
+    GBE_TRY(gbe_check_device_csr(ctx, H, "gbe_sp2_autotune H"));
     GBE_CUDA_TRY(cudaSetDevice(ctx->device));
     memset(rep, 0, sizeof(*rep));
 

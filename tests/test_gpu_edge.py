@@ -18,7 +18,7 @@ from oracle import sp2
 
 pytestmark = pytest.mark.gpu
 
-from tests.gpu_helpers import assembled_dense, device_csr, gbe, import_parts, lattice_case, oracle_graph_sp2  # noqa: E402
+from tests.gpu_helpers import assembled_dense, device_csr, gbe, import_parts, lattice_case, oracle_graph_sp2, torch  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -152,3 +152,37 @@ def test_replay_longer_than_n_max_rejected(ctx):
     assert e.value.code == gbe.GBE_EINVAL and "n_max" in str(e.value)
     X, rep = gbe.sp2_submatrices(ctx, Hd, parts, gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6, seq=seq, n_max=6))
     assert rep["iters"] == 6 and rep["seq"] == seq and rep["stop"] == "replay"
+
+
+def test_host_arrays_flagged_as_device_are_refused(ctx):
+    """Host arrays passed with on_device = 1 (H to gbe_sp2_run, D to gbe_assemble_D) are
+    refused with GBE_EINVAL before anything is enqueued; the context keeps working."""
+    import ctypes
+
+    from tests.gpu_helpers import host_csr
+    w, H, S, subs, nc = lattice_case(6, seed=3, thr=1e-2, ncell=(3, 3, 3))
+    N = H.shape[0]
+    parts = import_parts(ctx, N, subs, nc)
+    Hh = host_csr(H)
+    lie = gbe.Csr(Hh.n, Hh.nnz, Hh.rowptr, Hh.col, Hh.val, 1)
+    lie._keep = Hh
+    prm = gbe.sp2_params(N // 2, prec=gbe.PREC_FP16X6)
+    X = gbe.subs_create(ctx, parts, gbe.PREC_FP16X6)
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.sp2_run(ctx, lie, parts, prm, X)
+    assert e.value.code == gbe.GBE_EINVAL and "device memory" in str(e.value)
+    Hd = device_csr(H)
+    gbe.sp2_run(ctx, Hd, parts, prm, X)
+    n, width = gbe.assemble_width(ctx, X, parts)
+    colh = np.zeros((n, width), np.int32)
+    valh = np.zeros((n, width), np.float64)
+    e_lie = gbe.Ell(n, width, colh.ctypes.data, valh.ctypes.data, 1)
+    code = gbe.load_library().gbe_assemble_D(ctx.handle, X.handle, parts.handle, 0.0, ctypes.byref(e_lie))
+    assert code == gbe.GBE_EINVAL
+    gbe.assemble_D(ctx, X, parts, colh, valh)
+    cold = torch.empty((n, width), dtype=torch.int32, device="cuda")
+    vald = torch.empty((n, width), dtype=torch.float64, device="cuda")
+    gbe.assemble_D(ctx, X, parts, cold, vald)
+    torch.cuda.synchronize()
+    assert np.array_equal(colh, cold.cpu().numpy()) and np.array_equal(valh, vald.cpu().numpy())
+    assert np.isfinite(valh).all()

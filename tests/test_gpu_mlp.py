@@ -234,6 +234,10 @@ def test_labels_from_assembled_D(ctx, dis, tau):
     assert absent.any() and 0.0 < y.mean() < 1.0
     with pytest.raises(gbe.GbeError):
         gbe.mlp_labels(ctx, P, col.cpu(), val.cpu(), tau, lab)
+    # labels in host memory are refused before the kernel could write them
+    with pytest.raises(gbe.GbeError) as e:
+        gbe.mlp_labels(ctx, P, col, val, tau, np.zeros(len(I), np.uint8))
+    assert e.value.code == gbe.GBE_EINVAL and "device memory" in str(e.value)
 
 
 TRAIN_SEEDS = range(1000, 1008)   # eight seeded, jittered 16^3 lattices (4096 sites each)
