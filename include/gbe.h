@@ -62,7 +62,9 @@ typedef struct gbe_hamiltonian gbe_hamiltonian;
 
 /* Sparse symmetric H in CSR: rows [0, n); column indices ascending within a row;
  * the diagonal entry of every row present.  rowptr[n+1] int64, col[nnz] int32,
- * val[nnz] float64.  on_device = 1: device pointers; 0: host pointers (copied in). */
+ * val[nnz] float64.  on_device = 1: device pointers; 0: host pointers (copied in).
+ * Arrays flagged on_device = 1 that are not device (or managed) memory of the context's
+ * GPU are refused with GBE_EINVAL before any launch, here and in gbe_ell and gbe_sites. */
 typedef struct {
     int64_t n, nnz;
     const int64_t* rowptr;
