@@ -128,13 +128,17 @@ static __global__ void pos_f32_kernel(const double* __restrict__ pos, int64_t n,
 // Cheap pre-filter of a candidate pair in FP32: rejects only pairs whose FP32 minimum-image
 // distance exceeds the cutoff plus a margin larger than the FP32 error of the positions and
 // of the box (see filter_lim2), so every pair the exact FP64 test accepts passes.
-__device__ __forceinline__ bool near_f32(float4 a, float4 b, float bx, float by, float bz, float ix, float iy, float iz,
-                                         float lim2) {
+__device__ __forceinline__ float dist2_f32(float4 a, float4 b, float bx, float by, float bz, float ix, float iy,
+                                           float iz) {
     float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
     dx -= bx * rintf(dx * ix);
     dy -= by * rintf(dy * iy);
     dz -= bz * rintf(dz * iz);
-    return dx * dx + dy * dy + dz * dz < lim2;
+    return dx * dx + dy * dy + dz * dz;
+}
+__device__ __forceinline__ bool near_f32(float4 a, float4 b, float bx, float by, float bz, float ix, float iy, float iz,
+                                         float lim2) {
+    return dist2_f32(a, b, bx, by, bz, ix, iy, iz) < lim2;
 }
 // (cutoff + margin)^2 with margin = 1e-3 + 2^-16 * box: FP32 positions and box lengths are
 // off by at most 2^-24 * box each, so the FP32 separation is within ~2^-21 * box of the exact one
@@ -142,6 +146,16 @@ static inline float filter_lim2(double cutoff, const double box[3]) {
     const double bmax = std::max(box[0], std::max(box[1], box[2]));
     const double lim = cutoff + 1e-3 + bmax * (1.0 / 65536.0);
     return (float)(lim * lim);
+}
+// The inner bound: (cutoff - margin)^2, rounded down, or 0.  A pair whose FP32 squared
+// separation is below it lies inside the cutoff in exact arithmetic too (the margin is ~100
+// times the FP32 error), so the exact FP64 test is needed only between the two bounds.
+static inline float filter_lim2_in(double cutoff, const double box[3]) {
+    const double bmax = std::max(box[0], std::max(box[1], box[2]));
+    const double lim = cutoff - 1e-3 - bmax * (1.0 / 65536.0);
+    if (lim <= 0.0) return 0.0f;
+    const float l2 = (float)(lim * lim);
+    return (double)l2 > lim * lim ? std::nextafter(l2, 0.0f) : l2;
 }
 
 // squared minimum-image distance between sites i and j of a [n][3] position array

@@ -122,7 +122,7 @@ __global__ void cell_sort_kernel(const int64_t* __restrict__ start, int ncells, 
 }
 
 struct HModel {
-    double a, rcut, decay, hop, rcut2;
+    double a, rcut, inv_decay, hop, rcut2;
 };
 
 constexpr int kRowCap = 1024;
@@ -145,7 +145,7 @@ __global__ void compact_rows_kernel(const int32_t* __restrict__ scol, const doub
 // One warp per row.  pass 0: count neighbours; pass 1: write sorted (col, val).
 __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ pos, const float4* __restrict__ pos4,
                                                      const double* __restrict__ onsite, int64_t n, CellGrid g,
-                                                     float lim2, const int64_t* __restrict__ cstart,
+                                                     float lim2, float lim2_in, const int64_t* __restrict__ cstart,
                                                      const int32_t* __restrict__ members, HModel mdl, int pass,
                                                      int32_t* cnt, const int64_t* __restrict__ rowptr, int32_t* col,
                                                      double* val, int* overflow) {
@@ -203,10 +203,11 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
         const int64_t p = __shfl_sync(0xffffffffu, c0, c) + (t - __shfl_sync(0xffffffffu, excl, c));
         if (t < total) {
             const int j = members[p];
-            // FP32 pre-filter, then r^2 < rcut^2 in FP64 (differs from r < rcut only within an ulp
-            // of the cutoff)
-            if (j == i ||
-                (near_f32(pi, pos4[j], bx, by, bz, ix, iy, iz, lim2) && pair_dist2(pos, xi, yi, zi, j, g) < mdl.rcut2)) {
+            // FP32 separation first: below the inner bound the pair is inside, above the outer one
+            // outside; between them r^2 < rcut^2 decides in FP64 (which differs from r < rcut
+            // only within an ulp of the cutoff)
+            const float r2f = j == i ? 0.0f : dist2_f32(pi, pos4[j], bx, by, bz, ix, iy, iz);
+            if (j == i || r2f < lim2_in || (r2f < lim2 && pair_dist2(pos, xi, yi, zi, j, g) < mdl.rcut2)) {
                 const int k = atomicAdd(&bcount[w], 1);
                 if (k < kRowCap) buf[w][k] = j;
             }
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(256) hbuild_kernel(const double* __restrict__ 
             v = onsite[i];
         } else {
             const double r = sqrt(pair_dist2(pos, xi, yi, zi, j, g));
-            v = mdl.hop * exp(-(r - mdl.a) / mdl.decay);
+            v = mdl.hop * exp(-(r - mdl.a) * mdl.inv_decay);
         }
         col[base + t] = j;
         val[base + t] = v;
@@ -518,36 +519,58 @@ __global__ void compact_set_rows_kernel(const int32_t* __restrict__ stage, int64
 }
 
 // ELL D -> pattern of kept entries (|D_ki| >= tau) as CSR by ELL row (row i lists k),
-// and the transposed lists (row k lists i).
-__global__ void ell_count_kernel(const int32_t* __restrict__ col, const double* __restrict__ val, int64_t n, int64_t W,
-                                 double tau, int32_t* cnt_own, int32_t* cnt_tr) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int own = 0;
-    for (int64_t t = 0; t < W; ++t) {
-        const int k = col[i * W + t];
-        if (k < 0) break;
-        if (fabs(val[i * W + t]) >= tau) {
-            ++own;
-            atomicAdd(&cnt_tr[k], 1);
-        }
-    }
-    cnt_own[i] = own;
+// and the transposed lists (row k lists i).  A warp per ELL row, 32 consecutive entries at
+// a time (coalesced); an entry is kept when it lies before the row's first padding entry
+// (col < 0) and |val| >= tau.  The order within a list is free (the union that consumes
+// the lists sorts every row).
+constexpr int kEllWarps = 8;
+
+// The kept entries of ELL row i's chunk t0..t0+31: the lane's column (or -1) and whether the
+// row ends in this chunk.
+__device__ __forceinline__ int ell_kept(const int32_t* __restrict__ col, const double* __restrict__ val, int64_t i,
+                                        int64_t W, int64_t t0, double tau, int lane, bool& last) {
+    const int64_t t = t0 + lane;
+    const int k = t < W ? col[i * W + t] : -1;
+    const unsigned pad = __ballot_sync(0xffffffffu, k < 0);
+    const int limit = pad ? __ffs(pad) - 1 : 32;
+    last = pad != 0;
+    return (lane < limit && fabs(val[i * W + t]) >= tau) ? k : -1;
 }
 
-__global__ void ell_fill_kernel(const int32_t* __restrict__ col, const double* __restrict__ val, int64_t n, int64_t W,
-                                double tau, const int64_t* __restrict__ rp_own, int32_t* ci_own,
-                                const int64_t* __restrict__ rp_tr, int32_t* cur_tr, int32_t* ci_tr) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * kEllWarps) ell_count_kernel(const int32_t* __restrict__ col,
+                                                                   const double* __restrict__ val, int64_t n, int64_t W,
+                                                                   double tau, int32_t* cnt_own, int32_t* cnt_tr) {
+    const int64_t i = (int64_t)blockIdx.x * kEllWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;   // whole warps
+    int own = 0;
+    bool last = false;
+    for (int64_t t0 = 0; t0 < W && !last; t0 += 32) {
+        const int k = ell_kept(col, val, i, W, t0, tau, lane, last);
+        own += __popc(__ballot_sync(0xffffffffu, k >= 0));
+        if (k >= 0) atomicAdd(&cnt_tr[k], 1);
+    }
+    if (lane == 0) cnt_own[i] = own;
+}
+
+__global__ void __launch_bounds__(32 * kEllWarps) ell_fill_kernel(const int32_t* __restrict__ col,
+                                                                  const double* __restrict__ val, int64_t n, int64_t W,
+                                                                  double tau, const int64_t* __restrict__ rp_own,
+                                                                  int32_t* ci_own, const int64_t* __restrict__ rp_tr,
+                                                                  int32_t* cur_tr, int32_t* ci_tr) {
+    const int64_t i = (int64_t)blockIdx.x * kEllWarps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (i >= n) return;
     int64_t o = rp_own[i];
-    for (int64_t t = 0; t < W; ++t) {
-        const int k = col[i * W + t];
-        if (k < 0) break;
-        if (fabs(val[i * W + t]) >= tau) {
-            ci_own[o++] = k;
+    bool last = false;
+    for (int64_t t0 = 0; t0 < W && !last; t0 += 32) {
+        const int k = ell_kept(col, val, i, W, t0, tau, lane, last);
+        const unsigned keep = __ballot_sync(0xffffffffu, k >= 0);
+        if (k >= 0) {
+            ci_own[o + __popc(keep & ((1u << lane) - 1u))] = k;
             ci_tr[rp_tr[k] + atomicAdd(&cur_tr[k], 1)] = (int32_t)i;
         }
+        o += __popc(keep);
     }
 }
 
@@ -761,18 +784,18 @@ extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gb
     cell_count_kernel<<<nb, 256, 0, s>>>(pos, n, g, cell.as<int32_t>(), ccnt.as<int32_t>());
     GBE_TRY(scan_exclusive(ctx, ccnt.as<int32_t>(), cstart.as<int64_t>(), ncells, nullptr));
     cell_fill_kernel<<<nb, 256, 0, s>>>(cell.as<int32_t>(), n, cstart.as<int64_t>(), cur.as<int32_t>(), mem.as<int32_t>());
-    HModel mdl{model->a, model->rcut, model->decay, model->hop, model->rcut * model->rcut};
+    HModel mdl{model->a, model->rcut, 1.0 / model->decay, model->hop, model->rcut * model->rcut};
     DevBuf p4;
     GBE_TRY(gbe_alloc(&p4.p, n * 16));
     pos_f32_kernel<<<nb, 256, 0, s>>>(pos, n, p4.as<float4>());
-    const float lim2 = filter_lim2(model->rcut, st->box);
+    const float lim2 = filter_lim2(model->rcut, st->box), lim2_in = filter_lim2_in(model->rcut, st->box);
     const unsigned rb = (unsigned)((n + 7) / 8);
     // one neighbour search: sorted rows into staging slots, then a compaction; a row longer
     // than a slot falls back to a second search that writes the CSR directly
     DevBuf scol, sval;
     GBE_TRY(gbe_alloc(&scol.p, n * kStageCap * 4));
     GBE_TRY(gbe_alloc(&sval.p, n * kStageCap * 8));
-    hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 2,
+    hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, lim2_in, cstart.as<int64_t>(), mem.as<int32_t>(), mdl, 2,
                                      cnt.as<int32_t>(),
                                      nullptr, scol.as<int32_t>(), sval.as<double>(), flag.as<int>());
     GBE_CUDA_TRY(cudaGetLastError());
@@ -799,7 +822,7 @@ extern "C" int gbe_build_hamiltonian(gbe_ctx* ctx, const gbe_sites* st, const gb
         compact_rows_kernel<<<(unsigned)((n * kStageCap + 255) / 256), 256, 0, s>>>(
             scol.as<int32_t>(), sval.as<double>(), n, H->rowptr, H->col, H->val);
     else
-        hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cstart.as<int64_t>(), mem.as<int32_t>(), mdl,
+        hbuild_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, lim2_in, cstart.as<int64_t>(), mem.as<int32_t>(), mdl,
                                          1, cnt.as<int32_t>(), H->rowptr, H->col, H->val, flag.as<int>());
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -886,15 +909,16 @@ extern "C" int gbe_build_graph(gbe_ctx* ctx, const gbe_csr* Hin, const gbe_graph
             if (r != GBE_OK) break;
             cudaMemsetAsync(ct.p, 0, n * 4, ctx->stream);
             cudaMemsetAsync(cur.p, 0, n * 4, ctx->stream);
-            const unsigned nb = (unsigned)((n + 255) / 256);
-            ell_count_kernel<<<nb, 256, 0, ctx->stream>>>(ecol, eval, n, D->width, p->thresh, co.as<int32_t>(), ct.as<int32_t>());
+            const unsigned nb = (unsigned)((n + kEllWarps - 1) / kEllWarps);
+            ell_count_kernel<<<nb, 32 * kEllWarps, 0, ctx->stream>>>(ecol, eval, n, D->width, p->thresh, co.as<int32_t>(),
+                                                                     ct.as<int32_t>());
             int64_t no = 0, nt = 0;
             r = scan_exclusive(ctx, co.as<int32_t>(), rpo.as<int64_t>(), n, &no);
             if (r == GBE_OK) r = scan_exclusive(ctx, ct.as<int32_t>(), rpt.as<int64_t>(), n, &nt);
             if (r == GBE_OK) r = gbe_alloc(&cio.p, std::max<int64_t>(no, 1) * 4);
             if (r == GBE_OK) r = gbe_alloc(&cit.p, std::max<int64_t>(nt, 1) * 4);
             if (r != GBE_OK) break;
-            ell_fill_kernel<<<nb, 256, 0, ctx->stream>>>(ecol, eval, n, D->width, p->thresh, rpo.as<int64_t>(),
+            ell_fill_kernel<<<nb, 32 * kEllWarps, 0, ctx->stream>>>(ecol, eval, n, D->width, p->thresh, rpo.as<int64_t>(),
                                                          cio.as<int32_t>(), rpt.as<int64_t>(), cur.as<int32_t>(), cit.as<int32_t>());
             const bool eq8 = (p->mode == GBE_GRAPH_EQ8_SYMBOLIC);
             r = rowset_csr(ctx, 1, n, nullptr, 0.0, rpo.as<int64_t>(), cio.as<int32_t>(), rpt.as<int64_t>(),

@@ -35,7 +35,7 @@ constexpr int kLd = 68;            // padded row length of the batch activations
 // ------------------------------------------------------------------ candidate pairs + features
 __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ pos, const float4* __restrict__ pos4,
                                                     const double* __restrict__ onsite, int64_t n, CellGrid g, float lim2,
-                                                    const int64_t* __restrict__ cstart,
+                                                    float lim2_in, const int64_t* __restrict__ cstart,
                                                     const int32_t* __restrict__ members, double rcand, int pass,
                                                     int32_t* cnt, const int64_t* __restrict__ rowptr, int32_t* pj,
                                                     float* feat, const int64_t* __restrict__ hrp,
@@ -70,8 +70,10 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
                 for (int64_t p = cstart[cell] + lane; p < cstart[cell + 1]; p += 32) {
                     const int j = members[p];
                     if (j == i) continue;
-                    // FP32 pre-filter, then r < rcand in FP64 (up to an ulp at the cutoff)
-                    if (near_f32(pi, pos4[j], bx, by, bz, ix, iy, iz, lim2) && pair_dist2(pos, xi, yi, zi, j, g) < rcand2) {
+                    // FP32 separation: inside the inner bound kept, outside the outer one dropped,
+                    // between them r < rcand in FP64 (up to an ulp at the cutoff)
+                    const float r2f = dist2_f32(pi, pos4[j], bx, by, bz, ix, iy, iz);
+                    if (r2f < lim2_in || (r2f < lim2 && pair_dist2(pos, xi, yi, zi, j, g) < rcand2)) {
                         const int k = atomicAdd(&bcount[w], 1);
                         if (k < kPairCap) buf[w][k] = j;
                     }
@@ -709,8 +711,8 @@ extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr*
     DevBuf p4;
     GBE_TRY(gbe_alloc(&p4.p, n * 16));
     pos_f32_kernel<<<nb, 256, 0, s>>>(pos, n, p4.as<float4>());
-    const float lim2 = filter_lim2(rcand, st->box);
-    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 0,
+    const float lim2 = filter_lim2(rcand, st->box), lim2_in = filter_lim2_in(rcand, st->box);
+    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, lim2_in, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 0,
                                     cnt.as<int32_t>(),
                                     nullptr, nullptr, nullptr, rp, ci, va, flag.as<int>());
     GBE_CUDA_TRY(cudaGetLastError());
@@ -726,7 +728,7 @@ extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr*
     if (r == GBE_OK) r = gbe_alloc((void**)&P->feat, std::max<int64_t>(np, 1) * kNF * 4);
     if (r != GBE_OK) { gbe_free_pairs(P); return r; }
     P->npairs = np;
-    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 1,
+    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, lim2_in, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 1,
                                     cnt.as<int32_t>(),
                                     P->rowptr, P->j, P->feat, rp, ci, va, flag.as<int>());
     cudaError_t e = cudaGetLastError();

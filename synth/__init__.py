@@ -52,7 +52,22 @@ def velocities(N, sigma=0.01, a=1.0, seed=1):
 
 
 def advance(pos, vel, box, steps=1):
-    """Positions after `steps` constant-velocity steps, wrapped into [0, box)."""
-    p = np.mod(pos + steps * vel, box)
-    p[p >= box] -= box[0]
+    """Positions after `steps` constant-velocity steps, wrapped into [0, box).
+
+    The value is np.mod(pos + steps * vel, box), with a result that rounds up to its axis's
+    box length moved back by that length.  In a cubic box, when every coordinate stays within one box
+    length of [0, box), the wrap is taken with masked in-place adds instead of np.mod (its
+    per-element floor and remainder are far slower, and a (3,)-shaped divisor broadcasts in
+    inner loops of three): y in [0, b) is unchanged, y in [b, 2b) becomes y - b (exact), and
+    y in (-b, 0) becomes fl(y + b), which are np.mod's results on those ranges."""
+    y = pos + steps * vel
+    b = float(box[0])
+    if box[0] == box[1] == box[2] and y.min() > -b and y.max() < 2.0 * b:
+        np.add(y, b, out=y, where=y < 0.0)
+        np.subtract(y, b, out=y, where=y >= b)
+        if y.max() >= b:
+            y[y >= b] -= b
+        return np.ascontiguousarray(y)
+    p = np.mod(y, box)
+    p -= box * (p >= box)
     return np.ascontiguousarray(p)

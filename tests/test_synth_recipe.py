@@ -110,3 +110,36 @@ def test_velocities_and_advance():
         np.testing.assert_allclose(d / w["box"], np.round(d / w["box"]), atol=1e-12)
     # after 100 steps (displacement std 1a) sites at the faces have wrapped across them
     assert np.any(np.abs(d) > 1.0)
+
+
+def test_advance_equals_the_plain_remainder():
+    """synth.advance's masked wrap gives np.mod's bits: on lattices over short and long runs
+    (the long ones take the np.mod path), and on values at 0, just below the box length, with
+    denormal steps and with steps that land a hair below 0 (fl(y + b) rounds to b there)."""
+    def plain(pos, vel, box, steps):
+        p = np.mod(pos + steps * vel, box)
+        p -= box * (p >= box)
+        return p
+    for L in (4, 8, 32):
+        w = synth.lattice(L, seed=L)
+        v = synth.velocities(w["pos"].shape[0], seed=L + 1)
+        for steps in (0, 1, 3, 17, 64, 300, 5000, 100000):
+            a = synth.advance(w["pos"], v, w["box"], steps)
+            assert np.array_equal(a, plain(w["pos"], v, w["box"], steps))
+            assert np.all(a >= 0) and np.all(a < w["box"])
+    rng = np.random.default_rng(0)
+    box = np.array([10.0, 10.0, 10.0])
+    p0 = rng.uniform(0, 10, (20000, 3))
+    v0 = rng.choice([-1.0, 1.0], (20000, 3)) * rng.uniform(0, 1e-3, (20000, 3))
+    p0[:100] = 0.0
+    p0[100:200] = np.nextafter(10.0, 0.0)
+    v0[:50] = -1e-300
+    v0[50:100] = -5e-324
+    v0[200:300] = -(p0[200:300] + 1e-17)
+    for steps in (1, 2, 7):
+        a = synth.advance(p0, v0, box, steps)
+        assert np.array_equal(a, plain(p0, v0, box, steps))
+        assert np.all(a >= 0) and np.all(a < box)
+    # a non-cubic box takes the plain path
+    box2 = np.array([10.0, 12.0, 14.0])
+    assert np.array_equal(synth.advance(p0, v0, box2, 3), plain(p0, v0, box2, 3))
