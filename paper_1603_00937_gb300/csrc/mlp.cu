@@ -33,6 +33,36 @@ constexpr int kBatch = 128;        // pairs per training batch (one per thread)
 constexpr int kLd = 68;            // padded row length of the batch activations (floats)
 
 // ------------------------------------------------------------------ candidate pairs + features
+constexpr int kPairStage = 512;    // staging slot per site of the single-pass pair search
+
+// Features 0, 2, 3, 4 of the pair (i, j): -log10|H_ij| / 12 (H_ij by binary search in row i),
+// r / rcand, min and max of the two onsite energies.  Feature 1, the (H^2)_ij feature, is
+// written by h2_feature_kernel.
+__device__ __forceinline__ void pair_features(const double* __restrict__ pos, const double* __restrict__ onsite,
+                                              const CellGrid& g, int64_t i, double xi, double yi, double zi,
+                                              double ei, int j, double rcand, const int64_t* __restrict__ hrp,
+                                              const int32_t* __restrict__ hci, const double* __restrict__ hva,
+                                              float* f) {
+    const double r = sqrt(pair_dist2(pos, xi, yi, zi, j, g));
+    double hij = 0.0;
+    int64_t a = hrp[i], b = hrp[i + 1] - 1;
+    while (a <= b) {
+        const int64_t mid = (a + b) >> 1;
+        const int v = hci[mid];
+        if (v == j) { hij = hva[mid]; break; }
+        if (v < j) a = mid + 1; else b = mid - 1;
+    }
+    const double ej = onsite[j];
+    f[0] = -log10f(fmaxf((float)fabs(hij), 1e-12f)) / 12.0f;
+    f[2] = (float)(r / rcand);
+    f[3] = (float)fmin(ei, ej);
+    f[4] = (float)fmax(ei, ej);
+}
+
+// One warp per site.  pass 2: count the site's candidates and write them sorted into its
+// staging slot of kPairStage entries (pair_stage_kernel then writes the CSR and the
+// features); a site with more sets overflow[1], and the host runs pass 1, which writes the
+// sorted candidates and their features into the CSR directly.
 __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ pos, const float4* __restrict__ pos4,
                                                     const double* __restrict__ onsite, int64_t n, CellGrid g, float lim2,
                                                     float lim2_in, const int64_t* __restrict__ cstart,
@@ -60,34 +90,64 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
         if (g.nc[d] >= 3) { lo[d] = -1; hi[d] = 1; }
         else { lo[d] = -cc[d]; hi[d] = g.nc[d] - 1 - cc[d]; }
     }
-    for (int dx = lo[0]; dx <= hi[0]; ++dx)
-        for (int dy = lo[1]; dy <= hi[1]; ++dy)
-            for (int dz = lo[2]; dz <= hi[2]; ++dz) {
-                const int ax = (cc[0] + dx + g.nc[0]) % g.nc[0];
-                const int ay = (cc[1] + dy + g.nc[1]) % g.nc[1];
-                const int az = (cc[2] + dz + g.nc[2]) % g.nc[2];
-                const int cell = (ax * g.nc[1] + ay) * g.nc[2] + az;
-                for (int64_t p = cstart[cell] + lane; p < cstart[cell + 1]; p += 32) {
-                    const int j = members[p];
-                    if (j == i) continue;
-                    // FP32 separation: inside the inner bound kept, outside the outer one dropped,
-                    // between them r < rcand in FP64 (up to an ulp at the cutoff)
-                    const float r2f = dist2_f32(pi, pos4[j], bx, by, bz, ix, iy, iz);
-                    if (r2f < lim2_in || (r2f < lim2 && pair_dist2(pos, xi, yi, zi, j, g) < rcand2)) {
-                        const int k = atomicAdd(&bcount[w], 1);
-                        if (k < kPairCap) buf[w][k] = j;
-                    }
+    // the (at most 27) neighbour cells' member ranges, one per lane, and their exclusive prefix
+    // sums: the candidates of all cells are one flat range across the lanes (the row is sorted
+    // afterwards, so the order found is free)
+    const int ncx = hi[0] - lo[0] + 1, ncy = hi[1] - lo[1] + 1, ncz = hi[2] - lo[2] + 1;
+    const int ncell = ncx * ncy * ncz;
+    int64_t c0 = 0;
+    int clen = 0;
+    if (lane < ncell) {
+        const int dx = lo[0] + lane / (ncy * ncz), dy = lo[1] + (lane / ncz) % ncy, dz = lo[2] + lane % ncz;
+        const int ax = (cc[0] + dx + g.nc[0]) % g.nc[0];
+        const int ay = (cc[1] + dy + g.nc[1]) % g.nc[1];
+        const int az = (cc[2] + dz + g.nc[2]) % g.nc[2];
+        const int cell = (ax * g.nc[1] + ay) * g.nc[2] + az;
+        c0 = cstart[cell];
+        clen = (int)(cstart[cell + 1] - c0);
+    }
+    int incl = clen;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int excl = incl - clen;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    // (every lane runs every iteration: the shuffles need the whole warp)
+    for (int t0 = 0; t0 < total; t0 += 32) {
+        const int t = t0 + lane;
+        // the candidate's cell: the last one whose range starts at or before t
+        int c = 0;
+        for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(0xffffffffu, excl, (c + step) & 31);
+            if (c + step < ncell && e <= t) c += step;
+        }
+        const int64_t p = __shfl_sync(0xffffffffu, c0, c) + (t - __shfl_sync(0xffffffffu, excl, c));
+        if (t < total) {
+            const int j = members[p];
+            if (j != i) {
+                // FP32 separation: inside the inner bound kept, outside the outer one dropped,
+                // between them r < rcand in FP64 (up to an ulp at the cutoff)
+                const float r2f = dist2_f32(pi, pos4[j], bx, by, bz, ix, iy, iz);
+                if (r2f < lim2_in || (r2f < lim2 && pair_dist2(pos, xi, yi, zi, j, g) < rcand2)) {
+                    const int k = atomicAdd(&bcount[w], 1);
+                    if (k < kPairCap) buf[w][k] = j;
                 }
             }
+        }
+    }
     __syncwarp();
     const int m = bcount[w];
     if (m > kPairCap) {
         if (lane == 0) atomicExch(overflow, 1);
         return;
     }
-    if (pass == 0) {
+    if (pass == 2) {
         if (lane == 0) cnt[i] = m;
-        return;
+        if (m > kPairStage) {
+            if (lane == 0) atomicExch(overflow + 1, 1);
+            return;
+        }
     }
     // bitonic sort of the m candidates, padded to a power of two with INT_MAX
     int np2 = 1;
@@ -103,38 +163,48 @@ __global__ void __launch_bounds__(256) pairs_kernel(const double* __restrict__ p
             }
             __syncwarp();
         }
+    if (pass == 2) {
+        for (int t = lane; t < m; t += 32) pj[i * kPairStage + t] = buf[w][t];   // pj = the staging slots
+        return;
+    }
     const int64_t base = rowptr[i];
     const double ei = onsite[i];
     for (int t = lane; t < m; t += 32) {
         const int j = buf[w][t];
-        const double r = sqrt(pair_dist2(pos, xi, yi, zi, j, g));
-        // H_ij by binary search in row i, (H^2)_ij by the ordered merge dot product
-        double hij = 0.0;
-        int64_t a = hrp[i], b = hrp[i + 1] - 1;
-        while (a <= b) {
-            const int64_t mid = (a + b) >> 1;
-            const int v = hci[mid];
-            if (v == j) { hij = hva[mid]; break; }
-            if (v < j) a = mid + 1; else b = mid - 1;
-        }
-        const double ej = onsite[j];
-        float* f = feat + (base + t) * kNF;
-        f[0] = -log10f(fmaxf((float)fabs(hij), 1e-12f)) / 12.0f;
-        // f[1], the (H^2)_ij feature, is written by h2_feature_kernel
-        f[2] = (float)(r / rcand);
-        f[3] = (float)fmin(ei, ej);
-        f[4] = (float)fmax(ei, ej);
+        pair_features(pos, onsite, g, i, xi, yi, zi, ei, j, rcand, hrp, hci, hva, feat + (base + t) * kNF);
         pj[base + t] = j;
     }
 }
 
-// Row i of H^2 for every site i, then the (H^2)_ij feature of its candidate pairs.  One warp
-// per site accumulates (H^2)_il = sum_k H_ik H_kl in a shared-memory hash table keyed by l,
-// taking k in ascending order (one row k at a time, its entries across the lanes): every
-// (H^2)_ij is then the same sequence of products and additions as the ordered merge of rows
-// i and j (H is symmetric to the last bit), so the feature is symmetric in (i, j) bit for
-// bit.  A row of H^2 with more entries than the table holds is computed by that merge.
-constexpr int kH2Slots = 1024;   // hash slots per warp (a row of H^2 within 5a has ~520 entries)
+// Staged candidates (kPairStage apart) -> CSR and features 0, 2, 3, 4, one warp per site.
+__global__ void __launch_bounds__(256) pair_stage_kernel(const double* __restrict__ pos, const double* __restrict__ onsite,
+                                                         int64_t n, CellGrid g, double rcand,
+                                                         const int32_t* __restrict__ stage,
+                                                         const int64_t* __restrict__ rowptr, int32_t* pj, float* feat,
+                                                         const int64_t* __restrict__ hrp,
+                                                         const int32_t* __restrict__ hci,
+                                                         const double* __restrict__ hva) {
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const double xi = pos[3 * i], yi = pos[3 * i + 1], zi = pos[3 * i + 2];
+    const double ei = onsite[i];
+    const int64_t base = rowptr[i], m = rowptr[i + 1] - base;
+    for (int64_t t = lane; t < m; t += 32) {
+        const int j = stage[i * kPairStage + t];
+        pair_features(pos, onsite, g, i, xi, yi, zi, ei, j, rcand, hrp, hci, hva, feat + (base + t) * kNF);
+        pj[base + t] = j;
+    }
+}
+
+// The (H^2)_ij feature of every candidate pair.  One warp per site i keys a shared-memory hash
+// table by the site's candidates j and accumulates (H^2)_ij = sum_k H_ik H_kj into it, taking
+// k in ascending order (one row k at a time, its entries across the lanes; an entry l of row
+// k that is not a candidate is skipped): every (H^2)_ij is then the same sequence of products
+// and additions as the ordered merge of rows i and j (H is symmetric to the last bit), so the
+// feature is symmetric in (i, j) bit for bit.  A site with more candidates than half the
+// table is computed by that merge.
+constexpr int kH2Slots = 1024;   // hash slots per warp (a site has ~270 candidates within 4a)
 constexpr int kH2Warps = 4;
 constexpr size_t kH2Smem = (size_t)kH2Warps * kH2Slots * (4 + 8);
 
@@ -156,24 +226,52 @@ __global__ void __launch_bounds__(32 * kH2Warps) h2_feature_kernel(int64_t n, co
         vals[t] = 0.0;
     }
     __syncwarp();
-    bool ok = true;
-    for (int64_t p = hrp[i]; p < hrp[i + 1]; ++p) {
-        const int k = hci[p];
-        const double hik = hva[p];
-        for (int64_t q = hrp[k] + lane; q < hrp[k + 1]; q += 32) {
-            const int l = hci[q];
-            unsigned h = h2_hash(l);
-            int probes = 0;
-            while (true) {
-                const int old = atomicCAS(&keys[h], -1, l);
-                if (old == -1 || old == l) break;
-                if (++probes == kH2Slots) break;
+    // the table is keyed by the site's candidates (distinct j, at most half the slots, so
+    // every probe sequence ends at an empty slot); a product H_ik H_kl is added only when l
+    // is one of them, the other entries of row i of H^2 are not features
+    const int64_t c0 = prp[i], c1 = prp[i + 1];
+    bool ok = (c1 - c0) <= kH2Slots / 2;
+    if (ok) {
+        for (int64_t t = c0 + lane; t < c1; t += 32) {
+            const int j = pj[t];
+            unsigned h = h2_hash(j);
+            for (int probes = 0; probes < kH2Slots; ++probes) {
+                const int old = atomicCAS(&keys[h], -1, j);
+                if (old == -1 || old == j) break;
                 h = (h + 1) & (kH2Slots - 1);
             }
-            if (probes < kH2Slots) vals[h] = __dadd_rn(vals[h], __dmul_rn(hik, hva[q]));   // one lane per key
-            else ok = false;
         }
-        __syncwarp();
+    }
+    __syncwarp();
+    // row i's entries 32 at a time, each lane holding one k with its H_ik and the range of row
+    // k (loaded together), then taken in ascending order across the warp
+    const int64_t p0 = hrp[i], p1 = ok ? hrp[i + 1] : p0;
+    for (int64_t pb = p0; pb < p1; pb += 32) {
+        const int64_t pl = pb + lane;
+        double hl = 0.0;
+        int64_t ql0 = 0, ql1 = 0;
+        if (pl < p1) {
+            const int kl = hci[pl];
+            hl = hva[pl];
+            ql0 = hrp[kl];
+            ql1 = hrp[kl + 1];
+        }
+        const int nk = (p1 - pb) < 32 ? (int)(p1 - pb) : 32;
+        for (int u = 0; u < nk; ++u) {
+            const double hik = __shfl_sync(0xffffffffu, hl, u);
+            const int64_t q0 = __shfl_sync(0xffffffffu, ql0, u), q1 = __shfl_sync(0xffffffffu, ql1, u);
+            for (int64_t q = q0 + lane; q < q1; q += 32) {
+                const int l = hci[q];
+                unsigned h = h2_hash(l);
+                int key = keys[h];
+                for (int probes = 1; key != l && key != -1 && probes < kH2Slots; ++probes) {
+                    h = (h + 1) & (kH2Slots - 1);
+                    key = keys[h];
+                }
+                if (key == l) vals[h] = __dadd_rn(vals[h], __dmul_rn(hik, hva[q]));   // one lane per key
+            }
+            __syncwarp();
+        }
     }
     ok = __all_sync(0xffffffffu, ok);
     for (int64_t t = prp[i] + lane; t < prp[i + 1]; t += 32) {
@@ -699,10 +797,10 @@ extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr*
     GBE_TRY(gbe_alloc(&cur.p, ncells * 4));
     GBE_TRY(gbe_alloc(&mem.p, n * 4));
     GBE_TRY(gbe_alloc(&cnt.p, n * 4));
-    GBE_TRY(gbe_alloc(&flag.p, 4));
+    GBE_TRY(gbe_alloc(&flag.p, 8));   // [0] a site above kPairCap, [1] a site above kPairStage
     cudaMemsetAsync(ccnt.p, 0, ncells * 4, s);
     cudaMemsetAsync(cur.p, 0, ncells * 4, s);
-    cudaMemsetAsync(flag.p, 0, 4, s);
+    cudaMemsetAsync(flag.p, 0, 8, s);
     const unsigned nb = (unsigned)((n + 255) / 256);
     cell_count_kernel<<<nb, 256, 0, s>>>(pos, n, g, cell.as<int32_t>(), ccnt.as<int32_t>());
     GBE_TRY(scan_exclusive(ctx, ccnt.as<int32_t>(), cst.as<int64_t>(), ncells, nullptr));
@@ -712,25 +810,39 @@ extern "C" int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* st, const gbe_csr*
     GBE_TRY(gbe_alloc(&p4.p, n * 16));
     pos_f32_kernel<<<nb, 256, 0, s>>>(pos, n, p4.as<float4>());
     const float lim2 = filter_lim2(rcand, st->box), lim2_in = filter_lim2_in(rcand, st->box);
-    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, lim2_in, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 0,
+    // one search: sorted candidates into staging slots (pass 2); a site with more candidates
+    // than a slot sends the build through the counting and filling passes 0 and 1
+    DevBuf stage;
+    GBE_TRY(gbe_alloc(&stage.p, (size_t)n * kPairStage * 4));
+    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, lim2_in, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 2,
                                     cnt.as<int32_t>(),
-                                    nullptr, nullptr, nullptr, rp, ci, va, flag.as<int>());
+                                    nullptr, stage.as<int32_t>(), nullptr, rp, ci, va, flag.as<int>());
     GBE_CUDA_TRY(cudaGetLastError());
     gbe_pairs* P = new gbe_pairs();
     P->n = n;
     int r = gbe_alloc((void**)&P->rowptr, (n + 1) * 8);
     int64_t np = 0;
     if (r == GBE_OK) r = scan_exclusive(ctx, cnt.as<int32_t>(), P->rowptr, n, &np);
-    int ovf = 0;
-    if (r == GBE_OK) r = read_flag(ctx, flag.as<int>(), &ovf);
-    if (r == GBE_OK && ovf) { gbe_set_error("a site has more than %d candidates within rcand", kPairCap); r = GBE_ECAPACITY; }
+    int ovf[2] = {0, 0};
+    if (r == GBE_OK) {
+        cudaError_t fe = cudaMemcpyAsync(ovf, flag.p, 8, cudaMemcpyDeviceToHost, s);
+        if (fe == cudaSuccess) fe = cudaStreamSynchronize(s);
+        if (fe != cudaSuccess) {
+            gbe_set_error("pairs: reading the overflow flags: %s", cudaGetErrorString(fe));
+            r = GBE_ECUDA;
+        }
+    }
+    if (r == GBE_OK && ovf[0]) { gbe_set_error("a site has more than %d candidates within rcand", kPairCap); r = GBE_ECAPACITY; }
     if (r == GBE_OK) r = gbe_alloc((void**)&P->j, std::max<int64_t>(np, 1) * 4);
     if (r == GBE_OK) r = gbe_alloc((void**)&P->feat, std::max<int64_t>(np, 1) * kNF * 4);
     if (r != GBE_OK) { gbe_free_pairs(P); return r; }
     P->npairs = np;
-    pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, lim2_in, cst.as<int64_t>(), mem.as<int32_t>(), rcand, 1,
-                                    cnt.as<int32_t>(),
-                                    P->rowptr, P->j, P->feat, rp, ci, va, flag.as<int>());
+    if (!ovf[1])
+        pair_stage_kernel<<<rb, 256, 0, s>>>(pos, ons, n, g, rcand, stage.as<int32_t>(), P->rowptr, P->j, P->feat, rp, ci,
+                                             va);
+    else
+        pairs_kernel<<<rb, 256, 0, s>>>(pos, p4.as<float4>(), ons, n, g, lim2, lim2_in, cst.as<int64_t>(), mem.as<int32_t>(),
+                                        rcand, 1, cnt.as<int32_t>(), P->rowptr, P->j, P->feat, rp, ci, va, flag.as<int>());
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(h2_feature_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kH2Smem);

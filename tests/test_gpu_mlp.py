@@ -74,8 +74,11 @@ def dis(ctx):
 
 @pytest.mark.parametrize("kind", ["lattice", "disordered", "dense"])
 def test_pairs_and_features(ctx, kind, dis):
-    """"dense": density 3/a^3, whose rows of H^2 (~1600 sites within 5a) overflow the
-    per-warp hash table of the (H^2)_ij feature, so those sites take the ordered row merge."""
+    """Pairs, their order and features against the oracle.  "lattice" and "disordered" take the
+    single-pass search (candidates staged per site) and the candidate-keyed (H^2)_ij table;
+    "dense", density 3/a^3 (~800 candidates within 4a), has sites with more candidates than a
+    staging slot (512), so the build runs the filling pass, and more than half the table, so
+    those sites take the ordered row merge for (H^2)_ij."""
     if kind == "disordered":
         w, H, P, I, J, F = dis["w"], dis["H"], dis["P"], dis["I"], dis["J"], dis["F"]
     else:
