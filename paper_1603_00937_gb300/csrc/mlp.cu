@@ -202,13 +202,15 @@ __global__ void __launch_bounds__(256) pair_stage_kernel(const double* __restric
 // k in ascending order (one row k at a time, its entries across the lanes; an entry l of row
 // k that is not a candidate is skipped): every (H^2)_ij is then the same sequence of products
 // and additions as the ordered merge of rows i and j (H is symmetric to the last bit), so the
-// feature is symmetric in (i, j) bit for bit.  A site with more candidates than half the
-// table is computed by that merge.
-constexpr int kH2Slots = 1024;   // hash slots per warp (a site has ~270 candidates within 4a)
+// feature is symmetric in (i, j) bit for bit.  A site with more candidates than three
+// quarters of the table is computed by that merge.
+constexpr int kH2Bits = 9;
+constexpr int kH2Slots = 1 << kH2Bits;              // hash slots per warp (~270 candidates within 4a)
+constexpr int kH2MaxKeys = kH2Slots * 3 / 4;
 constexpr int kH2Warps = 4;
 constexpr size_t kH2Smem = (size_t)kH2Warps * kH2Slots * (4 + 8);
 
-__device__ __forceinline__ unsigned h2_hash(int l) { return ((unsigned)l * 2654435761u) >> 22; }   // 10 bits
+__device__ __forceinline__ unsigned h2_hash(int l) { return ((unsigned)l * 2654435761u) >> (32 - kH2Bits); }
 
 __global__ void __launch_bounds__(32 * kH2Warps) h2_feature_kernel(int64_t n, const int64_t* __restrict__ hrp,
                                                                     const int32_t* __restrict__ hci,
@@ -226,11 +228,11 @@ __global__ void __launch_bounds__(32 * kH2Warps) h2_feature_kernel(int64_t n, co
         vals[t] = 0.0;
     }
     __syncwarp();
-    // the table is keyed by the site's candidates (distinct j, at most half the slots, so
-    // every probe sequence ends at an empty slot); a product H_ik H_kl is added only when l
-    // is one of them, the other entries of row i of H^2 are not features
+    // the table is keyed by the site's candidates (distinct j, at most three quarters of the
+    // slots, so every probe sequence ends at an empty slot); a product H_ik H_kl is added only
+    // when l is one of them, the other entries of row i of H^2 are not features
     const int64_t c0 = prp[i], c1 = prp[i + 1];
-    bool ok = (c1 - c0) <= kH2Slots / 2;
+    bool ok = (c1 - c0) <= kH2MaxKeys;
     if (ok) {
         for (int64_t t = c0 + lane; t < c1; t += 32) {
             const int j = pj[t];
