@@ -536,7 +536,8 @@ typedef struct gbe_pairs gbe_pairs;
  * sites and H may be host or device; H must be symmetric with sorted rows ((H^2)_ij is
  * accumulated in row i over k ascending, which equals the row-j sum bit for bit when H is
  * symmetric to the last bit, as gbe_build_hamiltonian's H is).  GBE_ECAPACITY above 1024
- * candidates per site; GBE_EINVAL unless box > 2 rcand.  Synchronises. */
+ * candidates per site; GBE_EINVAL unless box > 2 rcand.  Temporary device memory: a
+ * staging slot of 512 candidates (2 KB) per site during the build.  Synchronises. */
 int gbe_pairs_build(gbe_ctx* ctx, const gbe_sites* sites, const gbe_csr* H, double rcand, gbe_pairs** pairs);
 int gbe_pairs_info(const gbe_pairs* pairs, int64_t* n, int64_t* npairs);
 /* Host copies of the pairs (not in the paper): rowptr[n+1] (int64), j[npairs] (int32),
