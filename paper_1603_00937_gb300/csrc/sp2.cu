@@ -983,6 +983,54 @@ static void make_items(const std::vector<int32_t>& dim, const std::vector<int32_
     }
 }
 
+// The number of items make_items builds for these arguments, and (rg non-NULL) each
+// subgraph's contiguous range of them, without building the list.
+static int64_t item_ranges(const std::vector<int32_t>& dim, const std::vector<int32_t>& cost, int tile, bool full,
+                           std::vector<int2>* rg) {
+    const int64_t P = (int64_t)dim.size();
+    std::vector<int64_t> order(P);
+    for (int64_t s = 0; s < P; ++s) order[s] = s;
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    int64_t n = 0;
+    for (int64_t s : order) {
+        const int64_t T = (dim[s] + tile - 1) / tile;
+        const int64_t c = full ? T * T : T * (T + 1) / 2;
+        if (rg) (*rg)[s] = make_int2((int)n, (int)c);
+        n += c;
+    }
+    return n;
+}
+
+// A device tile list built on first use: the 64-row tiles of the FP64 squaring (full = false)
+// or every 128- and 64-row tile of a Chebyshev expansion (full = true).  Enqueued on the
+// context's stream, outside any capture.
+static int ensure_items(gbe_ctx* ctx, gbe_subs* X, bool full) {
+    std::vector<int32_t> m64(X->h_m.begin(), X->h_m.end());
+    std::vector<TileItem> it;
+    if (!full && !X->d_items_64) {
+        make_items(m64, X->h_mpad, 64, it);
+        GBE_TRY(gbe_alloc((void**)&X->d_items_64, std::max<size_t>(1, it.size()) * sizeof(TileItem)));
+        if (!it.empty())
+            GBE_CUDA_TRY(cudaMemcpyAsync(X->d_items_64, it.data(), it.size() * sizeof(TileItem), cudaMemcpyHostToDevice,
+                                         ctx->stream));
+    }
+    if (full && !X->d_items_tc_full) {
+        make_items(X->h_mpad, X->h_mpad, 128, it, true);
+        GBE_TRY(gbe_alloc((void**)&X->d_items_tc_full, std::max<size_t>(1, it.size()) * sizeof(TileItem)));
+        if (!it.empty())
+            GBE_CUDA_TRY(cudaMemcpyAsync(X->d_items_tc_full, it.data(), it.size() * sizeof(TileItem),
+                                         cudaMemcpyHostToDevice, ctx->stream));
+    }
+    if (full && !X->d_items_64_full) {
+        make_items(m64, X->h_mpad, 64, it, true);
+        GBE_TRY(gbe_alloc((void**)&X->d_items_64_full, std::max<size_t>(1, it.size()) * sizeof(TileItem)));
+        if (!it.empty())
+            GBE_CUDA_TRY(cudaMemcpyAsync(X->d_items_64_full, it.data(), it.size() * sizeof(TileItem),
+                                         cudaMemcpyHostToDevice, ctx->stream));
+    }
+    return GBE_OK;
+}
+
 // Dynamic shared memory of the gather: 8 dense rows, the local->global list, and a hash
 // table of >= 2 m slots (global -> local).  Subgraphs up to 2432 vertices keep the rows in
 // the 227 KB of a GB300 CTA; larger ones stage them in global memory (L2) and keep the list
@@ -1060,33 +1108,23 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     X->fp64_flops_per_iter = f64;
     X->mma_flops_full = mma_full;
     X->fp64_flops_full = f64_full;
-    std::vector<TileItem> it_tc, it_64;
-    std::vector<int32_t> m64(X->P);
-    for (int64_t s = 0; s < X->P; ++s) m64[s] = X->h_m[s];
+    // the 128-row tiles of the squaring now; the 64-row tiles of FP64 steps and the full tile
+    // lists of a Chebyshev expansion are built on first use (ensure_items), only their
+    // counts and ranges here.  Work units of each subgraph per decision kind: the tiles of a
+    // subgraph are contiguous in its list.
+    std::vector<TileItem> it_tc;
+    std::vector<int32_t> m64(X->h_m.begin(), X->h_m.end());
     make_items(X->h_mpad, X->h_mpad, 128, it_tc);
-    make_items(m64, X->h_mpad, 64, it_64);
     X->n_items_tc = (int)it_tc.size();
-    X->n_items_64 = (int)it_64.size();
-    // every tile (I, J) for products of two different matrices (Chebyshev expansion)
-    std::vector<TileItem> ft_tc, ft_64;
-    make_items(X->h_mpad, X->h_mpad, 128, ft_tc, true);
-    make_items(m64, X->h_mpad, 64, ft_64, true);
-    X->n_items_tc_full = (int)ft_tc.size();
-    X->n_items_64_full = (int)ft_64.size();
-    X->gather_split = gather_split_of(ctx, X, gather_layout(ctx, X));
-    X->max_units = (int)std::max<int64_t>(X->P * X->gather_split, std::max(X->n_items_tc_full, X->n_items_64_full));
-    // work units of each subgraph per decision kind (the tiles of a subgraph are contiguous)
     std::vector<int2> rg[3];
     for (int k = 0; k < 3; ++k) rg[k].assign(X->P, make_int2(0, 0));
+    X->n_items_64 = (int)item_ranges(m64, X->h_mpad, 64, false, &rg[2]);
+    X->n_items_tc_full = (int)item_ranges(X->h_mpad, X->h_mpad, 128, true, nullptr);
+    X->n_items_64_full = (int)item_ranges(m64, X->h_mpad, 64, true, nullptr);
+    item_ranges(X->h_mpad, X->h_mpad, 128, false, &rg[1]);
+    X->gather_split = gather_split_of(ctx, X, gather_layout(ctx, X));
+    X->max_units = (int)std::max<int64_t>(X->P * X->gather_split, std::max(X->n_items_tc_full, X->n_items_64_full));
     for (int64_t q = 0; q < X->P; ++q) rg[0][q] = make_int2((int)q * X->gather_split, X->gather_split);
-    for (int k = 1; k < 3; ++k) {
-        const std::vector<TileItem>& its = k == 1 ? it_tc : it_64;
-        for (int i = 0; i < (int)its.size(); ++i) {
-            int2& e = rg[k][its[i].s];
-            if (e.y == 0) e.x = i;
-            ++e.y;
-        }
-    }
     X->P_global = parts->h_global_id.empty() ? X->P : parts->P_global;
     int r = GBE_OK;
 #define ALLOC(ptr, bytes) \
@@ -1096,9 +1134,6 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     ALLOC(X->d_m, X->P * 4);
     ALLOC(X->d_c, X->P * 4);
     ALLOC(X->d_items_tc, std::max<int64_t>(1, X->n_items_tc) * sizeof(TileItem));
-    ALLOC(X->d_items_64, std::max<int64_t>(1, X->n_items_64) * sizeof(TileItem));
-    ALLOC(X->d_items_tc_full, std::max<int64_t>(1, X->n_items_tc_full) * sizeof(TileItem));
-    ALLOC(X->d_items_64_full, std::max<int64_t>(1, X->n_items_64_full) * sizeof(TileItem));
     ALLOC(X->d_partials, 2 * (int64_t)X->max_units * 8);
     ALLOC(X->d_ctrl, sizeof(Sp2Ctrl));
     for (int k = 0; k < 3; ++k) ALLOC(X->d_ranges[k], X->P * sizeof(int2));
@@ -1127,11 +1162,6 @@ extern "C" int gbe_subs_create(gbe_ctx* ctx, const gbe_parts* parts, int prec, g
     cudaMemcpyAsync(X->d_m, X->h_m.data(), X->P * 4, cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(X->d_c, X->h_c.data(), X->P * 4, cudaMemcpyHostToDevice, st);
     if (X->n_items_tc) cudaMemcpyAsync(X->d_items_tc, it_tc.data(), it_tc.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
-    if (X->n_items_64) cudaMemcpyAsync(X->d_items_64, it_64.data(), it_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
-    if (X->n_items_tc_full)
-        cudaMemcpyAsync(X->d_items_tc_full, ft_tc.data(), ft_tc.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
-    if (X->n_items_64_full)
-        cudaMemcpyAsync(X->d_items_64_full, ft_64.data(), ft_64.size() * sizeof(TileItem), cudaMemcpyHostToDevice, st);
     for (int k = 0; k < 3; ++k) cudaMemcpyAsync(X->d_ranges[k], rg[k].data(), X->P * sizeof(int2), cudaMemcpyHostToDevice, st);
     // Side 1 starts at zero: a squaring leaves the columns of a subgraph's last block past the
     // next multiple of 16 above m unwritten, and they must read as zero.  Side 0 needs no
@@ -1453,7 +1483,10 @@ extern "C" int gbe_sp2_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     if (in.prec != GBE_PREC_FP64 && in.branch_mode == GBE_BRANCH_REPLAY && in.seq_len <= in.fp64_tail) in.mode = 1;
     const bool fp64_steps = X->prec == GBE_PREC_FP64 || in.fp64_tail > 0;
     GBE_TRY(prepare_gather(ctx, X));
-    if (fp64_steps) GBE_TRY(ensure_f64(X, st));
+    if (fp64_steps) {
+        GBE_TRY(ensure_f64(X, st));
+        GBE_TRY(ensure_items(ctx, X, false));
+    }
     // kernel attributes are set outside any capture
     {
         const GatherLayout L = gather_layout(ctx, X);
@@ -1868,6 +1901,7 @@ extern "C" int gbe_foe_run(gbe_ctx* ctx, const gbe_csr* H, const gbe_parts* part
     cudaStream_t st = ctx->stream;
     const bool fp64 = X->prec == GBE_PREC_FP64;
     if (fp64) GBE_TRY(ensure_f64(X, st));
+    GBE_TRY(ensure_items(ctx, X, true));
     // the fixed x lives on side 2
     if (fp64 && !X->f64[2]) GBE_TRY(gbe_alloc((void**)&X->f64[2], X->total_elems * 8));
     if (!fp64 && !X->planes[2]) {
